@@ -1,0 +1,61 @@
+/* oracle/oracle.h -- plain single-threaded CPU oracle of the TPC CA tracking path.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the package smoke check and the
+ * benchmark's CPU-baseline leg.  The CUDA library never includes, links or calls
+ * anything here, and this file shares no code with it.
+ *
+ * The paper (Sec. 1) states that the TPC tracking derives from the Run-2 HLT
+ * cellular-automaton tracker, that seeding works in native coordinates with time
+ * standing in for z, and that a whole ~10 ms time frame is processed at once.  It
+ * gives no formulas; every constant below is a stated reading (window sizes,
+ * fixed-point units, tie rules, Kalman model) that the oracle's tests pin.
+ */
+#ifndef TPC_ORACLE_H
+#define TPC_ORACLE_H
+#include <stdint.h>
+
+#define OR_NROWS 152
+#define OR_NSECT 36
+
+typedef struct {
+  int32_t wy_q;       /* |y_j - y_i| window in 1/64 um (2 cm -> 1 280 000) */
+  int32_t wt_q;       /* |t_j - t_i| window in 1/64 time bin (6 bins -> 384) */
+  int64_t cost_max_q; /* maximal accepted straight-line cost ((0.6 cm)^2 -> 384000^2) */
+  int32_t n_min;      /* minimal chain length kept as a track (10) */
+} or_params;
+
+typedef struct {
+  double t_ref;   /* time of the start cluster (bins) */
+  double x;       /* row radius where the state is reported (cm) */
+  double p[5];    /* y (cm), zeta - zeta_ref (cm), sin(phi), dzeta/ds, q/pT (c/GeV) */
+  double C[15];   /* lower triangle, row-major: (0,0),(1,0),(1,1),(2,0),... */
+  double chi2;
+  int32_t ndf, nhits, first_cluster; /* first_cluster in caller order */
+  int32_t sector, row_first, row_last, status;
+} or_track_rec;
+
+typedef struct {
+  int64_t n_findable, n_findable_found, n_matched_findable_tracks, n_fake, n_tracks;
+  double efficiency, clone_rate, fake_rate;
+} or_eval_out;
+
+void or_default_params(or_params *p);
+void or_geometry(double *x, int32_t *npads, int32_t *pitch_um);
+void or_quantize(int64_t n, const uint16_t *row, const float *pad, const float *time, int32_t *pad_q, int32_t *t_q,
+                 int32_t *y_q, int64_t *z_q);
+int or_sort_order(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                  int32_t *order);
+int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, int32_t *down, int32_t *up, int64_t *cost);
+int or_bruteforce_neighbours(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad,
+                             const float *time, const or_params *prm, int32_t *down, int32_t *up);
+int or_propagate(const double *p, double dx, double *pout, double *F);
+int or_seed_chain(int32_t L, const int32_t *rows, const float *pads, const float *times, double *p0);
+int or_fit_chain(int32_t L, int32_t sector, const int32_t *rows, const float *pads, const float *times,
+                 or_track_rec *rec);
+int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+             const or_params *prm, int32_t *order, int32_t *down, int32_t *up, int32_t *mdown, int32_t *mup,
+             uint8_t *is_start, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks);
+int or_eval(int64_t n, const int32_t *label, const uint16_t *sector, const int32_t *cluster_track, int64_t n_tracks,
+            int64_t n_gen_tracks, int32_t min_findable, double match_frac, or_eval_out *out);
+#endif
