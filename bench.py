@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark: TPC clusters tracked per second on a synthetic 10 ms continuous-
+readout time frame (36 sectors, ~500 Pb-Pb-like collisions at 50 kHz, ~32M
+clusters, seed 3) through the C ABI on one GB300 per rank.
+
+One step = the whole tracking path (ingest, neighbour finding, link cleaning,
+start hits, chain filter, Kalman fit) over one resident frame.  Prints one JSON
+line (rank 0).  `--impl reference` times the CPU oracle instead (on the host
+cores, on a bounded sample of the same frame).
+
+Multi-GPU (torchrun): every rank tracks its own independent frame (different
+seed, same generator), no data-path collective; `value` is the clusters of all
+ranks divided by the slowest rank's time ("scaling": "weak")."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters tracked/s on a 10 ms TF, learned-pruned vs plain CA at equal efficiency"
+UNIT = "clusters/s"
+# algorithmic bytes per cluster of each stage (read once + written once)
+ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a track
+STAGED_BYTES_PER_CLUSTER = 48.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gen_frame(workload, seed_offset=0):
+    import tpcsynth as ts
+    cfg = {"c1": ts.c1, "c2": ts.c2, "c3": ts.c3}[workload]()
+    cfg.seed = cfg.seed + seed_offset
+    return ts.generate(cfg)
+
+
+def cpu_oracle_rate(f, budget_s=10.0):
+    """The oracle as it stands, single-threaded, sector by sector on the frame
+    until the time budget is used: clusters/s on one host core."""
+    import oracle
+    done, t0, used = 0, time.perf_counter(), []
+    for s in range(36):
+        idx = np.where(f.sector == s)[0]
+        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx])
+        done += len(idx)
+        used.append(s)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, f"sectors {used[0]}-{used[-1]} of the frame ({done} clusters), {dt:.1f} s", done
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    f = gen_frame(args.workload)
+    import oracle
+    oracle.build()
+    # warm-up and timed steps; each step is a bounded sample (2 sectors) of the frame
+    secs = [np.where(f.sector == s)[0] for s in range(36)]
+    total, t_all = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        idx = np.concatenate([secs[(2 * k) % 36], secs[(2 * k + 1) % 36]])
+        t0 = time.perf_counter()
+        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx])
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total += len(idx)
+            t_all += dt
+    v = total / t_all
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+           "data": "synthetic", "config": {"workload": f"{args.workload}: 10 ms frame, {f.n} clusters, seed 3",
+                                           "model": "CPU oracle (plain single-threaded C)", "parallelism": "1 core"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "2 sectors of the frame per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fit-variant", type=int, default=0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2102_08862_gb300 import _build, tpcca
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    _build.build()
+
+    f = gen_frame(args.workload, seed_offset=1000 * rank)
+    n = f.n
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sec, row, pad, tim = t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time)
+    tr = tpcca.TimeFrameTracker(n, device=local, fit_variant=args.fit_variant)
+    cap = n // 10 + 1
+    cnt = tpcca.c_u32(0)
+    cl, out, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=cnt)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    # one checked call: correctness of the configuration and the track count
+    rc = tpcca.tpc_track_timeframe(tr.handle, cl, out, sh)
+    assert rc == 0, tpcca.tpc_last_error()
+    stream.synchronize()
+    n_tracks = int(cnt.value)
+    cl2, out2, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=None)
+
+    def step():
+        rc = tpcca.tpc_track_timeframe(tr.handle, cl2, out2, sh)
+        if rc != 0:
+            raise RuntimeError(tpcca.tpc_last_error())
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k in range(args.steps):
+                step()
+                ev[k + 1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    rc = tpcca.tpc_tf_status(tr.handle, sh)
+    assert rc == 0, tpcca.tpc_last_error()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        nn = torch.tensor([float(n)], device=dev)
+        dist.all_reduce(nn)
+        n_all = float(nn.item())
+    else:
+        n_all = float(n)
+    launches = tr.launches_per_call()
+    value = n_all * args.steps / (total_ms * 1e-3)
+
+    # stage timing (CUDA events between the stages of a call, on the call's stream)
+    prof = tpcca.TimeFrameTracker(n, device=local, profile_stages=1, fit_variant=args.fit_variant)
+    clp, outp, _, _ = prof.structs(sec, row, pad, tim, True, cap, host_count=None)
+    acc = {}
+    for k in range(args.warmup + 5):
+        assert tpcca.tpc_track_timeframe(prof.handle, clp, outp, sh) == 0
+        if k >= args.warmup:
+            for name, ms in prof.stage_times():
+                acc.setdefault(name, []).append(ms)
+    stage_ms = {k: statistics.mean(v) for k, v in acc.items()}
+    ct = prof._out["cluster_track"][:n]
+    in_tracks = int((ct >= 0).sum().item())
+    prof.close()
+    hbm, peak_kind = peaks()
+    alg = {"neighbours": ALG_BYTES["neighbours"] * n, "links": ALG_BYTES["links"] * n, "fit": 16.0 * in_tracks}
+    dom = max(stage_ms, key=stage_ms.get)
+    dom_alg = alg.get(dom)
+    roof = None
+    if dom_alg is not None:
+        achieved = dom_alg / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind}
+    step_ms = statistics.median(per)
+    step_gbs = STAGED_BYTES_PER_CLUSTER * n / (step_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hs = torch.from_numpy(np.ascontiguousarray(f.sector.view(np.int16))).pin_memory()
+    hr = torch.from_numpy(np.ascontiguousarray(f.row.view(np.int16))).pin_memory()
+    hp = torch.from_numpy(np.ascontiguousarray(f.pad)).pin_memory()
+    ht = torch.from_numpy(np.ascontiguousarray(f.time)).pin_memory()
+    hct = torch.empty(n, dtype=torch.int32).pin_memory()
+    tcap = n_tracks + 16
+    host_out = {k: torch.empty(sh_, dtype=dt).pin_memory() for k, sh_, dt in (
+        ("params", (tcap, 5), torch.float32), ("cov", (tcap, 15), torch.float32), ("t_ref", tcap, torch.float32),
+        ("x", tcap, torch.float32), ("chi2", tcap, torch.float32), ("ndf", tcap, torch.int32),
+        ("nhits", tcap, torch.int32), ("first_cluster", tcap, torch.int32), ("sector", tcap, torch.int16),
+        ("row_first", tcap, torch.int16), ("row_last", tcap, torch.int16), ("status", tcap, torch.uint8))}
+    hn = np.zeros(1, np.uint32)
+    hcl = tpcca.tpc_clusters(n=n, flags=tpcca.TPC_INPUT_SORTED, sector=hs.data_ptr(), row=hr.data_ptr(),
+                             pad=hp.data_ptr(), time=ht.data_ptr())
+    htr = tpcca.tpc_tracks(cluster_track=hct.data_ptr(), track_capacity=tcap, n_tracks=hn.ctypes.data,
+                           **{k: v.data_ptr() for k, v in host_out.items()})
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        assert tpcca.tpc_track_timeframe_host(tr.handle, hcl, htr, sh) == 0, tpcca.tpc_last_error()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        assert tpcca.tpc_track_timeframe_host(tr.handle, hcl, htr, sh) == 0
+    e1.record(stream)
+    stream.synchronize()
+    wall = time.perf_counter() - t0
+    e2e_ms = max(e0.elapsed_time(e1), 1e3 * wall) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    d2h = 4 * n + 4 + int(hn[0]) * (20 + 60 + 4 * 6 + 2 * 3 + 1)
+    tr.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, sample, _ = cpu_oracle_rate(f, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 10 ms continuous frame, 36 sectors, {f.n_collisions} collisions "
+                               f"at 50 kHz, {n} clusters, seed 3 (+1000*rank)",
+                   "mode": "plain CA", "fit": ["thread per track", "warp per track"][args.fit_variant],
+                   "l2": "inputs (12 B x %d = %.0f MB) larger than L2" % (n, 12 * n / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "tracks_per_s": n_tracks * args.steps / (total_ms * 1e-3) * (n_all / n),
+        "n_tracks": n_tracks,
+        "step_ms": {"median": step_ms, "min": min(per)},
+        "stage_ms": stage_ms,
+        "roofline": roof,
+        "roofline_step": {"bytes_per_cluster": STAGED_BYTES_PER_CLUSTER, "achieved": step_gbs, "peak": hbm,
+                          "unit": "GB/s", "frac": step_gbs / hbm},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_all / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

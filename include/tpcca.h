@@ -1,0 +1,166 @@
+/*
+ * tpcca.h -- C ABI of the GB300 TPC time-frame tracker.
+ *
+ * The library finds tracks in one continuous-readout TPC time frame: a
+ * cellular-automaton seeding stage in native (row, pad, time) coordinates with
+ * the drift time standing in for z, followed by a Kalman-filter tracklet fit.
+ * The paper (arXiv:2102.08862, Sec. 1) names this as the most compute-intensive
+ * step of the synchronous reconstruction, says it works on ~10 ms time frames
+ * held whole in GPU memory, reuses memory across its sequential steps, and
+ * derives from the Run-2 HLT tracker (CA seeding, Kalman tracklets).
+ *
+ * Steps of one call (all on the GPU, enqueued on the caller's stream):
+ *   A0 ingest      validate clusters, index the (sector, row) ranges
+ *                  (sort + permutation when the input is not already sorted);
+ *   A1 neighbours  for each cluster in row r = 1..150 the pair (j in r-1, k in r+1)
+ *                  minimising (y_j + y_k - 2 y_i)^2 + (z_j + z_k - 2 z_i)^2 in
+ *                  fixed-point units (y_q = (rint(64 pad) - 32 (npads-1)) * pitch_um,
+ *                  z_q = 5160 * rint(64 time)), inside |dy| <= wy_q, |dt| <= wt_q,
+ *                  cost <= cost_max_q; ties -> smaller j, then smaller k;
+ *   A2 cleaning    rows 0/151 adopt their best claimant; only mutual links remain;
+ *   A3 starts      clusters with a mutual up link and no mutual down link;
+ *   A4 chains      follow mutual up links; chains of >= n_min clusters become
+ *                  tracks, numbered in the order of their start cluster;
+ *   A5 fit         FP32 Kalman filter along each chain (helix in (x, y), straight
+ *                  line in (arc length, zeta = 0.516 cm/bin * time)), 3-point seed.
+ *
+ * Conventions
+ *   - Return value 0 on success, a negative TPC_ERR_* code otherwise;
+ *     tpc_last_error() gives a message (thread-local, valid until the next call
+ *     from the same thread).
+ *   - Device pointers are plain CUDA device addresses (cudaMalloc, PyTorch, ...),
+ *     owned by the caller; the library never frees or retains them past the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     tpc_track_timeframe only enqueues work; errors found on the device (invalid
+ *     input, too many tracks, a bounded wait that gave up) surface through
+ *     tpc_tf_status() or, when n_tracks_host is set, from the call itself.
+ *   - All device memory is allocated by tpc_tf_create; no call allocates.
+ *   - One handle serves one stream at a time; handles are not thread-safe.
+ */
+#ifndef TPCCA_H
+#define TPCCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPC_OK 0
+#define TPC_ERR_ARG (-1)      /* invalid argument (null pointer, bad config, misaligned buffer) */
+#define TPC_ERR_CAPACITY (-2) /* more clusters than max_clusters, or more tracks than track_capacity */
+#define TPC_ERR_CUDA (-3)     /* a CUDA runtime call failed */
+#define TPC_ERR_INPUT (-4)    /* device validation: sector >= 36, row >= 152, pad or time out of range or
+                                 not finite, or input flagged sorted but not sorted */
+#define TPC_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up */
+
+#define TPC_MODE_PLAIN 0  /* plain cellular automaton */
+#define TPC_MODE_PRUNED 1 /* CA with the learned link classifier pruning neighbour candidates */
+
+#define TPC_INPUT_SORTED 1u /* clusters are sorted by (sector, row, time, pad) */
+
+#define TPC_FIT_THREAD 0 /* one thread per tracklet in the Kalman fit (default) */
+#define TPC_FIT_WARP 1   /* one warp per tracklet, lanes own state and covariance entries */
+
+#define TPC_NSECTORS 36
+#define TPC_NROWS 152
+
+typedef struct tpc_tf tpc_tf; /* opaque: owns the device arena of one time-frame tracker */
+
+typedef struct {
+  uint32_t max_clusters; /* arena sized at create; calls with more clusters fail with TPC_ERR_CAPACITY */
+  uint32_t max_tracks;   /* capacity of the internal track list (0: max_clusters / n_min) */
+  int32_t wy_q;          /* pad-direction window, 1/64 um (default 1 280 000 = 2 cm); <= 2^28 */
+  int32_t wt_q;          /* time window, 1/64 bin (default 384 = 6 bins); <= 2^20 */
+  int64_t cost_max_q;    /* largest accepted cost, (1/64 um)^2 (default 384000^2 = (0.6 cm)^2) */
+  int32_t n_min;         /* shortest chain kept as a track (default 10, >= 3) */
+  int32_t mode;          /* TPC_MODE_PLAIN or TPC_MODE_PRUNED */
+  float tau;             /* pruning threshold on the classifier probability (TPC_MODE_PRUNED) */
+  int32_t device;        /* CUDA device ordinal */
+  int32_t fit_variant;   /* TPC_FIT_THREAD or TPC_FIT_WARP */
+  int32_t profile_stages;/* nonzero: record CUDA events between stages (tpc_tf_stage_times) */
+  int32_t row_cap;       /* clusters per staged row in the neighbour kernel (0: largest that fits
+                            shared memory); rows above it take the global-memory kernel */
+} tpc_tf_config;
+
+typedef struct {      /* input clusters: device pointers, read only, caller owned */
+  uint32_t n;         /* number of clusters */
+  uint32_t flags;     /* TPC_INPUT_SORTED or 0 */
+  const uint16_t *sector; /* [n] 0..35 */
+  const uint16_t *row;    /* [n] 0..151 */
+  const float *pad;       /* [n] pad coordinate, pads numbered 0..npads-1 */
+  const float *time;      /* [n] drift time in 200 ns bins */
+} tpc_clusters;
+
+typedef struct {              /* outputs: device pointers, caller owned */
+  int32_t *cluster_track;     /* [n] track id per cluster in caller order, -1 = none (required) */
+  uint32_t track_capacity;    /* rows of the per-track arrays below */
+  float *params;              /* [cap][5] y (cm), zeta - zeta_ref (cm), sin phi, dzeta/ds, q/pT (c/GeV) */
+  float *cov;                 /* [cap][15] covariance, lower triangle row-major */
+  float *t_ref;               /* [cap] time of the start cluster (bins); zeta_ref = 0.516 cm * t_ref */
+  float *x;                   /* [cap] row radius where the state is reported (cm) */
+  float *chi2;                /* [cap] */
+  int32_t *ndf;               /* [cap] 2 * fitted clusters - 5 */
+  int32_t *nhits;             /* [cap] chain length */
+  int32_t *first_cluster;     /* [cap] caller index of the start cluster */
+  uint16_t *sector;           /* [cap] */
+  uint16_t *row_first;        /* [cap] */
+  uint16_t *row_last;         /* [cap] */
+  uint8_t *status;            /* [cap] bit 0: straight-line seed; bit 1: fit stopped at |sin phi| >= 0.999 */
+  uint32_t *n_tracks;         /* device scalar: number of tracks (also when it exceeds track_capacity) */
+  uint32_t *n_tracks_host;    /* optional host scalar: when set, the call synchronises the stream,
+                                 stores the count here and returns device-side errors directly */
+} tpc_tracks;
+
+/* Fill *cfg with the defaults listed above (max_clusters = 0 must be set by the caller). */
+void tpc_default_config(tpc_tf_config *cfg);
+
+/* Create a tracker on cfg->device and allocate its arena for cfg->max_clusters
+ * clusters.  *out receives the handle.  Errors: TPC_ERR_ARG, TPC_ERR_CUDA. */
+int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out);
+
+/* Track one time frame (steps A0-A5 above) with device-resident inputs and
+ * outputs, enqueued on `stream`.  Errors: TPC_ERR_ARG (null or misaligned
+ * pointer), TPC_ERR_CAPACITY (n > max_clusters; or, with n_tracks_host, more
+ * tracks than track_capacity: *n_tracks holds the required count and records
+ * past the capacity are dropped), TPC_ERR_INPUT / TPC_ERR_TIMEOUT (with
+ * n_tracks_host only), TPC_ERR_CUDA. */
+int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
+
+/* Same with HOST input and output pointers (pageable or pinned): the call copies
+ * the clusters into the arena, tracks them, copies cluster_track and the track
+ * records back and synchronises the stream.  out->n_tracks and
+ * out->n_tracks_host are host pointers here (either may be NULL). */
+int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
+
+/* Synchronise `stream` and report the device-side status of the last call
+ * (TPC_OK, TPC_ERR_INPUT, TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT). */
+int tpc_tf_status(tpc_tf *tf, void *stream);
+
+/* Free the arena and the handle (NULL is ignored).  Synchronises the device. */
+void tpc_tf_destroy(tpc_tf *tf);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *tpc_last_error(void);
+
+/* Internal arrays of the last call, for inspection and tests; every pointer may
+ * be NULL.  All arrays are indexed by sorted position (sector, row, time, pad,
+ * caller index) and hold sorted positions or -1: order[p] = caller index,
+ * down/up = A1 links after the edge-row claims (A2), mup = mutual up link,
+ * is_start = A3 flag.  Device pointers, n entries each; enqueued on `stream`. */
+int tpc_tf_debug_links(tpc_tf *tf, int32_t *order, int32_t *down, int32_t *up, int32_t *mup, uint8_t *is_start,
+                       void *stream);
+
+/* Durations (ms) of the stages of the last call made with profile_stages set:
+ * writes up to `cap` values to ms[] and their names to names[] (static strings),
+ * returns the number of stages, or a negative error.  Synchronises. */
+int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int cap);
+
+/* Number of kernel launches (and memset nodes) one call enqueues on its stream. */
+int tpc_tf_launches_per_call(const tpc_tf *tf);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCCA_H */

@@ -1,0 +1,450 @@
+// api.cu -- the C ABI (include/tpcca.h): handle creation with one device arena
+// sized for the largest frame, the per-call orchestration of the stages on the
+// caller's stream, the host-buffer entry point, and inspection hooks.
+//
+// The paper holds a whole time frame in GPU memory and reuses memory across the
+// sequential tracking steps (Sec. 1).  Here every buffer a call needs is carved
+// from one arena allocated at create time; no call allocates, and the only
+// per-call clearing is one memset of the counters and look-back words.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/tpcca.h"
+#include "tpc_dev.cuh"
+#include "tpc_internal.h"
+
+using namespace tpc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define TPC_CK(x)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess) return fail(TPC_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kMaxStages = 12;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct tpc_tf {
+  tpc_tf_config cfg;
+  int device = 0, sms = 0;
+  int nb_cap = 0, nb_chunks = 1;
+  uint32_t N = 0, track_list_cap = 0;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  int32_t *row_begin = nullptr;
+  int2 *link = nullptr;
+  int32_t *mup = nullptr, *starts = nullptr, *track_start = nullptr;
+  uint32_t *reset = nullptr;
+  size_t reset_bytes_max = 0;
+  uint16_t *s_sector = nullptr, *s_row = nullptr;
+  float *s_pad = nullptr, *s_time = nullptr;
+  int32_t *perm = nullptr;
+  void *sort_scratch = nullptr;
+  size_t sort_scratch_bytes = 0;
+  // staging for tpc_track_timeframe_host
+  uint16_t *h_sector = nullptr, *h_row = nullptr;
+  float *h_pad = nullptr, *h_time = nullptr;
+  int32_t *h_ct = nullptr;
+  float *h_params = nullptr, *h_cov = nullptr, *h_tref = nullptr, *h_x = nullptr, *h_chi2 = nullptr;
+  int32_t *h_ndf = nullptr, *h_nhits = nullptr, *h_first = nullptr;
+  uint16_t *h_sec = nullptr, *h_rf = nullptr, *h_rl = nullptr;
+  uint8_t *h_status = nullptr;
+  uint32_t *h_ntracks = nullptr;
+  uint32_t *pinned = nullptr;  // [0] n_tracks, [1] error word
+  cudaEvent_t ev[kMaxStages + 1];
+  const char *ev_name[kMaxStages];
+  int n_ev = 0;
+  bool ev_ready = false;
+  int launches = 0;
+  uint32_t last_n = 0;
+  bool last_sorted = true;
+};
+
+extern "C" void tpc_default_config(tpc_tf_config *c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->wy_q = 1280000;
+  c->wt_q = 384;
+  c->cost_max_q = 147456000000LL;
+  c->n_min = 10;
+  c->mode = TPC_MODE_PLAIN;
+  c->tau = 0.5f;
+  c->device = 0;
+  c->fit_variant = TPC_FIT_THREAD;
+}
+
+extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
+
+static void free_all(tpc_tf *tf) {
+  if (!tf) return;
+  if (tf->arena) cudaFree(tf->arena);
+  if (tf->pinned) cudaFreeHost(tf->pinned);
+  for (int i = 0; i <= kMaxStages; ++i)
+    if (tf->ev_ready) cudaEventDestroy(tf->ev[i]);
+  delete tf;
+}
+
+extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(TPC_ERR_ARG, "tpc_tf_create: null argument");
+  *out = nullptr;
+  if (cfg->max_clusters == 0 || cfg->max_clusters > (1u << 30))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: max_clusters must be in [1, 2^30]");
+  if (cfg->n_min < 3 || cfg->n_min > TPC_NROWS) return fail(TPC_ERR_ARG, "tpc_tf_create: n_min must be in [3, 152]");
+  if (cfg->wy_q < 0 || cfg->wy_q > (1 << 28) || cfg->wt_q < 0 || cfg->wt_q > (1 << 20) || cfg->cost_max_q < 0)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: search window or cost cut out of range");
+  if (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_PRUNED)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown mode");
+  if (cfg->mode == TPC_MODE_PRUNED) return fail(TPC_ERR_ARG, "tpc_tf_create: TPC_MODE_PRUNED needs the link classifier");
+  if (cfg->fit_variant != TPC_FIT_THREAD && cfg->fit_variant != TPC_FIT_WARP)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown fit_variant");
+  tpc_tf *tf = new tpc_tf();
+  tf->cfg = *cfg;
+  tf->device = cfg->device;
+  tf->N = cfg->max_clusters;
+  cudaError_t e = cudaSetDevice(tf->device);
+  if (e != cudaSuccess) {
+    delete tf;
+    return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, tf->device);
+  // row capacity of the staged-row neighbour kernel: four slots of
+  // (y_q, t_q) rows plus bucket tables must fit the opt-in shared memory
+  const size_t stat = neighbours_rw_static_smem();
+  long avail = (long)optin - (long)stat - 256;
+  int cap = 0;
+  if (avail > 0) {
+    cap = (int)((avail / (4 * 4) - kNbTable - 1 - 3) / 2 - 8);
+    cap &= ~3;
+  }
+  if (cap < 4) cap = 4;
+  // the attribute is per kernel, shared by all handles: always allow the largest
+  const int cap_max = cap;
+  if (cfg->row_cap > 0 && cfg->row_cap < cap) cap = cfg->row_cap & ~3;
+  if (cap < 4) cap = 4;
+  tf->nb_cap = cap;
+  if (neighbours_set_smem(neighbours_rw_smem(cap_max)) != 0) {
+    free_all(tf);
+    return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot configure shared memory of the neighbour kernel");
+  }
+  tf->nb_chunks = tf->sms >= 2 * kNSect ? tf->sms / kNSect : 1;
+  tf->track_list_cap = cfg->max_tracks ? cfg->max_tracks : tf->N / (uint32_t)cfg->n_min + 1;
+
+  const size_t N = tf->N;
+  const size_t tiles_l = (N + kTile - 1) / kTile + 1, tiles_k = (N / 2 + 1 + kTile - 1) / kTile + 1;
+  tf->reset_bytes_max = kNCounters * 4 + 8 * (tiles_l + tiles_k);
+  struct Part {
+    void **p;
+    size_t bytes;
+  } parts[] = {
+      {(void **)&tf->row_begin, (kNKeys + 1) * 4},
+      {(void **)&tf->link, (N + 4) * 8},
+      {(void **)&tf->mup, (N + 4) * 4},
+      {(void **)&tf->starts, (N / 2 + 2) * 4},
+      {(void **)&tf->track_start, (size_t)(tf->track_list_cap + 1) * 4},
+      {(void **)&tf->reset, tf->reset_bytes_max},
+      {(void **)&tf->s_sector, (N + 8) * 2},
+      {(void **)&tf->s_row, (N + 8) * 2},
+      {(void **)&tf->s_pad, (N + 4) * 4},
+      {(void **)&tf->s_time, (N + 4) * 4},
+      {(void **)&tf->perm, (N + 4) * 4},
+      {(void **)&tf->sort_scratch, sort_scratch_bytes(tf->N)},
+      {(void **)&tf->h_sector, (N + 8) * 2},
+      {(void **)&tf->h_row, (N + 8) * 2},
+      {(void **)&tf->h_pad, (N + 4) * 4},
+      {(void **)&tf->h_time, (N + 4) * 4},
+      {(void **)&tf->h_ct, (N + 4) * 4},
+      {(void **)&tf->h_params, (size_t)tf->track_list_cap * 5 * 4},
+      {(void **)&tf->h_cov, (size_t)tf->track_list_cap * 15 * 4},
+      {(void **)&tf->h_tref, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_x, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_chi2, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_ndf, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_nhits, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_first, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->h_sec, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->h_rf, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->h_rl, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->h_status, (size_t)tf->track_list_cap},
+      {(void **)&tf->h_ntracks, 16},
+  };
+  size_t total = 0;
+  for (auto &p : parts) total += align_up(p.bytes, 256);
+  e = cudaMalloc(&tf->arena, total);
+  if (e != cudaSuccess) {
+    free_all(tf);
+    return fail(TPC_ERR_CUDA, std::string("cudaMalloc arena: ") + cudaGetErrorString(e));
+  }
+  tf->arena_bytes = total;
+  size_t off = 0;
+  for (auto &p : parts) {
+    *p.p = tf->arena + off;
+    off += align_up(p.bytes, 256);
+  }
+  tf->sort_scratch_bytes = sort_scratch_bytes(tf->N);
+  e = cudaMallocHost(&tf->pinned, 64);
+  if (e != cudaSuccess) {
+    free_all(tf);
+    return fail(TPC_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&tf->ev[i]);
+  tf->ev_ready = true;
+  *out = tf;
+  return TPC_OK;
+}
+
+extern "C" void tpc_tf_destroy(tpc_tf *tf) {
+  if (!tf) return;
+  cudaSetDevice(tf->device);
+  cudaDeviceSynchronize();
+  free_all(tf);
+}
+
+static int map_err(uint32_t w) {
+  if (w & kErrInput) return fail(TPC_ERR_INPUT, "invalid input clusters (range, finiteness or sort order)");
+  if (w & kErrTimeout) return fail(TPC_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (w & kErrSortCap)
+    return fail(TPC_ERR_CAPACITY, "unsorted input with more than 16384 clusters in one (sector, row): pass sorted input");
+  if (w & kErrCapacity) return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
+  if (w & kErrInternal) return fail(TPC_ERR_CUDA, "internal device error");
+  return TPC_OK;
+}
+
+static void stage(tpc_tf *tf, cudaStream_t st, const char *name) {
+  if (!tf->cfg.profile_stages || tf->n_ev >= kMaxStages) return;
+  tf->ev_name[tf->n_ev] = name;
+  cudaEventRecord(tf->ev[tf->n_ev + 1], st);
+  tf->n_ev++;
+}
+
+extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null argument");
+  const uint32_t n = cl->n;
+  if (n > tf->N) return fail(TPC_ERR_CAPACITY, "more clusters than max_clusters");
+  if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe: null cluster array");
+  if (n > 0 && !out->cluster_track) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null cluster_track");
+  if (!out->n_tracks) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null n_tracks");
+  if (out->track_capacity > 0 &&
+      (!out->params || !out->cov || !out->t_ref || !out->x || !out->chi2 || !out->ndf || !out->nhits ||
+       !out->first_cluster || !out->sector || !out->row_first || !out->row_last || !out->status))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe: null track array");
+  if (((uintptr_t)out->cluster_track & 3) || ((uintptr_t)cl->pad & 3) || ((uintptr_t)cl->time & 3) ||
+      ((uintptr_t)cl->sector & 1) || ((uintptr_t)cl->row & 1))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe: misaligned array");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool sorted = (cl->flags & TPC_INPUT_SORTED) != 0;
+
+  Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.row_begin = tf->row_begin;
+  a.link = tf->link;
+  a.mup = tf->mup;
+  a.starts = tf->starts;
+  a.track_start = tf->track_start;
+  a.ctr = tf->reset;
+  const size_t tiles_l = (n + kTile - 1) / kTile, tiles_k = (n / 2 + 1 + kTile - 1) / kTile;
+  a.lb_links = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(tf->reset) + kNCounters * 4);
+  a.lb_keep = a.lb_links + tiles_l;
+  a.starts_cap = n / 2 + 1;
+  a.track_list_cap = tf->track_list_cap;
+  a.wy = tf->cfg.wy_q;
+  a.wt = tf->cfg.wt_q;
+  a.cost_max = tf->cfg.cost_max_q;
+  a.n_min = tf->cfg.n_min;
+  a.cluster_track = out->cluster_track;
+  a.track_capacity = out->track_capacity;
+  a.params = out->params;
+  a.cov = out->cov;
+  a.t_ref = out->t_ref;
+  a.x = out->x;
+  a.chi2 = out->chi2;
+  a.ndf = out->ndf;
+  a.nhits = out->nhits;
+  a.first_cluster = out->first_cluster;
+  a.o_sector = out->sector;
+  a.o_row_first = out->row_first;
+  a.o_row_last = out->row_last;
+  a.o_status = out->status;
+  a.n_tracks_out = out->n_tracks;
+
+  tf->n_ev = 0;
+  tf->launches = 0;
+  if (tf->cfg.profile_stages) cudaEventRecord(tf->ev[0], st);
+  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 8 * (tiles_l + tiles_k), st));
+  ++tf->launches;
+  if (sorted) {
+    a.sector = cl->sector;
+    a.row = cl->row;
+    a.pad = cl->pad;
+    a.time = cl->time;
+    a.perm = nullptr;
+  } else {
+    a.sector = tf->s_sector;
+    a.row = tf->s_row;
+    a.pad = tf->s_pad;
+    a.time = tf->s_time;
+    a.perm = tf->perm;
+    const int nl = launch_sort(a, cl->sector, cl->row, cl->pad, cl->time, tf->s_sector, tf->s_row, tf->s_pad,
+                               tf->s_time, tf->perm, tf->sort_scratch, tf->sort_scratch_bytes, tf->sms, st);
+    if (nl < 0) return fail(TPC_ERR_CUDA, "sort of unsorted input failed");
+    tf->launches += nl;
+    stage(tf, st, "sort");
+  }
+  const int use_tma = (((uintptr_t)a.pad & 15) == 0 && ((uintptr_t)a.time & 15) == 0) ? 1 : 0;
+  launch_row_index(a, st);
+  stage(tf, st, "ingest");
+  launch_neighbours(a, tf->nb_chunks, tf->nb_cap, use_tma, tf->sms, st);
+  launch_edge_claims(a, tf->nb_cap, st);
+  stage(tf, st, "neighbours");
+  launch_links(a, tf->sms, st);
+  stage(tf, st, "links");
+  launch_keep(a, tf->sms, st);
+  stage(tf, st, "keep");
+  launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+  stage(tf, st, "fit");
+  tf->launches += 7;
+  TPC_CK(cudaGetLastError());
+  tf->last_n = n;
+  tf->last_sorted = sorted;
+  if (out->n_tracks_host) {
+    TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + kCtrTracks, 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(tf->pinned + 1, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaStreamSynchronize(st));
+    *out->n_tracks_host = tf->pinned[0];
+    return map_err(tf->pinned[1]);
+  }
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_status(tpc_tf *tf, void *stream) {
+  g_err.clear();
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_status: null handle");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  TPC_CK(cudaMemcpyAsync(tf->pinned + 1, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaStreamSynchronize(st));
+  return map_err(tf->pinned[1]);
+}
+
+extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null argument");
+  const uint32_t n = cl->n;
+  if (n > tf->N) return fail(TPC_ERR_CAPACITY, "more clusters than max_clusters");
+  if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time || !out->cluster_track))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null array");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0) {
+    TPC_CK(cudaMemcpyAsync(tf->h_sector, cl->sector, (size_t)n * 2, cudaMemcpyHostToDevice, st));
+    TPC_CK(cudaMemcpyAsync(tf->h_row, cl->row, (size_t)n * 2, cudaMemcpyHostToDevice, st));
+    TPC_CK(cudaMemcpyAsync(tf->h_pad, cl->pad, (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    TPC_CK(cudaMemcpyAsync(tf->h_time, cl->time, (size_t)n * 4, cudaMemcpyHostToDevice, st));
+  }
+  tpc_clusters dcl = *cl;
+  dcl.sector = tf->h_sector;
+  dcl.row = tf->h_row;
+  dcl.pad = tf->h_pad;
+  dcl.time = tf->h_time;
+  const uint32_t cap = out->track_capacity < tf->track_list_cap ? out->track_capacity : tf->track_list_cap;
+  tpc_tracks dt;
+  std::memset(&dt, 0, sizeof(dt));
+  dt.cluster_track = tf->h_ct;
+  dt.track_capacity = cap;
+  dt.params = tf->h_params;
+  dt.cov = tf->h_cov;
+  dt.t_ref = tf->h_tref;
+  dt.x = tf->h_x;
+  dt.chi2 = tf->h_chi2;
+  dt.ndf = tf->h_ndf;
+  dt.nhits = tf->h_nhits;
+  dt.first_cluster = tf->h_first;
+  dt.sector = tf->h_sec;
+  dt.row_first = tf->h_rf;
+  dt.row_last = tf->h_rl;
+  dt.status = tf->h_status;
+  dt.n_tracks = tf->h_ntracks;
+  uint32_t nt = 0;
+  dt.n_tracks_host = &nt;
+  int rc = tpc_track_timeframe(tf, &dcl, &dt, stream);
+  if (rc != TPC_OK && rc != TPC_ERR_CAPACITY) return rc;
+  const std::string msg = g_err;
+  if (n > 0) TPC_CK(cudaMemcpyAsync(out->cluster_track, tf->h_ct, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+  const uint32_t m = nt < out->track_capacity ? nt : out->track_capacity;
+  if (m > 0 && out->params) {
+    TPC_CK(cudaMemcpyAsync(out->params, tf->h_params, (size_t)m * 20, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->cov, tf->h_cov, (size_t)m * 60, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->t_ref, tf->h_tref, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->x, tf->h_x, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->chi2, tf->h_chi2, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->ndf, tf->h_ndf, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->nhits, tf->h_nhits, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->first_cluster, tf->h_first, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->sector, tf->h_sec, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
+  }
+  TPC_CK(cudaStreamSynchronize(st));
+  if (out->n_tracks) *out->n_tracks = nt;
+  if (out->n_tracks_host) *out->n_tracks_host = nt;
+  if (rc != TPC_OK) g_err = msg;
+  if (rc == TPC_OK && nt > out->track_capacity) return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
+  return rc;
+}
+
+extern "C" int tpc_tf_debug_links(tpc_tf *tf, int32_t *order, int32_t *down, int32_t *up, int32_t *mup,
+                                  uint8_t *is_start, void *stream) {
+  g_err.clear();
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_debug_links: null handle");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t n = tf->last_n;
+  if (n == 0) return TPC_OK;
+  if (down) TPC_CK(cudaMemcpy2DAsync(down, 4, tf->link, 8, 4, n, cudaMemcpyDeviceToDevice, st));
+  if (up)
+    TPC_CK(cudaMemcpy2DAsync(up, 4, reinterpret_cast<char *>(tf->link) + 4, 8, 4, n, cudaMemcpyDeviceToDevice, st));
+  if (mup) TPC_CK(cudaMemcpyAsync(mup, tf->mup, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+  launch_debug_flags(tf->link, tf->mup, tf->last_sorted ? nullptr : tf->perm, n, order, is_start, st);
+  TPC_CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int cap) {
+  g_err.clear();
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_stage_times: null handle");
+  if (!tf->cfg.profile_stages) return fail(TPC_ERR_ARG, "tpc_tf_stage_times: profile_stages is off");
+  TPC_CK(cudaSetDevice(tf->device));
+  TPC_CK(cudaEventSynchronize(tf->ev[tf->n_ev]));
+  for (int i = 0; i < tf->n_ev && i < cap; ++i) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, tf->ev[i], tf->ev[i + 1]);
+    if (ms) ms[i] = v;
+    if (names) names[i] = tf->ev_name[i];
+  }
+  return tf->n_ev;
+}
+
+extern "C" int tpc_tf_launches_per_call(const tpc_tf *tf) { return tf ? tf->launches : 0; }

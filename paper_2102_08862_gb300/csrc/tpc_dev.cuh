@@ -1,0 +1,162 @@
+// tpc_dev.cuh -- device-side definitions shared by the kernels of the GB300 TPC
+// time-frame tracker: detector geometry, fixed-point quantisation, the argument
+// block every kernel receives, the device status word, bounded waits and the
+// order-preserving compaction (decoupled look-back) used for start hits and
+// tracks.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tpcca.h"
+
+namespace tpc {
+
+constexpr int kNRows = TPC_NROWS;
+constexpr int kNSect = TPC_NSECTORS;
+constexpr int kNKeys = kNRows * kNSect;  // (sector, row) ranges
+
+// ---------------------------------------------------------------- geometry
+// 152 pad rows per 20-degree sector at x_r = 85 + r*160/151 cm; npads and pitch
+// grow linearly from 66 pads of 4.0 mm to 138 pads of 6.0 mm (rounded half up).
+__host__ __device__ __forceinline__ int row_npads(int r) { return 66 + (144 * r + 151) / 302; }
+__host__ __device__ __forceinline__ int row_pitch_um(int r) { return 4000 + (4000 * r + 151) / 302; }
+__host__ __device__ __forceinline__ float row_x(int r) { return 85.0f + (float)r * (160.0f / 151.0f); }
+constexpr float kRowDx = 160.0f / 151.0f;  // radial distance of adjacent rows (cm)
+
+// ------------------------------------------------------------ quantisation
+// Fixed-point units shared by both pad and time directions: 1/64 um.
+//   t_q = rint(64 * time)                      (time in 0.2 us bins)
+//   y_q = (rint(64 * pad) - 32 (npads - 1)) * pitch_um
+//   z_q = 5160 * t_q                           (0.516 cm per bin)
+// 64 * v is exact in float for the validated ranges, so the round-to-nearest-even
+// conversion gives the same integer as any exact implementation.
+constexpr int kUmPerBin = 5160;
+constexpr float kCmPerBin = 0.516f;
+__device__ __forceinline__ int32_t q64(float v) { return __float2int_rn(v * 64.0f); }
+__device__ __forceinline__ int32_t y_quant(float pad, int r) {
+  return (q64(pad) - 32 * (row_npads(r) - 1)) * row_pitch_um(r);
+}
+// validated input range: |pad| <= 1024, time in [-65536, 131072] bins
+__device__ __forceinline__ bool pad_ok(float p) { return p >= -1024.0f && p <= 1024.0f; }
+__device__ __forceinline__ bool time_ok(float t) { return t >= -65536.0f && t <= 131072.0f; }
+
+// straight-line midpoint cost of the triplet (j, i, k) in (1/64 um)^2
+__device__ __forceinline__ int64_t triplet_cost(int32_t dyj, int32_t dyk, int32_t dtj, int32_t dtk) {
+  const int64_t d2y = (int64_t)dyj + (int64_t)dyk;
+  const int64_t d2z = ((int64_t)dtj + (int64_t)dtk) * kUmPerBin;
+  return d2y * d2y + d2z * d2z;
+}
+
+// ------------------------------------------------------------ status word
+enum : uint32_t { kErrInput = 1u, kErrCapacity = 2u, kErrTimeout = 4u, kErrInternal = 8u, kErrSortCap = 16u };
+
+// counters at the head of the per-call reset region
+enum : int {
+  kCtrStarts = 0,   // number of start hits
+  kCtrTracks = 1,   // number of kept chains (tracks)
+  kCtrTileLinks = 2,
+  kCtrTileKeep = 3,
+  kCtrErr = 4,
+  kCtrIndexDone = 5,
+  kCtrMaxRow = 6,
+  kCtrFitNext = 7,
+  kCtrSortDone = 8,
+  kNCounters = 16
+};
+
+// A spin-wait gives up after this many polls (with a short sleep between polls,
+// far longer than any legitimate wait), records kErrTimeout and lets the kernel
+// finish so that the context stays usable.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ void raise(uint32_t *ctr, uint32_t bits) { atomicOr(&ctr[kCtrErr], bits); }
+
+// --------------------------------------------------------- argument block
+struct Args {
+  uint32_t n;              // clusters in this call
+  const uint16_t *sector;  // sorted views (the caller's arrays when already sorted)
+  const uint16_t *row;
+  const float *pad;
+  const float *time;
+  const int32_t *perm;     // sorted position -> caller index, nullptr for identity
+  int32_t *row_begin;      // [kNKeys + 1]
+  int2 *link;              // [n] (down, up) as sorted positions, -1 = none
+  int32_t *mup;            // [n] mutual up link
+  int32_t *starts;         // [n/2 + 1]
+  int32_t *track_start;    // [track list capacity]
+  uint64_t *lb_links;      // look-back words, one per 1024-cluster tile
+  uint64_t *lb_keep;       // look-back words, one per 1024-start tile
+  uint32_t *ctr;           // counters (kNCounters)
+  uint32_t starts_cap;
+  uint32_t track_list_cap;
+  int32_t wy, wt;
+  int64_t cost_max;
+  int32_t n_min;
+  // outputs
+  int32_t *cluster_track;
+  uint32_t track_capacity;
+  float *params, *cov, *t_ref, *x, *chi2;
+  int32_t *ndf, *nhits, *first_cluster;
+  uint16_t *o_sector, *o_row_first, *o_row_last;
+  uint8_t *o_status;
+  uint32_t *n_tracks_out;
+};
+
+__device__ __forceinline__ int32_t caller_index(const Args &a, int32_t i) { return a.perm ? a.perm[i] : i; }
+
+// ------------------------------------------------- ordered compaction
+// Decoupled look-back over tiles taken in increasing order from an atomic
+// counter: tile t publishes its aggregate, then accumulates predecessors until it
+// meets an inclusive prefix.  Word layout: bits 62-63 flag (0 empty, 1 aggregate,
+// 2 inclusive prefix), bits 0-61 value.  Called by one full warp (warp 0).
+// Returns the exclusive prefix of tile t.  Every poll loop is bounded.
+__device__ __forceinline__ uint64_t lb_load(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, uint32_t tile, uint32_t aggregate, uint32_t *ctr) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t kA = 1ull << 62, kP = 2ull << 62, kMask = (1ull << 62) - 1;
+  if (tile == 0) {
+    if (lane == 0) lb_store(&status[0], kP | aggregate);
+    return 0;
+  }
+  if (lane == 0) lb_store(&status[tile], kA | aggregate);
+  uint64_t excl = 0;
+  int64_t base = (int64_t)tile - 1;  // highest predecessor not yet accumulated
+  uint32_t polls = 0;
+  bool gave_up = false;
+  while (base >= 0) {
+    const int64_t idx = base - lane;
+    uint64_t v = (idx >= 0) ? lb_load(&status[idx]) : kP;  // before tile 0: prefix 0
+    uint32_t flag = (uint32_t)(v >> 62);
+    if (gave_up && flag == 0) { v = kP; flag = 2; }       // treat as zero after a timeout
+    const unsigned empty = __ballot_sync(0xffffffffu, flag == 0);
+    const unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
+    // first lane (nearest predecessor) holding an inclusive prefix
+    const int first_p = pref ? __ffs(pref) - 1 : 32;
+    const unsigned before_p = (first_p >= 31) ? 0xffffffffu : ((2u << first_p) - 1u);
+    if (empty & before_p) {  // a predecessor has not published yet: poll again
+      if (++polls > kSpinLimit) {
+        gave_up = true;
+        if (lane == 0) raise(ctr, kErrTimeout);
+      }
+      __nanosleep(64);
+      continue;
+    }
+    uint64_t val = ((unsigned)lane <= (unsigned)first_p && idx >= 0) ? (v & kMask) : 0;
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    excl += val;
+    if (first_p < 32) break;
+    base -= 32;
+  }
+  if (lane == 0) lb_store(&status[tile], kP | ((excl + aggregate) & kMask));
+  return (uint32_t)excl;
+}
+
+}  // namespace tpc

@@ -1,0 +1,269 @@
+"""ctypes binding of the C ABI in include/tpcca.h (same names, argument
+marshalling only: every step of the tracking path runs in libtpcca.so's CUDA
+kernels).  PyTorch provides device memory and streams.
+
+The library is built in tree by ``paper_2102_08862_gb300._build.build()``; if it is
+missing, loading fails loudly -- there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+from . import _build
+
+c_u32, c_i32, c_i64, c_f32, c_vp = ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
+
+TPC_OK = 0
+TPC_ERR_ARG = -1
+TPC_ERR_CAPACITY = -2
+TPC_ERR_CUDA = -3
+TPC_ERR_INPUT = -4
+TPC_ERR_TIMEOUT = -5
+TPC_MODE_PLAIN = 0
+TPC_MODE_PRUNED = 1
+TPC_INPUT_SORTED = 1
+TPC_FIT_THREAD = 0
+TPC_FIT_WARP = 1
+ERROR_NAMES = {0: "TPC_OK", -1: "TPC_ERR_ARG", -2: "TPC_ERR_CAPACITY", -3: "TPC_ERR_CUDA", -4: "TPC_ERR_INPUT",
+               -5: "TPC_ERR_TIMEOUT"}
+
+
+class tpc_tf_config(ctypes.Structure):
+    _fields_ = [("max_clusters", c_u32), ("max_tracks", c_u32), ("wy_q", c_i32), ("wt_q", c_i32),
+                ("cost_max_q", c_i64), ("n_min", c_i32), ("mode", c_i32), ("tau", c_f32), ("device", c_i32),
+                ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32)]
+
+
+class tpc_clusters(ctypes.Structure):
+    _fields_ = [("n", c_u32), ("flags", c_u32), ("sector", c_vp), ("row", c_vp), ("pad", c_vp), ("time", c_vp)]
+
+
+class tpc_tracks(ctypes.Structure):
+    _fields_ = [("cluster_track", c_vp), ("track_capacity", c_u32), ("params", c_vp), ("cov", c_vp),
+                ("t_ref", c_vp), ("x", c_vp), ("chi2", c_vp), ("ndf", c_vp), ("nhits", c_vp),
+                ("first_cluster", c_vp), ("sector", c_vp), ("row_first", c_vp), ("row_last", c_vp),
+                ("status", c_vp), ("n_tracks", c_vp), ("n_tracks_host", c_vp)]
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/tpcca.h."""
+    txt = open(os.path.join(_build.INCLUDE, "tpcca.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(tpc_\w+)\s*\(", txt, re.M)))
+
+
+def load():
+    """Load libtpcca.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: build it with paper_2102_08862_gb300._build.build() "
+                          "(the tracker has no CPU fallback)")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    lib.tpc_default_config.argtypes = [P(tpc_tf_config)]
+    lib.tpc_default_config.restype = None
+    lib.tpc_tf_create.argtypes = [P(tpc_tf_config), P(c_vp)]
+    lib.tpc_tf_create.restype = ctypes.c_int
+    lib.tpc_track_timeframe.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
+    lib.tpc_track_timeframe.restype = ctypes.c_int
+    lib.tpc_track_timeframe_host.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
+    lib.tpc_track_timeframe_host.restype = ctypes.c_int
+    lib.tpc_tf_status.argtypes = [c_vp, c_vp]
+    lib.tpc_tf_status.restype = ctypes.c_int
+    lib.tpc_tf_destroy.argtypes = [c_vp]
+    lib.tpc_tf_destroy.restype = None
+    lib.tpc_last_error.argtypes = []
+    lib.tpc_last_error.restype = ctypes.c_char_p
+    lib.tpc_tf_debug_links.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]
+    lib.tpc_tf_debug_links.restype = ctypes.c_int
+    lib.tpc_tf_stage_times.argtypes = [c_vp, P(c_f32), P(ctypes.c_char_p), ctypes.c_int]
+    lib.tpc_tf_stage_times.restype = ctypes.c_int
+    lib.tpc_tf_launches_per_call.argtypes = [c_vp]
+    lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class TpcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != TPC_OK:
+        raise TpcError(rc, load().tpc_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------ thin wrappers
+def tpc_default_config() -> tpc_tf_config:
+    c = tpc_tf_config()
+    load().tpc_default_config(ctypes.byref(c))
+    return c
+
+
+def tpc_tf_create(cfg: tpc_tf_config) -> int:
+    h = c_vp()
+    _check(load().tpc_tf_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def tpc_track_timeframe(handle, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:
+    return load().tpc_track_timeframe(handle, ctypes.byref(clusters), ctypes.byref(tracks), stream)
+
+
+def tpc_track_timeframe_host(handle, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:
+    return load().tpc_track_timeframe_host(handle, ctypes.byref(clusters), ctypes.byref(tracks), stream)
+
+
+def tpc_tf_status(handle, stream: int = 0) -> int:
+    return load().tpc_tf_status(handle, stream)
+
+
+def tpc_tf_destroy(handle) -> None:
+    load().tpc_tf_destroy(handle)
+
+
+def tpc_last_error() -> str:
+    return load().tpc_last_error().decode()
+
+
+def tpc_tf_debug_links(handle, order, down, up, mup, is_start, stream: int = 0) -> int:
+    return load().tpc_tf_debug_links(handle, order, down, up, mup, is_start, stream)
+
+
+def tpc_tf_stage_times(handle, cap: int = 16):
+    ms = (c_f32 * cap)()
+    names = (ctypes.c_char_p * cap)()
+    n = load().tpc_tf_stage_times(handle, ms, names, cap)
+    _check(min(n, 0))
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def tpc_tf_launches_per_call(handle) -> int:
+    return load().tpc_tf_launches_per_call(handle)
+
+
+# ------------------------------------------------------------ torch convenience
+@dataclass
+class Tracks:
+    cluster_track: "object"  # int32[n]
+    n_tracks: int
+    params: "object"         # float32[n_tracks, 5]
+    cov: "object"            # float32[n_tracks, 15]
+    t_ref: "object"
+    x: "object"
+    chi2: "object"
+    ndf: "object"
+    nhits: "object"
+    first_cluster: "object"
+    sector: "object"
+    row_first: "object"
+    row_last: "object"
+    status: "object"
+
+
+class TimeFrameTracker:
+    """Owns one tpc_tf handle; inputs and outputs are torch CUDA tensors."""
+
+    def __init__(self, max_clusters: int, device: int = 0, **overrides):
+        import torch
+        self.torch = torch
+        cfg = tpc_default_config()
+        cfg.max_clusters = int(max_clusters)
+        cfg.device = int(device)
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.device = torch.device("cuda", device)
+        self.handle = tpc_tf_create(cfg)
+        self._out = None
+        self._cap = 0
+        self._n = 0
+
+    def close(self):
+        if self.handle:
+            tpc_tf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outputs(self, n, capacity):
+        t = self.torch
+        if self._out is None or self._cap < capacity or self._out["cluster_track"].numel() < max(n, 1):
+            cap = max(capacity, 1)
+            d = self.device
+            self._out = dict(
+                cluster_track=t.empty(max(n, 1), dtype=t.int32, device=d),
+                params=t.empty((cap, 5), dtype=t.float32, device=d),
+                cov=t.empty((cap, 15), dtype=t.float32, device=d),
+                t_ref=t.empty(cap, dtype=t.float32, device=d), x=t.empty(cap, dtype=t.float32, device=d),
+                chi2=t.empty(cap, dtype=t.float32, device=d), ndf=t.empty(cap, dtype=t.int32, device=d),
+                nhits=t.empty(cap, dtype=t.int32, device=d), first_cluster=t.empty(cap, dtype=t.int32, device=d),
+                sector=t.empty(cap, dtype=t.int16, device=d), row_first=t.empty(cap, dtype=t.int16, device=d),
+                row_last=t.empty(cap, dtype=t.int16, device=d), status=t.empty(cap, dtype=t.uint8, device=d),
+                n_tracks=t.zeros(1, dtype=t.int32, device=d))
+            self._cap = cap
+        return self._out
+
+    def structs(self, sector, row, pad, time, sorted_input=True, capacity=None, host_count=None):
+        """Build the tpc_clusters / tpc_tracks structs for device tensors."""
+        n = int(sector.numel())
+        cap = int(capacity if capacity is not None else max(16, n // max(1, self.cfg.n_min) + 1))
+        o = self._outputs(n, cap)
+        cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED if sorted_input else 0, sector=sector.data_ptr(),
+                          row=row.data_ptr(), pad=pad.data_ptr(), time=time.data_ptr())
+        tr = tpc_tracks(cluster_track=o["cluster_track"].data_ptr(), track_capacity=cap,
+                        params=o["params"].data_ptr(), cov=o["cov"].data_ptr(), t_ref=o["t_ref"].data_ptr(),
+                        x=o["x"].data_ptr(), chi2=o["chi2"].data_ptr(), ndf=o["ndf"].data_ptr(),
+                        nhits=o["nhits"].data_ptr(), first_cluster=o["first_cluster"].data_ptr(),
+                        sector=o["sector"].data_ptr(), row_first=o["row_first"].data_ptr(),
+                        row_last=o["row_last"].data_ptr(), status=o["status"].data_ptr(),
+                        n_tracks=o["n_tracks"].data_ptr(),
+                        n_tracks_host=ctypes.addressof(host_count) if host_count is not None else None)
+        return cl, tr, n, cap
+
+    def track(self, sector, row, pad, time, sorted_input=True, capacity=None, stream=None) -> Tracks:
+        t = self.torch
+        st = stream if stream is not None else t.cuda.current_stream(self.device)
+        cnt = c_u32(0)
+        cl, tr, n, cap = self.structs(sector, row, pad, time, sorted_input, capacity, host_count=cnt)
+        _check(tpc_track_timeframe(self.handle, cl, tr, st.cuda_stream))
+        self._n = n
+        nt = int(cnt.value)
+        m = min(nt, cap)
+        o = self._out
+        return Tracks(cluster_track=o["cluster_track"][:n], n_tracks=nt, params=o["params"][:m], cov=o["cov"][:m],
+                      t_ref=o["t_ref"][:m], x=o["x"][:m], chi2=o["chi2"][:m], ndf=o["ndf"][:m],
+                      nhits=o["nhits"][:m], first_cluster=o["first_cluster"][:m], sector=o["sector"][:m],
+                      row_first=o["row_first"][:m], row_last=o["row_last"][:m], status=o["status"][:m])
+
+    def debug_links(self, stream=None):
+        t = self.torch
+        n = self._n
+        d = self.device
+        res = {k: t.empty(max(n, 1), dtype=t.int32, device=d) for k in ("order", "down", "up", "mup")}
+        res["is_start"] = t.empty(max(n, 1), dtype=t.uint8, device=d)
+        st = stream if stream is not None else t.cuda.current_stream(d)
+        _check(tpc_tf_debug_links(self.handle, res["order"].data_ptr(), res["down"].data_ptr(),
+                                  res["up"].data_ptr(), res["mup"].data_ptr(), res["is_start"].data_ptr(),
+                                  st.cuda_stream))
+        st.synchronize()
+        return {k: v[:n] for k, v in res.items()}
+
+    def stage_times(self):
+        return tpc_tf_stage_times(self.handle)
+
+    def launches_per_call(self) -> int:
+        return tpc_tf_launches_per_call(self.handle)

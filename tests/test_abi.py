@@ -1,0 +1,81 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, exports every
+function include/tpcca.h declares, and the ctypes structs match the C layout."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_2102_08862_gb300 import _build, tpcca
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return tpcca.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = tpcca.header_functions()
+    assert {"tpc_tf_create", "tpc_track_timeframe", "tpc_tf_destroy", "tpc_last_error"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "tpcca.h"
+#define F(T, m) printf(#T "." #m " %zu\n", offsetof(T, m))
+int main(void) {
+  printf("tpc_tf_config %zu\ntpc_clusters %zu\ntpc_tracks %zu\n", sizeof(tpc_tf_config), sizeof(tpc_clusters),
+         sizeof(tpc_tracks));
+  F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap);
+  F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True,
+                                                                 text=True).stdout.splitlines())
+    assert int(vals["tpc_tf_config"]) == ctypes.sizeof(tpcca.tpc_tf_config)
+    assert int(vals["tpc_clusters"]) == ctypes.sizeof(tpcca.tpc_clusters)
+    assert int(vals["tpc_tracks"]) == ctypes.sizeof(tpcca.tpc_tracks)
+    for key, v in vals.items():
+        if "." in key:
+            struct, member = key.split(".")
+            assert getattr(getattr(tpcca, struct), member).offset == int(v), key
+
+
+def test_defaults_and_argument_errors(lib):
+    c = tpcca.tpc_default_config()
+    assert (c.wy_q, c.wt_q, c.cost_max_q, c.n_min) == (1280000, 384, 384000 ** 2, 10)
+    # invalid configurations are rejected before any device call
+    c.max_clusters = 0
+    h = ctypes.c_void_p()
+    assert lib.tpc_tf_create(ctypes.byref(c), ctypes.byref(h)) == tpcca.TPC_ERR_ARG
+    assert "max_clusters" in tpcca.tpc_last_error()
+    c.max_clusters = 100
+    c.n_min = 2
+    assert lib.tpc_tf_create(ctypes.byref(c), ctypes.byref(h)) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_tf_create(None, ctypes.byref(h)) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_track_timeframe(None, None, None, None) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_tf_status(None, None) == tpcca.TPC_ERR_ARG
+    lib.tpc_tf_destroy(None)
+
+
+def test_no_oracle_in_product_path():
+    """The CUDA path must not import, link or call the oracle."""
+    pkg = os.path.join(ROOT, "paper_2102_08862_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "oracle.h" not in txt, f
