@@ -159,6 +159,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-variant", type=int, default=0)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -204,6 +206,20 @@ def main():
         for _ in range(args.warmup):
             step()
     stream.synchronize()
+    if args.kernel_only:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+        stream.synchronize()
+        assert tpcca.tpc_tf_status(tr.handle, sh) == 0, tpcca.tpc_last_error()
+        print(json.dumps({"workload": args.workload, "clusters": n, "tracks": n_tracks,
+                          "launches_per_step": tr.launches_per_call(),
+                          "ms_per_step": e0.elapsed_time(e1) / args.steps}), flush=True)
+        tr.close()
+        return
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     if dist:
         dist.barrier()

@@ -4,20 +4,30 @@
 // coordinates, the drift time standing in for z (Sec. 1).  The state at local
 // x (the pad-row radius) is p = (y, zeta - zeta_ref, s = sin phi, t = dzeta/ds,
 // Q = q/pT), zeta = 0.516 cm/bin * time, zeta_ref = 0.516 * t_ref with t_ref the
-// start cluster's time (track-local, so FP32 keeps its precision on 10 ms frames).
-// Transport by dx: helix in (x, y) with curvature c = -0.00149896229 Q (B = 0.5 T),
-// straight line in (arc length, zeta).  Measurement (y, zeta) with variances
-// (0.06 cm)^2 and (0.0516 cm)^2.  Seed at the first cluster from the circle through
-// the first, middle (L/2) and last cluster, C0 = diag(0.06^2, 0.0516^2, .01, .01, .01).
+// start cluster's time.  Transport by dx: helix in (x, y) with curvature
+// c = -0.00149896229 Q (B = 0.5 T), straight line in (arc length, zeta).
+// Measurement (y, zeta), variances (0.06 cm)^2 and (0.0516 cm)^2.  Seed at the
+// first cluster from the circle through the first, middle (L/2) and last cluster,
+// C0 = diag(0.06^2, 0.0516^2, 0.01, 0.01, 0.01).
 //
-// GB300 design: one thread per track (TPC_FIT_THREAD).  Pass 1 walks the mutual
-// up links once, writes cluster_track and finds the middle cluster with a second
-// pointer moving at half speed; pass 2 walks again, prefetching the next
-// cluster's (pad, time, link) before the filter step of the current one, so each
-// step costs one memory round trip overlapped with ~300 FP32 operations.  The
-// chain is one cluster per row, so the step dx is the constant row pitch.
-// TPC_FIT_WARP puts one tracklet on a warp instead, lanes holding the state and
-// covariance entries.
+// GB300 design: one thread per track.  Pass 1 walks the mutual up links once,
+// writes cluster_track and finds the middle cluster with a second pointer moving
+// at half speed; pass 2 walks again, prefetching the next cluster's (pad, time,
+// link) before the filter step of the current one, so each step costs one memory
+// round trip overlapped with the filter arithmetic.
+//
+// FP32 accuracy.  Three choices keep the FP32 filter within 1e-4 of an FP64 one:
+//  * the covariance is carried as C = U D U^T (U unit upper triangular, D
+//    diagonal).  With the state ordered (y, zeta, s, t, Q) the transport
+//    Jacobian is itself unit upper triangular, so transport is U <- F U with D
+//    unchanged, and the measurement is applied as two scalar updates (the
+//    measurement noise is diagonal) by Bierman's U-D update, which never
+//    subtracts nearly equal variances the way C - K H C does;
+//  * y is kept relative to the first cluster (|y| reaches 40 cm, where the FP32
+//    spacing is 4e-6 cm), and each measured y is formed exactly in um units
+//    (error-free difference pad - centre, then one fused multiply-add by the
+//    integer pitch);
+//  * the seed, computed once per track, is evaluated in FP64.
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -28,8 +38,6 @@ namespace {
 constexpr float kBz = 0.00149896229f;  // 1/cm per (GeV/c) at 0.5 T
 constexpr float kVy = 0.06f * 0.06f;
 constexpr float kVz = 0.0516f * 0.0516f;
-
-__device__ __forceinline__ int ci(int i, int j) { return i * (i + 1) / 2 + j; }  // lower triangle, i >= j
 
 // asin(u)/u and its derivative (Taylor series of asin near 0)
 __device__ __forceinline__ float asinc(float u) {
@@ -43,11 +51,38 @@ __device__ __forceinline__ float asinc_d(float u) {
   return (u / sqrtf((1.0f - u) * (1.0f + u)) - asinf(u)) / u2;
 }
 
+// index of U(i, j), i < j, in the packed strictly-upper triangle
+__host__ __device__ constexpr int ui(int i, int j) { return 4 * i - i * (i - 1) / 2 + (j - i - 1); }
+
 struct Kf {
-  float p[5];
-  float c[15];
+  float p[5];   // y - y_ref, zeta - zeta_ref, sin phi, dzeta/ds, q/pT
+  float u[10];  // U, strictly upper part
+  float d[5];   // D
   float chi2;
 };
+
+// exact a - b as hi + lo (Knuth's two-sum)
+__device__ __forceinline__ void two_diff(float a, float b, float &hi, float &lo) {
+  hi = a - b;
+  const float bb = hi - a;
+  lo = (a - (hi - bb)) - (b + bb);
+}
+
+// y of a cluster relative to y_ref, in um, with one rounding of the small result:
+// (pad - (npads - 1)/2) * pitch_um - yref_um
+__device__ __forceinline__ float y_local_um(float pad, int r, float yref_um) {
+  float hi, lo;
+  two_diff(pad, 0.5f * (float)(row_npads(r) - 1), hi, lo);
+  const float pitch = (float)row_pitch_um(r);
+  return fmaf(lo, pitch, fmaf(hi, pitch, -yref_um));
+}
+
+// zeta of a cluster relative to the start cluster, cm
+__device__ __forceinline__ float zeta_local(float time, float tref) {
+  float hi, lo;
+  two_diff(time, tref, hi, lo);
+  return fmaf(kCmPerBin, hi, kCmPerBin * lo);
+}
 
 // transport by dx; false (state untouched) when |sin phi| would reach 0.999
 __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
@@ -61,7 +96,7 @@ __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
   const float l = sqrtf(dx * dx + dy * dy);
   const float u = 0.5f * cv * l;
   const float ds = l * asinc(u);
-  // Jacobian entries (the others are those of the identity)
+  // Jacobian entries above the unit diagonal
   const float iD2 = iD * iD;
   const float Fys = dx * (2.0f * D + A * (s1 / c1 + s2 / c2)) * iD2;  // dy/ds1
   const float Fyc = dx * dx * (D + A * s2 / c2) * iD2;                // dy/dc
@@ -75,106 +110,122 @@ __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
   k.p[0] += dy;
   k.p[1] += t * ds;
   k.p[2] = s2;
-  float *C = k.c;
-  // B = F C (rows 0..2; rows 3, 4 equal those of C)
-  float B[3][5];
-#pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    const float C0j = C[ci(max(0, j), min(0, j))], C1j = C[ci(max(1, j), min(1, j))];
-    const float C2j = C[ci(max(2, j), min(2, j))], C3j = C[ci(max(3, j), min(3, j))];
-    const float C4j = C[ci(max(4, j), min(4, j))];
-    B[0][j] = C0j + a * C2j + b * C4j;
-    B[1][j] = C1j + e * C2j + f * C3j + gq * C4j;
-    B[2][j] = C2j + h * C4j;
-  }
-  const float C32 = C[ci(3, 2)], C33 = C[ci(3, 3)], C34 = C[ci(4, 3)];
-  const float C42 = C[ci(4, 2)], C43 = C34, C44 = C[ci(4, 4)];
-  const float C30 = C[ci(3, 0)], C31 = C[ci(3, 1)], C40 = C[ci(4, 0)], C41 = C[ci(4, 1)];
-  // C' = B F^T, lower triangle
-  C[ci(0, 0)] = B[0][0] + a * B[0][2] + b * B[0][4];
-  C[ci(1, 0)] = B[1][0] + a * B[1][2] + b * B[1][4];
-  C[ci(1, 1)] = B[1][1] + e * B[1][2] + f * B[1][3] + gq * B[1][4];
-  C[ci(2, 0)] = B[2][0] + a * B[2][2] + b * B[2][4];
-  C[ci(2, 1)] = B[2][1] + e * B[2][2] + f * B[2][3] + gq * B[2][4];
-  C[ci(2, 2)] = B[2][2] + h * B[2][4];
-  C[ci(3, 0)] = C30 + a * C32 + b * C34;
-  C[ci(3, 1)] = C31 + e * C32 + f * C33 + gq * C34;
-  C[ci(3, 2)] = C32 + h * C34;
-  C[ci(4, 0)] = C40 + a * C42 + b * C44;
-  C[ci(4, 1)] = C41 + e * C42 + f * C43 + gq * C44;
-  C[ci(4, 2)] = C42 + h * C44;
+  // U <- F U (rows 0 and 1 use the old row 2)
+  float *U = k.u;
+  const float u23 = U[ui(2, 3)], u24 = U[ui(2, 4)], u34 = U[ui(3, 4)];
+  U[ui(0, 2)] += a;
+  U[ui(0, 3)] = fmaf(a, u23, U[ui(0, 3)]);
+  U[ui(0, 4)] = fmaf(a, u24, U[ui(0, 4)]) + b;
+  U[ui(1, 2)] += e;
+  U[ui(1, 3)] = fmaf(e, u23, U[ui(1, 3)]) + f;
+  U[ui(1, 4)] = fmaf(f, u34, fmaf(e, u24, U[ui(1, 4)])) + gq;
+  U[ui(2, 4)] = u24 + h;
   return true;
 }
 
-// measurement update with m = (y, zeta), H = [I2 0]
-__device__ __forceinline__ void kf_update(Kf &k, float ym, float zm) {
-  float *C = k.c;
-  const float r0 = ym - k.p[0], r1 = zm - k.p[1];
-  const float S00 = C[0] + kVy, S01 = C[1], S11 = C[2] + kVz;
-  const float idet = 1.0f / (S00 * S11 - S01 * S01);
-  const float W00 = S11 * idet, W01 = -S01 * idet, W11 = S00 * idet;
-  float c0[5], c1[5], K0[5], K1[5];
+// Bierman's U-D update for a scalar measurement of state component M with
+// variance V; accumulates the normalised innovation into chi2.
+template <int M>
+__device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
+  float f[5], g[5], b[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    c0[i] = C[ci(max(i, 0), min(i, 0))];
-    c1[i] = C[ci(max(i, 1), min(i, 1))];
+  for (int j = 0; j < 5; ++j) {
+    f[j] = j < M ? 0.0f : (j == M ? 1.0f : k.u[ui(M < j ? M : 0, M < j ? j : 1)]);
+    g[j] = k.d[j] * f[j];
+    b[j] = 0.0f;
   }
+  const float r = meas - k.p[M];
+  float alpha = V, ibeta = 1.0f / V;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    K0[i] = c0[i] * W00 + c1[i] * W01;
-    K1[i] = c0[i] * W01 + c1[i] * W11;
-    k.p[i] += K0[i] * r0 + K1[i] * r1;
+  for (int j = M; j < 5; ++j) {
+    const float beta = alpha;
+    alpha = fmaf(f[j], g[j], beta);
+    const float ia = 1.0f / alpha;
+    const float lam = -f[j] * ibeta;
+    k.d[j] *= beta * ia;
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      const float uij = k.u[ui(i, j)];
+      k.u[ui(i, j)] = fmaf(b[i], lam, uij);
+      b[i] = fmaf(g[j], uij, b[i]);
+    }
+    b[j] = g[j];
+    ibeta = ia;
   }
+  const float rk = r * ibeta;  // r / alpha
+#pragma unroll
+  for (int i = 0; i < 5; ++i) k.p[i] = fmaf(b[i], rk, k.p[i]);
+  k.chi2 = fmaf(r, rk, k.chi2);
+}
+
+__device__ __forceinline__ double meas_y_d(float pad, int r) {
+  return ((double)pad - 0.5 * (double)(row_npads(r) - 1)) * ((double)row_pitch_um(r) * 1e-4);
+}
+
+// Seed at the first cluster; returns status bit 0 for a degenerate circle.  It
+// runs once per track in FP64: on short tracks the curvature comes from a
+// sagitta of a few um over ~10 cm, and with a prior that dominates such tracks
+// the seed's q/pT is the fit's.
+__device__ __forceinline__ int kf_seed(Kf &k, int L, int r0, float pad0, float pad1, float pad2, float dt2,
+                                       float y0_local_cm) {
+  const int mid = L / 2;
+  const double dx = 160.0 / 151.0;
+  const double y0 = meas_y_d(pad0, r0);
+  const double ax = mid * dx, ay = meas_y_d(pad1, r0 + mid) - y0;
+  const double bx = (L - 1) * dx, by = meas_y_d(pad2, r0 + L - 1) - y0;
+  const double cross = ax * by - ay * bx;
+  const double d01 = sqrt(ax * ax + ay * ay), d02 = sqrt(bx * bx + by * by);
+  const double ex = bx - ax, ey = by - ay;
+  const double d12 = sqrt(ex * ex + ey * ey);
+  double cv = 2.0 * cross / (d01 * d02 * d12);
+  double u = 0.5 * cv * d02;
+  int status = 0;
+  if (fabs(u) >= 0.999) {
+    status |= 1;
+    cv = 0.0;
+    u = 0.0;
+  }
+  const double sth = by / d02, cth = bx / d02;  // chord direction first -> last
+  double s0 = sth * sqrt((1.0 - u) * (1.0 + u)) - cth * u;  // sin(chord angle - asin u)
+  if (fabs(s0) >= 0.999) {
+    status |= 1;
+    cv = 0.0;
+    u = 0.0;
+    s0 = sth;
+  }
+  const double arc = fabs(u) < 1e-4 ? d02 * (1.0 + u * u / 6.0) : d02 * asin(u) / u;
+  k.p[0] = y0_local_cm;
+  k.p[1] = 0.0f;
+  k.p[2] = (float)s0;
+  k.p[3] = (float)(0.516 * (double)dt2 / arc);
+  k.p[4] = (float)(cv / -0.00149896229);
+#pragma unroll
+  for (int q = 0; q < 10; ++q) k.u[q] = 0.0f;
+  k.d[0] = kVy;
+  k.d[1] = kVz;
+  k.d[2] = 0.01f;
+  k.d[3] = 0.01f;
+  k.d[4] = 0.01f;
+  k.chi2 = 0.0f;
+  return status;
+}
+
+// C = U D U^T, lower triangle row-major
+__device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
+  int q = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) C[ci(i, j)] -= K0[i] * c0[j] + K1[i] * c1[j];
-  k.chi2 += r0 * (W00 * r0 + W01 * r1) + r1 * (W01 * r0 + W11 * r1);
-}
-
-__device__ __forceinline__ float meas_y(float pad, int r) {
-  return (pad - 0.5f * (float)(row_npads(r) - 1)) * ((float)row_pitch_um(r) * 1e-4f);
-}
-
-// seed at the first cluster; returns status bit 0 for a degenerate circle
-__device__ __forceinline__ int kf_seed(Kf &k, int L, float y0, float y1, float y2, float z2, int mid) {
-  const float ax = (float)mid * kRowDx, ay = y1 - y0;
-  const float bx = (float)(L - 1) * kRowDx, by = y2 - y0;
-  const float cross = ax * by - ay * bx;
-  const float d01 = sqrtf(ax * ax + ay * ay), d02 = sqrtf(bx * bx + by * by);
-  const float ex = bx - ax, ey = by - ay;
-  const float d12 = sqrtf(ex * ex + ey * ey);
-  float cv = 2.0f * cross / (d01 * d02 * d12);
-  float u = 0.5f * cv * d02;
-  int status = 0;
-  if (fabsf(u) >= 0.999f) {
-    status |= 1;
-    cv = 0.0f;
-    u = 0.0f;
-  }
-  const float sth = by / d02, cth = bx / d02;  // chord direction first -> last
-  float s0 = sth * sqrtf((1.0f - u) * (1.0f + u)) - cth * u;  // sin(chord angle - asin u)
-  if (fabsf(s0) >= 0.999f) {
-    status |= 1;
-    cv = 0.0f;
-    u = 0.0f;
-    s0 = sth;
-  }
-  const float arc = d02 * asinc(u);
-  k.p[0] = y0;
-  k.p[1] = 0.0f;
-  k.p[2] = s0;
-  k.p[3] = z2 / arc;
-  k.p[4] = cv / (-kBz);
+    for (int j = 0; j <= i; ++j) {
+      float acc = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 15; ++q) k.c[q] = 0.0f;
-  k.c[ci(0, 0)] = kVy;
-  k.c[ci(1, 1)] = kVz;
-  k.c[ci(2, 2)] = 0.01f;
-  k.c[ci(3, 3)] = 0.01f;
-  k.c[ci(4, 4)] = 0.01f;
-  k.chi2 = 0.0f;
-  return status;
+      for (int m = i; m < 5; ++m) {
+        const float uim = m == i ? 1.0f : k.u[ui(i < m ? i : 0, i < m ? m : 1)];
+        const float ujm = m == j ? 1.0f : k.u[ui(j < m ? j : 0, j < m ? m : 1)];
+        acc = fmaf(uim * k.d[m], ujm, acc);
+      }
+      c[q++] = acc;
+    }
 }
 
 }  // namespace
@@ -201,12 +252,14 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     const int32_t last = c, mid = tort;
     const int r0 = a.row[start];
     const float tref = a.time[start];
-    const float y0 = meas_y(a.pad[start], r0);
-    const float y1 = meas_y(a.pad[mid], r0 + L / 2);
-    const float y2 = meas_y(a.pad[last], r0 + L - 1);
-    const float z2 = kCmPerBin * (a.time[last] - tref);
+    const float pad0 = a.pad[start];
+    // y reference: the first cluster's y (rounded to FP32, in um)
+    float h0, l0;
+    two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
+    const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
     Kf k;
-    int status = kf_seed(k, L, y0, y1, y2, z2, L / 2);
+    int status = kf_seed(k, L, r0, pad0, a.pad[mid], a.pad[last], a.time[last] - tref,
+                         y_local_um(pad0, r0, yref_um) * 1e-4f);
     // pass 2: filter, prefetching the next cluster
     int used = 1, lastrow = r0;
     c = a.mup[start];
@@ -229,14 +282,19 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
         status |= 2;
         break;
       }
-      kf_update(k, meas_y(cpd, r0 + q), kCmPerBin * (ctm - tref));
+      kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
+      kf_measure<1>(k, zeta_local(ctm, tref), kVz);
       ++used;
       lastrow = r0 + q;
     }
+    float cov[15];
+    kf_covariance(k, cov);
+    float *po = a.params + (size_t)t * 5;
+    po[0] = fmaf(yref_um, 1e-4f, k.p[0]);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) a.params[(size_t)t * 5 + i] = k.p[i];
+    for (int i = 1; i < 5; ++i) po[i] = k.p[i];
 #pragma unroll
-    for (int i = 0; i < 15; ++i) a.cov[(size_t)t * 15 + i] = k.c[i];
+    for (int i = 0; i < 15; ++i) a.cov[(size_t)t * 15 + i] = cov[i];
     a.t_ref[t] = tref;
     a.x[t] = row_x(lastrow);
     a.chi2[t] = k.chi2;
