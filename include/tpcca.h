@@ -72,8 +72,8 @@ typedef struct {
   uint32_t max_clusters; /* arena sized at create; calls with more clusters fail with TPC_ERR_CAPACITY */
   uint32_t max_tracks;   /* capacity of the internal track list (0: max_clusters / n_min) */
   int32_t wy_q;          /* pad-direction window, 1/64 um (default 1 280 000 = 2 cm); <= 2^28 */
-  int32_t wt_q;          /* time window, 1/64 bin (default 384 = 6 bins); <= 2^20 */
-  int64_t cost_max_q;    /* largest accepted cost, (1/64 um)^2 (default 384000^2 = (0.6 cm)^2) */
+  int32_t wt_q;          /* time window, 1/64 bin (default 384 = 6 bins); <= 2^17 */
+  int64_t cost_max_q;    /* largest accepted cost, (1/64 um)^2 (default 384000^2 = (0.6 cm)^2); < 2^40 */
   int32_t n_min;         /* shortest chain kept as a track (default 10, >= 3) */
   int32_t mode;          /* TPC_MODE_PLAIN or TPC_MODE_PRUNED */
   float tau;             /* pruning threshold on the classifier probability (TPC_MODE_PRUNED) */

@@ -43,13 +43,18 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct tpc_tf {
   tpc_tf_config cfg;
   int device = 0, sms = 0;
-  int nb_cap = 0, nb_chunks = 1;
+  int nb_cap = 0;
+  uint32_t tile_cap = 0;
+  int32_t *tile_off = nullptr;
+  int4 *tile_win = nullptr;
   uint32_t N = 0, track_list_cap = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
   int32_t *row_begin = nullptr;
   int2 *link = nullptr;
-  int32_t *mup = nullptr, *starts = nullptr, *track_start = nullptr;
+  uint16_t *mup16 = nullptr;
+  int2 *starts = nullptr;
+  int32_t *trk_key = nullptr, *trk_len = nullptr, *chain = nullptr;
   uint32_t *reset = nullptr;
   size_t reset_bytes_max = 0;
   uint16_t *s_sector = nullptr, *s_row = nullptr;
@@ -74,6 +79,7 @@ struct tpc_tf {
   int launches = 0;
   uint32_t last_n = 0;
   bool last_sorted = true;
+  Args last_args;
 };
 
 extern "C" void tpc_default_config(tpc_tf_config *c) {
@@ -107,7 +113,8 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   if (cfg->max_clusters == 0 || cfg->max_clusters > (1u << 30))
     return fail(TPC_ERR_ARG, "tpc_tf_create: max_clusters must be in [1, 2^30]");
   if (cfg->n_min < 3 || cfg->n_min > TPC_NROWS) return fail(TPC_ERR_ARG, "tpc_tf_create: n_min must be in [3, 152]");
-  if (cfg->wy_q < 0 || cfg->wy_q > (1 << 28) || cfg->wt_q < 0 || cfg->wt_q > (1 << 20) || cfg->cost_max_q < 0)
+  if (cfg->wy_q < 0 || cfg->wy_q > (1 << 28) || cfg->wt_q < 0 || cfg->wt_q > (1 << 17) || cfg->cost_max_q < 0 ||
+      cfg->cost_max_q >= (1LL << 40))
     return fail(TPC_ERR_ARG, "tpc_tf_create: search window or cost cut out of range");
   if (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_PRUNED)
     return fail(TPC_ERR_ARG, "tpc_tf_create: unknown mode");
@@ -123,43 +130,29 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     delete tf;
     return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   }
-  int optin = 0;
   cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, tf->device);
-  // row capacity of the staged-row neighbour kernel: four slots of
-  // (y_q, t_q) rows plus bucket tables must fit the opt-in shared memory
-  const size_t stat = neighbours_rw_static_smem();
-  long avail = (long)optin - (long)stat - 256;
-  int cap = 0;
-  if (avail > 0) {
-    cap = (int)((avail / (4 * 4) - kNbTable - 1 - 3) / 2 - 8);
-    cap &= ~3;
-  }
-  if (cap < 4) cap = 4;
-  // the attribute is per kernel, shared by all handles: always allow the largest
-  const int cap_max = cap;
-  if (cfg->row_cap > 0 && cfg->row_cap < cap) cap = cfg->row_cap & ~3;
-  if (cap < 4) cap = 4;
-  tf->nb_cap = cap;
-  if (neighbours_set_smem(neighbours_rw_smem(cap_max)) != 0) {
-    free_all(tf);
-    return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot configure shared memory of the neighbour kernel");
-  }
-  tf->nb_chunks = tf->sms >= 2 * kNSect ? tf->sms / kNSect : 1;
+  // candidate windows staged in shared memory by the neighbour kernel; larger
+  // windows (or a smaller row_cap, used by tests) go through global memory
+  tf->nb_cap = kNbWin;
+  if (cfg->row_cap > 0 && cfg->row_cap < tf->nb_cap) tf->nb_cap = cfg->row_cap;
+  tf->tile_cap = neighbour_tiles_max(cfg->max_clusters);
   tf->track_list_cap = cfg->max_tracks ? cfg->max_tracks : tf->N / (uint32_t)cfg->n_min + 1;
 
   const size_t N = tf->N;
-  const size_t tiles_l = (N + kTile - 1) / kTile + 1, tiles_k = (N / 2 + 1 + kTile - 1) / kTile + 1;
-  tf->reset_bytes_max = kNCounters * 4 + 8 * (tiles_l + tiles_k);
+  tf->reset_bytes_max = kNCounters * 4 + 8 * (link_tiles(tf->N) + walk_tiles(tf->N) + 2);
   struct Part {
     void **p;
     size_t bytes;
   } parts[] = {
       {(void **)&tf->row_begin, (kNKeys + 1) * 4},
+      {(void **)&tf->tile_off, (kNKeys + 1) * 4},
+      {(void **)&tf->tile_win, (size_t)tf->tile_cap * 2 * 16},
       {(void **)&tf->link, (N + 4) * 8},
-      {(void **)&tf->mup, (N + 4) * 4},
-      {(void **)&tf->starts, (N / 2 + 2) * 4},
-      {(void **)&tf->track_start, (size_t)(tf->track_list_cap + 1) * 4},
+      {(void **)&tf->mup16, (N + 16) * 2},
+      {(void **)&tf->starts, (N / 2 + 2) * 8},
+      {(void **)&tf->trk_key, (size_t)(tf->track_list_cap + 1) * 4},
+      {(void **)&tf->trk_len, (size_t)(tf->track_list_cap + 1) * 4},
+      {(void **)&tf->chain, (size_t)kNRows * tf->track_list_cap * 4},
       {(void **)&tf->reset, tf->reset_bytes_max},
       {(void **)&tf->s_sector, (N + 8) * 2},
       {(void **)&tf->s_row, (N + 8) * 2},
@@ -259,12 +252,17 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   std::memset(&a, 0, sizeof(a));
   a.n = n;
   a.row_begin = tf->row_begin;
+  a.tile_off = tf->tile_off;
+  a.tile_win = tf->tile_win;
+  a.tile_cap = tf->tile_cap;
   a.link = tf->link;
-  a.mup = tf->mup;
+  a.mup16 = tf->mup16;
   a.starts = tf->starts;
-  a.track_start = tf->track_start;
+  a.trk_key = tf->trk_key;
+  a.trk_len = tf->trk_len;
+  a.chain = tf->chain;
   a.ctr = tf->reset;
-  const size_t tiles_l = (n + kTile - 1) / kTile, tiles_k = (n / 2 + 1 + kTile - 1) / kTile;
+  const size_t tiles_l = link_tiles(n), tiles_k = walk_tiles(n);
   a.lb_links = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(tf->reset) + kNCounters * 4);
   a.lb_keep = a.lb_links + tiles_l;
   a.starts_cap = n / 2 + 1;
@@ -312,22 +310,24 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     tf->launches += nl;
     stage(tf, st, "sort");
   }
-  const int use_tma = (((uintptr_t)a.pad & 15) == 0 && ((uintptr_t)a.time & 15) == 0) ? 1 : 0;
   launch_row_index(a, st);
+  launch_tile_windows(a, st);
   stage(tf, st, "ingest");
-  launch_neighbours(a, tf->nb_chunks, tf->nb_cap, use_tma, tf->sms, st);
-  launch_edge_claims(a, tf->nb_cap, st);
+  launch_neighbours(a, tf->nb_cap, st);
   stage(tf, st, "neighbours");
+  launch_edge_claims(a, st);
+  stage(tf, st, "edge_claims");
   launch_links(a, tf->sms, st);
   stage(tf, st, "links");
-  launch_keep(a, tf->sms, st);
-  stage(tf, st, "keep");
+  launch_walk(a, tf->sms, st);
+  stage(tf, st, "walk");
   launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
   stage(tf, st, "fit");
-  tf->launches += 7;
+  tf->launches += 7;  // index, tile windows, neighbours, edge claims, links, keep, fit
   TPC_CK(cudaGetLastError());
   tf->last_n = n;
   tf->last_sorted = sorted;
+  tf->last_args = a;
   if (out->n_tracks_host) {
     TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + kCtrTracks, 4, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaMemcpyAsync(tf->pinned + 1, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
@@ -426,8 +426,8 @@ extern "C" int tpc_tf_debug_links(tpc_tf *tf, int32_t *order, int32_t *down, int
   if (down) TPC_CK(cudaMemcpy2DAsync(down, 4, tf->link, 8, 4, n, cudaMemcpyDeviceToDevice, st));
   if (up)
     TPC_CK(cudaMemcpy2DAsync(up, 4, reinterpret_cast<char *>(tf->link) + 4, 8, 4, n, cudaMemcpyDeviceToDevice, st));
-  if (mup) TPC_CK(cudaMemcpyAsync(mup, tf->mup, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
-  launch_debug_flags(tf->link, tf->mup, tf->last_sorted ? nullptr : tf->perm, n, order, is_start, st);
+  if (mup || is_start) launch_debug_links(tf->last_args, mup, is_start, st);
+  if (order) launch_debug_order(tf->last_sorted ? nullptr : tf->perm, n, order, st);
   TPC_CK(cudaGetLastError());
   return TPC_OK;
 }

@@ -158,47 +158,78 @@ __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
   k.chi2 = fmaf(r, rk, k.chi2);
 }
 
-__device__ __forceinline__ double meas_y_d(float pad, int r) {
-  return ((double)pad - 0.5 * (double)(row_npads(r) - 1)) * ((double)row_pitch_um(r) * 1e-4);
+// ---- unevaluated float pairs (hi + lo) for the seed's sagitta
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_norm(float hi, float lo) {
+  const float s = hi + lo;
+  return {s, lo - (s - hi)};
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, -b.hi);
+  return ff_norm(s.hi, s.lo + (a.lo - b.lo));
+}
+// integer (|m| < 2^8) times a pair
+__device__ __forceinline__ ff ff_scale(ff a, float m) {
+  const float p = a.hi * m;
+  return ff_norm(p, fmaf(a.hi, m, -p) + a.lo * m);
+}
+// (pad - (npads - 1)/2) * pitch_um - yref_um as a pair (um)
+__device__ __forceinline__ ff ff_y_um(float pad, int r, float yref_um) {
+  float dh, dl;
+  two_diff(pad, 0.5f * (float)(row_npads(r) - 1), dh, dl);
+  const float pitch = (float)row_pitch_um(r);
+  const float p = dh * pitch;
+  const float e = fmaf(dh, pitch, -p) + dl * pitch;
+  const ff s = ff_two_sum(p, -yref_um);
+  return ff_norm(s.hi, s.lo + e);
 }
 
-// Seed at the first cluster; returns status bit 0 for a degenerate circle.  It
-// runs once per track in FP64: on short tracks the curvature comes from a
-// sagitta of a few um over ~10 cm, and with a prior that dominates such tracks
-// the seed's q/pT is the fit's.
+// Seed at the first cluster; returns status bit 0 for a degenerate circle.  On a
+// short track the curvature rests on a sagitta of a few um over ~10 cm, and its
+// prior makes the seed's q/pT the fit's, so the circle's cross product
+// dx * (mid * (y_last - y0) - (L - 1) * (y_mid - y0)) is formed in float pairs
+// from y values that are exact in um; the rest is plain FP32.
 __device__ __forceinline__ int kf_seed(Kf &k, int L, int r0, float pad0, float pad1, float pad2, float dt2,
-                                       float y0_local_cm) {
+                                       float yref_um) {
   const int mid = L / 2;
-  const double dx = 160.0 / 151.0;
-  const double y0 = meas_y_d(pad0, r0);
-  const double ax = mid * dx, ay = meas_y_d(pad1, r0 + mid) - y0;
-  const double bx = (L - 1) * dx, by = meas_y_d(pad2, r0 + L - 1) - y0;
-  const double cross = ax * by - ay * bx;
-  const double d01 = sqrt(ax * ax + ay * ay), d02 = sqrt(bx * bx + by * by);
-  const double ex = bx - ax, ey = by - ay;
-  const double d12 = sqrt(ex * ex + ey * ey);
-  double cv = 2.0 * cross / (d01 * d02 * d12);
-  double u = 0.5 * cv * d02;
+  const ff y0 = ff_y_um(pad0, r0, yref_um);
+  const ff ay = ff_sub(ff_y_um(pad1, r0 + mid, yref_um), y0);
+  const ff by = ff_sub(ff_y_um(pad2, r0 + L - 1, yref_um), y0);
+  const ff sag = ff_sub(ff_scale(by, (float)mid), ff_scale(ay, (float)(L - 1)));
+  const float cross = kRowDx * (sag.hi + sag.lo) * 1e-4f;  // cm^2
+  const float ax = (float)mid * kRowDx, bx = (float)(L - 1) * kRowDx;
+  const float ayc = (ay.hi + ay.lo) * 1e-4f, byc = (by.hi + by.lo) * 1e-4f;
+  const float d01 = sqrtf(ax * ax + ayc * ayc), d02 = sqrtf(bx * bx + byc * byc);
+  const float ex = bx - ax, ey = byc - ayc;
+  const float d12 = sqrtf(ex * ex + ey * ey);
+  float cv = 2.0f * cross / (d01 * d02 * d12);
+  float u = 0.5f * cv * d02;
   int status = 0;
-  if (fabs(u) >= 0.999) {
+  if (fabsf(u) >= 0.999f) {
     status |= 1;
-    cv = 0.0;
-    u = 0.0;
+    cv = 0.0f;
+    u = 0.0f;
   }
-  const double sth = by / d02, cth = bx / d02;  // chord direction first -> last
-  double s0 = sth * sqrt((1.0 - u) * (1.0 + u)) - cth * u;  // sin(chord angle - asin u)
-  if (fabs(s0) >= 0.999) {
+  const float sth = byc / d02, cth = bx / d02;  // chord direction first -> last
+  float s0 = sth * sqrtf((1.0f - u) * (1.0f + u)) - cth * u;  // sin(chord angle - asin u)
+  if (fabsf(s0) >= 0.999f) {
     status |= 1;
-    cv = 0.0;
-    u = 0.0;
+    cv = 0.0f;
+    u = 0.0f;
     s0 = sth;
   }
-  const double arc = fabs(u) < 1e-4 ? d02 * (1.0 + u * u / 6.0) : d02 * asin(u) / u;
-  k.p[0] = y0_local_cm;
+  const float arc = d02 * asinc(u);
+  k.p[0] = (y0.hi + y0.lo) * 1e-4f;
   k.p[1] = 0.0f;
-  k.p[2] = (float)s0;
-  k.p[3] = (float)(0.516 * (double)dt2 / arc);
-  k.p[4] = (float)(cv / -0.00149896229);
+  k.p[2] = s0;
+  k.p[3] = kCmPerBin * dt2 / arc;
+  k.p[4] = cv / -kBz;
 #pragma unroll
   for (int q = 0; q < 10; ++q) k.u[q] = 0.0f;
   k.d[0] = kVy;
@@ -231,26 +262,15 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 }  // namespace
 
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
-  const uint32_t nt = a.ctr[kCtrTracks];
-  const uint32_t nlist = min(nt, a.track_list_cap);
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nlist; t += gridDim.x * blockDim.x) {
-    const int32_t start = a.track_start[t];
-    // pass 1: membership, length, middle and last cluster
-    int32_t c = start, tort = start;
-    int m = 0;
-    a.cluster_track[caller_index(a, c)] = (int32_t)t;
-    while (m < kNRows - 1) {
-      const int32_t nx = a.mup[c];
-      if (nx < 0) break;
-      c = nx;
-      ++m;
-      a.cluster_track[caller_index(a, c)] = (int32_t)t;
-      if (m & 1) tort = a.mup[tort];
-    }
-    const int L = m + 1;
-    if (t >= a.track_capacity) continue;
-    const int32_t last = c, mid = tort;
-    const int r0 = a.row[start];
+  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
+  const size_t stride = a.track_list_cap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    // the chain's clusters were recorded by the walk as chain[step][track]
+    const int32_t *ch = a.chain + t;
+    const int L = a.trk_len[t];
+    const int key = a.trk_key[t];
+    const int r0 = key % kNRows;
+    const int32_t start = ch[0], mid = ch[(size_t)(L / 2) * stride], last = ch[(size_t)(L - 1) * stride];
     const float tref = a.time[start];
     const float pad0 = a.pad[start];
     // y reference: the first cluster's y (rounded to FP32, in um)
@@ -258,25 +278,24 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
     const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
     Kf k;
-    int status = kf_seed(k, L, r0, pad0, a.pad[mid], a.pad[last], a.time[last] - tref,
-                         y_local_um(pad0, r0, yref_um) * 1e-4f);
-    // pass 2: filter, prefetching the next cluster
+    int status = kf_seed(k, L, r0, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
+    // filter; the next cluster's (pad, time) and the one after's position are
+    // loaded before the current step's arithmetic
     int used = 1, lastrow = r0;
-    c = a.mup[start];
     float pd = 0.f, tm = 0.f;
-    int32_t nx = -1;
-    if (c >= 0) {
-      pd = a.pad[c];
-      tm = a.time[c];
-      nx = a.mup[c];
+    int32_t c2 = -1;
+    if (L > 1) {
+      const int32_t c1 = ch[stride];
+      pd = a.pad[c1];
+      tm = a.time[c1];
     }
-    for (int q = 1; q < L && c >= 0; ++q) {
+    if (L > 2) c2 = ch[2 * stride];
+    for (int q = 1; q < L; ++q) {
       const float cpd = pd, ctm = tm;
-      c = nx;
-      if (q + 1 < L && c >= 0) {
-        pd = a.pad[c];
-        tm = a.time[c];
-        nx = a.mup[c];
+      if (q + 1 < L) {
+        pd = a.pad[c2];
+        tm = a.time[c2];
+        if (q + 2 < L) c2 = ch[(size_t)(q + 2) * stride];
       }
       if (!kf_transport(k, kRowDx)) {
         status |= 2;
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     a.ndf[t] = 2 * used - 5;
     a.nhits[t] = L;
     a.first_cluster[t] = caller_index(a, start);
-    a.o_sector[t] = a.sector[start];
+    a.o_sector[t] = (uint16_t)(key / kNRows);
     a.o_row_first[t] = (uint16_t)r0;
     a.o_row_last[t] = (uint16_t)(r0 + L - 1);
     a.o_status[t] = (uint8_t)status;

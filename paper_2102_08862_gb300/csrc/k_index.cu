@@ -61,19 +61,45 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  int mx = 0;
-  for (int k = threadIdx.x; k < kNKeys; k += blockDim.x) {
-    const int32_t b = ((volatile int32_t *)a.row_begin)[k], e = ((volatile int32_t *)a.row_begin)[k + 1];
+  // largest row, monotonicity, and the first neighbour tile of every row
+  // (each thread owns a contiguous block of keys; block-wide exclusive scan)
+  const volatile int32_t *rbv = a.row_begin;
+  const int per = (kNKeys + blockDim.x - 1) / blockDim.x;
+  const int k0 = threadIdx.x * per, k1 = min(kNKeys, k0 + per);
+  int mx = 0, ntile = 0;
+  for (int k = k0; k < k1; ++k) {
+    const int32_t b = rbv[k], e = rbv[k + 1];
     if (e < b) raise(a.ctr, kErrInput);
-    mx = max(mx, e - b);
+    const int c = max(0, e - b);
+    mx = max(mx, c);
+    ntile += (c + kNbTile - 1) / kNbTile;
   }
+  __shared__ int s_scan[256];
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) s_max[threadIdx.x >> 5] = mx;
+  s_scan[threadIdx.x] = ntile;
   __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = threadIdx.x >= (unsigned)o ? s_scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int off = s_scan[threadIdx.x] - ntile;
+  for (int k = k0; k < k1; ++k) {
+    a.tile_off[k] = off;
+    off += (max(0, rbv[k + 1] - rbv[k]) + kNbTile - 1) / kNbTile;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    a.tile_off[kNKeys] = s_scan[threadIdx.x];
+    a.ctr[kCtrTiles] = (uint32_t)s_scan[threadIdx.x];
+    if ((uint32_t)s_scan[threadIdx.x] > a.tile_cap) raise(a.ctr, kErrInternal);
+  }
   if (threadIdx.x == 0) {
     int m = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
     a.ctr[kCtrMaxRow] = (uint32_t)m;
+    if (m > 65534) raise(a.ctr, kErrRowCap);  // row-local links are 16-bit
   }
 }
 

@@ -1,5 +1,5 @@
-// k_links.cu -- A2 link cleaning (mutual links), A3 start-hit compaction and the
-// A4 chain-length filter.
+// k_links.cu -- A2 link cleaning (mutual links), A3 start-hit compaction and
+// A4 chain membership.
 //
 // The CA tracker the paper builds on (Sec. 1) keeps a link only when both
 // clusters chose each other; the mutual links form disjoint vertical chains, one
@@ -7,12 +7,16 @@
 // mutual down link; chains of at least n_min clusters become tracks, numbered in
 // the order of their start cluster.
 //
-// GB300 design: both kernels are persistent, take 1024-item tiles in order from
-// an atomic counter and compact their flags with a block scan plus a decoupled
-// look-back across tiles, so the start list and the track list come out in
-// cluster order in one pass each.  Isolated clusters and members of short chains
-// get their final cluster_track = -1 here; members of kept chains get their track
-// id in the fit kernel, so every cluster_track entry is written exactly once.
+// GB300 design.  k_links streams the link array in 4096-cluster tiles (16
+// consecutive clusters per thread), stores each mutual up link as a 16-bit index
+// inside row r+1 (a 32M-cluster frame's links then take 64 MB and stay in L2 for
+// the walk) and compacts the start hits in cluster order with a block scan plus a
+// decoupled look-back across tiles.  k_walk gives each start hit one thread: it
+// follows the chain n_min - 1 links to decide whether it is a track, takes its
+// track id from a second ordered compaction, then walks the whole chain writing
+// cluster_track and the chain's cluster positions as [step][track], so the fit
+// reads them coalesced with no pointer chasing.  Isolated clusters and members
+// of short chains get cluster_track = -1, so every entry is written exactly once.
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -20,8 +24,9 @@ namespace tpc {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kItems = kTile / kThreads;  // 4 consecutive items per thread
-static_assert(kItems == 4, "tile layout");
+constexpr int kItems = kLinkTileN / 256;         // consecutive clusters per thread in k_links
+constexpr int kLinkTile = kThreads * kItems;     // clusters per look-back tile
+constexpr uint16_t kNone16 = 0xffff;
 
 // exclusive scan of v over the block; *total receives the block sum
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
@@ -46,52 +51,66 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
   *total = s_warp[kWarps - 1];
   return (w > 0 ? s_warp[w - 1] : 0) + x - v;
 }
+
+// last key with rb[key] <= i
+__device__ __forceinline__ int key_of(const int32_t *rb, int i) {
+  int lo = 0, hi = kNKeys;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (rb[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 }  // namespace
 
 // A2 + A3: mup[i] = up[i] if down[up[i]] = i; start(i) = no mutual down, a mutual up.
 __global__ void __launch_bounds__(kThreads) k_links(Args a) {
+  __shared__ int32_t s_rb[kNKeys + 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
+  for (int k = threadIdx.x; k <= kNKeys; k += kThreads) s_rb[k] = a.row_begin[k];
   const uint32_t n = a.n;
-  const uint32_t n_tiles = (n + kTile - 1) / kTile;
+  const uint32_t n_tiles = (n + kLinkTile - 1) / kLinkTile;
+  const uint64_t keep = l2_keep_policy();
+  bool bad = false;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrTileLinks], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const uint32_t i0 = tile * kTile + threadIdx.x * kItems;
-    int2 l[kItems];
-    if (i0 + kItems <= n) {
-      const int4 v0 = reinterpret_cast<const int4 *>(a.link)[i0 / 2];
-      const int4 v1 = reinterpret_cast<const int4 *>(a.link)[i0 / 2 + 1];
-      l[0] = make_int2(v0.x, v0.y);
-      l[1] = make_int2(v0.z, v0.w);
-      l[2] = make_int2(v1.x, v1.y);
-      l[3] = make_int2(v1.z, v1.w);
-    } else {
-#pragma unroll
-      for (int q = 0; q < kItems; ++q) l[q] = (i0 + q < n) ? a.link[i0 + q] : make_int2(-1, -1);
-    }
-    int32_t mu[kItems];
+    const int i0 = (int)(tile * kLinkTile + threadIdx.x * kItems);
+    int key = i0 < (int)n ? key_of(s_rb, i0) : 0;
     uint32_t flags = 0;
+    uint16_t m16[kItems];
+    int16_t skey[kItems];
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
-      const int32_t i = (int32_t)(i0 + q);
-      const int32_t up = l[q].y, dn = l[q].x;
-      const int32_t mup = (up >= 0 && a.link[up].x == i) ? up : -1;
-      const int32_t mdn = (dn >= 0 && a.link[dn].y == i) ? dn : -1;
-      mu[q] = mup;
-      if ((uint32_t)i < n) {
-        if (mdn < 0 && mup >= 0) flags |= 1u << q;
-        if (mdn < 0 && mup < 0) a.cluster_track[caller_index(a, i)] = -1;
+      const int i = i0 + q;
+      m16[q] = kNone16;
+      skey[q] = 0;
+      if (i >= (int)n) continue;
+      while (key < kNKeys - 1 && i >= s_rb[key + 1]) ++key;
+      const int2 l = __ldcs(a.link + i);
+      const int32_t mup = (l.y >= 0 && a.link[l.y].x == i) ? l.y : -1;
+      const int32_t mdn = (l.x >= 0 && a.link[l.x].y == i) ? l.x : -1;
+      if (mup >= 0) {
+        const int d = mup - s_rb[key + 1];
+        if (d < 0 || d >= kNone16) bad = true; else m16[q] = (uint16_t)d;
       }
+      skey[q] = (int16_t)key;
+      if (mdn < 0 && mup >= 0) flags |= 1u << q;
+      if (mdn < 0 && mup < 0) a.cluster_track[caller_index(a, i)] = -1;
     }
-    if (i0 + kItems <= n) {
-      reinterpret_cast<int4 *>(a.mup)[i0 / 4] = make_int4(mu[0], mu[1], mu[2], mu[3]);
+    if (i0 + kItems <= (int)n) {
+      auto pk = [&](int q) { return (uint32_t)m16[q] | ((uint32_t)m16[q + 1] << 16); };
+#pragma unroll
+      for (int v = 0; v < kItems / 8; ++v)
+        st_keep_v4(a.mup16 + i0 + 8 * v, make_uint4(pk(8 * v), pk(8 * v + 2), pk(8 * v + 4), pk(8 * v + 6)),
+                   keep);
     } else {
 #pragma unroll
       for (int q = 0; q < kItems; ++q)
-        if (i0 + q < n) a.mup[i0 + q] = mu[q];
+        if (i0 + q < (int)n) st_keep_u16(a.mup16 + i0 + q, m16[q], keep);
     }
     uint32_t total;
     const uint32_t excl = block_exclusive_scan((uint32_t)__popc(flags), s_warp, &total);
@@ -104,22 +123,25 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
 #pragma unroll
     for (int q = 0; q < kItems; ++q)
       if ((flags >> q) & 1u) {
-        if (pos < a.starts_cap) a.starts[pos] = (int32_t)(i0 + q);
+        if (pos < a.starts_cap) a.starts[pos] = make_int2(i0 + q, skey[q]);
         ++pos;
       }
     if (tile == n_tiles - 1 && threadIdx.x == 0) a.ctr[kCtrStarts] = s_prefix + total;
     __syncthreads();
   }
+  if (bad) raise(a.ctr, kErrRowCap);
 }
 
-// A4 filter: walk at most n_min - 1 links from every start; chains that reach
-// n_min clusters are kept (compacted in start order into track_start), the
-// clusters of shorter chains get cluster_track = -1.
-__global__ void __launch_bounds__(kThreads) k_keep(Args a) {
+// A4: two start hits per thread, walked interleaved so that two dependent load
+// chains are in flight.  Chains that reach n_min clusters become tracks (ids in
+// start order); their clusters get the track id and are recorded in the chain
+// buffer; the clusters of shorter chains get -1.
+__global__ void __launch_bounds__(kThreads) k_walk(Args a) {
+  __shared__ int32_t s_rb[kNKeys + 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
   const uint32_t ns = min(a.ctr[kCtrStarts], a.starts_cap);
-  const uint32_t n_tiles = (ns + kTile - 1) / kTile;
+  const uint32_t n_tiles = (ns + kWalkTileN - 1) / kWalkTileN;
   if (n_tiles == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.ctr[kCtrTracks] = 0;
@@ -127,52 +149,77 @@ __global__ void __launch_bounds__(kThreads) k_keep(Args a) {
     }
     return;
   }
+  for (int k = threadIdx.x; k <= kNKeys; k += kThreads) s_rb[k] = a.row_begin[k];
   const int n_min = a.n_min;
+  const size_t stride = a.track_list_cap;
+  const uint64_t keep = l2_keep_policy();
+  // one link step of a chain: (c, key) -> next cluster, or c = -1 at the end
+  auto next = [&](int &c, int &key) {
+    const uint16_t m = ld_keep_u16(a.mup16 + c, keep);
+    if (m == kNone16) {
+      c = -1;
+    } else {
+      c = s_rb[key + 1] + m;
+      ++key;
+    }
+  };
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrTileKeep], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const uint32_t j0 = tile * kTile + threadIdx.x * kItems;
-    int32_t st[kItems];
-    uint32_t flags = 0;
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      st[q] = (j0 + q < ns) ? a.starts[j0 + q] : -1;
-      if (st[q] < 0) continue;
-      int32_t c = st[q];
-      int len = 1;
-      while (len < n_min) {
-        const int32_t nx = a.mup[c];
-        if (nx < 0) break;
-        c = nx;
-        ++len;
+    const uint32_t j = tile * kWalkTileN + 2 * threadIdx.x;
+    const int2 st0 = j < ns ? a.starts[j] : make_int2(-1, 0);
+    const int2 st1 = j + 1 < ns ? a.starts[j + 1] : make_int2(-1, 0);
+    // walk at most n_min - 1 links of both chains
+    int c0 = st0.x, k0 = st0.y, c1 = st1.x, k1 = st1.y;
+    int len0 = c0 >= 0, len1 = c1 >= 0;
+    for (int s = 1; s < n_min && (c0 >= 0 || c1 >= 0); ++s) {
+      if (c0 >= 0) {
+        next(c0, k0);
+        len0 += c0 >= 0;
       }
-      if (len >= n_min) {
-        flags |= 1u << q;
-      } else {
-        c = st[q];
-        for (int m = 0; m < len && c >= 0; ++m) {
-          a.cluster_track[caller_index(a, c)] = -1;
-          c = a.mup[c];
-        }
+      if (c1 >= 0) {
+        next(c1, k1);
+        len1 += c1 >= 0;
       }
     }
+    const bool kept0 = len0 >= n_min, kept1 = len1 >= n_min;
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan((uint32_t)__popc(flags), s_warp, &total);
+    const uint32_t excl = block_exclusive_scan((uint32_t)kept0 + (uint32_t)kept1, s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(a.lb_keep, tile, total, a.ctr);
       if (threadIdx.x == 0) s_prefix = pre;
     }
     __syncthreads();
-    uint32_t pos = s_prefix + excl;
-#pragma unroll
-    for (int q = 0; q < kItems; ++q)
-      if ((flags >> q) & 1u) {
-        if (pos < a.track_list_cap) a.track_start[pos] = st[q];
-        else raise(a.ctr, kErrCapacity);
-        ++pos;
+    const uint32_t id0 = s_prefix + excl, id1 = id0 + (uint32_t)kept0;
+    if ((kept0 && id0 >= a.track_list_cap) || (kept1 && id1 >= a.track_list_cap)) raise(a.ctr, kErrCapacity);
+    const bool w0 = st0.x >= 0 && (!kept0 || id0 < a.track_list_cap);
+    const bool w1 = st1.x >= 0 && (!kept1 || id1 < a.track_list_cap);
+    // second walk of both chains: members of tracks get the id and go to the
+    // chain buffer, members of short chains get -1
+    c0 = w0 ? st0.x : -1;
+    k0 = st0.y;
+    c1 = w1 ? st1.x : -1;
+    k1 = st1.y;
+    const int32_t v0 = kept0 ? (int32_t)id0 : -1, v1 = kept1 ? (int32_t)id1 : -1;
+    int m = 0;
+    for (; m < kNRows && (c0 >= 0 || c1 >= 0); ++m) {
+      if (c0 >= 0) {
+        if (kept0) __stcs(a.chain + (size_t)m * stride + id0, c0);
+        __stcs(a.cluster_track + caller_index(a, c0), v0);
+        if (m + 1 < (kept0 ? kNRows : len0)) next(c0, k0); else c0 = -1;
+        if (c0 < 0 && kept0) a.trk_len[id0] = m + 1;
       }
+      if (c1 >= 0) {
+        if (kept1) __stcs(a.chain + (size_t)m * stride + id1, c1);
+        __stcs(a.cluster_track + caller_index(a, c1), v1);
+        if (m + 1 < (kept1 ? kNRows : len1)) next(c1, k1); else c1 = -1;
+        if (c1 < 0 && kept1) a.trk_len[id1] = m + 1;
+      }
+    }
+    if (kept0 && w0) a.trk_key[id0] = st0.y;
+    if (kept1 && w1) a.trk_key[id1] = st1.y;
     if (tile == n_tiles - 1 && threadIdx.x == 0) {
       const uint32_t nt = s_prefix + total;
       a.ctr[kCtrTracks] = nt;
@@ -183,12 +230,31 @@ __global__ void __launch_bounds__(kThreads) k_keep(Args a) {
   }
 }
 
+// inspection: the mutual up link as a sorted position, and the start flag
+__global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    const int key = (int)a.sector[i] * kNRows + a.row[i];
+    const uint16_t m = a.mup16[i];
+    const int32_t up = (m == kNone16 || key + 1 > kNKeys) ? -1 : a.row_begin[key + 1] + m;
+    if (mup) mup[i] = up;
+    if (is_start) {
+      const int dn = a.link[i].x;
+      const bool mdn = dn >= 0 && a.link[dn].y == (int32_t)i;
+      is_start[i] = (uint8_t)(!mdn && up >= 0);
+    }
+  }
+}
+
 void launch_links(const Args &a, int sms, cudaStream_t st) {
-  const uint32_t tiles = (a.n + kTile - 1) / kTile;
-  const uint32_t grid = tiles < (uint32_t)sms * 8u ? (tiles ? tiles : 1u) : (uint32_t)sms * 8u;
+  const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
+  const uint32_t grid = tiles < (uint32_t)sms * 4u ? (tiles ? tiles : 1u) : (uint32_t)sms * 4u;
   k_links<<<grid, kThreads, 0, st>>>(a);
 }
 
-void launch_keep(const Args &a, int sms, cudaStream_t st) { k_keep<<<sms * 4, kThreads, 0, st>>>(a); }
+void launch_walk(const Args &a, int sms, cudaStream_t st) { k_walk<<<sms * 8, kThreads, 0, st>>>(a); }
+
+void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st) {
+  k_debug_links<<<1024, 256, 0, st>>>(a, mup, is_start);
+}
 
 }  // namespace tpc

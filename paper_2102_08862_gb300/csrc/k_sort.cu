@@ -186,21 +186,13 @@ int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, cons
 }
 
 // ------------------------------------------------------------ inspection
-__global__ void k_debug_flags(const int2 *link, const int32_t *mup, const int32_t *perm, uint32_t n, int32_t *order,
-                              uint8_t *is_start) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (order) order[i] = perm ? perm[i] : (int32_t)i;
-    if (is_start) {
-      const int dn = link[i].x;
-      const bool mdn = dn >= 0 && link[dn].y == (int32_t)i;
-      is_start[i] = (uint8_t)(!mdn && mup[i] >= 0);
-    }
-  }
+__global__ void k_debug_order(const int32_t *perm, uint32_t n, int32_t *order) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    order[i] = perm ? perm[i] : (int32_t)i;
 }
 
-void launch_debug_flags(const int2 *link, const int32_t *mup, const int32_t *perm, uint32_t n, int32_t *order,
-                        uint8_t *is_start, cudaStream_t st) {
-  k_debug_flags<<<1024, 256, 0, st>>>(link, mup, perm, n, order, is_start);
+void launch_debug_order(const int32_t *perm, uint32_t n, int32_t *order, cudaStream_t st) {
+  k_debug_order<<<1024, 256, 0, st>>>(perm, n, order);
 }
 
 }  // namespace tpc

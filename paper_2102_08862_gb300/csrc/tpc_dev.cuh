@@ -41,14 +41,23 @@ __device__ __forceinline__ bool pad_ok(float p) { return p >= -1024.0f && p <= 1
 __device__ __forceinline__ bool time_ok(float t) { return t >= -65536.0f && t <= 131072.0f; }
 
 // straight-line midpoint cost of the triplet (j, i, k) in (1/64 um)^2
+// With |dy| <= wy <= 2^28 and |dt| <= wt <= 2^17 both sums fit 32 bits, and the
+// squares are 32x32 -> 64-bit products.
 __device__ __forceinline__ int64_t triplet_cost(int32_t dyj, int32_t dyk, int32_t dtj, int32_t dtk) {
-  const int64_t d2y = (int64_t)dyj + (int64_t)dyk;
-  const int64_t d2z = ((int64_t)dtj + (int64_t)dtk) * kUmPerBin;
-  return d2y * d2y + d2z * d2z;
+  const int32_t d2y = dyj + dyk;
+  const int32_t d2z = (dtj + dtk) * kUmPerBin;
+  return (int64_t)d2y * d2y + (int64_t)d2z * d2z;
 }
 
 // ------------------------------------------------------------ status word
-enum : uint32_t { kErrInput = 1u, kErrCapacity = 2u, kErrTimeout = 4u, kErrInternal = 8u, kErrSortCap = 16u };
+enum : uint32_t {
+  kErrInput = 1u,
+  kErrCapacity = 2u,
+  kErrTimeout = 4u,
+  kErrInternal = 8u,
+  kErrSortCap = 16u,
+  kErrRowCap = 32u  // a (sector, row) with more than 65534 clusters
+};
 
 // counters at the head of the per-call reset region
 enum : int {
@@ -61,6 +70,7 @@ enum : int {
   kCtrMaxRow = 6,
   kCtrFitNext = 7,
   kCtrSortDone = 8,
+  kCtrTiles = 9,    // neighbour tiles of this frame
   kNCounters = 16
 };
 
@@ -80,10 +90,15 @@ struct Args {
   const float *time;
   const int32_t *perm;     // sorted position -> caller index, nullptr for identity
   int32_t *row_begin;      // [kNKeys + 1]
+  int32_t *tile_off;       // [kNKeys + 1] first neighbour tile of each (sector, row)
+  int4 *tile_win;          // per tile: candidate ranges in rows r-1 and r+1 (lo, hi, lo, hi)
+  uint32_t tile_cap;       // tiles the arena holds
   int2 *link;              // [n] (down, up) as sorted positions, -1 = none
-  int32_t *mup;            // [n] mutual up link
-  int32_t *starts;         // [n/2 + 1]
-  int32_t *track_start;    // [track list capacity]
+  uint16_t *mup16;         // [n] mutual up link as index inside row r+1, 0xffff = none
+  int2 *starts;            // [n/2 + 1] (sorted position, sector*152 + row) of start hits
+  int32_t *trk_key;        // [track list capacity] (sector*152 + row) of the track's first cluster
+  int32_t *trk_len;        // [track list capacity] chain length
+  int32_t *chain;          // [152][track list capacity] sorted positions of each track's clusters
   uint64_t *lb_links;      // look-back words, one per 1024-cluster tile
   uint64_t *lb_keep;       // look-back words, one per 1024-start tile
   uint32_t *ctr;           // counters (kNCounters)
@@ -103,6 +118,29 @@ struct Args {
 };
 
 __device__ __forceinline__ int32_t caller_index(const Args &a, int32_t i) { return a.perm ? a.perm[i] : i; }
+
+// ------------------------------------------------- L2 residency hints
+// The 16-bit mutual links (2 B per cluster) are written by the link kernel and
+// chased by the walk: they are stored and loaded with an evict-last L2 policy,
+// while data touched once (link reads, chain and cluster_track writes) streams.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint16_t ld_keep_u16(const uint16_t *addr, uint64_t pol) {
+  uint16_t v;
+  asm volatile("ld.global.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(addr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_keep_v4(void *addr, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(addr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_keep_u16(uint16_t *addr, uint16_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(addr), "h"(v), "l"(pol) : "memory");
+}
 
 // ------------------------------------------------- ordered compaction
 // Decoupled look-back over tiles taken in increasing order from an atomic

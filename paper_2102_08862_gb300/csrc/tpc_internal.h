@@ -6,31 +6,36 @@
 
 namespace tpc {
 
-// staged-row neighbour kernel: threads per CTA and bucket-table entries per row
-constexpr int kNbThreads = 1024;
-constexpr int kNbTable = 1024;
-// clusters (and start hits) per look-back tile
-constexpr int kTile = 1024;
+// neighbour kernel: rows are cut into tiles of kNbTile clusters; a CTA of
+// kNbThreads stages its tile and the matching time windows of rows r-1 and r+1
+// (up to kNbWin clusters each, more goes through global memory)
+constexpr int kNbThreads = 256;
+constexpr int kNbTile = 768;
+constexpr int kNbWin = 1280;
+static_assert(kNbWin < 2048 && kNbTile % kNbThreads == 0, "window indices are packed in 11 bits");
+// look-back tiles: clusters per tile of the link kernel, start hits per tile of the walk
+constexpr int kLinkTileN = 2048;
+constexpr int kWalkTileN = 512;  // 256 threads, two chains each
+inline size_t link_tiles(uint32_t n) { return (n + kLinkTileN - 1) / kLinkTileN; }
+inline size_t walk_tiles(uint32_t n) { return (n / 2 + 1 + kWalkTileN - 1) / kWalkTileN; }
 
-// dynamic shared memory of the staged-row kernel for a row capacity `cap`
-size_t neighbours_rw_smem(int cap);
-// static shared memory of the staged-row kernel
-size_t neighbours_rw_static_smem();
+// upper bound of neighbour tiles for n clusters
+inline uint32_t neighbour_tiles_max(uint32_t n) { return n / kNbTile + kNKeys + 1; }
 
 void launch_row_index(const Args &a, cudaStream_t st);
-void launch_neighbours(const Args &a, int n_chunks, int cap, int use_tma, int sms, cudaStream_t st);
-void launch_edge_claims(const Args &a, int cap, cudaStream_t st);
-int neighbours_set_smem(size_t bytes);
+void launch_tile_windows(const Args &a, cudaStream_t st);
+void launch_neighbours(const Args &a, int win_cap, cudaStream_t st);
+void launch_edge_claims(const Args &a, cudaStream_t st);
 void launch_links(const Args &a, int sms, cudaStream_t st);
-void launch_keep(const Args &a, int sms, cudaStream_t st);
+void launch_walk(const Args &a, int sms, cudaStream_t st);
+void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st);
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st);
 // unsorted input: stable sort by (sector, row, time, pad) into the sorted views
 int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,
                 size_t scratch_bytes, int sms, cudaStream_t st);
 size_t sort_scratch_bytes(uint32_t max_n);
-// order[] and is_start[] of the last call (inspection)
-void launch_debug_flags(const int2 *link, const int32_t *mup, const int32_t *perm, uint32_t n, int32_t *order,
-                        uint8_t *is_start, cudaStream_t st);
+// order[] of the last call (inspection)
+void launch_debug_order(const int32_t *perm, uint32_t n, int32_t *order, cudaStream_t st);
 
 }  // namespace tpc
