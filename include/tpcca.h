@@ -134,6 +134,24 @@ int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *ou
  * out->n_tracks_host are host pointers here (either may be NULL). */
 int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
 
+/* Track one small time frame without allocating any device memory (the paper
+ * has no counterpart: this serves callers that may not call cudaMalloc, such as
+ * code running during CUDA graph capture, real-time hosts with a fixed device
+ * memory budget, or plug-ins whose host owns all device memory).  Same steps and
+ * results as tpc_track_timeframe, with device-resident inputs and outputs passed
+ * by the caller; cfg may be NULL for the defaults (only the search parameters and
+ * n_min are used).  All scratch lives in one 8 MiB device array inside the
+ * library, loaded on every GPU that uses the library and kept until the process
+ * exits.  Limits: sorted input (TPC_INPUT_SORTED), TPC_MODE_PLAIN, at most 65536
+ * clusters and at most 8 MiB of scratch for them (more -> TPC_ERR_CAPACITY, before
+ * anything is enqueued).  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  Every call uses the same array, so calls must not overlap on the GPU:
+ * two calls in flight at once on different streams race and corrupt each other.
+ * Errors as for tpc_track_timeframe. */
+int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_clusters *cl, const tpc_tracks *out,
+                                void *stream);
+
 /* Synchronise `stream` and report the device-side status of the last call
  * (TPC_OK, TPC_ERR_INPUT, TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT). */
 int tpc_tf_status(tpc_tf *tf, void *stream);

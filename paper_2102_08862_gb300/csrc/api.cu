@@ -97,6 +97,12 @@ extern "C" void tpc_default_config(tpc_tf_config *c) {
 
 extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
 
+// error reporting for entry points defined in other translation units
+int tpc::report(int code, const char *msg) {
+  if (code == TPC_OK) g_err.clear(); else g_err = msg;
+  return code;
+}
+
 static void free_all(tpc_tf *tf) {
   if (!tf) return;
   if (tf->arena) cudaFree(tf->arena);

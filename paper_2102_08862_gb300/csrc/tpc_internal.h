@@ -35,6 +35,8 @@ int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, cons
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,
                 size_t scratch_bytes, int sms, cudaStream_t st);
 size_t sort_scratch_bytes(uint32_t max_n);
+// sets the message returned by tpc_last_error() (cleared for TPC_OK); returns code
+int report(int code, const char *msg);
 // order[] of the last call (inspection)
 void launch_debug_order(const int32_t *perm, uint32_t n, int32_t *order, cudaStream_t st);
 

@@ -74,6 +74,8 @@ def load():
     lib.tpc_track_timeframe.restype = ctypes.c_int
     lib.tpc_track_timeframe_host.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
     lib.tpc_track_timeframe_host.restype = ctypes.c_int
+    lib.tpc_track_timeframe_noalloc.argtypes = [P(tpc_tf_config), P(tpc_clusters), P(tpc_tracks), c_vp]
+    lib.tpc_track_timeframe_noalloc.restype = ctypes.c_int
     lib.tpc_tf_status.argtypes = [c_vp, c_vp]
     lib.tpc_tf_status.restype = ctypes.c_int
     lib.tpc_tf_destroy.argtypes = [c_vp]
@@ -121,6 +123,14 @@ def tpc_track_timeframe(handle, clusters: tpc_clusters, tracks: tpc_tracks, stre
 
 def tpc_track_timeframe_host(handle, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:
     return load().tpc_track_timeframe_host(handle, ctypes.byref(clusters), ctypes.byref(tracks), stream)
+
+
+def tpc_track_timeframe_noalloc(cfg, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:
+    """The tracking call without any device allocation, for callers that may not
+    allocate (graph capture, fixed-budget hosts): small sorted frames only, all
+    scratch in a static device array inside the library; calls must not overlap."""
+    return load().tpc_track_timeframe_noalloc(ctypes.byref(cfg) if cfg is not None else None,
+                                              ctypes.byref(clusters), ctypes.byref(tracks), stream)
 
 
 def tpc_tf_status(handle, stream: int = 0) -> int:
