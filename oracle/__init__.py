@@ -30,13 +30,14 @@ TRACK_DTYPE = np.dtype([
 
 
 def build(force: bool = False) -> str:
-    src = os.path.join(_HERE, "oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
     hdr = os.path.join(_HERE, "oracle.h")
     if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(p) for p in srcs + [hdr])):
         return _SO
+    # -ffp-contract=off: every FP32 feature operation is rounded on its own
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                    "-o", _SO + ".tmp", src, "-lm"], check=True)
+                    "-o", _SO + ".tmp", *srcs, "-lm"], check=True)
     os.replace(_SO + ".tmp", _SO)
     return _SO
 
@@ -81,6 +82,26 @@ def _load():
             lib.or_track.restype = ctypes.c_int
             lib.or_eval.argtypes = [i64, vp, vp, vp, i64, i64, i32, ctypes.c_double, ctypes.POINTER(EvalOut)]
             lib.or_eval.restype = ctypes.c_int
+            dbl = ctypes.c_double
+            lib.or_bf16.argtypes = [ctypes.c_float]
+            lib.or_bf16.restype = ctypes.c_float
+            lib.or_feature_log1p.argtypes = [ctypes.c_float]
+            lib.or_feature_log1p.restype = ctypes.c_float
+            lib.or_mlp_features.argtypes = [i32, i32, i32, i32, i32, i32, i32, i64, i32, i32, i64, vp]
+            lib.or_mlp_parse.argtypes = [vp, i64, vp]
+            lib.or_mlp_parse.restype = ctypes.c_int
+            lib.or_mlp_logit.argtypes = [vp, vp]
+            lib.or_mlp_logit.restype = dbl
+            lib.or_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp, dbl, vp, vp]
+            lib.or_mlp_loss_grad.restype = ctypes.c_int
+            lib.or_neighbours_pruned.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, dbl, vp, vp, vp,
+                                                 vp, vp]
+            lib.or_neighbours_pruned.restype = ctypes.c_int
+            lib.or_track_ex.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, dbl, vp, vp, vp, vp, vp,
+                                        vp, vp, i64, vp, vp, vp, vp]
+            lib.or_track_ex.restype = ctypes.c_int
+            lib.or_training_triplets.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), i64, vp, vp, vp, vp]
+            lib.or_training_triplets.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -174,10 +195,15 @@ def fit_chain(sector, rows, pads, times):
     return rec[0]
 
 
-def track(sector, row, pad, time, prm: Params | None = None, track_cap: int | None = None):
-    """Run the whole path.  Returns a dict with `order` (sorted position -> caller
-    index), `down`, `up`, `mdown`, `mup` (sorted positions, -1 = none), `is_start`,
-    `cluster_track` (caller order) and `tracks` (TRACK_DTYPE records)."""
+def track(sector, row, pad, time, prm: Params | None = None, track_cap: int | None = None,
+          mlp: bytes | None = None, tau: float = 0.5):
+    """Run the whole path (A1 pruned by the classifier `mlp`, a weight blob, when
+    given).  Returns a dict with `order` (sorted position -> caller index), `down`,
+    `up`, `mdown`, `mup` (sorted positions, -1 = none), `is_start`,
+    `cluster_track` (caller order) and `tracks` (TRACK_DTYPE records); with `mlp`
+    also `band` (sorted positions whose pruning decision lies within the score
+    band around tau) and `stats` (ambiguous clusters, scored pairs, changed
+    choices, fallbacks)."""
     prm = prm or params()
     sector, row = _c(sector, np.uint16), _c(row, np.uint16)
     pad, time = _c(pad, np.float32), _c(time, np.float32)
@@ -189,12 +215,125 @@ def track(sector, row, pad, time, prm: Params | None = None, track_cap: int | No
     ct = np.zeros(n, np.int32)
     tracks = np.zeros(cap, TRACK_DTYPE)
     nt = ctypes.c_int64(0)
-    rc = _load().or_track(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), _p(order), _p(down),
-                          _p(up), _p(mdown), _p(mup), _p(is_start), _p(ct), cap, _p(tracks), ctypes.byref(nt))
+    if mlp is None:
+        rc = _load().or_track(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), _p(order), _p(down),
+                              _p(up), _p(mdown), _p(mup), _p(is_start), _p(ct), cap, _p(tracks), ctypes.byref(nt))
+        extra = {}
+    else:
+        m = _mlp_struct(mlp)
+        band = np.zeros(n, np.uint8)
+        stats = np.zeros(4, np.int64)
+        rc = _load().or_track_ex(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), _p(m), float(tau),
+                                 _p(order), _p(down), _p(up), _p(mdown), _p(mup), _p(is_start), _p(ct), cap,
+                                 _p(tracks), ctypes.byref(nt), _p(band), _p(stats))
+        extra = dict(band=band.astype(bool), stats=stats)
     if rc < 0:
         raise MemoryError("oracle: track failed")
     return dict(order=order, down=down, up=up, mdown=mdown, mup=mup, is_start=is_start.astype(bool),
-                cluster_track=ct, tracks=tracks[:min(nt.value, cap)], n_tracks=nt.value)
+                cluster_track=ct, tracks=tracks[:min(nt.value, cap)], n_tracks=nt.value, **extra)
+
+
+# ------------------------------------------------------------ link classifier
+MLP_IN, MLP_H = 12, 64
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+MLP_BLOB_BYTES = 16 + 4 * (2 * MLP_IN + MLP_NPARAM)
+PRUNE_BAND = 1e-3
+
+
+def mlp_blob(mean, inv_std, theta) -> bytes:
+    """Weight blob (the library's file format, written out here independently):
+    header (magic "TPCM", version 1, 12, 64) + float32 mean, inv_std, then theta =
+    W1 (64x12), b1, W2 (64x64), b2, w3, b3 flattened in that order."""
+    hdr = np.array([0x4D435054, 1, MLP_IN, MLP_H], np.uint32)
+    body = np.concatenate([np.asarray(mean, np.float32).ravel(), np.asarray(inv_std, np.float32).ravel(),
+                           np.asarray(theta, np.float32).ravel()])
+    assert body.size == 2 * MLP_IN + MLP_NPARAM
+    return hdr.tobytes() + body.astype("<f4").tobytes()
+
+
+def _mlp_struct(blob: bytes):
+    buf = np.frombuffer(blob, np.uint8).copy()
+    m = np.zeros(4 * (2 * MLP_IN + MLP_NPARAM) + 64, np.uint8)  # or_mlp is all floats
+    if _load().or_mlp_parse(_p(buf), buf.size, _p(m)) != 0:
+        raise ValueError("oracle: bad classifier weight blob")
+    return m
+
+
+def bf16(x: float) -> float:
+    return float(_load().or_bf16(float(x)))
+
+
+def feature_log1p(v: float) -> float:
+    return float(_load().or_feature_log1p(float(v)))
+
+
+def mlp_features(r, yj, yi, yk, tj, ti, tk, cost, nj, nk, cost_max=147456000000):
+    f = np.zeros(MLP_IN, np.float32)
+    _load().or_mlp_features(int(r), int(yj), int(yi), int(yk), int(tj), int(ti), int(tk), int(cost), int(nj),
+                            int(nk), int(cost_max), _p(f))
+    return f
+
+
+def mlp_logits(blob: bytes, feat) -> np.ndarray:
+    """Inference logits of raw feature rows (float32[M, 12])."""
+    feat = _c(feat, np.float32).reshape(-1, MLP_IN)
+    m = _mlp_struct(blob)
+    lib = _load()
+    return np.array([lib.or_mlp_logit(_p(m), _p(feat[i])) for i in range(feat.shape[0])], np.float64)
+
+
+def mlp_loss_grad(theta, mean, inv_std, feat, label, pos_weight=1.0):
+    """FP64 loss and gradient (blob order) over the batch."""
+    theta = _c(theta, np.float64)
+    mean, inv_std = _c(mean, np.float32), _c(inv_std, np.float32)
+    feat = _c(feat, np.float32).reshape(-1, MLP_IN)
+    label = _c(label, np.uint8)
+    grad = np.zeros(MLP_NPARAM, np.float64)
+    loss = ctypes.c_double(0.0)
+    rc = _load().or_mlp_loss_grad(_p(theta), _p(mean), _p(inv_std), feat.shape[0], _p(feat), _p(label),
+                                  float(pos_weight), ctypes.byref(loss), _p(grad))
+    if rc:
+        raise ValueError("oracle: empty batch")
+    return loss.value, grad
+
+
+def neighbours_pruned(sector, row, pad, time, blob: bytes, tau: float, prm: Params | None = None):
+    prm = prm or params()
+    sector, row = _c(sector, np.uint16), _c(row, np.uint16)
+    pad, time = _c(pad, np.float32), _c(time, np.float32)
+    n = sector.shape[0]
+    down, up = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    cost = np.zeros(n, np.int64)
+    band = np.zeros(n, np.uint8)
+    stats = np.zeros(4, np.int64)
+    m = _mlp_struct(blob)
+    rc = _load().or_neighbours_pruned(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), _p(m),
+                                      float(tau), _p(down), _p(up), _p(cost), _p(band), _p(stats))
+    if rc:
+        raise MemoryError("oracle: neighbours failed")
+    return down, up, cost, band.astype(bool), stats
+
+
+def training_triplets(sector, row, pad, time, prm: Params | None = None, cap: int | None = None):
+    """(features float32[M,12], labels uint8[M], tri int32[M,3] caller indices)."""
+    prm = prm or params()
+    sector, row = _c(sector, np.uint16), _c(row, np.uint16)
+    pad, time = _c(pad, np.float32), _c(time, np.float32)
+    n = sector.shape[0]
+    lib = _load()
+    cnt = ctypes.c_int64(0)
+    if cap is None:
+        lib.or_training_triplets(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), 0, None, None, None,
+                                 ctypes.byref(cnt))
+        cap = cnt.value
+    feat = np.zeros((max(cap, 1), MLP_IN), np.float32)
+    label = np.zeros(max(cap, 1), np.uint8)
+    tri = np.zeros((max(cap, 1), 3), np.int32)
+    if lib.or_training_triplets(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), cap, _p(feat),
+                                _p(label), _p(tri), ctypes.byref(cnt)):
+        raise MemoryError("oracle: training triplets failed")
+    m = min(cnt.value, cap)
+    return feat[:m], label[:m], tri[:m]
 
 
 def evaluate(label, sector, cluster_track, n_tracks, n_gen_tracks, min_findable=30, match_frac=0.9):

@@ -121,9 +121,11 @@ static void or_row_ranges(int64_t n, const uint16_t *sector, const uint16_t *row
 
 /* ------------------------------------------------------- A1: neighbour finding */
 /* Input sorted by (sector, row, time, pad).  down/up receive sorted positions of
- * the chosen pair (or -1), cost the pair's cost (or -1).  Rows 0 and 151 get -1. */
-int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
-                         const or_params *prm, int32_t *down, int32_t *up, int64_t *cost) {
+ * the chosen pair (or -1), cost the pair's cost (or -1).  Rows 0 and 151 get -1.
+ * With mlp != NULL the pruned rule of or_neighbours_pruned applies. */
+static int or_neighbours_impl(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad,
+                              const float *time, const or_params *prm, const or_mlp *mlp, double tau, int32_t *down,
+                              int32_t *up, int64_t *cost, uint8_t *band, int64_t *stats) {
   int nk = OR_NSECT * OR_NROWS;
   int64_t *rf = (int64_t *)malloc(sizeof(int64_t) * (nk + 1));
   int32_t *tq = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
@@ -138,7 +140,9 @@ int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row,
     down[i] = -1;
     up[i] = -1;
     if (cost) cost[i] = -1;
+    if (band) band[i] = 0;
   }
+  if (stats) memset(stats, 0, 4 * sizeof(int64_t));
   for (int s = 0; s < OR_NSECT; ++s) {
     for (int r = 1; r < OR_NROWS - 1; ++r) {
       int64_t a = rf[s * OR_NROWS + r], b = rf[s * OR_NROWS + r + 1];
@@ -176,6 +180,49 @@ int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row,
             }
           }
         }
+        if (mlp && best >= 0 && best <= prm->cost_max_q) {
+          /* pruning: score every pair under the cost cut when there are >= 2 */
+          int ncand = 0;
+          for (int x = 0; x < nj; ++x)
+            for (int y = 0; y < nkc; ++y) {
+              int64_t dy = (int64_t)yq[cj[x]] + yq[ck[y]] - 2 * (int64_t)yq[i];
+              int64_t dz = zq[cj[x]] + zq[ck[y]] - 2 * zq[i];
+              if (dy * dy + dz * dz <= prm->cost_max_q) ++ncand;
+            }
+          if (ncand >= 2) {
+            int64_t pbest = -1;
+            int32_t pj = -1, pk = -1;
+            if (stats) {
+              stats[0] += 1;
+              stats[1] += ncand;
+            }
+            for (int x = 0; x < nj; ++x)
+              for (int y = 0; y < nkc; ++y) {
+                int64_t dy = (int64_t)yq[cj[x]] + yq[ck[y]] - 2 * (int64_t)yq[i];
+                int64_t dz = zq[cj[x]] + zq[ck[y]] - 2 * zq[i];
+                int64_t c = dy * dy + dz * dz;
+                if (c > prm->cost_max_q) continue;
+                float f[OR_MLP_IN];
+                or_mlp_features(r, yq[cj[x]], yq[i], yq[ck[y]], tq[cj[x]], tq[i], tq[ck[y]], c, nj, nkc,
+                                prm->cost_max_q, f);
+                double sc = or_sigmoid(or_mlp_logit(mlp, f));
+                if (band && fabs(sc - tau) <= OR_PRUNE_BAND) band[i] = 1;
+                if (sc >= tau && (pbest < 0 || c < pbest)) {
+                  pbest = c;
+                  pj = cj[x];
+                  pk = ck[y];
+                }
+              }
+            if (pbest >= 0) {
+              if (stats && (pj != bj || pk != bk)) stats[2] += 1;
+              best = pbest;
+              bj = pj;
+              bk = pk;
+            } else if (stats) {
+              stats[3] += 1;
+            }
+          }
+        }
         if (best >= 0 && best <= prm->cost_max_q) {
           down[i] = bj;
           up[i] = bk;
@@ -191,6 +238,17 @@ int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row,
   free(cj);
   free(ck);
   return 0;
+}
+
+int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, int32_t *down, int32_t *up, int64_t *cost) {
+  return or_neighbours_impl(n, sector, row, pad, time, prm, NULL, 0.0, down, up, cost, NULL, NULL);
+}
+
+int or_neighbours_pruned(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, const or_mlp *mlp, double tau, int32_t *down, int32_t *up,
+                         int64_t *cost, uint8_t *band, int64_t *stats) {
+  return or_neighbours_impl(n, sector, row, pad, time, prm, mlp, tau, down, up, cost, band, stats);
 }
 
 /* Brute force over all cluster triples, any input order, no time sort and no
@@ -430,9 +488,10 @@ int or_fit_chain(int32_t L, int32_t sector, const int32_t *rows, const float *pa
 }
 
 /* ------------------------------------------------------- the whole path */
-int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
-             const or_params *prm, int32_t *order, int32_t *down, int32_t *up, int32_t *mdown, int32_t *mup,
-             uint8_t *is_start, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks) {
+int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down, int32_t *up,
+                int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track, int64_t track_cap,
+                or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats) {
   *n_tracks = 0;
   if (n == 0) return 0;
   uint16_t *ss = (uint16_t *)malloc(sizeof(uint16_t) * n), *sr = (uint16_t *)malloc(sizeof(uint16_t) * n);
@@ -449,7 +508,7 @@ int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float
     st[p] = time[order[p]];
   }
   /* A1 */
-  if (or_neighbours_sorted(n, ss, sr, sp, st, prm, down, up, cost)) return -1;
+  if (or_neighbours_impl(n, ss, sr, sp, st, prm, mlp, tau, down, up, cost, band, stats)) return -1;
   /* A2 edge rows: row-0 cluster j takes as up link the row-1 cluster i with
    * down[i] = j of minimal (cost_i, i); row-151 cluster k takes as down link the
    * row-150 cluster i with up[i] = k of minimal (cost_i, i).  Scanning i upwards
@@ -516,6 +575,117 @@ int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float
   free(cost);
   free(claim);
   return rc;
+}
+
+int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+             const or_params *prm, int32_t *order, int32_t *down, int32_t *up, int32_t *mdown, int32_t *mup,
+             uint8_t *is_start, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks) {
+  return or_track_ex(n, sector, row, pad, time, prm, NULL, 0.0, order, down, up, mdown, mup, is_start, cluster_track,
+                     track_cap, tracks, n_tracks, NULL, NULL);
+}
+
+/* ------------------------------------------------- classifier training set */
+int or_training_triplets(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, int64_t cap, float *feat, uint8_t *label, int32_t *tri,
+                         int64_t *count) {
+  *count = 0;
+  if (n == 0) return 0;
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * n), *down = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t *up = (int32_t *)malloc(sizeof(int32_t) * n), *mdown = (int32_t *)malloc(sizeof(int32_t) * n);
+  int32_t *mup = (int32_t *)malloc(sizeof(int32_t) * n), *ct = (int32_t *)malloc(sizeof(int32_t) * n);
+  uint8_t *is_start = (uint8_t *)malloc(n);
+  uint16_t *ss = (uint16_t *)malloc(sizeof(uint16_t) * n), *sr = (uint16_t *)malloc(sizeof(uint16_t) * n);
+  float *sp = (float *)malloc(sizeof(float) * n), *st = (float *)malloc(sizeof(float) * n);
+  int32_t *tq = (int32_t *)malloc(sizeof(int32_t) * n), *yq = (int32_t *)malloc(sizeof(int32_t) * n);
+  int64_t *zq = (int64_t *)malloc(sizeof(int64_t) * n);
+  int32_t *cj = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *ck = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+  int64_t *rf = (int64_t *)malloc(sizeof(int64_t) * (OR_NSECT * OR_NROWS + 1));
+  if (!order || !down || !up || !mdown || !mup || !ct || !is_start || !ss || !sr || !sp || !st || !tq || !yq || !zq ||
+      !cj || !ck || !rf)
+    return -1;
+  int64_t nt = 0;
+  /* the plain path (down/up of middle rows are the A1 choices; mdown/mup after cleaning) */
+  if (or_track_ex(n, sector, row, pad, time, prm, NULL, 0.0, order, down, up, mdown, mup, is_start, ct, 0, NULL, &nt,
+                  NULL, NULL) < 0)
+    return -1;
+  for (int64_t p = 0; p < n; ++p) {
+    ss[p] = sector[order[p]];
+    sr[p] = row[order[p]];
+    sp[p] = pad[order[p]];
+    st[p] = time[order[p]];
+  }
+  or_row_ranges(n, ss, sr, rf);
+  or_quantize(n, sr, sp, st, NULL, tq, yq, zq);
+  int64_t m = 0;
+  for (int s = 0; s < OR_NSECT; ++s)
+    for (int r = 1; r < OR_NROWS - 1; ++r) {
+      int64_t a = rf[s * OR_NROWS + r], b = rf[s * OR_NROWS + r + 1];
+      int64_t ja = rf[s * OR_NROWS + r - 1], jb = a, ka = b, kb = rf[s * OR_NROWS + r + 2];
+      for (int64_t i = a; i < b; ++i) {
+        int nj = 0, nkc = 0;
+        int64_t lo = ja, hi = jb; /* rows are time-sorted: binary search, then scan the window */
+        while (lo < hi) {
+          int64_t mid = lo + (hi - lo) / 2;
+          if (tq[mid] < tq[i] - prm->wt_q) lo = mid + 1; else hi = mid;
+        }
+        for (int64_t j = lo; j < jb && tq[j] <= tq[i] + prm->wt_q; ++j)
+          if (llabs((int64_t)yq[j] - yq[i]) <= prm->wy_q) cj[nj++] = (int32_t)j;
+        lo = ka;
+        hi = kb;
+        while (lo < hi) {
+          int64_t mid = lo + (hi - lo) / 2;
+          if (tq[mid] < tq[i] - prm->wt_q) lo = mid + 1; else hi = mid;
+        }
+        for (int64_t k = lo; k < kb && tq[k] <= tq[i] + prm->wt_q; ++k)
+          if (llabs((int64_t)yq[k] - yq[i]) <= prm->wy_q) ck[nkc++] = (int32_t)k;
+        int ncand = 0;
+        for (int x = 0; x < nj; ++x)
+          for (int y = 0; y < nkc; ++y) {
+            int64_t dy = (int64_t)yq[cj[x]] + yq[ck[y]] - 2 * (int64_t)yq[i];
+            int64_t dz = zq[cj[x]] + zq[ck[y]] - 2 * zq[i];
+            if (dy * dy + dz * dz <= prm->cost_max_q) ++ncand;
+          }
+        if (ncand < 2) continue;
+        for (int x = 0; x < nj; ++x)
+          for (int y = 0; y < nkc; ++y) {
+            int64_t dy = (int64_t)yq[cj[x]] + yq[ck[y]] - 2 * (int64_t)yq[i];
+            int64_t dz = zq[cj[x]] + zq[ck[y]] - 2 * zq[i];
+            int64_t c = dy * dy + dz * dz;
+            if (c > prm->cost_max_q) continue;
+            if (m < cap) {
+              int32_t j = cj[x], k = ck[y];
+              or_mlp_features(r, yq[j], yq[i], yq[k], tq[j], tq[i], tq[k], c, nj, nkc, prm->cost_max_q,
+                              feat + m * OR_MLP_IN);
+              label[m] = (uint8_t)(down[i] == j && up[i] == k && mdown[i] == j && mup[i] == k);
+              if (tri) {
+                tri[3 * m] = order[i];
+                tri[3 * m + 1] = order[j];
+                tri[3 * m + 2] = order[k];
+              }
+            }
+            ++m;
+          }
+      }
+    }
+  *count = m;
+  free(order);
+  free(down);
+  free(up);
+  free(mdown);
+  free(mup);
+  free(ct);
+  free(is_start);
+  free(ss);
+  free(sr);
+  free(sp);
+  free(st);
+  free(tq);
+  free(yq);
+  free(zq);
+  free(cj);
+  free(ck);
+  free(rf);
+  return 0;
 }
 
 /* ------------------------------------------------------------- evaluation */

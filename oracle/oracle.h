@@ -56,6 +56,51 @@ int or_fit_chain(int32_t L, int32_t sector, const int32_t *rows, const float *pa
 int or_track(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
              const or_params *prm, int32_t *order, int32_t *down, int32_t *up, int32_t *mdown, int32_t *mup,
              uint8_t *is_start, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks);
+/* ---- learned link classifier (an extension; the paper has no learned part) ---- */
+#define OR_MLP_IN 12
+#define OR_MLP_H 64
+#define OR_MLP_NPARAM (OR_MLP_H * OR_MLP_IN + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H + OR_MLP_H + 1)
+#define OR_MLP_BLOB_FLOATS (2 * OR_MLP_IN + OR_MLP_NPARAM)
+#define OR_PRUNE_BAND 1e-3 /* scores this close to tau may legitimately decide differently */
+
+typedef struct {
+  float mean[OR_MLP_IN], inv_std[OR_MLP_IN];
+  float W1[OR_MLP_H][OR_MLP_IN], b1[OR_MLP_H];
+  float W2[OR_MLP_H][OR_MLP_H], b2[OR_MLP_H];
+  float w3[OR_MLP_H], b3;
+} or_mlp;
+
+float or_bf16(float x);
+float or_feature_log1p(float v);
+void or_mlp_features(int32_t r, int32_t yj, int32_t yi, int32_t yk, int32_t tj, int32_t ti, int32_t tk, int64_t cost,
+                     int32_t nj, int32_t nk, int64_t cost_max, float *f);
+int or_mlp_parse(const void *blob, int64_t bytes, or_mlp *m);
+double or_mlp_logit(const or_mlp *m, const float *f);
+double or_sigmoid(double z);
+int or_mlp_loss_grad(const double *theta, const float *mean, const float *inv_std, int64_t B, const float *feat,
+                     const uint8_t *label, double pos_weight, double *loss, double *grad);
+/* A1 with pruning: as or_neighbours_sorted, but a cluster with >= 2 candidate
+ * pairs of cost <= cost_max keeps the smallest (cost, j, k) among the pairs whose
+ * score sigmoid(logit) >= tau, or its plain choice when none qualifies.  band[i]
+ * (optional) = 1 when some scored pair of i has |score - tau| <= OR_PRUNE_BAND;
+ * stats (optional) = {ambiguous clusters, scored pairs, clusters whose choice
+ * changed, clusters that fell back}. */
+int or_neighbours_pruned(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, const or_mlp *mlp, double tau, int32_t *down, int32_t *up,
+                         int64_t *cost, uint8_t *band, int64_t *stats);
+/* The whole path with pruned A1 (mlp == NULL: plain). */
+int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down, int32_t *up,
+                int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track, int64_t track_cap,
+                or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats);
+/* Training set of the classifier from the plain path: every pair of cost <=
+ * cost_max of every cluster with >= 2 such pairs; label 1 iff the pair is the
+ * plain choice and both of its links are mutual after cleaning.  tri = caller
+ * indices (i, j, k).  Rows are written in sorted-cluster order, pairs in (j, k)
+ * order; *count = number of rows (may exceed cap: rows beyond cap are dropped). */
+int or_training_triplets(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, int64_t cap, float *feat, uint8_t *label, int32_t *tri,
+                         int64_t *count);
 int or_eval(int64_t n, const int32_t *label, const uint16_t *sector, const int32_t *cluster_track, int64_t n_tracks,
             int64_t n_gen_tracks, int32_t min_findable, double match_frac, or_eval_out *out);
 #endif
