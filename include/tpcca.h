@@ -23,6 +23,8 @@
  *                  tracks, numbered in the order of their start cluster;
  *   A5 fit         FP32 Kalman filter along each chain (helix in (x, y), straight
  *                  line in (arc length, zeta = 0.516 cm/bin * time)), 3-point seed.
+ * With TPC_MODE_PRUNED a learned link classifier rescores the ambiguous clusters
+ * of A1 (see the classifier section at the end of this file).
  *
  * Conventions
  *   - Return value 0 on success, a negative TPC_ERR_* code otherwise;
@@ -76,7 +78,8 @@ typedef struct {
   int64_t cost_max_q;    /* largest accepted cost, (1/64 um)^2 (default 384000^2 = (0.6 cm)^2); < 2^40 */
   int32_t n_min;         /* shortest chain kept as a track (default 10, >= 3) */
   int32_t mode;          /* TPC_MODE_PLAIN or TPC_MODE_PRUNED */
-  float tau;             /* pruning threshold on the classifier probability (TPC_MODE_PRUNED) */
+  float tau;             /* pruning threshold on the classifier probability (TPC_MODE_PRUNED); <= 0 keeps
+                            every pair, >= 1 none (every ambiguous cluster keeps its plain choice) */
   int32_t device;        /* CUDA device ordinal */
   int32_t fit_variant;   /* TPC_FIT_THREAD or TPC_FIT_WARP */
   int32_t profile_stages;/* nonzero: record CUDA events between stages (tpc_tf_stage_times) */
@@ -177,6 +180,99 @@ int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int cap);
 
 /* Number of kernel launches (and memset nodes) one call enqueues on its stream. */
 int tpc_tf_launches_per_call(const tpc_tf *tf);
+
+/* ----------------------------------------------------------------------------
+ * Learned link classifier (an extension: the paper has no learned component).
+ *
+ * A small network scores the candidate pairs of the A1 neighbour search before
+ * the choice: for a cluster i with at least two pairs (j, k) of cost <=
+ * cost_max_q, every such pair gets a logit from 12 triplet features ->
+ * 64 ReLU -> 64 ReLU -> 1, and A1 keeps the smallest (cost, j, k) among the pairs
+ * with sigmoid(logit) >= tau; when no pair reaches tau the plain choice stays.
+ * Clusters with fewer than two pairs keep the plain rule.  Steps A2-A5 are
+ * unchanged.  Operands are BF16 (inputs, weights, first hidden layer) with FP32
+ * accumulation.
+ *
+ * Features of a triplet (j in row r-1, i in r, k in r+1), FP32, computed from the
+ * fixed-point coordinates by correctly rounded single-precision operations:
+ *   f0 = y_i - y_j, f1 = y_k - y_i, f2 = zeta_i - zeta_j, f3 = zeta_k - zeta_i (cm),
+ *   f4 = y_j + y_k - 2 y_i, f5 = zeta_j + zeta_k - 2 zeta_i (cm),
+ *   f6 = x_r / 250, f7 = y_i / x_r, f8 = f4 / dx^2 (dx = 160/151 cm),
+ *   f9 = nj / 8, f10 = nk / 8 (candidates of i inside the windows of rows r-1, r+1),
+ *   f11 = ln(1 + 100 cost / cost_max_q).
+ * The network standardises them as (f - mean) * inv_std before rounding to BF16.
+ *
+ * Weight blob (little-endian, tpc_mlp_blob_bytes() = 20340 bytes): uint32 magic
+ * 0x4d435054 ("TPCM"), version 1, 12 (inputs), 64 (hidden units); then float32
+ * mean[12], inv_std[12], W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3
+ * (weights row-major, output unit first).
+ * ------------------------------------------------------------------------- */
+
+/* Size in bytes of a weight blob. */
+size_t tpc_mlp_blob_bytes(void);
+
+/* Load classifier weights (host blob) into the handle; required before a
+ * TPC_MODE_PRUNED call.  Synchronises the device.  Errors: TPC_ERR_ARG (bad
+ * blob), TPC_ERR_CUDA. */
+int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes);
+
+/* Logits of m raw feature rows (device float[m][12], caller order) with the
+ * loaded weights, written to logit[m] (device).  Enqueued on `stream`. */
+int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void *stream);
+
+/* Training set of the classifier from one time frame: runs A0-A2 of the plain
+ * path on `cl` and writes, for every cluster with at least two pairs under the
+ * cost cut, one row per such pair: raw features feat[row][12], label[row] = 1 iff
+ * the pair is the plain A1 choice and both of its links are mutual after A2, and
+ * (optional, may be NULL) tri[row][3] = caller indices (i, j, k).  Row order is
+ * unspecified.  *count (device scalar, set by the call) receives the number of
+ * rows, also when it exceeds cap; rows past cap are not written.  Enqueued on
+ * `stream`.  Errors as for tpc_track_timeframe (the device-side ones surface
+ * through tpc_tf_status). */
+int tpc_mlp_extract(tpc_tf *tf, const tpc_clusters *cl, float *feat, uint8_t *label, int32_t *tri, uint32_t cap,
+                    uint32_t *count, void *stream);
+
+/* Number of clusters the classifier rescored in the last TPC_MODE_PRUNED call
+ * (synchronises `stream`). */
+int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n, void *stream);
+
+typedef struct tpc_mlp_trainer tpc_mlp_trainer; /* opaque: FP32 master weights, Adam moments, BF16 copy */
+
+typedef struct {
+  float lr;          /* Adam step size (default 1e-3) */
+  float beta1;       /* default 0.9 */
+  float beta2;       /* default 0.999 */
+  float eps;         /* default 1e-8 */
+  float pos_weight;  /* weight of label-1 rows in the loss (default 1) */
+  uint32_t max_batch;/* largest batch of a step (default 8192) */
+  int32_t device;    /* CUDA device ordinal */
+} tpc_mlp_train_config;
+
+void tpc_mlp_default_train_config(tpc_mlp_train_config *cfg);
+
+/* Create a trainer whose parameters start from the host blob `init`.  Errors:
+ * TPC_ERR_ARG (bad settings or blob), TPC_ERR_CUDA. */
+int tpc_mlp_trainer_create(const tpc_mlp_train_config *cfg, const void *init, size_t bytes, tpc_mlp_trainer **out);
+void tpc_mlp_trainer_destroy(tpc_mlp_trainer *tr);
+
+/* Set the standardisation from m raw feature rows (device float[m][12]):
+ * mean and 1/std of each feature (1 for a constant feature).  Enqueued. */
+int tpc_mlp_trainer_normalise(tpc_mlp_trainer *tr, const float *feat, uint32_t m, void *stream);
+
+/* One Adam step on a batch: rows index[0..batch) of (feat, label) (device
+ * arrays; index may be NULL for rows 0..batch-1; every index must address a row
+ * of the caller's arrays).  loss (optional device float) receives the batch's
+ * mean weighted cross-entropy before the step.  Enqueued on `stream`. */
+int tpc_mlp_train_step(tpc_mlp_trainer *tr, const float *feat, const uint8_t *label, const int32_t *index,
+                       uint32_t batch, float *loss, void *stream);
+
+/* The batch gradient d loss / d theta (device float[5057], blob order W1, b1,
+ * W2, b2, w3, b3) and loss, without a step.  Enqueued on `stream`. */
+int tpc_mlp_trainer_gradient(tpc_mlp_trainer *tr, const float *feat, const uint8_t *label, const int32_t *index,
+                             uint32_t batch, float *grad, float *loss, void *stream);
+
+/* Write the current weights as a blob into host memory (synchronises). */
+int tpc_mlp_trainer_blob(tpc_mlp_trainer *tr, void *blob, size_t bytes);
 
 #ifdef __cplusplus
 }

@@ -8,12 +8,14 @@
 // per-call clearing is one memset of the counters and look-back words.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
 
 #include "../../include/tpcca.h"
+#include "mlp_dev.cuh"
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -80,6 +82,12 @@ struct tpc_tf {
   uint32_t last_n = 0;
   bool last_sorted = true;
   Args last_args;
+  // learned link classifier (TPC_MODE_PRUNED)
+  int4 *amb = nullptr;        // clusters listed for rescoring (arena, pruned mode only)
+  MlpW *mlp = nullptr;        // packed weights (allocated by tpc_mlp_load)
+  float *mlp_stage = nullptr; // FP32 blob body staged for packing
+  bool mlp_ready = false;
+  float logit_tau = 0.f;
 };
 
 extern "C" void tpc_default_config(tpc_tf_config *c) {
@@ -106,6 +114,7 @@ int tpc::report(int code, const char *msg) {
 static void free_all(tpc_tf *tf) {
   if (!tf) return;
   if (tf->arena) cudaFree(tf->arena);
+  if (tf->mlp) cudaFree(tf->mlp);
   if (tf->pinned) cudaFreeHost(tf->pinned);
   for (int i = 0; i <= kMaxStages; ++i)
     if (tf->ev_ready) cudaEventDestroy(tf->ev[i]);
@@ -124,7 +133,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     return fail(TPC_ERR_ARG, "tpc_tf_create: search window or cost cut out of range");
   if (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_PRUNED)
     return fail(TPC_ERR_ARG, "tpc_tf_create: unknown mode");
-  if (cfg->mode == TPC_MODE_PRUNED) return fail(TPC_ERR_ARG, "tpc_tf_create: TPC_MODE_PRUNED needs the link classifier");
+  if (cfg->mode == TPC_MODE_PRUNED && !(cfg->tau == cfg->tau)) return fail(TPC_ERR_ARG, "tpc_tf_create: tau is NaN");
   if (cfg->fit_variant != TPC_FIT_THREAD && cfg->fit_variant != TPC_FIT_WARP)
     return fail(TPC_ERR_ARG, "tpc_tf_create: unknown fit_variant");
   tpc_tf *tf = new tpc_tf();
@@ -184,6 +193,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
       {(void **)&tf->h_rl, (size_t)tf->track_list_cap * 2},
       {(void **)&tf->h_status, (size_t)tf->track_list_cap},
       {(void **)&tf->h_ntracks, 16},
+      {(void **)&tf->amb, cfg->mode == TPC_MODE_PRUNED ? (N + 4) * 16 : 0},
   };
   size_t total = 0;
   for (auto &p : parts) total += align_up(p.bytes, 256);
@@ -195,7 +205,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   tf->arena_bytes = total;
   size_t off = 0;
   for (auto &p : parts) {
-    *p.p = tf->arena + off;
+    *p.p = p.bytes ? tf->arena + off : nullptr;
     off += align_up(p.bytes, 256);
   }
   tf->sort_scratch_bytes = sort_scratch_bytes(tf->N);
@@ -206,6 +216,9 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   }
   for (int i = 0; i <= kMaxStages; ++i) cudaEventCreate(&tf->ev[i]);
   tf->ev_ready = true;
+  // sigmoid(logit) >= tau  <=>  logit >= ln(tau / (1 - tau))
+  const double tau = cfg->tau;
+  tf->logit_tau = tau <= 0.0 ? -INFINITY : tau >= 1.0 ? INFINITY : (float)std::log(tau / (1.0 - tau));
   *out = tf;
   return TPC_OK;
 }
@@ -234,27 +247,19 @@ static void stage(tpc_tf *tf, cudaStream_t st, const char *name) {
   tf->n_ev++;
 }
 
-extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
-  g_err.clear();
-  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null argument");
+static int check_clusters(tpc_tf *tf, const tpc_clusters *cl, const char *who) {
   const uint32_t n = cl->n;
   if (n > tf->N) return fail(TPC_ERR_CAPACITY, "more clusters than max_clusters");
   if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time))
-    return fail(TPC_ERR_ARG, "tpc_track_timeframe: null cluster array");
-  if (n > 0 && !out->cluster_track) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null cluster_track");
-  if (!out->n_tracks) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null n_tracks");
-  if (out->track_capacity > 0 &&
-      (!out->params || !out->cov || !out->t_ref || !out->x || !out->chi2 || !out->ndf || !out->nhits ||
-       !out->first_cluster || !out->sector || !out->row_first || !out->row_last || !out->status))
-    return fail(TPC_ERR_ARG, "tpc_track_timeframe: null track array");
-  if (((uintptr_t)out->cluster_track & 3) || ((uintptr_t)cl->pad & 3) || ((uintptr_t)cl->time & 3) ||
-      ((uintptr_t)cl->sector & 1) || ((uintptr_t)cl->row & 1))
-    return fail(TPC_ERR_ARG, "tpc_track_timeframe: misaligned array");
-  TPC_CK(cudaSetDevice(tf->device));
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool sorted = (cl->flags & TPC_INPUT_SORTED) != 0;
+    return fail(TPC_ERR_ARG, std::string(who) + ": null cluster array");
+  if (((uintptr_t)cl->pad & 3) || ((uintptr_t)cl->time & 3) || ((uintptr_t)cl->sector & 1) ||
+      ((uintptr_t)cl->row & 1))
+    return fail(TPC_ERR_ARG, std::string(who) + ": misaligned array");
+  return TPC_OK;
+}
 
-  Args a;
+// Arguments of one call (outputs may be absent for the linking-only uses).
+static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   std::memset(&a, 0, sizeof(a));
   a.n = n;
   a.row_begin = tf->row_begin;
@@ -268,7 +273,7 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   a.trk_len = tf->trk_len;
   a.chain = tf->chain;
   a.ctr = tf->reset;
-  const size_t tiles_l = link_tiles(n), tiles_k = walk_tiles(n);
+  const size_t tiles_l = link_tiles(n);
   a.lb_links = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(tf->reset) + kNCounters * 4);
   a.lb_keep = a.lb_links + tiles_l;
   a.starts_cap = n / 2 + 1;
@@ -277,26 +282,35 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   a.wt = tf->cfg.wt_q;
   a.cost_max = tf->cfg.cost_max_q;
   a.n_min = tf->cfg.n_min;
-  a.cluster_track = out->cluster_track;
-  a.track_capacity = out->track_capacity;
-  a.params = out->params;
-  a.cov = out->cov;
-  a.t_ref = out->t_ref;
-  a.x = out->x;
-  a.chi2 = out->chi2;
-  a.ndf = out->ndf;
-  a.nhits = out->nhits;
-  a.first_cluster = out->first_cluster;
-  a.o_sector = out->sector;
-  a.o_row_first = out->row_first;
-  a.o_row_last = out->row_last;
-  a.o_status = out->status;
-  a.n_tracks_out = out->n_tracks;
+  a.amb = tf->amb;
+  a.amb_cap = tf->amb ? tf->N + 4 : 0;
+  if (out) {
+    a.cluster_track = out->cluster_track;
+    a.track_capacity = out->track_capacity;
+    a.params = out->params;
+    a.cov = out->cov;
+    a.t_ref = out->t_ref;
+    a.x = out->x;
+    a.chi2 = out->chi2;
+    a.ndf = out->ndf;
+    a.nhits = out->nhits;
+    a.first_cluster = out->first_cluster;
+    a.o_sector = out->sector;
+    a.o_row_first = out->row_first;
+    a.o_row_last = out->row_last;
+    a.o_status = out->status;
+    a.n_tracks_out = out->n_tracks;
+  }
+}
 
+// A0-A2 (with the classifier's rescoring when prune is set) on stream st.
+static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStream_t st, bool prune) {
+  const uint32_t n = cl->n;
+  const bool sorted = (cl->flags & TPC_INPUT_SORTED) != 0;
   tf->n_ev = 0;
   tf->launches = 0;
   if (tf->cfg.profile_stages) cudaEventRecord(tf->ev[0], st);
-  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 8 * (tiles_l + tiles_k), st));
+  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 8 * (link_tiles(n) + walk_tiles(n)), st));
   ++tf->launches;
   if (sorted) {
     a.sector = cl->sector;
@@ -319,20 +333,55 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   launch_row_index(a, st);
   launch_tile_windows(a, st);
   stage(tf, st, "ingest");
-  launch_neighbours(a, tf->nb_cap, st);
+  launch_neighbours(a, tf->nb_cap, st, prune);
   stage(tf, st, "neighbours");
+  tf->launches += 3;
+  if (prune) {
+    launch_prune(a, tf->mlp, tf->logit_tau, tf->sms, st);
+    stage(tf, st, "prune");
+    ++tf->launches;
+  }
   launch_edge_claims(a, st);
   stage(tf, st, "edge_claims");
+  ++tf->launches;
+  tf->last_n = n;
+  tf->last_sorted = sorted;
+  return TPC_OK;
+}
+
+extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null argument");
+  const uint32_t n = cl->n;
+  {
+    const int rc = check_clusters(tf, cl, "tpc_track_timeframe");
+    if (rc != TPC_OK) return rc;
+  }
+  const bool prune = tf->cfg.mode == TPC_MODE_PRUNED;
+  if (prune && !tf->mlp_ready) return fail(TPC_ERR_ARG, "TPC_MODE_PRUNED: load the classifier weights first");
+  if (n > 0 && !out->cluster_track) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null cluster_track");
+  if (!out->n_tracks) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null n_tracks");
+  if (out->track_capacity > 0 &&
+      (!out->params || !out->cov || !out->t_ref || !out->x || !out->chi2 || !out->ndf || !out->nhits ||
+       !out->first_cluster || !out->sector || !out->row_first || !out->row_last || !out->status))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe: null track array");
+  if ((uintptr_t)out->cluster_track & 3) return fail(TPC_ERR_ARG, "tpc_track_timeframe: misaligned array");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Args a;
+  fill_args(tf, n, out, a);
+  {
+    const int rc = enqueue_linking(tf, cl, a, st, prune);
+    if (rc != TPC_OK) return rc;
+  }
   launch_links(a, tf->sms, st);
   stage(tf, st, "links");
   launch_walk(a, tf->sms, st);
   stage(tf, st, "walk");
   launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
   stage(tf, st, "fit");
-  tf->launches += 7;  // index, tile windows, neighbours, edge claims, links, keep, fit
+  tf->launches += 3;  // links, walk, fit
   TPC_CK(cudaGetLastError());
-  tf->last_n = n;
-  tf->last_sorted = sorted;
   tf->last_args = a;
   if (out->n_tracks_host) {
     TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + kCtrTracks, 4, cudaMemcpyDeviceToHost, st));
@@ -454,3 +503,78 @@ extern "C" int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int
 }
 
 extern "C" int tpc_tf_launches_per_call(const tpc_tf *tf) { return tf ? tf->launches : 0; }
+
+// ================================================================ classifier
+extern "C" size_t tpc_mlp_blob_bytes(void);
+
+extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
+  g_err.clear();
+  if (!tf || !blob) return fail(TPC_ERR_ARG, "tpc_mlp_load: null argument");
+  const size_t need = tpc_mlp_blob_bytes();
+  if (bytes < need) return fail(TPC_ERR_ARG, "tpc_mlp_load: blob too short");
+  uint32_t hdr[4];
+  std::memcpy(hdr, blob, 16);
+  if (hdr[0] != 0x4d435054u || hdr[1] != 1u || hdr[2] != 12u || hdr[3] != 64u)
+    return fail(TPC_ERR_ARG, "tpc_mlp_load: bad header (magic, version 1, 12 inputs, 64 hidden units)");
+  TPC_CK(cudaSetDevice(tf->device));
+  if (!tf->mlp) {
+    TPC_CK(cudaMalloc(&tf->mlp, mlp_weights_bytes() + need + 256));
+    tf->mlp_stage = reinterpret_cast<float *>(reinterpret_cast<char *>(tf->mlp) + (mlp_weights_bytes() + 255) / 256 * 256);
+    TPC_CK(cudaMemset(tf->mlp, 0, mlp_weights_bytes()));
+  }
+  TPC_CK(cudaMemcpy(tf->mlp_stage, static_cast<const char *>(blob) + 16, need - 16, cudaMemcpyHostToDevice));
+  const float *body = tf->mlp_stage;
+  launch_mlp_pack(body + 24, body, body + 12, tf->mlp, 0);
+  TPC_CK(cudaGetLastError());
+  TPC_CK(cudaDeviceSynchronize());
+  tf->mlp_ready = true;
+  return TPC_OK;
+}
+
+extern "C" int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void *stream) {
+  g_err.clear();
+  if (!tf || (m > 0 && (!feat || !logit))) return fail(TPC_ERR_ARG, "tpc_mlp_score: null argument");
+  if (!tf->mlp_ready) return fail(TPC_ERR_ARG, "tpc_mlp_score: load the classifier weights first");
+  if (((uintptr_t)feat & 3) || ((uintptr_t)logit & 3)) return fail(TPC_ERR_ARG, "tpc_mlp_score: misaligned array");
+  TPC_CK(cudaSetDevice(tf->device));
+  launch_mlp_score(tf->mlp, feat, m, logit, tf->sms, (cudaStream_t)stream);
+  TPC_CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+extern "C" int tpc_mlp_extract(tpc_tf *tf, const tpc_clusters *cl, float *feat, uint8_t *label, int32_t *tri,
+                               uint32_t cap, uint32_t *count, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !count) return fail(TPC_ERR_ARG, "tpc_mlp_extract: null argument");
+  if (cap > 0 && (!feat || !label)) return fail(TPC_ERR_ARG, "tpc_mlp_extract: null output array");
+  if (((uintptr_t)feat & 3) || ((uintptr_t)tri & 3) || ((uintptr_t)count & 3))
+    return fail(TPC_ERR_ARG, "tpc_mlp_extract: misaligned array");
+  {
+    const int rc = check_clusters(tf, cl, "tpc_mlp_extract");
+    if (rc != TPC_OK) return rc;
+  }
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Args a;
+  fill_args(tf, cl->n, nullptr, a);
+  {
+    const int rc = enqueue_linking(tf, cl, a, st, false);
+    if (rc != TPC_OK) return rc;
+  }
+  TPC_CK(cudaMemsetAsync(count, 0, 4, st));
+  launch_mlp_extract(a, feat, label, tri, cap, count, st);
+  TPC_CK(cudaGetLastError());
+  tf->last_args = a;
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n, void *stream) {
+  g_err.clear();
+  if (!tf || !n) return fail(TPC_ERR_ARG, "tpc_tf_pruned_clusters: null argument");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  TPC_CK(cudaMemcpyAsync(tf->pinned + 2, tf->reset + kCtrAmb, 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaStreamSynchronize(st));
+  *n = tf->pinned[2];
+  return TPC_OK;
+}

@@ -39,6 +39,23 @@ __device__ __forceinline__ int gm_lower_bound(const float *time, int lo, int hi,
 __device__ __forceinline__ float sane_pad(float p) { return pad_ok(p) ? p : 0.0f; }
 __device__ __forceinline__ float sane_time(float t) { return time_ok(t) ? t : 0.0f; }
 
+// quantised (t, y) of a cluster of row r: y_q = (rint(64 pad) - half) * pitch
+__device__ __forceinline__ int2 quant_ty(float pad, float time, int half, int pitch) {
+  return make_int2(q64(time), (q64(pad) - half) * pitch);
+}
+
+// Pruned mode: append a cluster with >= 2 pairs under the cost cut to the list
+// the classifier rescores.  The lanes that append together share one atomic.
+__device__ __forceinline__ void amb_push(const Args &a, int4 e) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&a.ctr[kCtrAmb], (uint32_t)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+  if (slot < a.amb_cap) a.amb[slot] = e; else raise(a.ctr, kErrInternal);
+}
+
 // first e in [0, n) with t(e) >= x, searched outwards from `guess` (galloping)
 template <class T>
 __device__ __forceinline__ int gallop_lower_bound(T t, int n, int x, int guess) {
@@ -74,9 +91,10 @@ __device__ __forceinline__ int gallop_lower_bound(T t, int n, int x, int guess) 
 // return quantised (t, y) of the tile's clusters and of the windows of rows r-1
 // (np entries) and r+1 (nn entries).  Links are written as sorted positions
 // (window base + window-local index).
-template <class CT, class PT, class NT_>
-__device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, int np, NT_ N, int nn, int wy,
-                                         int wt, int64_t cost_max, int2 *out, int base_p, int base_n) {
+template <bool kPrune, class CT, class PT, class NT_>
+__device__ __forceinline__ void link_run(const Args &a, int li0, int li1, int cnt, CT C, PT P, int np, NT_ N, int nn,
+                                         int wy, int wt, int64_t cost_max, int2 *out, int base_p, int base_n,
+                                         int base_c) {
   if (li0 >= li1) return;
   auto tp = [&](int j) { return P(j).x; };
   auto tn = [&](int k) { return N(k).x; };
@@ -113,7 +131,7 @@ __device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, 
       }
     }
     int64_t best = INT64_MAX;
-    int bj = -1, bk = -1;
+    int bj = -1, bk = -1, nc = 0;
     if (nj <= kMaxCand && nk <= kMaxCand) {
       const int cj[4] = {cj0, cj1, cj2, cj3}, ck[4] = {ck0, ck1, ck2, ck3};
 #pragma unroll
@@ -126,6 +144,7 @@ __device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, 
           if (z >= nk) break;
           const int2 ek = N(ck[z]);
           const int64_t c = triplet_cost(dyj, ek.y - yi, dtj, ek.x - ti);
+          if (kPrune) nc += (c <= cost_max);
           if (c < best) {
             best = c;
             bj = cj[x];
@@ -147,6 +166,7 @@ __device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, 
           const int32_t dyk = ek.y - yi;
           if (abs(dyk) > wy) continue;
           const int64_t c = triplet_cost(dyj, dyk, dtj, dtk);
+          if (kPrune) nc += (c <= cost_max);
           if (c < best) {
             best = c;
             bj = j;
@@ -156,6 +176,7 @@ __device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, 
       }
     }
     out[li] = (bj >= 0 && best <= cost_max) ? make_int2(base_p + bj, base_n + bk) : make_int2(-1, -1);
+    if (kPrune && nc >= 2) amb_push(a, make_int4(base_c + li, base_p + jlo, base_n + klo, nc));
   }
 }
 
@@ -164,10 +185,11 @@ __device__ __forceinline__ void link_run(int li0, int li1, int cnt, CT C, PT P, 
 // key (min(cost, cost_max + 1) << 22 | j << 11 | k): the smallest key is the
 // lexicographic minimum of (cost, j, k), so the scan order does not matter and
 // costs above cost_max (which never link) cannot overflow the key.
-__device__ __forceinline__ void link_run_smem(int li0, int li1, int cnt, const int2 *__restrict__ sc,
+template <bool kPrune>
+__device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, int cnt, const int2 *__restrict__ sc,
                                               const int2 *__restrict__ sp, int np, const int2 *__restrict__ sn,
                                               int nn, int wy, int wt, int64_t cost_max, int2 *out, int base_p,
-                                              int base_n) {
+                                              int base_n, int base_c) {
   if (li0 >= li1) return;
   const uint64_t capc = (uint64_t)cost_max + 1;
   const float frac = (float)li0 / (float)cnt;
@@ -194,6 +216,7 @@ __device__ __forceinline__ void link_run_smem(int li0, int li1, int cnt, const i
       ++nj;
     }
     uint64_t best = ~0ull;
+    int nc = 0;  // pairs under the cost cut (pruned mode only)
     if (nj > 0 && nj <= kMaxCand) {
       const int cj[4] = {cj0, cj1, cj2, cj3};
       const int2 ej[4] = {ej0, ej1, ej2, ej3};
@@ -206,6 +229,7 @@ __device__ __forceinline__ void link_run_smem(int li0, int li1, int cnt, const i
         for (int x = 0; x < kMaxCand; ++x) {
           if (x >= nj) break;
           const uint64_t c = (uint64_t)triplet_cost(ej[x].y - yi, dyk, ej[x].x - ti, e.x - ti);
+          if (kPrune) nc += (c < capc);
           best = min(best, (min(c, capc) << 22) | ((uint64_t)cj[x] << 11) | (uint64_t)k);
         }
       }
@@ -221,6 +245,7 @@ __device__ __forceinline__ void link_run_smem(int li0, int li1, int cnt, const i
           const int32_t dyk = ek.y - yi;
           if (abs(dyk) > wy) continue;
           const uint64_t c = (uint64_t)triplet_cost(dyj, dyk, ej.x - ti, ek.x - ti);
+          if (kPrune) nc += (c < capc);
           best = min(best, (min(c, capc) << 22) | ((uint64_t)j << 11) | (uint64_t)k);
         }
       }
@@ -228,13 +253,11 @@ __device__ __forceinline__ void link_run_smem(int li0, int li1, int cnt, const i
     out[li] = (best != ~0ull && (best >> 22) <= (uint64_t)cost_max)
                   ? make_int2(base_p + (int)((best >> 11) & 2047), base_n + (int)(best & 2047))
                   : make_int2(-1, -1);
+    if (kPrune && nc >= 2) amb_push(a, make_int4(base_c + li, base_p + jlo, base_n + klo, nc));
   }
 }
 
-// quantised (t, y) of a cluster of row r: y_q = (rint(64 pad) - half) * pitch
-__device__ __forceinline__ int2 quant_ty(float pad, float time, int half, int pitch) {
-  return make_int2(q64(time), (q64(pad) - half) * pitch);
-}
+
 
 }  // namespace
 
@@ -271,6 +294,7 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 }
 
 // ------------------------------------------------------------ neighbours
+template <bool kPrune>
 __global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) {
   __shared__ int2 s_c[kNbTile], s_p[kNbWin], s_n[kNbWin];  // quantised (t, y)
   const uint32_t t = blockIdx.x;
@@ -342,13 +366,13 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) 
   const int K = (cnt + NT - 1) / NT, li0 = tid * K, li1 = min(cnt, li0 + K);
   auto C = [&](int i) { return s_c[i]; };
   if (staged) {
-    link_run_smem(li0, li1, cnt, s_c, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z);
+    link_run_smem<kPrune>(a, li0, li1, cnt, s_c, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta);
   } else {
     const float *pp = a.pad + w.x, *tpg = a.time + w.x, *pn = a.pad + w.z, *tng = a.time + w.z;
-    link_run(
-        li0, li1, cnt, C, [&](int j) { return quant_ty(sane_pad(pp[j]), sane_time(tpg[j]), half_p, pitch_p); }, np,
-        [&](int k) { return quant_ty(sane_pad(pn[k]), sane_time(tng[k]), half_n, pitch_n); }, nn, a.wy, a.wt,
-        a.cost_max, a.link + ta, w.x, w.z);
+    link_run<kPrune>(
+        a, li0, li1, cnt, C, [&](int j) { return quant_ty(sane_pad(pp[j]), sane_time(tpg[j]), half_p, pitch_p); },
+        np, [&](int k) { return quant_ty(sane_pad(pn[k]), sane_time(tng[k]), half_n, pitch_n); }, nn, a.wy, a.wt,
+        a.cost_max, a.link + ta, w.x, w.z, ta);
   }
   if (bad) raise(a.ctr, kErrInput);
 }
@@ -399,8 +423,9 @@ void launch_tile_windows(const Args &a, cudaStream_t st) {
   k_tile_windows<<<(tiles + 255) / 256, 256, 0, st>>>(a);
 }
 
-void launch_neighbours(const Args &a, int win_cap, cudaStream_t st) {
-  k_neighbours<<<neighbour_tiles_max(a.n), kNbThreads, 0, st>>>(a, win_cap);
+void launch_neighbours(const Args &a, int win_cap, cudaStream_t st, bool prune) {
+  if (prune) k_neighbours<true><<<neighbour_tiles_max(a.n), kNbThreads, 0, st>>>(a, win_cap);
+  else k_neighbours<false><<<neighbour_tiles_max(a.n), kNbThreads, 0, st>>>(a, win_cap);
 }
 
 void launch_edge_claims(const Args &a, cudaStream_t st) { k_edge_claims<<<dim3(32, 2 * kNSect), 256, 0, st>>>(a); }

@@ -71,6 +71,7 @@ enum : int {
   kCtrFitNext = 7,
   kCtrSortDone = 8,
   kCtrTiles = 9,    // neighbour tiles of this frame
+  kCtrAmb = 10,     // clusters with >= 2 candidate pairs under the cost cut (pruned mode)
   kNCounters = 16
 };
 
@@ -115,6 +116,9 @@ struct Args {
   uint16_t *o_sector, *o_row_first, *o_row_last;
   uint8_t *o_status;
   uint32_t *n_tracks_out;
+  // pruned mode: clusters whose pairs the link classifier scores
+  int4 *amb;               // (sorted position, first j of the window, first k of the window, pairs under the cut)
+  uint32_t amb_cap;
 };
 
 __device__ __forceinline__ int32_t caller_index(const Args &a, int32_t i) { return a.perm ? a.perm[i] : i; }

@@ -24,7 +24,8 @@ inline uint32_t neighbour_tiles_max(uint32_t n) { return n / kNbTile + kNKeys + 
 
 void launch_row_index(const Args &a, cudaStream_t st);
 void launch_tile_windows(const Args &a, cudaStream_t st);
-void launch_neighbours(const Args &a, int win_cap, cudaStream_t st);
+// prune = true also lists the clusters with >= 2 pairs under the cost cut in a.amb
+void launch_neighbours(const Args &a, int win_cap, cudaStream_t st, bool prune = false);
 void launch_edge_claims(const Args &a, cudaStream_t st);
 void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);
@@ -35,6 +36,16 @@ int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, cons
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,
                 size_t scratch_bytes, int sms, cudaStream_t st);
 size_t sort_scratch_bytes(uint32_t max_n);
+// link classifier (k_mlp.cu)
+struct MlpW;
+size_t mlp_weights_bytes();
+// rescoring of the listed clusters' pairs; rewrites their links
+void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
+// FP32 parameters (blob order) + standardisation -> packed BF16 weights
+void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);
+void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit, int sms, cudaStream_t st);
+void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,
+                        cudaStream_t st);
 // sets the message returned by tpc_last_error() (cleared for TPC_OK); returns code
 int report(int code, const char *msg);
 // order[] of the last call (inspection)

@@ -47,6 +47,11 @@ class tpc_tracks(ctypes.Structure):
                 ("status", c_vp), ("n_tracks", c_vp), ("n_tracks_host", c_vp)]
 
 
+class tpc_mlp_train_config(ctypes.Structure):
+    _fields_ = [("lr", c_f32), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32), ("pos_weight", c_f32),
+                ("max_batch", c_u32), ("device", c_i32)]
+
+
 _lib = None
 
 
@@ -88,6 +93,31 @@ def load():
     lib.tpc_tf_stage_times.restype = ctypes.c_int
     lib.tpc_tf_launches_per_call.argtypes = [c_vp]
     lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    sz = ctypes.c_size_t
+    lib.tpc_mlp_blob_bytes.argtypes = []
+    lib.tpc_mlp_blob_bytes.restype = sz
+    lib.tpc_mlp_load.argtypes = [c_vp, c_vp, sz]
+    lib.tpc_mlp_load.restype = ctypes.c_int
+    lib.tpc_mlp_score.argtypes = [c_vp, c_vp, c_u32, c_vp, c_vp]
+    lib.tpc_mlp_score.restype = ctypes.c_int
+    lib.tpc_mlp_extract.argtypes = [c_vp, P(tpc_clusters), c_vp, c_vp, c_vp, c_u32, c_vp, c_vp]
+    lib.tpc_mlp_extract.restype = ctypes.c_int
+    lib.tpc_tf_pruned_clusters.argtypes = [c_vp, P(c_u32), c_vp]
+    lib.tpc_tf_pruned_clusters.restype = ctypes.c_int
+    lib.tpc_mlp_default_train_config.argtypes = [P(tpc_mlp_train_config)]
+    lib.tpc_mlp_default_train_config.restype = None
+    lib.tpc_mlp_trainer_create.argtypes = [P(tpc_mlp_train_config), c_vp, sz, P(c_vp)]
+    lib.tpc_mlp_trainer_create.restype = ctypes.c_int
+    lib.tpc_mlp_trainer_destroy.argtypes = [c_vp]
+    lib.tpc_mlp_trainer_destroy.restype = None
+    lib.tpc_mlp_trainer_normalise.argtypes = [c_vp, c_vp, c_u32, c_vp]
+    lib.tpc_mlp_trainer_normalise.restype = ctypes.c_int
+    lib.tpc_mlp_train_step.argtypes = [c_vp, c_vp, c_vp, c_vp, c_u32, c_vp, c_vp]
+    lib.tpc_mlp_train_step.restype = ctypes.c_int
+    lib.tpc_mlp_trainer_gradient.argtypes = [c_vp, c_vp, c_vp, c_vp, c_u32, c_vp, c_vp, c_vp]
+    lib.tpc_mlp_trainer_gradient.restype = ctypes.c_int
+    lib.tpc_mlp_trainer_blob.argtypes = [c_vp, c_vp, sz]
+    lib.tpc_mlp_trainer_blob.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -159,6 +189,142 @@ def tpc_tf_stage_times(handle, cap: int = 16):
 
 def tpc_tf_launches_per_call(handle) -> int:
     return load().tpc_tf_launches_per_call(handle)
+
+
+def tpc_mlp_blob_bytes() -> int:
+    return int(load().tpc_mlp_blob_bytes())
+
+
+def tpc_mlp_load(handle, blob: bytes) -> int:
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    return load().tpc_mlp_load(handle, ctypes.cast(buf, c_vp), len(blob))
+
+
+def tpc_mlp_score(handle, feat_ptr, m, logit_ptr, stream=0) -> int:
+    return load().tpc_mlp_score(handle, feat_ptr, m, logit_ptr, stream)
+
+
+def tpc_mlp_extract(handle, clusters, feat_ptr, label_ptr, tri_ptr, cap, count_ptr, stream=0) -> int:
+    return load().tpc_mlp_extract(handle, ctypes.byref(clusters), feat_ptr, label_ptr, tri_ptr, cap, count_ptr,
+                                  stream)
+
+
+def tpc_tf_pruned_clusters(handle, stream=0) -> int:
+    n = c_u32(0)
+    _check(load().tpc_tf_pruned_clusters(handle, ctypes.byref(n), stream))
+    return int(n.value)
+
+
+def tpc_mlp_default_train_config() -> tpc_mlp_train_config:
+    c = tpc_mlp_train_config()
+    load().tpc_mlp_default_train_config(ctypes.byref(c))
+    return c
+
+
+# ------------------------------------------------------------ classifier weights
+MLP_IN, MLP_H = 12, 64
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+MLP_PARAM_SHAPES = [("W1", (MLP_H, MLP_IN)), ("b1", (MLP_H,)), ("W2", (MLP_H, MLP_H)), ("b2", (MLP_H,)),
+                    ("w3", (MLP_H,)), ("b3", (1,))]
+_BLOB_MAGIC = 0x4D435054  # "TPCM"
+
+
+def pack_blob(mean, inv_std, theta) -> bytes:
+    """Weight blob of the C ABI: header (magic, version 1, 12, 64) + float32 mean,
+    inv_std, then theta = W1, b1, W2, b2, w3, b3 flattened in that order."""
+    import numpy as np
+    hdr = np.array([_BLOB_MAGIC, 1, MLP_IN, MLP_H], "<u4")
+    body = np.concatenate([np.asarray(mean, "<f4").ravel(), np.asarray(inv_std, "<f4").ravel(),
+                           np.asarray(theta, "<f4").ravel()])
+    if body.size != 2 * MLP_IN + MLP_NPARAM:
+        raise ValueError("classifier blob: wrong number of parameters")
+    return hdr.tobytes() + body.tobytes()
+
+
+def unpack_blob(blob: bytes):
+    """(mean, inv_std, theta) of a weight blob."""
+    import numpy as np
+    hdr = np.frombuffer(blob[:16], "<u4")
+    if hdr[0] != _BLOB_MAGIC or hdr[1] != 1 or hdr[2] != MLP_IN or hdr[3] != MLP_H:
+        raise ValueError("classifier blob: bad header")
+    body = np.frombuffer(blob[16:16 + 4 * (2 * MLP_IN + MLP_NPARAM)], "<f4")
+    return body[:MLP_IN].copy(), body[MLP_IN:2 * MLP_IN].copy(), body[2 * MLP_IN:].copy()
+
+
+def init_blob(seed: int = 0) -> bytes:
+    """He-initialised weights (zero biases, identity standardisation)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in MLP_PARAM_SHAPES:
+        if name.startswith("W"):
+            parts.append(rng.standard_normal(shape) * np.sqrt(2.0 / shape[1]))
+        elif name == "w3":
+            parts.append(rng.standard_normal(shape) * np.sqrt(1.0 / MLP_H))
+        else:
+            parts.append(np.zeros(shape))
+    theta = np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+    return pack_blob(np.zeros(MLP_IN), np.ones(MLP_IN), theta)
+
+
+class Trainer:
+    """Owns one tpc_mlp_trainer (FP32 master weights, Adam moments, BF16 copy);
+    batches are torch CUDA tensors."""
+
+    def __init__(self, blob: bytes, device: int = 0, **overrides):
+        import torch
+        self.torch = torch
+        cfg = tpc_mlp_default_train_config()
+        cfg.device = int(device)
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.device = torch.device("cuda", device)
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        h = c_vp()
+        _check(load().tpc_mlp_trainer_create(ctypes.byref(cfg), ctypes.cast(buf, c_vp), len(blob), ctypes.byref(h)))
+        self.handle = h.value
+        self._loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self._grad = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=self.device)
+
+    def close(self):
+        if self.handle:
+            load().tpc_mlp_trainer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def normalise(self, feat):
+        _check(load().tpc_mlp_trainer_normalise(self.handle, feat.data_ptr(), int(feat.shape[0]), self._stream()))
+
+    def step(self, feat, label, index=None, batch=None):
+        """One Adam step; returns the device loss tensor (mean weighted BCE before the step)."""
+        b = int(batch if batch is not None else (index.numel() if index is not None else feat.shape[0]))
+        _check(load().tpc_mlp_train_step(self.handle, feat.data_ptr(), label.data_ptr(),
+                                         index.data_ptr() if index is not None else None, b,
+                                         self._loss.data_ptr(), self._stream()))
+        return self._loss
+
+    def gradient(self, feat, label, index=None):
+        b = int(index.numel() if index is not None else feat.shape[0])
+        _check(load().tpc_mlp_trainer_gradient(self.handle, feat.data_ptr(), label.data_ptr(),
+                                               index.data_ptr() if index is not None else None, b,
+                                               self._grad.data_ptr(), self._loss.data_ptr(), self._stream()))
+        self.torch.cuda.synchronize(self.device)
+        return self._grad.clone(), float(self._loss.item())
+
+    def blob(self) -> bytes:
+        n = tpc_mlp_blob_bytes()
+        buf = ctypes.create_string_buffer(n)
+        _check(load().tpc_mlp_trainer_blob(self.handle, ctypes.cast(buf, c_vp), n))
+        return buf.raw
 
 
 # ------------------------------------------------------------ torch convenience
@@ -274,6 +440,43 @@ class TimeFrameTracker:
 
     def stage_times(self):
         return tpc_tf_stage_times(self.handle)
+
+    def load_mlp(self, blob: bytes):
+        _check(tpc_mlp_load(self.handle, blob))
+
+    def score(self, feat):
+        """Logits of raw feature rows (float32[m, 12] CUDA tensor)."""
+        t = self.torch
+        m = int(feat.shape[0])
+        out = t.empty(max(m, 1), dtype=t.float32, device=self.device)
+        _check(tpc_mlp_score(self.handle, feat.data_ptr(), m, out.data_ptr(),
+                             t.cuda.current_stream(self.device).cuda_stream))
+        return out[:m]
+
+    def extract(self, sector, row, pad, time, sorted_input=True, cap=None):
+        """Training rows of one frame: (features float32[M,12], labels uint8[M], tri int32[M,3])."""
+        t = self.torch
+        d = self.device
+        n = int(sector.numel())
+        cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED if sorted_input else 0, sector=sector.data_ptr(),
+                          row=row.data_ptr(), pad=pad.data_ptr(), time=time.data_ptr())
+        count = t.zeros(1, dtype=t.int32, device=d)
+        st = t.cuda.current_stream(d).cuda_stream
+        if cap is None:
+            _check(tpc_mlp_extract(self.handle, cl, None, None, None, 0, count.data_ptr(), st))
+            cap = int(count.item())
+        feat = t.empty((max(cap, 1), MLP_IN), dtype=t.float32, device=d)
+        label = t.empty(max(cap, 1), dtype=t.uint8, device=d)
+        tri = t.empty((max(cap, 1), 3), dtype=t.int32, device=d)
+        _check(tpc_mlp_extract(self.handle, cl, feat.data_ptr(), label.data_ptr(), tri.data_ptr(), cap,
+                               count.data_ptr(), st))
+        self._n = n
+        m = min(int(count.item()), cap)
+        _check(tpc_tf_status(self.handle, st))
+        return feat[:m], label[:m], tri[:m]
+
+    def pruned_clusters(self) -> int:
+        return tpc_tf_pruned_clusters(self.handle, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def launches_per_call(self) -> int:
         return tpc_tf_launches_per_call(self.handle)

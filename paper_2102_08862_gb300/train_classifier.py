@@ -1,0 +1,159 @@
+"""Train the learned link classifier on the GPU and choose its threshold.
+
+    python -m paper_2102_08862_gb300.train_classifier --out DIR
+
+1. Training set: for each generated 2 ms Pb-Pb-like time frame (seeds
+   1001..1050), the plain path's kernels list every pair under the cost cut of
+   every cluster with at least two such pairs, with its 12 features and its label
+   (1 iff the pair is the plain A1 choice and both links are mutual after
+   cleaning): tpc_mlp_extract.
+2. Training: standardisation from the training rows, then Adam (lr 1e-3,
+   betas 0.9/0.999, eps 1e-8) on BF16 tensor-core forward/backward kernels with
+   FP32 master weights, batch 8192, positive class weighted by neg/pos, rows
+   shuffled every epoch (tpc_mlp_trainer_*).
+3. Threshold: pruned tracking on separate frames (seeds 1051, 1052) for a grid
+   of tau; the tracking efficiency against generator truth decides (largest
+   efficiency; among thresholds within 1e-3 of it, the lowest fake rate).
+
+Writes DIR/link_classifier.bin (the weight blob) and DIR/link_classifier.json
+(training and threshold record).  Every step of the tracking, the extraction and
+the training runs in libtpcca.so's kernels; the frames come from the seeded
+generator (tpcsynth)."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+TRAIN_SEEDS = list(range(1001, 1051))
+TUNE_SEEDS = [1051, 1052]
+TAU_GRID = [0.02, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9]
+
+
+def _frame(seed, ms):
+    import tpcsynth as ts
+    return ts.generate(ts.continuous(ms, seed))
+
+
+def _dev(torch, f, dev):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time)
+
+
+def quality(tpcca, torch, dev, frames, mode, tau=0.5, blob=None):
+    """Efficiency / clone / fake summed over frames (counts, then rates)."""
+    from .evaluate import evaluate
+    nmax = max(f.n for f in frames)
+    tr = tpcca.TimeFrameTracker(nmax + 16, mode=mode, tau=float(tau))
+    tot = dict(n_findable=0, n_findable_found=0, n_matched_findable_tracks=0, n_fake=0, n_tracks=0)
+    pruned = 0
+    try:
+        if blob is not None:
+            tr.load_mlp(blob)
+        for f in frames:
+            res = tr.track(*_dev(torch, f, dev))
+            if mode == tpcca.TPC_MODE_PRUNED:
+                pruned += tr.pruned_clusters()
+            e = evaluate(f.label, f.sector, res.cluster_track.cpu().numpy(), res.n_tracks, f.trk_qpt.shape[0])
+            for k in tot:
+                tot[k] += e[k]
+    finally:
+        tr.close()
+    nf, nt = max(tot["n_findable"], 1), max(tot["n_tracks"], 1)
+    return dict(efficiency=tot["n_findable_found"] / nf,
+                clone_rate=(tot["n_matched_findable_tracks"] - tot["n_findable_found"]) / nf,
+                fake_rate=tot["n_fake"] / nt, n_tracks=tot["n_tracks"], n_findable=tot["n_findable"],
+                rescored_clusters=pruned)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--frames", type=int, default=len(TRAIN_SEEDS))
+    ap.add_argument("--frame-ms", type=float, default=2.0)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--device", type=int, default=0)
+    args = ap.parse_args(argv)
+
+    import torch
+    from . import _build, tpcca
+    _build.build()
+    dev = torch.device("cuda", args.device)
+    t0 = time.time()
+    rec = dict(train_seeds=TRAIN_SEEDS[:args.frames], tune_seeds=TUNE_SEEDS, frame_ms=args.frame_ms,
+               epochs=args.epochs, batch=args.batch, lr=1e-3, betas=[0.9, 0.999], eps=1e-8, init_seed=args.seed)
+
+    # 1. training rows, extracted on the GPU frame by frame
+    feats, labels = [], []
+    tr = None
+    n_clusters = 0
+    for s in TRAIN_SEEDS[:args.frames]:
+        f = _frame(s, args.frame_ms)
+        n_clusters += f.n
+        if tr is None or tr.cfg.max_clusters < f.n:
+            if tr is not None:
+                tr.close()
+            tr = tpcca.TimeFrameTracker(int(f.n * 1.2) + 16, device=args.device)
+        F, L, _ = tr.extract(*_dev(torch, f, dev))
+        feats.append(F.clone())
+        labels.append(L.clone())
+    tr.close()
+    F = torch.cat(feats)
+    L = torch.cat(labels)
+    del feats, labels
+    M = int(F.shape[0])
+    npos = int(L.sum().item())
+    pos_weight = (M - npos) / max(npos, 1)
+    rec.update(train_clusters=n_clusters, train_rows=M, train_positives=npos, pos_weight=pos_weight,
+               extract_s=time.time() - t0)
+    print(f"training rows {M} ({npos} positive) from {args.frames} frames, {n_clusters} clusters", flush=True)
+
+    # 2. training
+    t1 = time.time()
+    trainer = tpcca.Trainer(tpcca.init_blob(args.seed), device=args.device, pos_weight=pos_weight,
+                            max_batch=args.batch)
+    trainer.normalise(F)
+    gen = torch.Generator(device=dev).manual_seed(args.seed)
+    curve = []
+    for ep in range(args.epochs):
+        perm = torch.randperm(M, device=dev, generator=gen).to(torch.int32)
+        losses = []
+        for b0 in range(0, M, args.batch):
+            idx = perm[b0:b0 + args.batch]
+            losses.append(trainer.step(F, L, idx).clone())
+        curve.append(float(torch.stack(losses).mean().item()))
+        print(f"epoch {ep}: mean loss {curve[-1]:.5f}", flush=True)
+    torch.cuda.synchronize(dev)
+    blob = trainer.blob()
+    trainer.close()
+    rec.update(loss_per_epoch=curve, train_s=time.time() - t1, steps=args.epochs * ((M + args.batch - 1) // args.batch))
+
+    # 3. threshold on separate frames
+    tune = [_frame(s, args.frame_ms) for s in TUNE_SEEDS]
+    plain = quality(tpcca, torch, dev, tune, tpcca.TPC_MODE_PLAIN)
+    grid = []
+    for tau in TAU_GRID:
+        q = quality(tpcca, torch, dev, tune, tpcca.TPC_MODE_PRUNED, tau, blob)
+        q["tau"] = tau
+        grid.append(q)
+        print(f"tau {tau}: eff {q['efficiency']:.5f} clone {q['clone_rate']:.5f} fake {q['fake_rate']:.5f} "
+              f"(plain eff {plain['efficiency']:.5f} fake {plain['fake_rate']:.5f})", flush=True)
+    best_eff = max(q["efficiency"] for q in grid)
+    pick = min((q for q in grid if q["efficiency"] >= best_eff - 1e-3), key=lambda q: (q["fake_rate"], -q["efficiency"]))
+    rec.update(plain_tune=plain, tau_grid=grid, tau=pick["tau"], total_s=time.time() - t0)
+
+    os.makedirs(args.out, exist_ok=True)
+    with open(os.path.join(args.out, "link_classifier.bin"), "wb") as fh:
+        fh.write(blob)
+    with open(os.path.join(args.out, "link_classifier.json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(dict(tau=pick["tau"], pruned=pick, plain=plain)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

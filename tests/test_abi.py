@@ -4,6 +4,8 @@ import ctypes
 import os
 import subprocess
 
+import numpy as np
+
 import pytest
 
 from paper_2102_08862_gb300 import _build, tpcca
@@ -39,6 +41,8 @@ int main(void) {
          sizeof(tpc_tracks));
   F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
+  printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
+  F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device);
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -48,6 +52,7 @@ int main(void) {
     assert int(vals["tpc_tf_config"]) == ctypes.sizeof(tpcca.tpc_tf_config)
     assert int(vals["tpc_clusters"]) == ctypes.sizeof(tpcca.tpc_clusters)
     assert int(vals["tpc_tracks"]) == ctypes.sizeof(tpcca.tpc_tracks)
+    assert int(vals["tpc_mlp_train_config"]) == ctypes.sizeof(tpcca.tpc_mlp_train_config)
     for key, v in vals.items():
         if "." in key:
             struct, member = key.split(".")
@@ -79,3 +84,16 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "oracle.h" not in txt, f
+
+
+def test_classifier_blob_roundtrip_and_size(lib):
+    rng = np.random.default_rng(0)
+    mean, inv_std = rng.standard_normal(12), rng.random(12)
+    theta = rng.standard_normal(tpcca.MLP_NPARAM)
+    blob = tpcca.pack_blob(mean, inv_std, theta)
+    assert len(blob) == tpcca.tpc_mlp_blob_bytes() == 20340
+    m, s, t = tpcca.unpack_blob(blob)
+    assert np.array_equal(m, mean.astype(np.float32)) and np.array_equal(t, theta.astype(np.float32))
+    assert len(tpcca.init_blob(3)) == 20340
+    with pytest.raises(ValueError):
+        tpcca.unpack_blob(b"XXXX" + blob[4:])

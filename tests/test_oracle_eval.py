@@ -5,6 +5,8 @@ with >= 30 clusters)."""
 import numpy as np
 
 import oracle as orc
+import pytest
+import tpcsynth as ts
 
 
 def test_eval_hand_built_case():
@@ -44,3 +46,21 @@ def test_eval_perfect_and_empty():
     assert ev["efficiency"] == 1.0 and ev["clone_rate"] == 0.0 and ev["fake_rate"] == 0.0
     ev = orc.evaluate(lab, sec, np.full_like(lab, -1), n_tracks=0, n_gen_tracks=4)
     assert ev["efficiency"] == 0.0 and ev["n_tracks"] == 0
+
+
+def test_package_evaluator_matches_oracle():
+    """The host-side evaluator of the package reproduces the oracle's counts."""
+    from paper_2102_08862_gb300.evaluate import evaluate as pkg_eval
+    f = ts.generate(ts.c1())
+    res = orc.track(f.sector, f.row, f.pad, f.time)
+    ng = int(f.trk_qpt.shape[0])
+    for mf in (10, 30):
+        want = orc.evaluate(f.label, f.sector, res["cluster_track"], res["n_tracks"], ng, min_findable=mf)
+        got = pkg_eval(f.label, f.sector, res["cluster_track"], res["n_tracks"], ng, min_findable=mf)
+        assert got == pytest.approx(want)
+    # a noisy assignment: random track ids over a subset of clusters
+    rng = np.random.default_rng(3)
+    ct = np.where(rng.random(f.n) < 0.7, rng.integers(0, 50, f.n), -1).astype(np.int32)
+    want = orc.evaluate(f.label, f.sector, ct, 50, ng, min_findable=5, match_frac=0.3)
+    got = pkg_eval(f.label, f.sector, ct, 50, ng, min_findable=5, match_frac=0.3)
+    assert got == pytest.approx(want)
