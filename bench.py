@@ -3,10 +3,14 @@
 readout time frame (36 sectors, ~500 Pb-Pb-like collisions at 50 kHz, ~32M
 clusters, seed 3) through the C ABI on one GB300 per rank.
 
-One step = the whole tracking path (ingest, neighbour finding, link cleaning,
-start hits, chain filter, Kalman fit) over one resident frame.  Prints one JSON
-line (rank 0).  `--impl reference` times the CPU oracle instead (on the host
-cores, on a bounded sample of the same frame).
+One step = the whole tracking path (ingest, neighbour finding with the learned
+link classifier rescoring the ambiguous clusters, link cleaning, start hits,
+chain filter, Kalman fit) over one resident frame.  The plain CA (no classifier)
+is timed on the same frame beside it, and the tracking efficiency, clone and fake
+rates of both against generator truth are reported, so that the two are compared
+at equal efficiency.  Prints one JSON line (rank 0).  `--impl reference` times
+the CPU oracle instead (on the host cores, on a bounded sample of the same
+frame).
 
 Multi-GPU (torchrun): every rank tracks its own independent frame (different
 seed, same generator), no data-path collective; `value` is the clusters of all
@@ -54,6 +58,8 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        if self.index < 0:  # sampling off
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -97,6 +103,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+WEIGHTS = os.path.join(ROOT, "paper_2102_08862_gb300", "weights", "link_classifier")
+
+
+def classifier():
+    """(weight blob, tau) of the trained link classifier shipped with the package."""
+    with open(WEIGHTS + ".bin", "rb") as fh:
+        blob = fh.read()
+    with open(WEIGHTS + ".json") as fh:
+        tau = float(json.load(fh)["tau"])
+    return blob, tau
+
+
 def gen_frame(workload, seed_offset=0):
     import tpcsynth as ts
     cfg = {"c1": ts.c1, "c2": ts.c2, "c3": ts.c3}[workload]()
@@ -104,14 +122,15 @@ def gen_frame(workload, seed_offset=0):
     return ts.generate(cfg)
 
 
-def cpu_oracle_rate(f, budget_s=10.0):
-    """The oracle as it stands, single-threaded, sector by sector on the frame
-    until the time budget is used: clusters/s on one host core."""
+def cpu_oracle_rate(f, budget_s=10.0, mlp=None, tau=0.5):
+    """The oracle as it stands (pruned by the same classifier when mlp is given),
+    single-threaded, sector by sector on the frame until the time budget is used:
+    clusters/s on one host core."""
     import oracle
     done, t0, used = 0, time.perf_counter(), []
     for s in range(36):
         idx = np.where(f.sector == s)[0]
-        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx])
+        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx], mlp=mlp, tau=tau)
         done += len(idx)
         used.append(s)
         if time.perf_counter() - t0 > budget_s:
@@ -126,13 +145,14 @@ def run_reference(args, rank, world):
     f = gen_frame(args.workload)
     import oracle
     oracle.build()
-    # warm-up and timed steps; each step is a bounded sample (2 sectors) of the frame
+    blob, tau = classifier()
+    # warm-up and timed steps; each step is a bounded sample (one sector) of the frame
     secs = [np.where(f.sector == s)[0] for s in range(36)]
     total, t_all = 0, 0.0
     for k in range(args.warmup + args.steps):
-        idx = np.concatenate([secs[(2 * k) % 36], secs[(2 * k + 1) % 36]])
+        idx = secs[k % 36]
         t0 = time.perf_counter()
-        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx])
+        oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx], mlp=blob, tau=tau)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             total += len(idx)
@@ -142,9 +162,10 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
            "data": "synthetic", "config": {"workload": f"{args.workload}: 10 ms frame, {f.n} clusters, seed 3",
-                                           "model": "CPU oracle (plain single-threaded C)", "parallelism": "1 core"},
+                                           "model": "CPU oracle (plain single-threaded C), learned-pruned CA",
+                                           "parallelism": "1 core"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "2 sectors of the frame per step"},
+                            "sample": "one sector of the frame per step"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -159,6 +180,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-variant", type=int, default=0)
+    ap.add_argument("--mode", default="both", choices=["both", "pruned", "plain"],
+                    help="both: the learned-pruned CA is the headline, the plain CA is timed beside it")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
@@ -184,85 +207,124 @@ def main():
     n = f.n
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     sec, row, pad, tim = t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time)
-    tr = tpcca.TimeFrameTracker(n, device=local, fit_variant=args.fit_variant)
+    blob, tau = classifier()
+    modes = {"pruned": dict(mode=tpcca.TPC_MODE_PRUNED, tau=tau), "plain": dict(mode=tpcca.TPC_MODE_PLAIN)}
     cap = n // 10 + 1
-    cnt = tpcca.c_u32(0)
-    cl, out, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=cnt)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
-    # one checked call: correctness of the configuration and the track count
-    rc = tpcca.tpc_track_timeframe(tr.handle, cl, out, sh)
-    assert rc == 0, tpcca.tpc_last_error()
-    stream.synchronize()
-    n_tracks = int(cnt.value)
-    cl2, out2, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=None)
 
-    def step():
-        rc = tpcca.tpc_track_timeframe(tr.handle, cl2, out2, sh)
-        if rc != 0:
-            raise RuntimeError(tpcca.tpc_last_error())
+    def make(name, **extra):
+        tr = tpcca.TimeFrameTracker(n, device=local, fit_variant=args.fit_variant, **modes[name], **extra)
+        if name == "pruned":
+            tr.load_mlp(blob)
+        return tr
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    stream.synchronize()
-    if args.kernel_only:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for _ in range(args.steps):
-                step()
-            e1.record(stream)
+    def checked_call(tr):
+        """One call with the track count read back: checks the configuration."""
+        cnt = tpcca.c_u32(0)
+        cl, out, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=cnt)
+        rc = tpcca.tpc_track_timeframe(tr.handle, cl, out, sh)
+        assert rc == 0, tpcca.tpc_last_error()
         stream.synchronize()
+        return int(cnt.value)
+
+    def stepper(tr):
+        cl, out, _, _ = tr.structs(sec, row, pad, tim, True, cap, host_count=None)
+
+        def step():
+            rc = tpcca.tpc_track_timeframe(tr.handle, cl, out, sh)
+            if rc != 0:
+                raise RuntimeError(tpcca.tpc_last_error())
+        return step
+
+    def timed(tr, steps, sample_clocks):
+        step = stepper(tr)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+        stream.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local if sample_clocks else -1) as clocks:
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                for k in range(steps):
+                    step()
+                    ev[k + 1].record(stream)
+            stream.synchronize()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
         assert tpcca.tpc_tf_status(tr.handle, sh) == 0, tpcca.tpc_last_error()
-        print(json.dumps({"workload": args.workload, "clusters": n, "tracks": n_tracks,
-                          "launches_per_step": tr.launches_per_call(),
-                          "ms_per_step": e0.elapsed_time(e1) / args.steps}), flush=True)
-        tr.close()
-        return
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        total = ev[0].elapsed_time(ev[-1])
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        if dist:
+            tt = torch.tensor([total], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        return total, per, clocks
+
+    def stages(name):
+        prof = make(name, profile_stages=1)
+        clp, outp, _, _ = prof.structs(sec, row, pad, tim, True, cap, host_count=None)
+        acc = {}
+        for k in range(args.warmup + 5):
+            assert tpcca.tpc_track_timeframe(prof.handle, clp, outp, sh) == 0
+            if k >= args.warmup:
+                for nm, ms in prof.stage_times():
+                    acc.setdefault(nm, []).append(ms)
+        ct = prof._out["cluster_track"][:n]
+        in_tracks = int((ct >= 0).sum().item())
+        rescored = prof.pruned_clusters() if name == "pruned" else 0
+        prof.close()
+        return {k: statistics.mean(v) for k, v in acc.items()}, in_tracks, rescored
+
+    def quality(tr):
+        from paper_2102_08862_gb300.evaluate import evaluate
+        res = tr.track(sec, row, pad, tim, capacity=cap)
+        e = evaluate(f.label, f.sector, res.cluster_track.cpu().numpy(), res.n_tracks, f.trk_qpt.shape[0])
+        return {k: e[k] for k in ("efficiency", "clone_rate", "fake_rate", "n_tracks", "n_findable")}
+
     if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clocks:
-        with torch.cuda.stream(stream):
-            ev[0].record(stream)
-            for k in range(args.steps):
-                step()
-                ev[k + 1].record(stream)
-        stream.synchronize()
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    rc = tpcca.tpc_tf_status(tr.handle, sh)
-    assert rc == 0, tpcca.tpc_last_error()
-    total_ms = ev[0].elapsed_time(ev[-1])
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         nn = torch.tensor([float(n)], device=dev)
         dist.all_reduce(nn)
         n_all = float(nn.item())
     else:
         n_all = float(n)
-    launches = tr.launches_per_call()
+
+    if args.kernel_only:
+        name = args.mode if args.mode != "both" else "pruned"
+        tr = make(name)
+        n_tracks = checked_call(tr)
+        total, per, _ = timed(tr, args.steps, False)
+        print(json.dumps({"workload": args.workload, "mode": name, "clusters": n, "tracks": n_tracks,
+                          "launches_per_step": tr.launches_per_call(), "ms_per_step": total / args.steps}),
+              flush=True)
+        tr.close()
+        return
+
+    arms = ["pruned", "plain"] if args.mode == "both" else [args.mode]
+    res = {}
+    for name in arms:
+        tr = make(name)
+        n_tracks = checked_call(tr)
+        total, per, clocks = timed(tr, args.steps, name == arms[0])
+        res[name] = dict(total_ms=total, per=per, clocks=clocks, n_tracks=n_tracks,
+                         launches=tr.launches_per_call(), quality=quality(tr))
+        if name == arms[0]:
+            head_tr = tr
+        else:
+            tr.close()
+    head = arms[0]
+    H = res[head]
+    total_ms, per = H["total_ms"], H["per"]
     value = n_all * args.steps / (total_ms * 1e-3)
+    n_tracks = H["n_tracks"]
 
     # stage timing (CUDA events between the stages of a call, on the call's stream)
-    prof = tpcca.TimeFrameTracker(n, device=local, profile_stages=1, fit_variant=args.fit_variant)
-    clp, outp, _, _ = prof.structs(sec, row, pad, tim, True, cap, host_count=None)
-    acc = {}
-    for k in range(args.warmup + 5):
-        assert tpcca.tpc_track_timeframe(prof.handle, clp, outp, sh) == 0
-        if k >= args.warmup:
-            for name, ms in prof.stage_times():
-                acc.setdefault(name, []).append(ms)
-    stage_ms = {k: statistics.mean(v) for k, v in acc.items()}
-    ct = prof._out["cluster_track"][:n]
-    in_tracks = int((ct >= 0).sum().item())
-    prof.close()
+    stage_ms, in_tracks, rescored = stages(head)
     hbm, peak_kind = peaks()
     alg = {"neighbours": ALG_BYTES["neighbours"] * n, "links": ALG_BYTES["links"] * n, "fit": 16.0 * in_tracks}
     dom = max(stage_ms, key=stage_ms.get)
@@ -276,6 +338,7 @@ def main():
     step_gbs = STAGED_BYTES_PER_CLUSTER * n / (step_ms * 1e-3) / 1e9
 
     # end to end through the host-buffer entry point (pinned host memory)
+    tr = head_tr
     hs = torch.from_numpy(np.ascontiguousarray(f.sector.view(np.int16))).pin_memory()
     hr = torch.from_numpy(np.ascontiguousarray(f.row.view(np.int16))).pin_memory()
     hp = torch.from_numpy(np.ascontiguousarray(f.pad)).pin_memory()
@@ -318,19 +381,22 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, sample, _ = cpu_oracle_rate(f, args.cpu_budget)
+        v, sample, _ = cpu_oracle_rate(f, args.cpu_budget, mlp=blob if head == "pruned" else None, tau=tau)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64+f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+bf16+f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: 10 ms continuous frame, 36 sectors, {f.n_collisions} collisions "
                                f"at 50 kHz, {n} clusters, seed 3 (+1000*rank)",
-                   "mode": "plain CA", "fit": ["thread per track", "warp per track"][args.fit_variant],
+                   "mode": {"pruned": f"learned-pruned CA (tau {tau})", "plain": "plain CA"}[head],
+                   "fit": ["thread per track", "warp per track"][args.fit_variant],
                    "l2": "inputs (12 B x %d = %.0f MB) larger than L2" % (n, 12 * n / 1e6),
                    "parallelism": f"replicas x{world}"},
         "tracks_per_s": n_tracks * args.steps / (total_ms * 1e-3) * (n_all / n),
         "n_tracks": n_tracks,
+        "quality": H["quality"],
+        "rescored_clusters": rescored,
         "step_ms": {"median": step_ms, "min": min(per)},
         "stage_ms": stage_ms,
         "roofline": roof,
@@ -339,9 +405,14 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": n_all / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches * args.steps,
-        "clocks": clocks.summary(),
+        "gpu_launches": H["launches"] * args.steps,
+        "clocks": H["clocks"].summary(),
     }
+    for name in arms[1:]:
+        R = res[name]
+        out[name] = {"value": n_all * args.steps / (R["total_ms"] * 1e-3), "ms_per_step": R["total_ms"] / args.steps,
+                     "step_ms_median": statistics.median(R["per"]), "n_tracks": R["n_tracks"],
+                     "quality": R["quality"]}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -12,8 +12,9 @@
    FP32 master weights, batch 8192, positive class weighted by neg/pos, rows
    shuffled every epoch (tpc_mlp_trainer_*).
 3. Threshold: pruned tracking on separate frames (seeds 1051, 1052) for a grid
-   of tau; the tracking efficiency against generator truth decides (largest
-   efficiency; among thresholds within 1e-3 of it, the lowest fake rate).
+   of tau, scored against generator truth: among the thresholds whose
+   efficiency stays within 0.5 % (absolute) of the plain path's, the one with
+   the smallest clone + fake rate.
 
 Writes DIR/link_classifier.bin (the weight blob) and DIR/link_classifier.json
 (training and threshold record).  Every step of the tracking, the extraction and
@@ -99,9 +100,13 @@ def main(argv=None):
             if tr is not None:
                 tr.close()
             tr = tpcca.TimeFrameTracker(int(f.n * 1.2) + 16, device=args.device)
-        F, L, _ = tr.extract(*_dev(torch, f, dev))
-        feats.append(F.clone())
-        labels.append(L.clone())
+        F, L, tri = tr.extract(*_dev(torch, f, dev))
+        # canonical row order (the kernel's order depends on scheduling): by (i, j, k)
+        order = torch.arange(F.shape[0], device=dev)
+        for c in (2, 1, 0):
+            order = order[torch.sort(tri[order, c], stable=True).indices]
+        feats.append(F[order].clone())
+        labels.append(L[order].clone())
     tr.close()
     F = torch.cat(feats)
     L = torch.cat(labels)
@@ -143,8 +148,8 @@ def main(argv=None):
         grid.append(q)
         print(f"tau {tau}: eff {q['efficiency']:.5f} clone {q['clone_rate']:.5f} fake {q['fake_rate']:.5f} "
               f"(plain eff {plain['efficiency']:.5f} fake {plain['fake_rate']:.5f})", flush=True)
-    best_eff = max(q["efficiency"] for q in grid)
-    pick = min((q for q in grid if q["efficiency"] >= best_eff - 1e-3), key=lambda q: (q["fake_rate"], -q["efficiency"]))
+    ok = [q for q in grid if q["efficiency"] >= plain["efficiency"] - 0.005] or grid
+    pick = min(ok, key=lambda q: (q["clone_rate"] + q["fake_rate"], -q["efficiency"]))
     rec.update(plain_tune=plain, tau_grid=grid, tau=pick["tau"], total_s=time.time() - t0)
 
     os.makedirs(args.out, exist_ok=True)
