@@ -232,9 +232,11 @@ int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void 
 int tpc_mlp_extract(tpc_tf *tf, const tpc_clusters *cl, float *feat, uint8_t *label, int32_t *tri, uint32_t cap,
                     uint32_t *count, void *stream);
 
-/* Number of clusters the classifier rescored in the last TPC_MODE_PRUNED call
- * (synchronises `stream`). */
-int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n, void *stream);
+/* Number of clusters the classifier rescored in the last TPC_MODE_PRUNED call:
+ * *n_region from the neighbour tiles' pair regions, *n_list from the overflow list
+ * (windows too large to stage, more than four pairs, or a full region); either
+ * pointer may be NULL.  Synchronises `stream`. */
+int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n_region, uint32_t *n_list, void *stream);
 
 typedef struct tpc_mlp_trainer tpc_mlp_trainer; /* opaque: FP32 master weights, Adam moments, BF16 copy */
 

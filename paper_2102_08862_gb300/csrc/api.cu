@@ -84,6 +84,8 @@ struct tpc_tf {
   Args last_args;
   // learned link classifier (TPC_MODE_PRUNED)
   int4 *amb = nullptr;        // clusters listed for rescoring (arena, pruned mode only)
+  PruneRow *q_rows = nullptr; // per-tile regions of rescored pairs (pruned mode only)
+  int32_t *q_count = nullptr;
   MlpW *mlp = nullptr;        // packed weights (allocated by tpc_mlp_load)
   float *mlp_stage = nullptr; // FP32 blob body staged for packing
   bool mlp_ready = false;
@@ -194,6 +196,9 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
       {(void **)&tf->h_status, (size_t)tf->track_list_cap},
       {(void **)&tf->h_ntracks, 16},
       {(void **)&tf->amb, cfg->mode == TPC_MODE_PRUNED ? (N + 4) * 16 : 0},
+      {(void **)&tf->q_rows,
+       cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * sizeof(PruneRow) : 0},
+      {(void **)&tf->q_count, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * 4 : 0},
   };
   size_t total = 0;
   for (auto &p : parts) total += align_up(p.bytes, 256);
@@ -284,6 +289,10 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.n_min = tf->cfg.n_min;
   a.amb = tf->amb;
   a.amb_cap = tf->amb ? tf->N + 4 : 0;
+  a.mlp = tf->mlp;
+  a.logit_tau = tf->logit_tau;
+  a.q_rows = tf->q_rows;
+  a.q_count = tf->q_count;
   if (out) {
     a.cluster_track = out->cluster_track;
     a.track_capacity = out->track_capacity;
@@ -337,9 +346,11 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   stage(tf, st, "neighbours");
   tf->launches += 3;
   if (prune) {
+    launch_prune_tiles(a, tf->mlp, tf->logit_tau, tf->sms, st);
+    stage(tf, st, "prune_tiles");
     launch_prune(a, tf->mlp, tf->logit_tau, tf->sms, st);
-    stage(tf, st, "prune");
-    ++tf->launches;
+    stage(tf, st, "prune_list");
+    tf->launches += 2;
   }
   launch_edge_claims(a, st);
   stage(tf, st, "edge_claims");
@@ -568,13 +579,14 @@ extern "C" int tpc_mlp_extract(tpc_tf *tf, const tpc_clusters *cl, float *feat, 
   return TPC_OK;
 }
 
-extern "C" int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n, void *stream) {
+extern "C" int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n_region, uint32_t *n_list, void *stream) {
   g_err.clear();
-  if (!tf || !n) return fail(TPC_ERR_ARG, "tpc_tf_pruned_clusters: null argument");
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_pruned_clusters: null handle");
   TPC_CK(cudaSetDevice(tf->device));
   cudaStream_t st = (cudaStream_t)stream;
-  TPC_CK(cudaMemcpyAsync(tf->pinned + 2, tf->reset + kCtrAmb, 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(tf->pinned + 2, tf->reset + kCtrAmb, 8, cudaMemcpyDeviceToHost, st));
   TPC_CK(cudaStreamSynchronize(st));
-  *n = tf->pinned[2];
+  if (n_list) *n_list = tf->pinned[2];
+  if (n_region) *n_region = tf->pinned[3];
   return TPC_OK;
 }

@@ -18,6 +18,7 @@
 // a contiguous run of clusters, moving its window pointers forward only.  Windows
 // larger than the staging buffers are read from global memory with the same
 // arithmetic.
+#include "mlp_dev.cuh"
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -26,6 +27,20 @@ namespace tpc {
 namespace {
 
 constexpr int kMaxCand = 4;  // candidates per neighbour row kept in registers
+
+// Pruned mode: the pairs under the cut of the tile's ambiguous clusters (the
+// first four kept in registers while the pairs are scored, more enumerated again)
+// are written to the tile's own region of kPruneRegionRows rows (a shared-memory
+// counter reserves them, so no global atomic is taken); the rescoring kernel
+// reads the region.  Clusters with more than kPruneMaxPairs such pairs, or that
+// do not fit, go to the global list.
+constexpr int kPruneMaxPairs = 32;
+struct NbQueue {
+  uint32_t pairs[4][kNbThreads];  // a thread's first four pairs under the cut (j | k << 11)
+  int count, end;
+};
+template <bool kPrune> struct NbExtra {};
+template <> struct NbExtra<true> { NbQueue q; };
 
 // first e in [lo, hi) with q64(time[e]) >= x
 __device__ __forceinline__ int gm_lower_bound(const float *time, int lo, int hi, int x) {
@@ -189,7 +204,7 @@ template <bool kPrune>
 __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, int cnt, const int2 *__restrict__ sc,
                                               const int2 *__restrict__ sp, int np, const int2 *__restrict__ sn,
                                               int nn, int wy, int wt, int64_t cost_max, int2 *out, int base_p,
-                                              int base_n, int base_c) {
+                                              int base_n, int base_c, NbQueue *q, PruneRow *region) {
   if (li0 >= li1) return;
   const uint64_t capc = (uint64_t)cost_max + 1;
   const float frac = (float)li0 / (float)cnt;
@@ -216,7 +231,13 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
       ++nj;
     }
     uint64_t best = ~0ull;
-    int nc = 0;  // pairs under the cost cut (pruned mode only)
+    // pruned mode: pairs under the cost cut, the first four kept (j | k << 11) in
+    // the thread's shared-memory slots
+    int nc = 0, nkc = 0;
+    auto keep_pair = [&](uint32_t v) {
+      if (nc < 4) q->pairs[nc][threadIdx.x] = v;
+      ++nc;
+    };
     if (nj > 0 && nj <= kMaxCand) {
       const int cj[4] = {cj0, cj1, cj2, cj3};
       const int2 ej[4] = {ej0, ej1, ej2, ej3};
@@ -225,11 +246,12 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
         if (e.x > thi) break;
         const int32_t dyk = e.y - yi;
         if (abs(dyk) > wy) continue;
+        if (kPrune) ++nkc;
 #pragma unroll
         for (int x = 0; x < kMaxCand; ++x) {
           if (x >= nj) break;
           const uint64_t c = (uint64_t)triplet_cost(ej[x].y - yi, dyk, ej[x].x - ti, e.x - ti);
-          if (kPrune) nc += (c < capc);
+          if (kPrune && c < capc) keep_pair((uint32_t)cj[x] | ((uint32_t)k << 11));
           best = min(best, (min(c, capc) << 22) | ((uint64_t)cj[x] << 11) | (uint64_t)k);
         }
       }
@@ -245,7 +267,7 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
           const int32_t dyk = ek.y - yi;
           if (abs(dyk) > wy) continue;
           const uint64_t c = (uint64_t)triplet_cost(dyj, dyk, ej.x - ti, ek.x - ti);
-          if (kPrune) nc += (c < capc);
+          if (kPrune && c < capc) keep_pair((uint32_t)j | ((uint32_t)k << 11));
           best = min(best, (min(c, capc) << 22) | ((uint64_t)j << 11) | (uint64_t)k);
         }
       }
@@ -253,7 +275,51 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
     out[li] = (best != ~0ull && (best >> 22) <= (uint64_t)cost_max)
                   ? make_int2(base_p + (int)((best >> 11) & 2047), base_n + (int)(best & 2047))
                   : make_int2(-1, -1);
-    if (kPrune && nc >= 2) amb_push(a, make_int4(base_c + li, base_p + jlo, base_n + klo, nc));
+    if (kPrune && nc >= 2) {
+      // the pairs go to the tile's region (rows in any order: the rescoring
+      // compares (cost, j, k) explicitly); a cluster that does not fit goes to the list
+      int old = kPruneRegionRows;
+      if (nc <= kPruneMaxPairs) old = atomicAdd(&q->count, nc);
+      if (old + nc <= kPruneRegionRows) {
+        atomicMax(&q->end, old + nc);  // reservations that fit form a prefix of the region
+        if (nj > kMaxCand) {           // crowded path: count the row r+1 candidates
+          nkc = 0;
+          for (int k = klo; k < nn; ++k) {
+            const int2 e = sn[k];
+            if (e.x > thi) break;
+            nkc += abs(e.y - yi) <= wy;
+          }
+        }
+        const int cn = nj | (nkc << 16), ci_ = base_c + li;
+        auto put = [&](int slot, uint32_t jk) {
+          const int j = (int)(jk & 2047u), k = (int)(jk >> 11);
+          const int2 ej = sp[j], ek = sn[k];
+          PruneRow &w = region[slot];
+          reinterpret_cast<int4 *>(&w)[0] = make_int4(ci_, base_p + j, base_n + k, cn);
+          reinterpret_cast<int4 *>(&w)[1] = make_int4(ti, yi, ej.x, ej.y);
+          reinterpret_cast<int4 *>(&w)[2] = make_int4(ek.x, ek.y, 0, 0);
+        };
+        if (nc <= 4) {
+          for (int e = 0; e < nc; ++e) put(old + e, q->pairs[e][threadIdx.x]);
+        } else {  // more than four pairs (rare): enumerate them again from the windows
+          int slot = old;
+          for (int j = jlo; j < np; ++j) {
+            const int2 ej = sp[j];
+            if (ej.x > thi) break;
+            if (abs(ej.y - yi) > wy) continue;
+            for (int k = klo; k < nn; ++k) {
+              const int2 ek = sn[k];
+              if (ek.x > thi) break;
+              if (abs(ek.y - yi) > wy) continue;
+              if ((uint64_t)triplet_cost(ej.y - yi, ek.y - yi, ej.x - ti, ek.x - ti) < capc)
+                put(slot++, (uint32_t)j | ((uint32_t)k << 11));
+            }
+          }
+        }
+      } else {
+        amb_push(a, make_int4(base_c + li, base_p + jlo, base_n + klo, nc));
+      }
+    }
   }
 }
 
@@ -295,8 +361,9 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 
 // ------------------------------------------------------------ neighbours
 template <bool kPrune>
-__global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) {
+__global__ void __launch_bounds__(kNbThreads, kPrune ? 6 : 0) k_neighbours(Args a, int win_cap) {
   __shared__ int2 s_c[kNbTile], s_p[kNbWin], s_n[kNbWin];  // quantised (t, y)
+  __shared__ NbExtra<kPrune> ex;
   const uint32_t t = blockIdx.x;
   if (t >= min(a.ctr[kCtrTiles], a.tile_cap)) return;
   const int4 h = a.tile_win[2 * t], w = a.tile_win[2 * t + 1];
@@ -326,6 +393,7 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) 
     }
   }
   if (r == 0 || r == kNRows - 1) {  // edge rows: no A1 links (claims come later)
+    if (kPrune && tid == 0) a.q_count[t] = 0;
     __syncthreads();
     for (int e = tid; e < cnt; e += NT) {
       if (e > 0 && s_c[e].x < s_c[e - 1].x) bad = true;
@@ -336,6 +404,11 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) 
   }
   const int np = w.y - w.x, nn = w.w - w.z;
   const bool staged = np <= win_cap && nn <= win_cap;
+  NbQueue *q = nullptr;
+  if constexpr (kPrune) {
+    q = &ex.q;
+    if (tid == 0) q->count = q->end = 0;
+  }
   const int half_p = 32 * (row_npads(r - 1) - 1), pitch_p = row_pitch_um(r - 1);
   const int half_n = 32 * (row_npads(r + 1) - 1), pitch_n = row_pitch_um(r + 1);
   if (staged) {
@@ -366,13 +439,18 @@ __global__ void __launch_bounds__(kNbThreads) k_neighbours(Args a, int win_cap) 
   const int K = (cnt + NT - 1) / NT, li0 = tid * K, li1 = min(cnt, li0 + K);
   auto C = [&](int i) { return s_c[i]; };
   if (staged) {
-    link_run_smem<kPrune>(a, li0, li1, cnt, s_c, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta);
+    link_run_smem<kPrune>(a, li0, li1, cnt, s_c, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta,
+                          q, a.q_rows + (size_t)t * kPruneRegionRows);
   } else {
     const float *pp = a.pad + w.x, *tpg = a.time + w.x, *pn = a.pad + w.z, *tng = a.time + w.z;
     link_run<kPrune>(
         a, li0, li1, cnt, C, [&](int j) { return quant_ty(sane_pad(pp[j]), sane_time(tpg[j]), half_p, pitch_p); },
         np, [&](int k) { return quant_ty(sane_pad(pn[k]), sane_time(tng[k]), half_n, pitch_n); }, nn, a.wy, a.wt,
         a.cost_max, a.link + ta, w.x, w.z, ta);
+  }
+  if constexpr (kPrune) {  // rows used in this tile's region
+    __syncthreads();
+    if (tid == 0) a.q_count[t] = q->end;
   }
   if (bad) raise(a.ctr, kErrInput);
 }

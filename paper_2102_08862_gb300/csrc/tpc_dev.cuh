@@ -71,7 +71,8 @@ enum : int {
   kCtrFitNext = 7,
   kCtrSortDone = 8,
   kCtrTiles = 9,    // neighbour tiles of this frame
-  kCtrAmb = 10,     // clusters with >= 2 candidate pairs under the cost cut (pruned mode)
+  kCtrAmb = 10,     // clusters listed for the separate rescoring kernel (pruned mode)
+  kCtrQueued = 11,  // clusters rescored from the tile regions (pruned mode)
   kNCounters = 16
 };
 
@@ -116,9 +117,24 @@ struct Args {
   uint16_t *o_sector, *o_row_first, *o_row_last;
   uint8_t *o_status;
   uint32_t *n_tracks_out;
-  // pruned mode: clusters whose pairs the link classifier scores
+  // pruned mode: clusters whose pairs the link classifier rescores outside the
+  // neighbour kernel (windows not staged, or the kernel's queue full)
   int4 *amb;               // (sorted position, first j of the window, first k of the window, pairs under the cut)
   uint32_t amb_cap;
+  const struct MlpW *mlp;  // packed classifier weights
+  float logit_tau;         // a pair is kept when its logit >= logit_tau
+  struct PruneRow *q_rows;  // per neighbour tile: kPruneRegionRows rows
+  int32_t *q_count;         // per neighbour tile: rows used in its region
+};
+// rows of a neighbour tile's region in pruned mode
+constexpr int kPruneRegionRows = 128;
+// one pair under the cost cut of an ambiguous cluster: sorted positions of the
+// triplet, the cluster's candidate counts and the quantised (t, y) of the three
+// clusters (so that the rescoring reads no cluster arrays)
+struct __align__(16) PruneRow {
+  int32_t i, j, k, cn;  // cn = nj | nk << 16
+  int32_t ti, yi, tj, yj;
+  int32_t tk, yk, pad0, pad1;
 };
 
 __device__ __forceinline__ int32_t caller_index(const Args &a, int32_t i) { return a.perm ? a.perm[i] : i; }

@@ -39,7 +39,9 @@ size_t sort_scratch_bytes(uint32_t max_n);
 // link classifier (k_mlp.cu)
 struct MlpW;
 size_t mlp_weights_bytes();
-// rescoring of the listed clusters' pairs; rewrites their links
+// rescoring of the ambiguous clusters' pairs from the neighbour tiles' regions,
+// and of the clusters on the overflow list; rewrite their links
+void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
 // FP32 parameters (blob order) + standardisation -> packed BF16 weights
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);

@@ -102,7 +102,7 @@ def load():
     lib.tpc_mlp_score.restype = ctypes.c_int
     lib.tpc_mlp_extract.argtypes = [c_vp, P(tpc_clusters), c_vp, c_vp, c_vp, c_u32, c_vp, c_vp]
     lib.tpc_mlp_extract.restype = ctypes.c_int
-    lib.tpc_tf_pruned_clusters.argtypes = [c_vp, P(c_u32), c_vp]
+    lib.tpc_tf_pruned_clusters.argtypes = [c_vp, P(c_u32), P(c_u32), c_vp]
     lib.tpc_tf_pruned_clusters.restype = ctypes.c_int
     lib.tpc_mlp_default_train_config.argtypes = [P(tpc_mlp_train_config)]
     lib.tpc_mlp_default_train_config.restype = None
@@ -209,10 +209,11 @@ def tpc_mlp_extract(handle, clusters, feat_ptr, label_ptr, tri_ptr, cap, count_p
                                   stream)
 
 
-def tpc_tf_pruned_clusters(handle, stream=0) -> int:
-    n = c_u32(0)
-    _check(load().tpc_tf_pruned_clusters(handle, ctypes.byref(n), stream))
-    return int(n.value)
+def tpc_tf_pruned_clusters(handle, stream=0):
+    """(clusters rescored from the tile regions, clusters rescored from the overflow list)."""
+    a, b = c_u32(0), c_u32(0)
+    _check(load().tpc_tf_pruned_clusters(handle, ctypes.byref(a), ctypes.byref(b), stream))
+    return int(a.value), int(b.value)
 
 
 def tpc_mlp_default_train_config() -> tpc_mlp_train_config:
@@ -476,6 +477,11 @@ class TimeFrameTracker:
         return feat[:m], label[:m], tri[:m]
 
     def pruned_clusters(self) -> int:
+        """Clusters the classifier rescored in the last pruned call."""
+        return sum(self.pruned_split())
+
+    def pruned_split(self):
+        """(from the tile regions, from the overflow list) of the last pruned call."""
         return tpc_tf_pruned_clusters(self.handle, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def launches_per_call(self) -> int:

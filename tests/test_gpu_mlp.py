@@ -159,7 +159,10 @@ def _pruned_gpu(tpcca, dev, f, blob, tau, **kw):
     return g
 
 
-def test_pruned_c1_full_parity(env, c1):
+@pytest.mark.parametrize("row_cap", [0, 16])
+def test_pruned_c1_full_parity(env, c1, row_cap):
+    """row_cap 0: windows staged, rescoring inside the neighbour kernel; row_cap 16:
+    windows read from global memory, rescoring by the separate kernel."""
     tpcca, dev = env
     blob = _net()
     feat, _, _ = orc.training_triplets(c1.sector, c1.row, c1.pad, c1.time)
@@ -167,7 +170,7 @@ def test_pruned_c1_full_parity(env, c1):
     o = orc.track(c1.sector, c1.row, c1.pad, c1.time, mlp=blob, tau=tau)
     assert not o["band"].any()
     assert o["stats"][2] > 0, "the classifier changes some choices"
-    g = _pruned_gpu(tpcca, dev, c1, blob, tau)
+    g = _pruned_gpu(tpcca, dev, c1, blob, tau, row_cap=row_cap)
     assert g["n_pruned"] == o["stats"][0]
     compare_links(g, o)
     compare_tracks(g, o)
