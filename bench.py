@@ -36,6 +36,20 @@ UNIT = "clusters/s"
 # algorithmic bytes per cluster of each stage (read once + written once)
 ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a track
 STAGED_BYTES_PER_CLUSTER = 48.0
+# DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
+# valid while k_neighbours.cu is the file captured (its SHA-256)
+NB_TRAFFIC = {"sha256": "31cf8b2d74dd20dc4efd5a8b2b784cc2b7a959803470423233118dbac279c805",
+              "pruned": (204.053760e6 + 128.951808e6) / 16765809, "plain": (202.049792e6 + 100.518656e6) / 16765809}
+
+
+def neighbours_traffic(mode, n):
+    """Measured DRAM bytes of one k_neighbours launch on n clusters, or None when the
+    kernel source changed since the capture."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2102_08862_gb300", "csrc", "k_neighbours.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != NB_TRAFFIC["sha256"]:
+        return None
+    return NB_TRAFFIC[mode] * n
 
 
 def peaks():
@@ -333,8 +347,10 @@ def main():
     roof = None
     if dom_alg is not None:
         achieved = dom_alg / (stage_ms[dom] * 1e-3) / 1e9
+        traffic = neighbours_traffic(head, n) if dom == "neighbours" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind}
+                "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                "alg_bytes": dom_alg}
     step_ms = statistics.median(per)
     step_gbs = STAGED_BYTES_PER_CLUSTER * n / (step_ms * 1e-3) / 1e9
 
