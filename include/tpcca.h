@@ -62,8 +62,9 @@ extern "C" {
 
 #define TPC_INPUT_SORTED 1u /* clusters are sorted by (sector, row, time, pad) */
 
-#define TPC_FIT_THREAD 0 /* one thread per tracklet in the Kalman fit (default) */
-#define TPC_FIT_WARP 1   /* one warp per tracklet, lanes own state and covariance entries */
+#define TPC_FIT_THREAD 0 /* one thread per tracklet in the Kalman fit (default, fastest) */
+#define TPC_FIT_WARP 1   /* one warp per tracklet: the lanes load the chain's clusters together and run
+                            the same filter in lockstep (identical arithmetic, slower) */
 
 #define TPC_NSECTORS 36
 #define TPC_NROWS 152

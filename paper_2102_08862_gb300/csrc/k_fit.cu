@@ -327,9 +327,102 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
   }
 }
 
+// One warp per tracklet (TPC_FIT_WARP): the warp loads the chain cooperatively
+// (lane l holds the clusters of steps l, l + 32, ...; up to 160 steps), then every
+// lane runs the same filter in lockstep, each step's cluster arriving by shuffle
+// from the lane that holds it, so the warp never diverges; the outputs are
+// written by the lanes in parallel.  The arithmetic is the thread kernel's, so
+// the results are identical.  It issues ~32x more warp instructions per track
+// than k_fit_thread (one filter per warp instead of per lane), which the
+// coalesced chain loads do not pay back: the thread kernel stays the default.
+__global__ void __launch_bounds__(256) k_fit_warp(Args a) {
+  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
+  const size_t stride = a.track_list_cap;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += warps) {
+    const int32_t *ch = a.chain + t;
+    const int L = a.trk_len[t];
+    const int key = a.trk_key[t];
+    const int r0 = key % kNRows;
+    float pv0 = 0.f, pv1 = 0.f, pv2 = 0.f, pv3 = 0.f, pv4 = 0.f;
+    float tv0 = 0.f, tv1 = 0.f, tv2 = 0.f, tv3 = 0.f, tv4 = 0.f;
+    int32_t first = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int q = b * 32 + lane;
+      float pq = 0.f, tq = 0.f;
+      if (q < L) {
+        const int32_t c = ch[(size_t)q * stride];
+        if (q == 0) first = c;
+        pq = a.pad[c];
+        tq = a.time[c];
+      }
+      if (b == 0) { pv0 = pq; tv0 = tq; }
+      else if (b == 1) { pv1 = pq; tv1 = tq; }
+      else if (b == 2) { pv2 = pq; tv2 = tq; }
+      else if (b == 3) { pv3 = pq; tv3 = tq; }
+      else { pv4 = pq; tv4 = tq; }
+    }
+    const int32_t start = __shfl_sync(0xffffffffu, first, 0);
+    auto pad_at = [&](int q) {
+      const int b = q >> 5;
+      const float v = b == 0 ? pv0 : b == 1 ? pv1 : b == 2 ? pv2 : b == 3 ? pv3 : pv4;
+      return __shfl_sync(0xffffffffu, v, q & 31);
+    };
+    auto time_at = [&](int q) {
+      const int b = q >> 5;
+      const float v = b == 0 ? tv0 : b == 1 ? tv1 : b == 2 ? tv2 : b == 3 ? tv3 : tv4;
+      return __shfl_sync(0xffffffffu, v, q & 31);
+    };
+    const float tref = time_at(0);
+    const float pad0 = pad_at(0);
+    float h0, l0;
+    two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
+    const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
+    Kf k;
+    int status = kf_seed(k, L, r0, pad0, pad_at(L / 2), pad_at(L - 1), time_at(L - 1) - tref, yref_um);
+    int used = 1, lastrow = r0;
+    for (int q = 1; q < L; ++q) {
+      const float cpd = pad_at(q), ctm = time_at(q);
+      if (!kf_transport(k, kRowDx)) {
+        status |= 2;
+        break;
+      }
+      kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
+      kf_measure<1>(k, zeta_local(ctm, tref), kVz);
+      ++used;
+      lastrow = r0 + q;
+    }
+    float cov[15];
+    kf_covariance(k, cov);
+    float mine = 0.f;  // lane l < 15 writes covariance entry l, lanes 15..19 the parameters
+#pragma unroll
+    for (int i = 0; i < 15; ++i)
+      if (lane == i) mine = cov[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (lane == 15 + i) mine = i == 0 ? fmaf(yref_um, 1e-4f, k.p[0]) : k.p[i];
+    if (lane < 15) a.cov[(size_t)t * 15 + lane] = mine;
+    else if (lane < 20) a.params[(size_t)t * 5 + (lane - 15)] = mine;
+    if (lane == 0) {
+      a.t_ref[t] = tref;
+      a.x[t] = row_x(lastrow);
+      a.chi2[t] = k.chi2;
+      a.ndf[t] = 2 * used - 5;
+      a.nhits[t] = L;
+      a.first_cluster[t] = caller_index(a, start);
+      a.o_sector[t] = (uint16_t)(key / kNRows);
+      a.o_row_first[t] = (uint16_t)r0;
+      a.o_row_last[t] = (uint16_t)(r0 + L - 1);
+      a.o_status[t] = (uint8_t)status;
+    }
+  }
+}
+
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st) {
-  (void)variant;
-  k_fit_thread<<<sms * 8, 256, 0, st>>>(a);
+  if (variant == TPC_FIT_WARP) k_fit_warp<<<sms * 8, 256, 0, st>>>(a);
+  else k_fit_thread<<<sms * 8, 256, 0, st>>>(a);
 }
 
 }  // namespace tpc
