@@ -184,14 +184,75 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args, rank, world):
+    """c4: 256 sector x time-frame instances of uneven size (log-uniform 1e4-2e6
+    clusters, 0.2-10 ms) in one batched call, replayed from a CUDA graph, with the
+    neighbour tile and fit kernel chosen by the autotuner on the batch itself."""
+    import torch
+    import tpcsynth as ts
+    from paper_2102_08862_gb300 import _build, tpcca
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    _build.build()
+    b = ts.batched(256, seed=4 + 1000 * rank)
+    f, n_inst = b.frame, b.offsets.size - 1
+    n = f.n
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sec, row, pad, tim = t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time)
+    blob, tau = classifier()
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, kw in (("pruned", dict(mode=tpcca.TPC_MODE_PRUNED, tau=tau)), ("plain", {})):
+        tr = tpcca.TimeFrameTracker(n, device=dev.index, n_sectors=n_inst, **kw)
+        if name == "pruned":
+            tr.load_mlp(blob)
+        cap = n // 10 + 1
+        with torch.cuda.stream(stream):
+            tile, fit = tr.autotune(sec, row, pad, tim, capacity=cap, trials=3)
+            for _ in range(args.warmup):
+                tr.track_graph(sec, row, pad, tim, capacity=cap, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index if name == "pruned" else -1) as clocks:
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(args.steps):
+                    tr.track_graph(sec, row, pad, tim, capacity=cap, stream=stream)
+                e1.record(stream)
+            stream.synchronize()
+        assert tpcca.tpc_tf_status(tr.handle, stream.cuda_stream) == 0, tpcca.tpc_last_error()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = dict(ms=ms, tile=tile, fit=["thread", "warp"][fit], launches=tr.launches_per_call(),
+                         n_tracks=int(tr._out["n_tracks"].item()), clocks=clocks)
+        tr.close()
+    if rank != 0:
+        return
+    P, Q = res["pruned"], res["plain"]
+    sizes = np.diff(b.offsets)
+    out = {"metric": METRIC, "value": n / (P["ms"] * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": P["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64+bf16+f32", "data": "synthetic",
+           "config": {"workload": f"c4: {n_inst} sector x time-frame instances in one batched call, {n} clusters "
+                                  f"(per instance {int(sizes.min())}-{int(sizes.max())}, median {int(np.median(sizes))}), "
+                                  f"frames 0.2-10 ms, seed 4",
+                      "mode": f"learned-pruned CA (tau {tau})", "launch": "CUDA graph replay of one batched call",
+                      "autotuned": {"nb_tile": P["tile"], "fit": P["fit"]}, "parallelism": f"replicas x{world}"},
+           "n_tracks": P["n_tracks"], "gpu_launches": P["launches"] * args.steps, "graph_launches": args.steps,
+           "clocks": P["clocks"].summary(),
+           "plain": {"value": n / (Q["ms"] * 1e-3), "ms_per_step": Q["ms"], "n_tracks": Q["n_tracks"],
+                     "autotuned": {"nb_tile": Q["tile"], "fit": Q["fit"]}}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3half"],
-                    help="c3: the 10 ms frame; c3half: its first 5 ms (profiler captures); c1, c2: smaller cases")
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3half", "c4"],
+                    help="c3: the 10 ms frame; c3half: its first 5 ms (profiler captures); c1, c2: smaller "
+                         "cases; c4: 256 sector x time-frame instances in one batched, graph-replayed call")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-variant", type=int, default=0)
@@ -205,6 +266,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "c4":
+        run_batched(args, rank, world)
         return
 
     import torch

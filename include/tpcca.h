@@ -86,6 +86,11 @@ typedef struct {
   int32_t profile_stages;/* nonzero: record CUDA events between stages (tpc_tf_stage_times) */
   int32_t row_cap;       /* clusters per staged row in the neighbour kernel (0: largest that fits
                             shared memory); rows above it take the global-memory kernel */
+  int32_t n_sectors;     /* independent sectors per call (0: the TPC's 36).  A batched call packs
+                            many instances (one sector of one time frame each) into one call: the
+                            `sector` field of a cluster is then its instance id, < n_sectors <= 16384,
+                            and a track's `sector` output is that id.  More than 36 needs sorted input. */
+  int32_t nb_tile;       /* clusters per neighbour tile: 512, 768 or 1024 (0: 768); see tpc_tf_autotune */
 } tpc_tf_config;
 
 typedef struct {      /* input clusters: device pointers, read only, caller owned */
@@ -155,6 +160,26 @@ int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
  * Errors as for tpc_track_timeframe. */
 int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_clusters *cl, const tpc_tracks *out,
                                 void *stream);
+
+/* tpc_track_timeframe replayed from a CUDA graph (one graph launch per call; the
+ * paper has no counterpart).  The first call with a given pair of argument
+ * structs captures the call's kernels into a graph owned by the handle; a later
+ * call with byte-identical structs (same pointers, n, flags, capacities) and the
+ * same tile choice launches that graph; any other call recaptures.  The graph
+ * reads the buffers the structs point to at launch time, so the caller refills
+ * them between calls.  out->n_tracks_host must be NULL.  Errors as for
+ * tpc_track_timeframe; device-side errors surface through tpc_tf_status. */
+int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
+
+/* The project's autotuner (the paper has no counterpart): times the neighbour
+ * tile variants (512, 768, 1024 clusters per tile) and the two fit kernels on
+ * calls with `cl` and `out` (one untimed call, then the median of `trials`
+ * timed calls per variant), keeps the fastest choice in the handle and returns
+ * it in *nb_tile and *fit_variant (either may be NULL).  The results of a call
+ * do not depend on the choice.  Synchronises `stream`.  Errors as for
+ * tpc_track_timeframe; TPC_ERR_ARG for trials outside [1, 100]. */
+int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
+                    int32_t *nb_tile, int32_t *fit_variant);
 
 /* Synchronise `stream` and report the device-side status of the last call
  * (TPC_OK, TPC_ERR_INPUT, TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT). */

@@ -11,8 +11,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/tpcca.h"
 #include "mlp_dev.cuh"
@@ -45,7 +47,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct tpc_tf {
   tpc_tf_config cfg;
   int device = 0, sms = 0;
-  int nb_cap = 0;
+  int nsect = kNSect, nkeys = kNKeys, nb_tile = kNbTile;
   uint32_t tile_cap = 0;
   int32_t *tile_off = nullptr;
   int4 *tile_win = nullptr;
@@ -90,6 +92,13 @@ struct tpc_tf {
   float *mlp_stage = nullptr; // FP32 blob body staged for packing
   bool mlp_ready = false;
   float logit_tau = 0.f;
+  // CUDA graph of one call (tpc_track_timeframe_graph)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  tpc_clusters graph_cl;
+  tpc_tracks graph_out;
+  int graph_nb_tile = 0;
+  int graph_launches = 0;
 };
 
 extern "C" void tpc_default_config(tpc_tf_config *c) {
@@ -115,6 +124,8 @@ int tpc::report(int code, const char *msg) {
 
 static void free_all(tpc_tf *tf) {
   if (!tf) return;
+  if (tf->graph_exec) cudaGraphExecDestroy(tf->graph_exec);
+  if (tf->cap_stream) cudaStreamDestroy(tf->cap_stream);
   if (tf->arena) cudaFree(tf->arena);
   if (tf->mlp) cudaFree(tf->mlp);
   if (tf->pinned) cudaFreeHost(tf->pinned);
@@ -138,6 +149,10 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   if (cfg->mode == TPC_MODE_PRUNED && !(cfg->tau == cfg->tau)) return fail(TPC_ERR_ARG, "tpc_tf_create: tau is NaN");
   if (cfg->fit_variant != TPC_FIT_THREAD && cfg->fit_variant != TPC_FIT_WARP)
     return fail(TPC_ERR_ARG, "tpc_tf_create: unknown fit_variant");
+  if (cfg->n_sectors < 0 || cfg->n_sectors > 16384)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: n_sectors must be in [0, 16384]");
+  if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
   tpc_tf *tf = new tpc_tf();
   tf->cfg = *cfg;
   tf->device = cfg->device;
@@ -148,11 +163,11 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   }
   cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
-  // candidate windows staged in shared memory by the neighbour kernel; larger
-  // windows (or a smaller row_cap, used by tests) go through global memory
-  tf->nb_cap = kNbWin;
-  if (cfg->row_cap > 0 && cfg->row_cap < tf->nb_cap) tf->nb_cap = cfg->row_cap;
-  tf->tile_cap = neighbour_tiles_max(cfg->max_clusters);
+  tf->nsect = cfg->n_sectors ? cfg->n_sectors : kNSect;
+  tf->nkeys = tf->nsect * kNRows;
+  tf->nb_tile = cfg->nb_tile ? cfg->nb_tile : kNbTile;
+  // tiles for the smallest tile variant, so that the autotuner may pick any
+  tf->tile_cap = neighbour_tiles_max(cfg->max_clusters, tf->nkeys, kNbTileMin);
   tf->track_list_cap = cfg->max_tracks ? cfg->max_tracks : tf->N / (uint32_t)cfg->n_min + 1;
 
   const size_t N = tf->N;
@@ -161,8 +176,8 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     void **p;
     size_t bytes;
   } parts[] = {
-      {(void **)&tf->row_begin, (kNKeys + 1) * 4},
-      {(void **)&tf->tile_off, (kNKeys + 1) * 4},
+      {(void **)&tf->row_begin, (size_t)(tf->nkeys + 1) * 4},
+      {(void **)&tf->tile_off, (size_t)(tf->nkeys + 1) * 4},
       {(void **)&tf->tile_win, (size_t)tf->tile_cap * 2 * 16},
       {(void **)&tf->link, (N + 4) * 8},
       {(void **)&tf->mup16, (N + 16) * 2},
@@ -255,6 +270,8 @@ static void stage(tpc_tf *tf, cudaStream_t st, const char *name) {
 static int check_clusters(tpc_tf *tf, const tpc_clusters *cl, const char *who) {
   const uint32_t n = cl->n;
   if (n > tf->N) return fail(TPC_ERR_CAPACITY, "more clusters than max_clusters");
+  if (!(cl->flags & TPC_INPUT_SORTED) && tf->nsect > kNSect)
+    return fail(TPC_ERR_ARG, std::string(who) + ": more than 36 sectors need sorted input");
   if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time))
     return fail(TPC_ERR_ARG, std::string(who) + ": null cluster array");
   if (((uintptr_t)cl->pad & 3) || ((uintptr_t)cl->time & 3) || ((uintptr_t)cl->sector & 1) ||
@@ -287,6 +304,9 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.wt = tf->cfg.wt_q;
   a.cost_max = tf->cfg.cost_max_q;
   a.n_min = tf->cfg.n_min;
+  a.nsect = tf->nsect;
+  a.nkeys = tf->nkeys;
+  a.nb_tile = tf->nb_tile;
   a.amb = tf->amb;
   a.amb_cap = tf->amb ? tf->N + 4 : 0;
   a.mlp = tf->mlp;
@@ -342,7 +362,7 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   launch_row_index(a, st);
   launch_tile_windows(a, st);
   stage(tf, st, "ingest");
-  launch_neighbours(a, tf->nb_cap, st, prune);
+  launch_neighbours(a, tf->cfg.row_cap, st, prune);
   stage(tf, st, "neighbours");
   tf->launches += 3;
   if (prune) {
@@ -588,5 +608,108 @@ extern "C" int tpc_tf_pruned_clusters(tpc_tf *tf, uint32_t *n_region, uint32_t *
   TPC_CK(cudaStreamSynchronize(st));
   if (n_list) *n_list = tf->pinned[2];
   if (n_region) *n_region = tf->pinned[3];
+  return TPC_OK;
+}
+
+// ================================================================ graph replay
+extern "C" int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe_graph: null argument");
+  if (out->n_tracks_host)
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe_graph: n_tracks_host must be NULL (a graph does not synchronise)");
+  TPC_CK(cudaSetDevice(tf->device));
+  const bool same = tf->graph_exec && std::memcmp(&tf->graph_cl, cl, sizeof(*cl)) == 0 &&
+                    std::memcmp(&tf->graph_out, out, sizeof(*out)) == 0 && tf->graph_nb_tile == tf->nb_tile;
+  if (!same) {
+    if (tf->graph_exec) {
+      cudaGraphExecDestroy(tf->graph_exec);
+      tf->graph_exec = nullptr;
+    }
+    if (!tf->cap_stream) TPC_CK(cudaStreamCreateWithFlags(&tf->cap_stream, cudaStreamNonBlocking));
+    const int prof = tf->cfg.profile_stages;
+    tf->cfg.profile_stages = 0;  // no event records inside the graph
+    TPC_CK(cudaStreamBeginCapture(tf->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = tpc_track_timeframe(tf, cl, out, tf->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(tf->cap_stream, &graph);
+    tf->cfg.profile_stages = prof;
+    if (rc != TPC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(TPC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&tf->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(TPC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    tf->graph_cl = *cl;
+    tf->graph_out = *out;
+    tf->graph_nb_tile = tf->nb_tile;
+    tf->graph_launches = tf->launches;
+  }
+  TPC_CK(cudaGraphLaunch(tf->graph_exec, (cudaStream_t)stream));
+  tf->launches = tf->graph_launches;
+  return TPC_OK;
+}
+
+// ================================================================ autotuner
+extern "C" int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
+                               int32_t *nb_tile, int32_t *fit_variant) {
+  g_err.clear();
+  if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_tf_autotune: null argument");
+  if (trials < 1 || trials > 100) return fail(TPC_ERR_ARG, "tpc_tf_autotune: trials must be in [1, 100]");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  tpc_tracks o = *out;
+  o.n_tracks_host = nullptr;
+  cudaEvent_t e0, e1;
+  TPC_CK(cudaEventCreate(&e0));
+  TPC_CK(cudaEventCreate(&e1));
+  // median time of `trials` calls (after one untimed call) with the handle's current choice
+  auto time_calls = [&](float *ms) -> int {
+    std::vector<float> v;
+    for (int k = 0; k <= trials; ++k) {
+      cudaEventRecord(e0, st);
+      const int rc = tpc_track_timeframe(tf, cl, &o, st);
+      if (rc != TPC_OK) return rc;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return fail(TPC_ERR_CUDA, "tpc_tf_autotune: synchronise");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (k > 0) v.push_back(t);
+    }
+    std::sort(v.begin(), v.end());
+    *ms = v[v.size() / 2];
+    return tpc_tf_status(tf, stream);
+  };
+  int rc = TPC_OK;
+  const int tiles[3] = {512, 768, 1024};
+  int best_tile = tf->nb_tile;
+  float best = 1e30f;
+  for (int t : tiles) {
+    tf->nb_tile = t;
+    float ms = 0.f;
+    rc = time_calls(&ms);
+    if (rc != TPC_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_tile = t;
+    }
+  }
+  tf->nb_tile = best_tile;
+  int best_fit = tf->cfg.fit_variant;
+  if (rc == TPC_OK) {
+    float fit_ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && rc == TPC_OK; ++v) {
+      tf->cfg.fit_variant = v;
+      rc = time_calls(&fit_ms[v]);
+    }
+    best_fit = fit_ms[1] < fit_ms[0] ? TPC_FIT_WARP : TPC_FIT_THREAD;
+    tf->cfg.fit_variant = best_fit;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TPC_OK) return rc;
+  if (nb_tile) *nb_tile = best_tile;
+  if (fit_variant) *fit_variant = best_fit;
   return TPC_OK;
 }

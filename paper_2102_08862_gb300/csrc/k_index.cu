@@ -41,12 +41,12 @@ __device__ __forceinline__ uint32_t warp_lower_bound_key(const uint16_t *sector,
 __global__ void __launch_bounds__(256) k_row_index(Args a) {
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp <= kNKeys) {
+  if (warp <= a.nkeys) {
     const uint32_t r = warp_lower_bound_key(a.sector, a.row, a.n, warp);
     if (lane == 0) {
       a.row_begin[warp] = (int32_t)r;
-      // clusters with a key >= 36*152 sit after row_begin[kNKeys]: invalid input
-      if (warp == kNKeys && r != a.n) raise(a.ctr, kErrInput);
+      // clusters with a key >= nsect*152 sit after row_begin[nkeys]: invalid input
+      if (warp == a.nkeys && r != a.n) raise(a.ctr, kErrInput);
     }
   }
   // the last block to finish computes the largest row and checks monotonicity
@@ -64,15 +64,16 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
   // largest row, monotonicity, and the first neighbour tile of every row
   // (each thread owns a contiguous block of keys; block-wide exclusive scan)
   const volatile int32_t *rbv = a.row_begin;
-  const int per = (kNKeys + blockDim.x - 1) / blockDim.x;
-  const int k0 = threadIdx.x * per, k1 = min(kNKeys, k0 + per);
+  const int nkeys = a.nkeys, tile = a.nb_tile;
+  const int per = (nkeys + blockDim.x - 1) / blockDim.x;
+  const int k0 = threadIdx.x * per, k1 = min(nkeys, k0 + per);
   int mx = 0, ntile = 0;
   for (int k = k0; k < k1; ++k) {
     const int32_t b = rbv[k], e = rbv[k + 1];
     if (e < b) raise(a.ctr, kErrInput);
     const int c = max(0, e - b);
     mx = max(mx, c);
-    ntile += (c + kNbTile - 1) / kNbTile;
+    ntile += (c + tile - 1) / tile;
   }
   __shared__ int s_scan[256];
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -88,10 +89,10 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
   int off = s_scan[threadIdx.x] - ntile;
   for (int k = k0; k < k1; ++k) {
     a.tile_off[k] = off;
-    off += (max(0, rbv[k + 1] - rbv[k]) + kNbTile - 1) / kNbTile;
+    off += (max(0, rbv[k + 1] - rbv[k]) + tile - 1) / tile;
   }
   if (threadIdx.x == blockDim.x - 1) {
-    a.tile_off[kNKeys] = s_scan[threadIdx.x];
+    a.tile_off[nkeys] = s_scan[threadIdx.x];
     a.ctr[kCtrTiles] = (uint32_t)s_scan[threadIdx.x];
     if ((uint32_t)s_scan[threadIdx.x] > a.tile_cap) raise(a.ctr, kErrInternal);
   }
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
 }
 
 void launch_row_index(const Args &a, cudaStream_t st) {
-  const int warps = kNKeys + 1;
+  const int warps = a.nkeys + 1;
   const int blocks = (warps * 32 + 255) / 256;
   k_row_index<<<blocks, 256, 0, st>>>(a);
 }

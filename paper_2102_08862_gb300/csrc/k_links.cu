@@ -53,8 +53,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 }
 
 // last key with rb[key] <= i
-__device__ __forceinline__ int key_of(const int32_t *rb, int i) {
-  int lo = 0, hi = kNKeys;
+__device__ __forceinline__ int key_of(const int32_t *rb, int i, int nkeys) {
+  int lo = 0, hi = nkeys;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (rb[mid] <= i) lo = mid; else hi = mid;
@@ -64,11 +64,19 @@ __device__ __forceinline__ int key_of(const int32_t *rb, int i) {
 }  // namespace
 
 // A2 + A3: mup[i] = up[i] if down[up[i]] = i; start(i) = no mutual down, a mutual up.
+// The row table rb (row_begin) sits in shared memory for up to 36 sectors and is
+// read through the L1 cache for batched calls with more.
+template <bool kSmemRb>
 __global__ void __launch_bounds__(kThreads) k_links(Args a) {
-  __shared__ int32_t s_rb[kNKeys + 1];
+  __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
-  for (int k = threadIdx.x; k <= kNKeys; k += kThreads) s_rb[k] = a.row_begin[k];
+  const int nkeys = a.nkeys;
+  const int32_t *rb = a.row_begin;
+  if constexpr (kSmemRb) {
+    for (int k = threadIdx.x; k <= nkeys; k += kThreads) s_rb[k] = a.row_begin[k];
+    rb = s_rb;
+  }
   const uint32_t n = a.n;
   const uint32_t n_tiles = (n + kLinkTile - 1) / kLinkTile;
   const uint64_t keep = l2_keep_policy();
@@ -79,25 +87,25 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
     const int i0 = (int)(tile * kLinkTile + threadIdx.x * kItems);
-    int key = i0 < (int)n ? key_of(s_rb, i0) : 0;
+    int key = i0 < (int)n ? key_of(rb, i0, nkeys) : 0;
     uint32_t flags = 0;
     uint16_t m16[kItems];
-    int16_t skey[kItems];
+    int32_t skey[kItems];
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
       const int i = i0 + q;
       m16[q] = kNone16;
       skey[q] = 0;
       if (i >= (int)n) continue;
-      while (key < kNKeys - 1 && i >= s_rb[key + 1]) ++key;
+      while (key < nkeys - 1 && i >= rb[key + 1]) ++key;
       const int2 l = __ldcs(a.link + i);
       const int32_t mup = (l.y >= 0 && a.link[l.y].x == i) ? l.y : -1;
       const int32_t mdn = (l.x >= 0 && a.link[l.x].y == i) ? l.x : -1;
       if (mup >= 0) {
-        const int d = mup - s_rb[key + 1];
+        const int d = mup - rb[key + 1];
         if (d < 0 || d >= kNone16) bad = true; else m16[q] = (uint16_t)d;
       }
-      skey[q] = (int16_t)key;
+      skey[q] = key;
       if (mdn < 0 && mup >= 0) flags |= 1u << q;
       if (mdn < 0 && mup < 0) a.cluster_track[caller_index(a, i)] = -1;
     }
@@ -136,8 +144,9 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
 // chains are in flight.  Chains that reach n_min clusters become tracks (ids in
 // start order); their clusters get the track id and are recorded in the chain
 // buffer; the clusters of shorter chains get -1.
+template <bool kSmemRb>
 __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
-  __shared__ int32_t s_rb[kNKeys + 1];
+  __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
   const uint32_t ns = min(a.ctr[kCtrStarts], a.starts_cap);
@@ -149,7 +158,11 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
     }
     return;
   }
-  for (int k = threadIdx.x; k <= kNKeys; k += kThreads) s_rb[k] = a.row_begin[k];
+  const int32_t *rb = a.row_begin;
+  if constexpr (kSmemRb) {
+    for (int k = threadIdx.x; k <= a.nkeys; k += kThreads) s_rb[k] = a.row_begin[k];
+    rb = s_rb;
+  }
   const int n_min = a.n_min;
   const size_t stride = a.track_list_cap;
   const uint64_t keep = l2_keep_policy();
@@ -159,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
     if (m == kNone16) {
       c = -1;
     } else {
-      c = s_rb[key + 1] + m;
+      c = rb[key + 1] + m;
       ++key;
     }
   };
@@ -235,7 +248,7 @@ __global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
     const int key = (int)a.sector[i] * kNRows + a.row[i];
     const uint16_t m = a.mup16[i];
-    const int32_t up = (m == kNone16 || key + 1 > kNKeys) ? -1 : a.row_begin[key + 1] + m;
+    const int32_t up = (m == kNone16 || key + 1 > a.nkeys) ? -1 : a.row_begin[key + 1] + m;
     if (mup) mup[i] = up;
     if (is_start) {
       const int dn = a.link[i].x;
@@ -248,10 +261,14 @@ __global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
 void launch_links(const Args &a, int sms, cudaStream_t st) {
   const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
   const uint32_t grid = tiles < (uint32_t)sms * 4u ? (tiles ? tiles : 1u) : (uint32_t)sms * 4u;
-  k_links<<<grid, kThreads, 0, st>>>(a);
+  if (a.nkeys <= kNKeys) k_links<true><<<grid, kThreads, 0, st>>>(a);
+  else k_links<false><<<grid, kThreads, 0, st>>>(a);
 }
 
-void launch_walk(const Args &a, int sms, cudaStream_t st) { k_walk<<<sms * 8, kThreads, 0, st>>>(a); }
+void launch_walk(const Args &a, int sms, cudaStream_t st) {
+  if (a.nkeys <= kNKeys) k_walk<true><<<sms * 8, kThreads, 0, st>>>(a);
+  else k_walk<false><<<sms * 8, kThreads, 0, st>>>(a);
+}
 
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st) {
   k_debug_links<<<1024, 256, 0, st>>>(a, mup, is_start);

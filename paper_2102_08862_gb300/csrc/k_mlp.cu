@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) k_mlp_extract(Args a, float *__restrict__
                                                      uint32_t *__restrict__ count) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
     const int s = a.sector[i], r = a.row[i];
-    if (r < 1 || r > kNRows - 2 || s >= kNSect) continue;
+    if (r < 1 || r > kNRows - 2 || s >= a.nsect) continue;
     if (!pad_ok(a.pad[i]) || !time_ok(a.time[i])) continue;
     const int2 ci = ty_of(a, i, r);
     const int ti = ci.x, yi = ci.y;

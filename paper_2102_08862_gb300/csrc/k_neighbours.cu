@@ -9,7 +9,7 @@
 // when the residual is <= cost_max; ties go to the smaller row-local j, then k.
 // All of it is integer arithmetic in 1/64 um units, so results are exact.
 //
-// GB300 design: every (sector, row) is cut into tiles of kNbTile clusters.  The
+// GB300 design: every (sector, row) is cut into tiles of nb_tile clusters.  The
 // tile-window kernel finds, for each tile, the clusters of rows r-1 and r+1 whose
 // time lies within wt of the tile's time span (binary searches, all tiles in
 // parallel).  The neighbour kernel gives each tile one CTA: it validates and
@@ -36,7 +36,7 @@ constexpr int kMaxCand = 4;  // candidates per neighbour row kept in registers
 // do not fit, go to the global list.
 constexpr int kPruneMaxPairs = 32;
 struct NbQueue {
-  uint32_t pairs[4][kNbThreads];  // a thread's first four pairs under the cut (j | k << 11)
+  uint32_t pairs[4][256];  // a thread's first four pairs under the cut (j | k << 11); <= 256 threads
   int count, end;
 };
 template <bool kPrune> struct NbExtra {};
@@ -334,15 +334,15 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
   const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
     // key = last (sector, row) whose first tile is <= t
-    int lo = 0, hi = kNKeys;
+    int lo = 0, hi = a.nkeys;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (a.tile_off[mid] <= (int)t) lo = mid; else hi = mid;
     }
     const int key = lo, r = key % kNRows;
     const int rb = a.row_begin[key], re = a.row_begin[key + 1];
-    const int ta = rb + ((int)t - a.tile_off[key]) * kNbTile;
-    const int tb = min(re, ta + kNbTile);
+    const int ta = rb + ((int)t - a.tile_off[key]) * a.nb_tile;
+    const int tb = min(re, ta + a.nb_tile);
     int4 win = make_int4(0, 0, 0, 0);
     if (r >= 1 && r <= kNRows - 2 && tb > ta) {
       const int t0 = q64(sane_time(a.time[ta])), t1 = q64(sane_time(a.time[tb - 1]));
@@ -360,9 +360,10 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 }
 
 // ------------------------------------------------------------ neighbours
-template <bool kPrune>
-__global__ void __launch_bounds__(kNbThreads, kPrune ? 6 : 0) k_neighbours(Args a, int win_cap) {
-  __shared__ int2 s_c[kNbTile], s_p[kNbWin], s_n[kNbWin];  // quantised (t, y)
+template <bool kPrune, int TILE, int WIN, int THREADS>
+__global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 0) k_neighbours(Args a, int win_cap) {
+  static_assert(WIN < 2048 && TILE % THREADS == 0 && THREADS <= 256, "window indices are packed in 11 bits");
+  __shared__ int2 s_c[TILE], s_p[WIN], s_n[WIN];  // quantised (t, y)
   __shared__ NbExtra<kPrune> ex;
   const uint32_t t = blockIdx.x;
   if (t >= min(a.ctr[kCtrTiles], a.tile_cap)) return;
@@ -377,8 +378,8 @@ __global__ void __launch_bounds__(kNbThreads, kPrune ? 6 : 0) k_neighbours(Args 
   {
     const int half = 32 * (row_npads(r) - 1), pitch = row_pitch_um(r);
 #pragma unroll
-    for (int q = 0; q < kNbTile / kNbThreads; ++q) {
-      const int e = tid + q * kNbThreads;
+    for (int q = 0; q < TILE / THREADS; ++q) {
+      const int e = tid + q * THREADS;
       if (e >= cnt) break;
       const int gi = ta + e;
       float p = a.pad[gi], tt = a.time[gi];
@@ -412,11 +413,11 @@ __global__ void __launch_bounds__(kNbThreads, kPrune ? 6 : 0) k_neighbours(Args 
   const int half_p = 32 * (row_npads(r - 1) - 1), pitch_p = row_pitch_um(r - 1);
   const int half_n = 32 * (row_npads(r + 1) - 1), pitch_n = row_pitch_um(r + 1);
   if (staged) {
-    constexpr int kPer = (kNbWin + kNbThreads - 1) / kNbThreads;
+    constexpr int kPer = (WIN + THREADS - 1) / THREADS;
     float pp[kPer], tp[kPer], pn[kPer], tn[kPer];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {  // issue all loads first
-      const int e = tid + q * kNbThreads;
+      const int e = tid + q * THREADS;
       if (e < np) {
         pp[q] = a.pad[w.x + e];
         tp[q] = a.time[w.x + e];
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(kNbThreads, kPrune ? 6 : 0) k_neighbours(Args 
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-      const int e = tid + q * kNbThreads;
+      const int e = tid + q * THREADS;
       if (e < np) s_p[e] = quant_ty(sane_pad(pp[q]), sane_time(tp[q]), half_p, pitch_p);
       if (e < nn) s_n[e] = quant_ty(sane_pad(pn[q]), sane_time(tn[q]), half_n, pitch_n);
     }
@@ -497,15 +498,24 @@ __global__ void __launch_bounds__(256) k_edge_claims(Args a) {
 
 // ------------------------------------------------------------------ launchers
 void launch_tile_windows(const Args &a, cudaStream_t st) {
-  const uint32_t tiles = neighbour_tiles_max(a.n);
+  const uint32_t tiles = neighbour_tiles_max(a.n, a.nkeys, a.nb_tile);
   k_tile_windows<<<(tiles + 255) / 256, 256, 0, st>>>(a);
 }
 
-void launch_neighbours(const Args &a, int win_cap, cudaStream_t st, bool prune) {
-  if (prune) k_neighbours<true><<<neighbour_tiles_max(a.n), kNbThreads, 0, st>>>(a, win_cap);
-  else k_neighbours<false><<<neighbour_tiles_max(a.n), kNbThreads, 0, st>>>(a, win_cap);
+template <int TILE, int WIN>
+static void launch_nb(const Args &a, int row_cap, cudaStream_t st, bool prune) {
+  const int cap = row_cap > 0 && row_cap < WIN ? row_cap : WIN;
+  const uint32_t grid = neighbour_tiles_max(a.n, a.nkeys, TILE);
+  if (prune) k_neighbours<true, TILE, WIN, 256><<<grid, 256, 0, st>>>(a, cap);
+  else k_neighbours<false, TILE, WIN, 256><<<grid, 256, 0, st>>>(a, cap);
 }
 
-void launch_edge_claims(const Args &a, cudaStream_t st) { k_edge_claims<<<dim3(32, 2 * kNSect), 256, 0, st>>>(a); }
+void launch_neighbours(const Args &a, int row_cap, cudaStream_t st, bool prune) {
+  if (a.nb_tile == 512) launch_nb<512, 896>(a, row_cap, st, prune);
+  else if (a.nb_tile == 1024) launch_nb<1024, 1664>(a, row_cap, st, prune);
+  else launch_nb<768, 1280>(a, row_cap, st, prune);
+}
+
+void launch_edge_claims(const Args &a, cudaStream_t st) { k_edge_claims<<<dim3(32, 2 * a.nsect), 256, 0, st>>>(a); }
 
 }  // namespace tpc

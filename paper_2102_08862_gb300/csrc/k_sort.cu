@@ -165,13 +165,15 @@ size_t sort_scratch_bytes(uint32_t max_n) { return (size_t)(3 * 5504 + max_n + 4
 int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,
                 size_t scratch_bytes, int sms, cudaStream_t st) {
-  static bool configured = false;
+  static bool configured[64] = {};  // per device: the attribute is a per-device property
   const size_t smem = (size_t)kSegCap * (8 + 4);
-  if (!configured) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
     if (cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return -1;
-    configured = true;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   if (scratch_bytes < sort_scratch_bytes(a.n)) return -1;
   SortScratch s = carve(scratch, a.n);

@@ -75,7 +75,10 @@ size_t carve(unsigned char *base, uint32_t n, uint32_t list_cap, Args *a, size_t
   a->lb_keep = a->lb_links ? a->lb_links + tiles_l : nullptr;
   a->row_begin = reinterpret_cast<int32_t *>(take((kNKeys + 1) * 4));
   a->tile_off = reinterpret_cast<int32_t *>(take((kNKeys + 1) * 4));
-  a->tile_cap = neighbour_tiles_max(n);
+  a->nsect = kNSect;
+  a->nkeys = kNKeys;
+  a->nb_tile = kNbTile;
+  a->tile_cap = neighbour_tiles_max(n, kNKeys, kNbTile);
   a->tile_win = reinterpret_cast<int4 *>(take((size_t)a->tile_cap * 32));
   a->link = reinterpret_cast<int2 *>(take(((size_t)n + 4) * 8));
   a->mup16 = reinterpret_cast<uint16_t *>(take(((size_t)n + 16) * 2));
@@ -158,7 +161,7 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
     return report(TPC_ERR_CUDA, "tpc_track_timeframe_noalloc: clearing the counters failed");
   launch_row_index(a, st);
   launch_tile_windows(a, st);
-  launch_neighbours(a, kNbWin, st);
+  launch_neighbours(a, 0, st);
   launch_edge_claims(a, st);
   launch_links(a, sms, st);
   launch_walk(a, sms, st);

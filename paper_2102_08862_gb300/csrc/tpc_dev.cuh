@@ -109,6 +109,9 @@ struct Args {
   int32_t wy, wt;
   int64_t cost_max;
   int32_t n_min;
+  int32_t nsect, nkeys;  // independent sectors of this call (36 for one TPC frame; one per instance
+                         // in a batched call) and their (sector, row) keys, nsect * 152
+  int32_t nb_tile;       // clusters per neighbour tile
   // outputs
   int32_t *cluster_track;
   uint32_t track_capacity;

@@ -6,13 +6,16 @@
 
 namespace tpc {
 
-// neighbour kernel: rows are cut into tiles of kNbTile clusters; a CTA of
-// kNbThreads stages its tile and the matching time windows of rows r-1 and r+1
-// (up to kNbWin clusters each, more goes through global memory)
+// neighbour kernel: rows are cut into tiles of nb_tile clusters; a CTA stages its
+// tile and the matching time windows of rows r-1 and r+1 (up to the variant's
+// window capacity each, more goes through global memory).  Variants (tile,
+// window, threads): (512, 896, 256), (768, 1280, 256), (1024, 1664, 256); the
+// default is 768, the autotuner may pick another.
 constexpr int kNbThreads = 256;
 constexpr int kNbTile = 768;
 constexpr int kNbWin = 1280;
-static_assert(kNbWin < 2048 && kNbTile % kNbThreads == 0, "window indices are packed in 11 bits");
+constexpr int kNbTileMin = 512;
+inline bool nb_tile_ok(int t) { return t == 512 || t == 768 || t == 1024; }
 // look-back tiles: clusters per tile of the link kernel, start hits per tile of the walk
 constexpr int kLinkTileN = 2048;
 constexpr int kWalkTileN = 512;  // 256 threads, two chains each
@@ -20,12 +23,13 @@ inline size_t link_tiles(uint32_t n) { return (n + kLinkTileN - 1) / kLinkTileN;
 inline size_t walk_tiles(uint32_t n) { return (n / 2 + 1 + kWalkTileN - 1) / kWalkTileN; }
 
 // upper bound of neighbour tiles for n clusters
-inline uint32_t neighbour_tiles_max(uint32_t n) { return n / kNbTile + kNKeys + 1; }
+inline uint32_t neighbour_tiles_max(uint32_t n, int nkeys, int tile) { return n / (uint32_t)tile + (uint32_t)nkeys + 1; }
 
 void launch_row_index(const Args &a, cudaStream_t st);
 void launch_tile_windows(const Args &a, cudaStream_t st);
 // prune = true also lists the clusters with >= 2 pairs under the cost cut in a.amb
-void launch_neighbours(const Args &a, int win_cap, cudaStream_t st, bool prune = false);
+// row_cap > 0 lowers the staged window capacity (tests of the global-memory path)
+void launch_neighbours(const Args &a, int row_cap, cudaStream_t st, bool prune = false);
 void launch_edge_claims(const Args &a, cudaStream_t st);
 void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);

@@ -33,7 +33,8 @@ ERROR_NAMES = {0: "TPC_OK", -1: "TPC_ERR_ARG", -2: "TPC_ERR_CAPACITY", -3: "TPC_
 class tpc_tf_config(ctypes.Structure):
     _fields_ = [("max_clusters", c_u32), ("max_tracks", c_u32), ("wy_q", c_i32), ("wt_q", c_i32),
                 ("cost_max_q", c_i64), ("n_min", c_i32), ("mode", c_i32), ("tau", c_f32), ("device", c_i32),
-                ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32)]
+                ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32), ("n_sectors", c_i32),
+                ("nb_tile", c_i32)]
 
 
 class tpc_clusters(ctypes.Structure):
@@ -93,6 +94,10 @@ def load():
     lib.tpc_tf_stage_times.restype = ctypes.c_int
     lib.tpc_tf_launches_per_call.argtypes = [c_vp]
     lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    lib.tpc_track_timeframe_graph.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
+    lib.tpc_track_timeframe_graph.restype = ctypes.c_int
+    lib.tpc_tf_autotune.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), ctypes.c_int, c_vp, P(c_i32), P(c_i32)]
+    lib.tpc_tf_autotune.restype = ctypes.c_int
     sz = ctypes.c_size_t
     lib.tpc_mlp_blob_bytes.argtypes = []
     lib.tpc_mlp_blob_bytes.restype = sz
@@ -189,6 +194,18 @@ def tpc_tf_stage_times(handle, cap: int = 16):
 
 def tpc_tf_launches_per_call(handle) -> int:
     return load().tpc_tf_launches_per_call(handle)
+
+
+def tpc_track_timeframe_graph(handle, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:
+    return load().tpc_track_timeframe_graph(handle, ctypes.byref(clusters), ctypes.byref(tracks), stream)
+
+
+def tpc_tf_autotune(handle, clusters: tpc_clusters, tracks: tpc_tracks, trials: int = 3, stream: int = 0):
+    """(nb_tile, fit_variant) chosen by the autotuner (kept in the handle)."""
+    t, f = c_i32(0), c_i32(0)
+    _check(load().tpc_tf_autotune(handle, ctypes.byref(clusters), ctypes.byref(tracks), trials, stream,
+                                  ctypes.byref(t), ctypes.byref(f)))
+    return int(t.value), int(f.value)
 
 
 def tpc_mlp_blob_bytes() -> int:
@@ -425,6 +442,20 @@ class TimeFrameTracker:
                       t_ref=o["t_ref"][:m], x=o["x"][:m], chi2=o["chi2"][:m], ndf=o["ndf"][:m],
                       nhits=o["nhits"][:m], first_cluster=o["first_cluster"][:m], sector=o["sector"][:m],
                       row_first=o["row_first"][:m], row_last=o["row_last"][:m], status=o["status"][:m])
+
+    def track_graph(self, sector, row, pad, time, sorted_input=True, capacity=None, stream=None):
+        """tpc_track_timeframe_graph on device tensors; returns the device track count
+        tensor (nothing is synchronised)."""
+        t = self.torch
+        st = stream if stream is not None else t.cuda.current_stream(self.device)
+        cl, tr, n, cap = self.structs(sector, row, pad, time, sorted_input, capacity, host_count=None)
+        _check(tpc_track_timeframe_graph(self.handle, cl, tr, st.cuda_stream))
+        self._n = n
+        return self._out["n_tracks"]
+
+    def autotune(self, sector, row, pad, time, sorted_input=True, capacity=None, trials=3):
+        cl, tr, n, cap = self.structs(sector, row, pad, time, sorted_input, capacity, host_count=None)
+        return tpc_tf_autotune(self.handle, cl, tr, trials, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def debug_links(self, stream=None):
         t = self.torch

@@ -121,3 +121,27 @@ def test_c2_size_and_pt_distribution():
     assert ks.pvalue > 1e-3
     eta = f.trk_eta
     assert eta.min() >= -0.9 and eta.max() <= 0.9
+
+
+def test_batched_instances():
+    """Batched workload: one sector id per instance, each instance sorted, counts
+    spread over the log-uniform range, the rate rescaled per instance."""
+    b = ts.batched(30, seed=11, n_min=2e3, n_max=2e5, ms_min=0.2, ms_max=3.0)
+    f, off = b.frame, b.offsets
+    assert off[0] == 0 and off[-1] == f.n and np.all(np.diff(off) > 0)
+    for k in range(30):
+        a, e = off[k], off[k + 1]
+        assert np.all(f.sector[a:e] == k)
+        r, t = f.row[a:e].astype(np.int64), f.time[a:e]
+        assert np.all(np.diff(r) >= 0)
+        same_row = np.diff(r) == 0
+        assert np.all(np.diff(t)[same_row] >= 0)
+    sz = np.diff(off)
+    assert sz.max() / sz.min() > 10
+    # expected counts follow the rescaled rate: the median lies inside the drawn range
+    assert 2e3 / 3 < np.median(sz) < 2e5 * 3
+    # labels of different instances never collide
+    lab = f.label[f.label >= 0]
+    inst = f.sector[f.label >= 0]
+    for k in range(29):
+        assert lab[inst == k].max(initial=-1) < lab[inst == k + 1].min(initial=2**31 - 1)

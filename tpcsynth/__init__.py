@@ -210,3 +210,53 @@ def c2(seed: int = 2) -> TGConfig:
 def c3(seed: int = 3) -> TGConfig:
     """36 sectors, 10 ms continuous frame (~500 collisions)."""
     return continuous(10.0, seed)
+
+
+# clusters per sector per ms at 50 kHz in this generator (10 ms frame, seed 3: 31.96M / 36 / 10)
+CLUSTERS_PER_SECTOR_MS_50KHZ = 8.88e4
+
+
+@dataclass
+class Batch:
+    """Many independent (sector x time frame) instances packed for one batched call:
+    `frame.sector` holds the instance id; instance k occupies clusters
+    [offsets[k], offsets[k+1]) and came from sector `src_sector[k]` of a frame of
+    `length_ms[k]` at `rate_khz[k]` (seed `seeds[k]`)."""
+    frame: Frame
+    offsets: np.ndarray
+    length_ms: np.ndarray
+    rate_khz: np.ndarray
+    seeds: np.ndarray
+    src_sector: np.ndarray
+
+
+def batched(n_inst: int = 256, seed: int = 4, n_min: float = 1e4, n_max: float = 2e6, ms_min: float = 0.2,
+            ms_max: float = 10.0) -> Batch:
+    """Instances with cluster counts log-uniform in [n_min, n_max] and frame lengths
+    uniform in [ms_min, ms_max]: each is one sector of its own continuous frame whose
+    collision rate is rescaled from 50 kHz so that the expected count is the drawn one."""
+    rng = np.random.default_rng(seed)
+    target = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_inst))
+    length = rng.uniform(ms_min, ms_max, n_inst)
+    rate = 50.0 * target / (CLUSTERS_PER_SECTOR_MS_50KHZ * length)
+    seeds = seed * 1_000_003 + np.arange(n_inst, dtype=np.int64)
+    parts, offsets, labels_off = [], [0], 0
+    src = np.arange(n_inst) % 36
+    for k in range(n_inst):
+        c = continuous(float(length[k]), int(seeds[k]))
+        c.rate_khz = float(rate[k])
+        c.sector_only = int(src[k])
+        f = generate(c)
+        f.sector = np.full(f.n, k, np.uint16)
+        f.label = np.where(f.label >= 0, f.label + labels_off, -1).astype(np.int32)
+        labels_off += f.trk_qpt.shape[0]
+        parts.append(f)
+        offsets.append(offsets[-1] + f.n)
+    cat = lambda name, dt: np.concatenate([getattr(p, name) for p in parts]).astype(dt)
+    frame = Frame(sector=cat("sector", np.uint16), row=cat("row", np.uint16), pad=cat("pad", np.float32),
+                  time=cat("time", np.float32), label=cat("label", np.int32), trk_qpt=cat("trk_qpt", np.float64),
+                  trk_phi0=cat("trk_phi0", np.float64), trk_eta=cat("trk_eta", np.float64),
+                  trk_t0=cat("trk_t0", np.float64), trk_collision=cat("trk_collision", np.int32),
+                  n_collisions=int(sum(p.n_collisions for p in parts)), frame_bins=float(max(p.frame_bins for p in parts)))
+    return Batch(frame=frame, offsets=np.array(offsets, np.int64), length_ms=length, rate_khz=rate, seeds=seeds,
+                 src_sector=src)
