@@ -244,15 +244,103 @@ def run_batched(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args, rank, world):
+    """c5: time frames of 2-12 ms arriving Poisson at 80 % of the measured capacity,
+    served by the library's runtime (slots admitted by free HBM within 180 GiB,
+    state device-resident, learned-pruned CA); p50/p99 latency and clusters/s."""
+    import torch
+    import tpcsynth as ts
+    from paper_2102_08862_gb300 import _build, tpcca
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    _build.build()
+    rng = np.random.default_rng(5 + 1000 * rank)
+    lengths = rng.uniform(2.0, 12.0, 6)
+    pool = []
+    for k, ms in enumerate(lengths):
+        f = ts.generate(ts.continuous(float(ms), 5000 + 1000 * rank + k))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pool.append((pin(f.sector.view(np.int16)), pin(f.row.view(np.int16)), pin(f.pad), pin(f.time), f.n))
+    blob, tau = classifier()
+    srv = tpcca.Server(budget_bytes=180 << 30, max_slots=4, device=dev, mlp_blob=blob,
+                       mode=tpcca.TPC_MODE_PRUNED, tau=tau)
+
+    def drain(expected, done, deadline=300.0):
+        t_end = time.time() + deadline
+        while len(done) < expected:
+            if time.time() > t_end:
+                raise RuntimeError("server did not finish in time")
+            for r, _ in srv.poll(wait_ms=200):
+                if r["status"] != 0:
+                    raise RuntimeError(f"request failed: {r['status']} {tpcca.tpc_last_error()}")
+                done.append(r)
+        return done
+
+    # warm-up: every pool frame once (creates the slots)
+    for fr in pool:
+        srv.submit(*fr[:4])
+    drain(len(pool), [])
+    # capacity: a burst of requests all queued at once
+    burst = [pool[k % len(pool)] for k in range(max(12, args.steps))]
+    t0 = time.perf_counter()
+    for fr in burst:
+        srv.submit(*fr[:4])
+    done = drain(len(burst), [])
+    span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done)
+    cap_fps = len(burst) / span
+    cap_cps = sum(fr[4] for fr in burst) / span
+    # Poisson arrivals at 80 % of the capacity
+    lam = 0.8 * cap_fps
+    n_req = max(40, 2 * args.steps)
+    gaps = rng.exponential(1.0 / lam, n_req)
+    picks = rng.integers(0, len(pool), n_req)
+    done, clusters = [], 0
+    t_start = time.perf_counter()
+    next_t = t_start
+    for k in range(n_req):
+        next_t += gaps[k]
+        while time.perf_counter() < next_t:
+            wait = max(0.0, next_t - time.perf_counter())
+            for r, _ in srv.poll(wait_ms=int(wait * 1000)):
+                done.append(r)
+        fr = pool[picks[k]]
+        srv.submit(*fr[:4])
+        clusters += fr[4]
+    drain(n_req, done)
+    st = srv.stats()
+    srv.close()
+    if rank != 0:
+        return
+    lat = np.array([r["t_done"] - r["t_submit"] for r in done]) * 1e3
+    queue = np.array([r["t_start"] - r["t_submit"] for r in done]) * 1e3
+    span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done)
+    out = {"metric": METRIC, "value": clusters / span, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": len(pool),
+           "ms_per_step": 1e3 * span / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "int64+bf16+f32", "data": "synthetic",
+           "config": {"workload": f"c5: {n_req} requests, frames of 2-12 ms ({', '.join(f'{x:.1f}' for x in lengths)} ms "
+                                  f"pool, {sum(fr[4] for fr in pool)} clusters), Poisson at 80 % of the measured "
+                                  f"capacity ({cap_fps:.1f} frames/s), host buffers (pinned), seed 5",
+                      "mode": f"learned-pruned CA (tau {tau})", "server": "180 GiB budget, up to 4 slots",
+                      "parallelism": f"replicas x{world}"},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "queue_p50": float(np.percentile(queue, 50))},
+           "capacity": {"frames_per_s": cap_fps, "clusters_per_s": cap_cps},
+           "arrival_rate_per_s": lam, "slots": st["slots"], "slot_bytes": st["bytes"],
+           "e2e": {"value": clusters / span, "unit": UNIT, "h2d_bytes_per_step": int(12 * clusters / n_req),
+                   "d2h_bytes_per_step": int(4 * clusters / n_req)}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3half", "c4"],
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3half", "c4", "c5"],
                     help="c3: the 10 ms frame; c3half: its first 5 ms (profiler captures); c1, c2: smaller "
-                         "cases; c4: 256 sector x time-frame instances in one batched, graph-replayed call")
+                         "cases; c4: 256 sector x time-frame instances in one batched, graph-replayed call; "
+                         "c5: the serving loop under Poisson arrivals")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-variant", type=int, default=0)
@@ -269,6 +357,9 @@ def main():
         return
     if args.workload == "c4":
         run_batched(args, rank, world)
+        return
+    if args.workload == "c5":
+        run_serving(args, rank, world)
         return
 
     import torch

@@ -104,7 +104,8 @@ typedef struct {      /* input clusters: device pointers, read only, caller owne
 
 typedef struct {              /* outputs: device pointers, caller owned */
   int32_t *cluster_track;     /* [n] track id per cluster in caller order, -1 = none (required) */
-  uint32_t track_capacity;    /* rows of the per-track arrays below */
+  uint32_t track_capacity;    /* rows of the per-track arrays below; 0: no track records are wanted
+                                 (cluster_track and the count only, never a capacity error) */
   float *params;              /* [cap][5] y (cm), zeta - zeta_ref (cm), sin phi, dzeta/ds, q/pT (c/GeV) */
   float *cov;                 /* [cap][15] covariance, lower triangle row-major */
   float *t_ref;               /* [cap] time of the start cluster (bins); zeta_ref = 0.516 cm * t_ref */
@@ -180,6 +181,10 @@ int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, const tpc_trac
  * tpc_track_timeframe; TPC_ERR_ARG for trials outside [1, 100]. */
 int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
                     int32_t *nb_tile, int32_t *fit_variant);
+
+/* Device memory (bytes) that tpc_tf_create allocates for cfg, plus the classifier
+ * weights in TPC_MODE_PRUNED; nothing is allocated.  Errors: TPC_ERR_ARG. */
+int tpc_tf_arena_bytes(const tpc_tf_config *cfg, size_t *bytes);
 
 /* Synchronise `stream` and report the device-side status of the last call
  * (TPC_OK, TPC_ERR_INPUT, TPC_ERR_CAPACITY, TPC_ERR_TIMEOUT). */
@@ -301,6 +306,74 @@ int tpc_mlp_trainer_gradient(tpc_mlp_trainer *tr, const float *feat, const uint8
 
 /* Write the current weights as a blob into host memory (synchronises). */
 int tpc_mlp_trainer_blob(tpc_mlp_trainer *tr, void *blob, size_t bytes);
+
+/* ----------------------------------------------------------------------------
+ * Serving runtime (the paper has no counterpart: it replays recorded time frames
+ * through its chain from memory).  A server owns slots, each a tracker handle
+ * (arena sized for a cluster capacity) with its own CUDA stream and worker
+ * thread; several frames run at once.  Requests are admitted in arrival order
+ * (FIFO): to the free slot of smallest sufficient capacity, else to a new slot
+ * (capacity 1.25 x n rounded up to 2^20 clusters) if max_slots and the memory
+ * budget allow, else by replacing the largest free slot with a larger one if the
+ * budget allows; otherwise the request waits until a slot frees up (when no slot
+ * is busy, the idle slots too small for it are freed first).  A request that no
+ * slot and no budget can ever hold fails with TPC_ERR_CAPACITY.
+ * ------------------------------------------------------------------------- */
+typedef struct tpc_server tpc_server;
+
+typedef struct {
+  uint64_t hbm_budget_bytes;  /* device memory the slots may hold (default 180 GiB) */
+  int32_t max_slots;          /* frames in flight at once, 1..64 (default 4) */
+  int32_t device;             /* CUDA device ordinal */
+  tpc_tf_config tf;           /* tracker settings of every slot (max_clusters is set per slot) */
+  const void *mlp_blob;       /* classifier weights for TPC_MODE_PRUNED (copied at create) */
+  size_t mlp_bytes;
+} tpc_server_config;
+
+typedef struct {
+  uint64_t id;                /* as returned by tpc_server_submit */
+  int32_t status;             /* TPC_OK or the call's error code */
+  uint32_t n_clusters, n_tracks;
+  int32_t slot;               /* slot that ran it (-1 if none) */
+  double t_submit, t_start, t_done; /* seconds since the server was created */
+} tpc_server_result;
+
+#define TPC_ADMIT_RUN 0
+#define TPC_ADMIT_CREATE 1
+#define TPC_ADMIT_REPLACE 2
+#define TPC_ADMIT_WAIT 3
+
+void tpc_server_default_config(tpc_server_config *cfg);
+
+/* Start the scheduler thread.  Errors: TPC_ERR_ARG. */
+int tpc_server_create(const tpc_server_config *cfg, tpc_server **out);
+
+/* Queue one time frame.  `cl` and `out` hold HOST pointers, as for
+ * tpc_track_timeframe_host; the arrays must stay valid and untouched until the
+ * request's result is returned by tpc_server_poll (out->n_tracks and
+ * n_tracks_host are ignored: the count is in the result).  *id receives the
+ * request id.  Thread-safe. */
+int tpc_server_submit(tpc_server *s, const tpc_clusters *cl, const tpc_tracks *out, uint64_t *id);
+
+/* Up to `max` finished requests (in completion order), waiting up to wait_ms
+ * milliseconds for the first; returns how many were written, or a negative
+ * error.  Thread-safe. */
+int tpc_server_poll(tpc_server *s, tpc_server_result *res, int max, int wait_ms);
+
+/* Current slots, their device memory and the queued requests (any may be NULL). */
+int tpc_server_stats(tpc_server *s, int *n_slots, uint64_t *bytes_in_use, int *queued);
+
+/* Finish the queued and running requests, stop the threads, free the slots.
+ * Results not yet polled are discarded. */
+void tpc_server_destroy(tpc_server *s);
+
+/* The admission policy above as a pure function (used by the scheduler; exposed
+ * for tests): for a request of n clusters and the slots' capacities, device
+ * bytes and busy flags, returns the slot to use and sets *action to
+ * TPC_ADMIT_RUN / _CREATE (returns the new slot's index) / _REPLACE, or sets
+ * TPC_ADMIT_WAIT and returns -1.  new_bytes = device bytes of a new slot. */
+int tpc_server_admit(uint32_t n, const uint32_t *slot_cap, const uint64_t *slot_bytes, const uint8_t *slot_busy,
+                     int n_slots, int max_slots, uint64_t budget, uint64_t new_bytes, int *action);
 
 #ifdef __cplusplus
 }

@@ -134,35 +134,17 @@ static void free_all(tpc_tf *tf) {
   delete tf;
 }
 
-extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
-  g_err.clear();
-  if (!cfg || !out) return fail(TPC_ERR_ARG, "tpc_tf_create: null argument");
-  *out = nullptr;
-  if (cfg->max_clusters == 0 || cfg->max_clusters > (1u << 30))
-    return fail(TPC_ERR_ARG, "tpc_tf_create: max_clusters must be in [1, 2^30]");
-  if (cfg->n_min < 3 || cfg->n_min > TPC_NROWS) return fail(TPC_ERR_ARG, "tpc_tf_create: n_min must be in [3, 152]");
-  if (cfg->wy_q < 0 || cfg->wy_q > (1 << 28) || cfg->wt_q < 0 || cfg->wt_q > (1 << 17) || cfg->cost_max_q < 0 ||
-      cfg->cost_max_q >= (1LL << 40))
-    return fail(TPC_ERR_ARG, "tpc_tf_create: search window or cost cut out of range");
-  if (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_PRUNED)
-    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown mode");
-  if (cfg->mode == TPC_MODE_PRUNED && !(cfg->tau == cfg->tau)) return fail(TPC_ERR_ARG, "tpc_tf_create: tau is NaN");
-  if (cfg->fit_variant != TPC_FIT_THREAD && cfg->fit_variant != TPC_FIT_WARP)
-    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown fit_variant");
-  if (cfg->n_sectors < 0 || cfg->n_sectors > 16384)
-    return fail(TPC_ERR_ARG, "tpc_tf_create: n_sectors must be in [0, 16384]");
-  if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
-    return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
-  tpc_tf *tf = new tpc_tf();
+namespace {
+struct Part {
+  void **p;
+  size_t bytes;
+};
+}  // namespace
+
+// Sizes of the arena's parts for cfg (host only; nothing is allocated).
+static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
   tf->cfg = *cfg;
-  tf->device = cfg->device;
   tf->N = cfg->max_clusters;
-  cudaError_t e = cudaSetDevice(tf->device);
-  if (e != cudaSuccess) {
-    delete tf;
-    return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-  }
-  cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
   tf->nsect = cfg->n_sectors ? cfg->n_sectors : kNSect;
   tf->nkeys = tf->nsect * kNRows;
   tf->nb_tile = cfg->nb_tile ? cfg->nb_tile : kNbTile;
@@ -172,10 +154,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
 
   const size_t N = tf->N;
   tf->reset_bytes_max = kNCounters * 4 + 8 * (link_tiles(tf->N) + walk_tiles(tf->N) + 2);
-  struct Part {
-    void **p;
-    size_t bytes;
-  } parts[] = {
+  std::vector<Part> parts = {
       {(void **)&tf->row_begin, (size_t)(tf->nkeys + 1) * 4},
       {(void **)&tf->tile_off, (size_t)(tf->nkeys + 1) * 4},
       {(void **)&tf->tile_win, (size_t)tf->tile_cap * 2 * 16},
@@ -215,8 +194,54 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
        cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * sizeof(PruneRow) : 0},
       {(void **)&tf->q_count, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * 4 : 0},
   };
+  return parts;
+}
+
+static size_t arena_total(const std::vector<Part> &parts) {
   size_t total = 0;
   for (auto &p : parts) total += align_up(p.bytes, 256);
+  return total;
+}
+
+static int validate_config(const tpc_tf_config *cfg) {
+  if (cfg->max_clusters == 0 || cfg->max_clusters > (1u << 30))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: max_clusters must be in [1, 2^30]");
+  if (cfg->n_min < 3 || cfg->n_min > TPC_NROWS) return fail(TPC_ERR_ARG, "tpc_tf_create: n_min must be in [3, 152]");
+  if (cfg->wy_q < 0 || cfg->wy_q > (1 << 28) || cfg->wt_q < 0 || cfg->wt_q > (1 << 17) || cfg->cost_max_q < 0 ||
+      cfg->cost_max_q >= (1LL << 40))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: search window or cost cut out of range");
+  if (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_PRUNED)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown mode");
+  if (cfg->mode == TPC_MODE_PRUNED && !(cfg->tau == cfg->tau)) return fail(TPC_ERR_ARG, "tpc_tf_create: tau is NaN");
+  if (cfg->fit_variant != TPC_FIT_THREAD && cfg->fit_variant != TPC_FIT_WARP)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: unknown fit_variant");
+  if (cfg->n_sectors < 0 || cfg->n_sectors > 16384)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: n_sectors must be in [0, 16384]");
+  if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(TPC_ERR_ARG, "tpc_tf_create: null argument");
+  *out = nullptr;
+  {
+    const int rc = validate_config(cfg);
+    if (rc != TPC_OK) return rc;
+  }
+  tpc_tf *tf = new tpc_tf();
+  tf->cfg = *cfg;
+  tf->device = cfg->device;
+  tf->N = cfg->max_clusters;
+  cudaError_t e = cudaSetDevice(tf->device);
+  if (e != cudaSuccess) {
+    delete tf;
+    return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  }
+  cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
+  const std::vector<Part> parts = plan_arena(tf, cfg);
+  const size_t total = arena_total(parts);
   e = cudaMalloc(&tf->arena, total);
   if (e != cudaSuccess) {
     free_all(tf);
@@ -224,7 +249,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   }
   tf->arena_bytes = total;
   size_t off = 0;
-  for (auto &p : parts) {
+  for (const auto &p : parts) {
     *p.p = p.bytes ? tf->arena + off : nullptr;
     off += align_up(p.bytes, 256);
   }
@@ -497,7 +522,8 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   if (out->n_tracks) *out->n_tracks = nt;
   if (out->n_tracks_host) *out->n_tracks_host = nt;
   if (rc != TPC_OK) g_err = msg;
-  if (rc == TPC_OK && nt > out->track_capacity) return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
+  if (rc == TPC_OK && out->track_capacity > 0 && nt > out->track_capacity)
+    return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
   return rc;
 }
 
@@ -711,5 +737,17 @@ extern "C" int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tra
   if (rc != TPC_OK) return rc;
   if (nb_tile) *nb_tile = best_tile;
   if (fit_variant) *fit_variant = best_fit;
+  return TPC_OK;
+}
+
+// ================================================================ sizing
+extern "C" int tpc_tf_arena_bytes(const tpc_tf_config *cfg, size_t *bytes) {
+  g_err.clear();
+  if (!cfg || !bytes) return fail(TPC_ERR_ARG, "tpc_tf_arena_bytes: null argument");
+  const int rc = validate_config(cfg);
+  if (rc != TPC_OK) return rc;
+  tpc_tf tmp;
+  const std::vector<Part> parts = plan_arena(&tmp, cfg);
+  *bytes = arena_total(parts) + (cfg->mode == TPC_MODE_PRUNED ? mlp_weights_bytes() + 32768 : 0);
   return TPC_OK;
 }

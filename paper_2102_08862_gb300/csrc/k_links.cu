@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
       const uint32_t nt = s_prefix + total;
       a.ctr[kCtrTracks] = nt;
       if (a.n_tracks_out) *a.n_tracks_out = nt;
-      if (nt > a.track_capacity) raise(a.ctr, kErrCapacity);
+      if (a.track_capacity > 0 && nt > a.track_capacity) raise(a.ctr, kErrCapacity);
     }
     __syncthreads();
   }

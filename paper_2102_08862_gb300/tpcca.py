@@ -53,6 +53,19 @@ class tpc_mlp_train_config(ctypes.Structure):
                 ("max_batch", c_u32), ("device", c_i32)]
 
 
+class tpc_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", c_i32), ("device", c_i32),
+                ("tf", tpc_tf_config), ("mlp_blob", c_vp), ("mlp_bytes", ctypes.c_size_t)]
+
+
+class tpc_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", c_i32), ("n_clusters", c_u32), ("n_tracks", c_u32),
+                ("slot", c_i32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+TPC_ADMIT_RUN, TPC_ADMIT_CREATE, TPC_ADMIT_REPLACE, TPC_ADMIT_WAIT = 0, 1, 2, 3
+
 _lib = None
 
 
@@ -94,6 +107,23 @@ def load():
     lib.tpc_tf_stage_times.restype = ctypes.c_int
     lib.tpc_tf_launches_per_call.argtypes = [c_vp]
     lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    lib.tpc_tf_arena_bytes.argtypes = [P(tpc_tf_config), P(ctypes.c_size_t)]
+    lib.tpc_tf_arena_bytes.restype = ctypes.c_int
+    lib.tpc_server_default_config.argtypes = [P(tpc_server_config)]
+    lib.tpc_server_default_config.restype = None
+    lib.tpc_server_create.argtypes = [P(tpc_server_config), P(c_vp)]
+    lib.tpc_server_create.restype = ctypes.c_int
+    lib.tpc_server_submit.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), P(ctypes.c_uint64)]
+    lib.tpc_server_submit.restype = ctypes.c_int
+    lib.tpc_server_poll.argtypes = [c_vp, P(tpc_server_result), ctypes.c_int, ctypes.c_int]
+    lib.tpc_server_poll.restype = ctypes.c_int
+    lib.tpc_server_stats.argtypes = [c_vp, P(c_i32), P(ctypes.c_uint64), P(c_i32)]
+    lib.tpc_server_stats.restype = ctypes.c_int
+    lib.tpc_server_destroy.argtypes = [c_vp]
+    lib.tpc_server_destroy.restype = None
+    lib.tpc_server_admit.argtypes = [c_u32, c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_uint64, P(ctypes.c_int)]
+    lib.tpc_server_admit.restype = ctypes.c_int
     lib.tpc_track_timeframe_graph.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
     lib.tpc_track_timeframe_graph.restype = ctypes.c_int
     lib.tpc_tf_autotune.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), ctypes.c_int, c_vp, P(c_i32), P(c_i32)]
@@ -206,6 +236,98 @@ def tpc_tf_autotune(handle, clusters: tpc_clusters, tracks: tpc_tracks, trials: 
     _check(load().tpc_tf_autotune(handle, ctypes.byref(clusters), ctypes.byref(tracks), trials, stream,
                                   ctypes.byref(t), ctypes.byref(f)))
     return int(t.value), int(f.value)
+
+
+def tpc_tf_arena_bytes(cfg: tpc_tf_config) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().tpc_tf_arena_bytes(ctypes.byref(cfg), ctypes.byref(b)))
+    return int(b.value)
+
+
+def tpc_server_admit(n, cap, nbytes, busy, max_slots, budget, new_bytes):
+    """(slot, action) of the serving runtime's admission policy."""
+    import numpy as np
+    cap = np.ascontiguousarray(cap, np.uint32)
+    nbytes = np.ascontiguousarray(nbytes, np.uint64)
+    busy = np.ascontiguousarray(busy, np.uint8)
+    act = ctypes.c_int(-1)
+    k = load().tpc_server_admit(int(n), cap.ctypes.data, nbytes.ctypes.data, busy.ctypes.data, int(cap.size),
+                                int(max_slots), int(budget), int(new_bytes), ctypes.byref(act))
+    return k, act.value
+
+
+class Server:
+    """The serving runtime (tpc_server_*): submit host frames, poll results.  The
+    host arrays of a request are kept alive here until its result is polled."""
+
+    def __init__(self, budget_bytes=180 << 30, max_slots=4, device=0, mlp_blob: bytes | None = None, **tf):
+        cfg = tpc_server_config()
+        load().tpc_server_default_config(ctypes.byref(cfg))
+        cfg.hbm_budget_bytes = int(budget_bytes)
+        cfg.max_slots = int(max_slots)
+        cfg.device = int(device)
+        for k, v in tf.items():
+            setattr(cfg.tf, k, v)
+        self._blob = None
+        if mlp_blob is not None:
+            self._blob = ctypes.create_string_buffer(bytes(mlp_blob), len(mlp_blob))
+            cfg.mlp_blob = ctypes.cast(self._blob, c_vp)
+            cfg.mlp_bytes = len(mlp_blob)
+        h = c_vp()
+        _check(load().tpc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._live = {}
+
+    def submit(self, sector, row, pad, time, track_capacity=0):
+        """Queue one frame (numpy arrays, or pinned torch CPU tensors); returns the
+        request id.  Its cluster_track array is returned by poll()."""
+        import numpy as np
+        arrs = []
+        for a, dt in ((sector, np.uint16), (row, np.uint16), (pad, np.float32), (time, np.float32)):
+            if hasattr(a, "data_ptr"):
+                arrs.append((a, a.data_ptr()))
+            else:
+                a = np.ascontiguousarray(a, dtype=dt)
+                arrs.append((a, a.ctypes.data))
+        n = int(len(arrs[0][0]))
+        ct = np.empty(max(n, 1), np.int32)
+        cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED, sector=arrs[0][1], row=arrs[1][1], pad=arrs[2][1],
+                          time=arrs[3][1])
+        tr = tpc_tracks(cluster_track=ct.ctypes.data, track_capacity=0)
+        rid = ctypes.c_uint64(0)
+        _check(load().tpc_server_submit(self.handle, ctypes.byref(cl), ctypes.byref(tr), ctypes.byref(rid)))
+        self._live[rid.value] = (arrs, ct, n)
+        return rid.value
+
+    def poll(self, max_results=64, wait_ms=100):
+        """Finished requests: list of (result dict, cluster_track numpy array)."""
+        buf = (tpc_server_result * max_results)()
+        k = load().tpc_server_poll(self.handle, buf, max_results, int(wait_ms))
+        if k < 0:
+            _check(k)
+        out = []
+        for r in buf[:k]:
+            arrs, ct, n = self._live.pop(r.id)
+            out.append(({f: getattr(r, f) for f, _ in tpc_server_result._fields_}, ct[:n]))
+        return out
+
+    def stats(self):
+        ns, q = c_i32(0), c_i32(0)
+        b = ctypes.c_uint64(0)
+        _check(load().tpc_server_stats(self.handle, ctypes.byref(ns), ctypes.byref(b), ctypes.byref(q)))
+        return dict(slots=ns.value, bytes=b.value, queued=q.value)
+
+    def close(self):
+        if self.handle:
+            load().tpc_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tpc_mlp_blob_bytes() -> int:

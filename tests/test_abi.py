@@ -97,3 +97,34 @@ def test_classifier_blob_roundtrip_and_size(lib):
     assert len(tpcca.init_blob(3)) == 20340
     with pytest.raises(ValueError):
         tpcca.unpack_blob(b"XXXX" + blob[4:])
+
+
+def test_server_admission_policy(lib):
+    """The serving runtime's admission rule on hand-built slot states (host logic, no GPU)."""
+    G = 1 << 30
+    adm = tpcca.tpc_server_admit
+    # no slots: create one if it fits the budget, else wait
+    assert adm(1000, [], [], [], 4, 10 * G, 2 * G) == (0, tpcca.TPC_ADMIT_CREATE)
+    assert adm(1000, [], [], [], 4, 1 * G, 2 * G) == (-1, tpcca.TPC_ADMIT_WAIT)
+    # the free slot of smallest sufficient capacity wins
+    assert adm(500, [1000, 600, 400], [3 * G, 2 * G, G], [0, 0, 0], 4, 100 * G, G) == (1, tpcca.TPC_ADMIT_RUN)
+    # a busy fitting slot is skipped; a new slot is made while the budget allows
+    assert adm(500, [1000, 400], [3 * G, G], [1, 0], 4, 100 * G, 2 * G) == (2, tpcca.TPC_ADMIT_CREATE)
+    # at max_slots: replace the largest free slot (too small) if the budget allows
+    assert adm(500, [1000, 400, 300], [3 * G, G, G // 2], [1, 0, 0], 3, 100 * G, 2 * G) == \
+        (1, tpcca.TPC_ADMIT_REPLACE)
+    # budget exhausted and the only fitting slot busy: wait
+    assert adm(500, [1000, 400], [3 * G, G], [1, 0], 4, 4 * G, 2 * G) == (-1, tpcca.TPC_ADMIT_WAIT)
+    # everything busy: wait
+    assert adm(10, [1000, 1000], [G, G], [1, 1], 2, 100 * G, G) == (-1, tpcca.TPC_ADMIT_WAIT)
+
+
+def test_arena_estimate_grows_with_clusters(lib):
+    c = tpcca.tpc_default_config()
+    c.max_clusters = 1 << 20
+    small = tpcca.tpc_tf_arena_bytes(c)
+    c.max_clusters = 1 << 24
+    big = tpcca.tpc_tf_arena_bytes(c)
+    assert big > 10 * small
+    c.mode = tpcca.TPC_MODE_PRUNED
+    assert tpcca.tpc_tf_arena_bytes(c) > big  # the pair regions and the overflow list
