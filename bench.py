@@ -545,6 +545,30 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     d2h = 4 * n + 4 + int(hn[0]) * (20 + 60 + 4 * 6 + 2 * 3 + 1)
+    # hit removal (compression consumer of cluster_track): the tracked clusters, in input order
+    ct_dev = tr._out["cluster_track"][:n]
+    with torch.cuda.stream(stream):
+        tr.track(sec, row, pad, tim, capacity=cap, stream=stream)
+        kept = tr.remove_unassigned(sec, row, pad, tim, ct_dev)  # checked once
+    n_kept = int(kept["sector"].numel())
+    ho = [torch.empty(n, dtype=dt, device=dev) for dt in (torch.int16, torch.int16, torch.float32, torch.float32,
+                                                          torch.int32)]
+    hcnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    rcl = tpcca.tpc_clusters(n=n, flags=0, sector=sec.data_ptr(), row=row.data_ptr(), pad=pad.data_ptr(),
+                             time=tim.data_ptr())
+    rm = lambda: tpcca.load().tpc_tf_remove_unassigned(tr.handle, tpcca.ctypes.byref(rcl), ct_dev.data_ptr(),
+                                                       *[x.data_ptr() for x in ho], hcnt.data_ptr(), sh)
+    for _ in range(3):
+        assert rm() == 0
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(10):
+        rm()
+    h1.record(stream)
+    stream.synchronize()
+    assert int(hcnt.item()) == n_kept and tpcca.tpc_tf_status(tr.handle, sh) == 0
+    hr_ms = h0.elapsed_time(h1) / 10
+    hr_bytes = 4 * n + 16 * n_kept + 16 * n_kept  # cluster_track read; kept fields read and written
     tr.close()
 
     if rank != 0:
@@ -577,6 +601,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": n_all / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},
+        "hit_removal": {"ms": hr_ms, "kept": n_kept, "kept_fraction": n_kept / n,
+                        "achieved_gbs": hr_bytes / (hr_ms * 1e-3) / 1e9},
         "gpu_launches": H["launches"] * args.steps,
         "clocks": H["clocks"].summary(),
     }

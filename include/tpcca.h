@@ -182,6 +182,18 @@ int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, const tpc_trac
 int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
                     int32_t *nb_tile, int32_t *fit_variant);
 
+/* Hit removal for compression (the consumer of cluster_track in the paper's
+ * synchronous chain, Sec. 1): copies the clusters with cluster_track[i] >= 0 to
+ * the output arrays, in caller order, and their track ids to track[] (may be
+ * NULL); *count (device scalar) receives the number kept.  All pointers are
+ * device arrays with room for cl->n entries; cl->flags is ignored (inputs in
+ * caller order).  Uses the handle's scratch: enqueue it on the stream of the
+ * tracking call, after it.  Errors: TPC_ERR_ARG, TPC_ERR_CAPACITY (n >
+ * max_clusters), TPC_ERR_CUDA; a bounded wait that gave up surfaces through
+ * tpc_tf_status. */
+int tpc_tf_remove_unassigned(tpc_tf *tf, const tpc_clusters *cl, const int32_t *cluster_track, uint16_t *sector,
+                             uint16_t *row, float *pad, float *time, int32_t *track, uint32_t *count, void *stream);
+
 /* Device memory (bytes) that tpc_tf_create allocates for cfg, plus the classifier
  * weights in TPC_MODE_PRUNED; nothing is allocated.  Errors: TPC_ERR_ARG. */
 int tpc_tf_arena_bytes(const tpc_tf_config *cfg, size_t *bytes);

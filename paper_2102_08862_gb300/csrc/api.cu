@@ -751,3 +751,30 @@ extern "C" int tpc_tf_arena_bytes(const tpc_tf_config *cfg, size_t *bytes) {
   *bytes = arena_total(parts) + (cfg->mode == TPC_MODE_PRUNED ? mlp_weights_bytes() + 32768 : 0);
   return TPC_OK;
 }
+
+// ================================================================ hit removal
+extern "C" int tpc_tf_remove_unassigned(tpc_tf *tf, const tpc_clusters *cl, const int32_t *cluster_track,
+                                        uint16_t *sector, uint16_t *row, float *pad, float *time, int32_t *track,
+                                        uint32_t *count, void *stream) {
+  g_err.clear();
+  if (!tf || !cl || !count) return fail(TPC_ERR_ARG, "tpc_tf_remove_unassigned: null argument");
+  const uint32_t n = cl->n;
+  if (n > tf->N) return fail(TPC_ERR_CAPACITY, "more clusters than max_clusters");
+  if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time || !cluster_track || !sector || !row || !pad ||
+                !time))
+    return fail(TPC_ERR_ARG, "tpc_tf_remove_unassigned: null array");
+  if (((uintptr_t)cluster_track & 3) || ((uintptr_t)pad & 3) || ((uintptr_t)time & 3) || ((uintptr_t)track & 3) ||
+      ((uintptr_t)count & 3) || ((uintptr_t)sector & 1) || ((uintptr_t)row & 1))
+    return fail(TPC_ERR_ARG, "tpc_tf_remove_unassigned: misaligned array");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Args a;
+  fill_args(tf, n, nullptr, a);
+  // the compaction's counters and look-back words (the error word stays)
+  TPC_CK(cudaMemsetAsync(tf->reset + kCtrCompactTile, 0, 8, st));
+  TPC_CK(cudaMemsetAsync(a.lb_links, 0, 8 * link_tiles(n), st));
+  launch_compact(a, cl->sector, cl->row, cl->pad, cl->time, cluster_track, sector, row, pad, time, track, count,
+                 tf->sms, st);
+  TPC_CK(cudaGetLastError());
+  return TPC_OK;
+}

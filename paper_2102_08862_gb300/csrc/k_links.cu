@@ -243,6 +243,65 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
   }
 }
 
+// Hit removal: the clusters attached to a track, in caller order (an ordered
+// compaction: block scan plus decoupled look-back over 2048-cluster tiles taken
+// in order from a counter).  Inputs and outputs are in caller order.
+__global__ void __launch_bounds__(kThreads) k_compact(uint32_t n, const uint16_t *__restrict__ sector,
+                                                      const uint16_t *__restrict__ row, const float *__restrict__ pad,
+                                                      const float *__restrict__ time, const int32_t *__restrict__ ct,
+                                                      uint16_t *o_sector, uint16_t *o_row, float *o_pad,
+                                                      float *o_time, int32_t *o_track, uint32_t *o_count,
+                                                      uint64_t *lb, uint32_t *ctr) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t s_warp[kThreads / 32];
+  const uint32_t n_tiles = (n + kLinkTile - 1) / kLinkTile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[kCtrCompactTile], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const uint32_t i0 = tile * kLinkTile + threadIdx.x * kItems;
+    int32_t t[kItems];
+    uint32_t keep = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      t[q] = i0 + q < n ? __ldcs(ct + i0 + q) : -1;
+      if (t[q] >= 0) keep |= 1u << q;
+    }
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan((uint32_t)__popc(keep), s_warp, &total);
+    if (threadIdx.x < 32) {
+      const uint32_t pre = lookback_exclusive(lb, tile, total, ctr);
+      if (threadIdx.x == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q)
+      if ((keep >> q) & 1u) {
+        const uint32_t i = i0 + q;
+        o_sector[pos] = sector[i];
+        o_row[pos] = row[i];
+        o_pad[pos] = pad[i];
+        o_time[pos] = time[i];
+        if (o_track) o_track[pos] = t[q];
+        ++pos;
+      }
+    if (tile == n_tiles - 1 && threadIdx.x == 0) *o_count = s_prefix + total;
+    __syncthreads();
+  }
+  if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) *o_count = 0;
+}
+
+void launch_compact(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                    const int32_t *ct, uint16_t *o_sector, uint16_t *o_row, float *o_pad, float *o_time,
+                    int32_t *o_track, uint32_t *o_count, int sms, cudaStream_t st) {
+  const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
+  const uint32_t grid = tiles < (uint32_t)sms * 4u ? (tiles ? tiles : 1u) : (uint32_t)sms * 4u;
+  k_compact<<<grid, kThreads, 0, st>>>(a.n, sector, row, pad, time, ct, o_sector, o_row, o_pad, o_time, o_track,
+                                       o_count, a.lb_links, a.ctr);
+}
+
 // inspection: the mutual up link as a sorted position, and the start flag
 __global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {

@@ -73,6 +73,8 @@ enum : int {
   kCtrTiles = 9,    // neighbour tiles of this frame
   kCtrAmb = 10,     // clusters listed for the separate rescoring kernel (pruned mode)
   kCtrQueued = 11,  // clusters rescored from the tile regions (pruned mode)
+  kCtrCompactTile = 12,  // hit removal: next tile
+  kCtrCompactKept = 13,  // hit removal: clusters kept
   kNCounters = 16
 };
 

@@ -40,6 +40,11 @@ int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, cons
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,
                 size_t scratch_bytes, int sms, cudaStream_t st);
 size_t sort_scratch_bytes(uint32_t max_n);
+// hit removal: clusters with ct >= 0 in caller order (uses a.lb_links and a.ctr,
+// which must be cleared)
+void launch_compact(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                    const int32_t *ct, uint16_t *o_sector, uint16_t *o_row, float *o_pad, float *o_time,
+                    int32_t *o_track, uint32_t *o_count, int sms, cudaStream_t st);
 // link classifier (k_mlp.cu)
 struct MlpW;
 size_t mlp_weights_bytes();

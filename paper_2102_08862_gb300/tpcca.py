@@ -107,6 +107,8 @@ def load():
     lib.tpc_tf_stage_times.restype = ctypes.c_int
     lib.tpc_tf_launches_per_call.argtypes = [c_vp]
     lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    lib.tpc_tf_remove_unassigned.argtypes = [c_vp, P(tpc_clusters), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]
+    lib.tpc_tf_remove_unassigned.restype = ctypes.c_int
     lib.tpc_tf_arena_bytes.argtypes = [P(tpc_tf_config), P(ctypes.c_size_t)]
     lib.tpc_tf_arena_bytes.restype = ctypes.c_int
     lib.tpc_server_default_config.argtypes = [P(tpc_server_config)]
@@ -628,6 +630,25 @@ class TimeFrameTracker:
         m = min(int(count.item()), cap)
         _check(tpc_tf_status(self.handle, st))
         return feat[:m], label[:m], tri[:m]
+
+    def remove_unassigned(self, sector, row, pad, time, cluster_track):
+        """Hit removal: (sector, row, pad, time, track) of the clusters attached to a track, in input order."""
+        t = self.torch
+        d = self.device
+        n = int(sector.numel())
+        cl = tpc_clusters(n=n, flags=0, sector=sector.data_ptr(), row=row.data_ptr(), pad=pad.data_ptr(),
+                          time=time.data_ptr())
+        o = dict(sector=t.empty(max(n, 1), dtype=t.int16, device=d), row=t.empty(max(n, 1), dtype=t.int16, device=d),
+                 pad=t.empty(max(n, 1), dtype=t.float32, device=d), time=t.empty(max(n, 1), dtype=t.float32, device=d),
+                 track=t.empty(max(n, 1), dtype=t.int32, device=d))
+        cnt = t.zeros(1, dtype=t.int32, device=d)
+        st = t.cuda.current_stream(d).cuda_stream
+        _check(load().tpc_tf_remove_unassigned(self.handle, ctypes.byref(cl), cluster_track.data_ptr(),
+                                               o["sector"].data_ptr(), o["row"].data_ptr(), o["pad"].data_ptr(),
+                                               o["time"].data_ptr(), o["track"].data_ptr(), cnt.data_ptr(), st))
+        m = int(cnt.item())
+        _check(tpc_tf_status(self.handle, st))
+        return {k: v[:m] for k, v in o.items()}
 
     def pruned_clusters(self) -> int:
         """Clusters the classifier rescored in the last pruned call."""
