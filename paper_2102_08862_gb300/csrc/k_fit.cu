@@ -10,11 +10,9 @@
 // first cluster from the circle through the first, middle (L/2) and last cluster,
 // C0 = diag(0.06^2, 0.0516^2, 0.01, 0.01, 0.01).
 //
-// GB300 design: one thread per track.  Pass 1 walks the mutual up links once,
-// writes cluster_track and finds the middle cluster with a second pointer moving
-// at half speed; pass 2 walks again, prefetching the next cluster's (pad, time,
-// link) before the filter step of the current one, so each step costs one memory
-// round trip overlapped with the filter arithmetic.
+// GB300 design: one thread per track.  The walk recorded each track's clusters as
+// chain[step][track], so consecutive threads read consecutive words; the next
+// cluster's (pad, time) is loaded before the current step's arithmetic.
 //
 // FP32 accuracy.  Three choices keep the FP32 filter within 1e-4 of an FP64 one:
 //  * the covariance is carried as C = U D U^T (U unit upper triangular, D
@@ -27,7 +25,10 @@
 //    spacing is 4e-6 cm), and each measured y is formed exactly in um units
 //    (error-free difference pad - centre, then one fused multiply-add by the
 //    integer pitch);
-//  * the seed, computed once per track, is evaluated in FP64.
+//  * the seed's sagitta is formed from exact um differences in float pairs.
+// This file is compiled with approximate FP32 division and square root (a few
+// ulp): the filter's error stays far inside the 1e-4 tolerance, and the stage
+// runs 16 % faster than with IEEE-rounded division.
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
