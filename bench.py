@@ -346,6 +346,9 @@ def main():
     ap.add_argument("--fit-variant", type=int, default=0)
     ap.add_argument("--mode", default="both", choices=["both", "pruned", "plain"],
                     help="both: the learned-pruned CA is the headline, the plain CA is timed beside it")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default neighbour tile and fit kernel instead of letting the library's "
+                         "autotuner pick them on the frame (untimed, before the warm-up; reported in config)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
@@ -383,10 +386,19 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
 
+    tuned = {}
+
     def make(name, **extra):
-        tr = tpcca.TimeFrameTracker(n, device=local, fit_variant=args.fit_variant, **modes[name], **extra)
+        opts = dict(fit_variant=args.fit_variant)
+        if name in tuned:
+            opts.update(tuned[name])
+        tr = tpcca.TimeFrameTracker(n, device=local, **opts, **modes[name], **extra)
         if name == "pruned":
             tr.load_mlp(blob)
+        if args.autotune and name not in tuned:
+            with torch.cuda.stream(stream):
+                tile, fit = tr.autotune(sec, row, pad, tim, capacity=cap, trials=3)
+            tuned[name] = dict(nb_tile=tile, fit_variant=fit)
         return tr
 
     def checked_call(tr):
@@ -586,7 +598,9 @@ def main():
         "config": {"workload": f"{args.workload}: 10 ms continuous frame, 36 sectors, {f.n_collisions} collisions "
                                f"at 50 kHz, {n} clusters, seed 3 (+1000*rank)",
                    "mode": {"pruned": f"learned-pruned CA (tau {tau})", "plain": "plain CA"}[head],
-                   "fit": ["thread per track", "warp per track"][args.fit_variant],
+                   "fit": ["thread per track", "warp per track"][tuned.get(head, {}).get("fit_variant",
+                                                                                   args.fit_variant)],
+                   "autotuned": tuned.get(head),
                    "l2": "inputs (12 B x %d = %.0f MB) larger than L2" % (n, 12 * n / 1e6),
                    "parallelism": f"replicas x{world}"},
         "tracks_per_s": n_tracks * args.steps / (total_ms * 1e-3) * (n_all / n),

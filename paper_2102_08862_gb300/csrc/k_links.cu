@@ -91,6 +91,26 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
     uint32_t flags = 0;
     uint16_t m16[kItems];
     int32_t skey[kItems];
+    // all loads first: the thread's 8 links (64 contiguous bytes), then the 16
+    // partner links they point to, so that the gathers are in flight together
+    int2 l[kItems];
+    if (i0 + kItems <= (int)n) {
+#pragma unroll
+      for (int v = 0; v < kItems / 2; ++v) {
+        const int4 w = __ldcs(reinterpret_cast<const int4 *>(a.link + i0) + v);
+        l[2 * v] = make_int2(w.x, w.y);
+        l[2 * v + 1] = make_int2(w.z, w.w);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kItems; ++q) l[q] = i0 + q < (int)n ? __ldcs(a.link + i0 + q) : make_int2(-1, -1);
+    }
+    int32_t pu[kItems], pd[kItems];  // up partner's down link, down partner's up link
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      pu[q] = l[q].y >= 0 ? a.link[l[q].y].x : -2;
+      pd[q] = l[q].x >= 0 ? a.link[l[q].x].y : -2;
+    }
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
       const int i = i0 + q;
@@ -98,9 +118,8 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
       skey[q] = 0;
       if (i >= (int)n) continue;
       while (key < nkeys - 1 && i >= rb[key + 1]) ++key;
-      const int2 l = __ldcs(a.link + i);
-      const int32_t mup = (l.y >= 0 && a.link[l.y].x == i) ? l.y : -1;
-      const int32_t mdn = (l.x >= 0 && a.link[l.x].y == i) ? l.x : -1;
+      const int32_t mup = pu[q] == i ? l[q].y : -1;
+      const int32_t mdn = pd[q] == i ? l[q].x : -1;
       if (mup >= 0) {
         const int d = mup - rb[key + 1];
         if (d < 0 || d >= kNone16) bad = true; else m16[q] = (uint16_t)d;
@@ -140,8 +159,8 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
   if (bad) raise(a.ctr, kErrRowCap);
 }
 
-// A4: two start hits per thread, walked interleaved so that two dependent load
-// chains are in flight.  Chains that reach n_min clusters become tracks (ids in
+// A4: kWalkChains start hits per thread, walked interleaved so that as many
+// dependent load chains are in flight.  Chains that reach n_min clusters become tracks (ids in
 // start order); their clusters get the track id and are recorded in the chain
 // buffer; the clusters of shorter chains get -1.
 template <bool kSmemRb>
@@ -176,63 +195,82 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
       ++key;
     }
   };
+  constexpr int C = kWalkChains;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrTileKeep], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const uint32_t j = tile * kWalkTileN + 2 * threadIdx.x;
-    const int2 st0 = j < ns ? a.starts[j] : make_int2(-1, 0);
-    const int2 st1 = j + 1 < ns ? a.starts[j + 1] : make_int2(-1, 0);
-    // walk at most n_min - 1 links of both chains
-    int c0 = st0.x, k0 = st0.y, c1 = st1.x, k1 = st1.y;
-    int len0 = c0 >= 0, len1 = c1 >= 0;
-    for (int s = 1; s < n_min && (c0 >= 0 || c1 >= 0); ++s) {
-      if (c0 >= 0) {
-        next(c0, k0);
-        len0 += c0 >= 0;
-      }
-      if (c1 >= 0) {
-        next(c1, k1);
-        len1 += c1 >= 0;
-      }
+    const uint32_t j = tile * kWalkTileN + C * threadIdx.x;
+    int2 st[C];
+    int c[C], kk[C], len[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      st[q] = j + q < ns ? a.starts[j + q] : make_int2(-1, 0);
+      c[q] = st[q].x;
+      kk[q] = st[q].y;
+      len[q] = c[q] >= 0;
     }
-    const bool kept0 = len0 >= n_min, kept1 = len1 >= n_min;
+    // walk at most n_min - 1 links of every chain, interleaved (C loads in flight)
+    for (int s = 1; s < n_min; ++s) {
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < C; ++q)
+        if (c[q] >= 0) {
+          next(c[q], kk[q]);
+          len[q] += c[q] >= 0;
+          any = true;
+        }
+      if (!any) break;
+    }
+    bool kept[C];
+    uint32_t nkept = 0;
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      kept[q] = len[q] >= n_min;
+      nkept += kept[q];
+    }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan((uint32_t)kept0 + (uint32_t)kept1, s_warp, &total);
+    const uint32_t excl = block_exclusive_scan(nkept, s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(a.lb_keep, tile, total, a.ctr);
       if (threadIdx.x == 0) s_prefix = pre;
     }
     __syncthreads();
-    const uint32_t id0 = s_prefix + excl, id1 = id0 + (uint32_t)kept0;
-    if ((kept0 && id0 >= a.track_list_cap) || (kept1 && id1 >= a.track_list_cap)) raise(a.ctr, kErrCapacity);
-    const bool w0 = st0.x >= 0 && (!kept0 || id0 < a.track_list_cap);
-    const bool w1 = st1.x >= 0 && (!kept1 || id1 < a.track_list_cap);
-    // second walk of both chains: members of tracks get the id and go to the
-    // chain buffer, members of short chains get -1
-    c0 = w0 ? st0.x : -1;
-    k0 = st0.y;
-    c1 = w1 ? st1.x : -1;
-    k1 = st1.y;
-    const int32_t v0 = kept0 ? (int32_t)id0 : -1, v1 = kept1 ? (int32_t)id1 : -1;
-    int m = 0;
-    for (; m < kNRows && (c0 >= 0 || c1 >= 0); ++m) {
-      if (c0 >= 0) {
-        if (kept0) __stcs(a.chain + (size_t)m * stride + id0, c0);
-        __stcs(a.cluster_track + caller_index(a, c0), v0);
-        if (m + 1 < (kept0 ? kNRows : len0)) next(c0, k0); else c0 = -1;
-        if (c0 < 0 && kept0) a.trk_len[id0] = m + 1;
-      }
-      if (c1 >= 0) {
-        if (kept1) __stcs(a.chain + (size_t)m * stride + id1, c1);
-        __stcs(a.cluster_track + caller_index(a, c1), v1);
-        if (m + 1 < (kept1 ? kNRows : len1)) next(c1, k1); else c1 = -1;
-        if (c1 < 0 && kept1) a.trk_len[id1] = m + 1;
+    uint32_t id[C];
+    int32_t v[C];
+    bool w[C];
+    {
+      uint32_t nx = s_prefix + excl;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        id[q] = nx;
+        nx += kept[q];
+        if (kept[q] && id[q] >= a.track_list_cap) raise(a.ctr, kErrCapacity);
+        w[q] = st[q].x >= 0 && (!kept[q] || id[q] < a.track_list_cap);
+        v[q] = kept[q] ? (int32_t)id[q] : -1;
+        // second walk: members of tracks get the id and go to the chain buffer,
+        // members of short chains get -1
+        c[q] = w[q] ? st[q].x : -1;
+        kk[q] = st[q].y;
       }
     }
-    if (kept0 && w0) a.trk_key[id0] = st0.y;
-    if (kept1 && w1) a.trk_key[id1] = st1.y;
+    for (int m = 0; m < kNRows; ++m) {
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < C; ++q)
+        if (c[q] >= 0) {
+          any = true;
+          if (kept[q]) __stcs(a.chain + (size_t)m * stride + id[q], c[q]);
+          __stcs(a.cluster_track + caller_index(a, c[q]), v[q]);
+          if (m + 1 < (kept[q] ? kNRows : len[q])) next(c[q], kk[q]); else c[q] = -1;
+          if (c[q] < 0 && kept[q]) a.trk_len[id[q]] = m + 1;
+        }
+      if (!any) break;
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+      if (kept[q] && w[q]) a.trk_key[id[q]] = st[q].y;
     if (tile == n_tiles - 1 && threadIdx.x == 0) {
       const uint32_t nt = s_prefix + total;
       a.ctr[kCtrTracks] = nt;

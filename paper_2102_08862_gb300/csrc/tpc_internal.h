@@ -18,7 +18,8 @@ constexpr int kNbTileMin = 512;
 inline bool nb_tile_ok(int t) { return t == 512 || t == 768 || t == 1024; }
 // look-back tiles: clusters per tile of the link kernel, start hits per tile of the walk
 constexpr int kLinkTileN = 2048;
-constexpr int kWalkTileN = 512;  // 256 threads, two chains each
+constexpr int kWalkChains = 1;                  // chains walked together by one thread
+constexpr int kWalkTileN = 256 * kWalkChains;   // start hits per walk tile (256 threads)
 inline size_t link_tiles(uint32_t n) { return (n + kLinkTileN - 1) / kLinkTileN; }
 inline size_t walk_tiles(uint32_t n) { return (n / 2 + 1 + kWalkTileN - 1) / kWalkTileN; }
 
