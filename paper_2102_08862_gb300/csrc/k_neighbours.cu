@@ -38,6 +38,7 @@ constexpr int kPruneMaxPairs = 32;
 struct NbQueue {
   uint32_t pairs[4][256];  // a thread's first four pairs under the cut (j | k << 11); <= 256 threads
   int count, end;
+  unsigned warps_done;     // the last warp to finish publishes the region's row count
 };
 template <bool kPrune> struct NbExtra {};
 template <> struct NbExtra<true> { NbQueue q; };
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 0) k_neighb
   NbQueue *q = nullptr;
   if constexpr (kPrune) {
     q = &ex.q;
-    if (tid == 0) q->count = q->end = 0;
+    if (tid == 0) q->count = q->end = 0, q->warps_done = 0;
   }
   const int half_p = 32 * (row_npads(r - 1) - 1), pitch_p = row_pitch_um(r - 1);
   const int half_n = 32 * (row_npads(r + 1) - 1), pitch_n = row_pitch_um(r + 1);
@@ -449,9 +450,12 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 0) k_neighb
         np, [&](int k) { return quant_ty(sane_pad(pn[k]), sane_time(tng[k]), half_n, pitch_n); }, nn, a.wy, a.wt,
         a.cost_max, a.link + ta, w.x, w.z, ta);
   }
-  if constexpr (kPrune) {  // rows used in this tile's region
-    __syncthreads();
-    if (tid == 0) a.q_count[t] = q->end;
+  if constexpr (kPrune) {  // rows used in this tile's region, published by the last warp to finish
+    __syncwarp();
+    if ((tid & 31) == 0) {
+      __threadfence_block();
+      if (atomicAdd(&q->warps_done, 1u) == (unsigned)(THREADS / 32 - 1)) a.q_count[t] = atomicAdd(&q->end, 0);
+    }
   }
   if (bad) raise(a.ctr, kErrInput);
 }
