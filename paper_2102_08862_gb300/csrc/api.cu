@@ -328,6 +328,7 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.wy = tf->cfg.wy_q;
   a.wt = tf->cfg.wt_q;
   a.cost_max = tf->cfg.cost_max_q;
+  a.cost_rmax = isqrt64(tf->cfg.cost_max_q);
   a.n_min = tf->cfg.n_min;
   a.nsect = tf->nsect;
   a.nkeys = tf->nkeys;

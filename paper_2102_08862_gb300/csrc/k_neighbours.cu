@@ -231,7 +231,6 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
       else if (nj == 3) { cj3 = j; ej3 = e; }
       ++nj;
     }
-    uint64_t best = ~0ull;
     // pruned mode: pairs under the cost cut, the first four kept (j | k << 11) in
     // the thread's shared-memory slots
     int nc = 0, nkc = 0;
@@ -239,21 +238,39 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
       if (nc < 4) q->pairs[nc][threadIdx.x] = v;
       ++nc;
     };
+    // best pair under the cut as (cost, j, k); a pair whose y or z kink alone
+    // exceeds floor(sqrt(cost_max)) costs more than cost_max and is skipped with
+    // two 32-bit compares (most pairs of a window are not on a straight line)
+    uint64_t bc = ~0ull;
+    int bj = 2047, bk = 2047;
+    const int32_t rmax = a.cost_rmax;
+    auto consider = [&](int j, int k, int32_t d2y, int32_t d2t) {
+      const int32_t d2z = d2t * kUmPerBin;
+      if (abs(d2y) > rmax || abs(d2z) > rmax) return;
+      const uint64_t c = (uint64_t)((int64_t)d2y * d2y) + (uint64_t)((int64_t)d2z * d2z);
+      if (c >= capc) return;
+      if (kPrune) keep_pair((uint32_t)j | ((uint32_t)k << 11));
+      if (c < bc || (c == bc && (j < bj || (j == bj && k < bk)))) {
+        bc = c;
+        bj = j;
+        bk = k;
+      }
+    };
     if (nj > 0 && nj <= kMaxCand) {
       const int cj[4] = {cj0, cj1, cj2, cj3};
-      const int2 ej[4] = {ej0, ej1, ej2, ej3};
+      const int32_t dyj[4] = {ej0.y - yi, ej1.y - yi, ej2.y - yi, ej3.y - yi};
+      const int32_t dtj[4] = {ej0.x - ti, ej1.x - ti, ej2.x - ti, ej3.x - ti};
       for (int k = klo; k < nn; ++k) {
         const int2 e = sn[k];
         if (e.x > thi) break;
         const int32_t dyk = e.y - yi;
         if (abs(dyk) > wy) continue;
         if (kPrune) ++nkc;
+        const int32_t dtk = e.x - ti;
 #pragma unroll
         for (int x = 0; x < kMaxCand; ++x) {
           if (x >= nj) break;
-          const uint64_t c = (uint64_t)triplet_cost(ej[x].y - yi, dyk, ej[x].x - ti, e.x - ti);
-          if (kPrune && c < capc) keep_pair((uint32_t)cj[x] | ((uint32_t)k << 11));
-          best = min(best, (min(c, capc) << 22) | ((uint64_t)cj[x] << 11) | (uint64_t)k);
+          consider(cj[x], k, dyj[x] + dyk, dtj[x] + dtk);
         }
       }
     } else if (nj > kMaxCand) {  // crowded windows: every pair
@@ -267,15 +284,11 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
           if (ek.x > thi) break;
           const int32_t dyk = ek.y - yi;
           if (abs(dyk) > wy) continue;
-          const uint64_t c = (uint64_t)triplet_cost(dyj, dyk, ej.x - ti, ek.x - ti);
-          if (kPrune && c < capc) keep_pair((uint32_t)j | ((uint32_t)k << 11));
-          best = min(best, (min(c, capc) << 22) | ((uint64_t)j << 11) | (uint64_t)k);
+          consider(j, k, dyj + dyk, (ej.x - ti) + (ek.x - ti));
         }
       }
     }
-    out[li] = (best != ~0ull && (best >> 22) <= (uint64_t)cost_max)
-                  ? make_int2(base_p + (int)((best >> 11) & 2047), base_n + (int)(best & 2047))
-                  : make_int2(-1, -1);
+    out[li] = bc != ~0ull ? make_int2(base_p + bj, base_n + bk) : make_int2(-1, -1);
     if (kPrune && nc >= 2) {
       // the pairs go to the tile's region (rows in any order: the rescoring
       // compares (cost, j, k) explicitly); a cluster that does not fit goes to the list

@@ -139,6 +139,7 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
   a.wy = c.wy_q;
   a.wt = c.wt_q;
   a.cost_max = c.cost_max_q;
+  a.cost_rmax = isqrt64(c.cost_max_q);
   a.n_min = c.n_min;
   a.cluster_track = out->cluster_track;
   a.track_capacity = out->track_capacity;

@@ -110,6 +110,7 @@ struct Args {
   uint32_t track_list_cap;
   int32_t wy, wt;
   int64_t cost_max;
+  int32_t cost_rmax;       // floor(sqrt(cost_max)): a kink |d2y| or |d2z| above it costs more than cost_max
   int32_t n_min;
   int32_t nsect, nkeys;  // independent sectors of this call (36 for one TPC frame; one per instance
                          // in a batched call) and their (sector, row) keys, nsect * 152

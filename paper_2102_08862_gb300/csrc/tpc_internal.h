@@ -58,6 +58,13 @@ void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std
 void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit, int sms, cudaStream_t st);
 void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,
                         cudaStream_t st);
+// floor(sqrt(v)) for 0 <= v < 2^62, exact
+inline int32_t isqrt64(int64_t v) {
+  int64_t r = 0;
+  for (int64_t b = int64_t(1) << 31; b > 0; b >>= 1)
+    if ((r + b) * (r + b) <= v) r += b;
+  return (int32_t)r;
+}
 // sets the message returned by tpc_last_error() (cleared for TPC_OK); returns code
 int report(int code, const char *msg);
 // order[] of the last call (inspection)
