@@ -260,8 +260,17 @@ size_t tpc_mlp_blob_bytes(void);
 int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes);
 
 /* Logits of m raw feature rows (device float[m][12], caller order) with the
- * loaded weights, written to logit[m] (device).  Enqueued on `stream`. */
+ * loaded weights, written to logit[m] (device).  Enqueued on `stream`.  Runs on
+ * the tcgen05 tensor cores (128-row tiles, accumulators in tensor memory); a
+ * bounded wait that gave up surfaces through tpc_tf_status as TPC_ERR_TIMEOUT. */
 int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void *stream);
+
+#define TPC_MMA_TCGEN05 0 /* fifth-generation tensor cores: tcgen05.mma into tensor memory */
+#define TPC_MMA_SYNC 1    /* warp-level mma.sync m16n8k16 tiles in registers */
+
+/* tpc_mlp_score with the tensor-core engine chosen (TPC_MMA_TCGEN05 or
+ * TPC_MMA_SYNC); both compute the same network and agree to FP32 rounding. */
+int tpc_mlp_score_ex(tpc_tf *tf, const float *feat, uint32_t m, float *logit, int engine, void *stream);
 
 /* Training set of the classifier from one time frame: runs A0-A2 of the plain
  * path on `cl` and writes, for every cluster with at least two pairs under the

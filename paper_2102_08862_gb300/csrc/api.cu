@@ -590,12 +590,22 @@ extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
 }
 
 extern "C" int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void *stream) {
+  return tpc_mlp_score_ex(tf, feat, m, logit, TPC_MMA_TCGEN05, stream);
+}
+
+extern "C" int tpc_mlp_score_ex(tpc_tf *tf, const float *feat, uint32_t m, float *logit, int engine, void *stream) {
   g_err.clear();
   if (!tf || (m > 0 && (!feat || !logit))) return fail(TPC_ERR_ARG, "tpc_mlp_score: null argument");
   if (!tf->mlp_ready) return fail(TPC_ERR_ARG, "tpc_mlp_score: load the classifier weights first");
   if (((uintptr_t)feat & 3) || ((uintptr_t)logit & 3)) return fail(TPC_ERR_ARG, "tpc_mlp_score: misaligned array");
+  if (engine != TPC_MMA_TCGEN05 && engine != TPC_MMA_SYNC) return fail(TPC_ERR_ARG, "tpc_mlp_score: unknown engine");
   TPC_CK(cudaSetDevice(tf->device));
-  launch_mlp_score(tf->mlp, feat, m, logit, tf->sms, (cudaStream_t)stream);
+  if (engine == TPC_MMA_SYNC) {
+    launch_mlp_score(tf->mlp, feat, m, logit, tf->sms, (cudaStream_t)stream);
+  } else if (launch_mlp_score_tc(tf->mlp, feat, m, logit, reinterpret_cast<int *>(tf->reset + kCtrErr), tf->sms,
+                                 (cudaStream_t)stream) < 0) {
+    return fail(TPC_ERR_CUDA, "tpc_mlp_score: tensor-core kernel configuration failed");
+  }
   TPC_CK(cudaGetLastError());
   return TPC_OK;
 }

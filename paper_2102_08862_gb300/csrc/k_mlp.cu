@@ -16,6 +16,7 @@
 // and k_prune rescores those: each warp takes 32 listed clusters and
 // re-enumerates their pairs from global memory.
 #include "mlp_dev.cuh"
+#include "tc_dev.cuh"
 #include "tpc_internal.h"
 
 namespace tpc {
@@ -55,6 +56,28 @@ __device__ __forceinline__ void stage_weights(PruneSmem &sm, const MlpW *__restr
   for (int e = tid; e < kMlpIn; e += nt) {
     sm.mean[e] = W->mean[e];
     sm.inv_std[e] = W->inv_std[e];
+  }
+}
+
+// raw features of row `row` (float[m][12], 48-byte rows) as three 16-byte loads,
+// or zeros past the end; a misaligned array falls back to scalar loads
+__device__ __forceinline__ void load_feature_row(const float *__restrict__ feat, uint32_t row, uint32_t m, float *f) {
+  if (row >= m) {
+#pragma unroll
+    for (int c = 0; c < kMlpIn; ++c) f[c] = 0.0f;
+  } else if (((uintptr_t)feat & 15) == 0) {
+    const float4 *p = reinterpret_cast<const float4 *>(feat + (size_t)row * kMlpIn);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const float4 q = __ldg(p + v);
+      f[4 * v] = q.x;
+      f[4 * v + 1] = q.y;
+      f[4 * v + 2] = q.z;
+      f[4 * v + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kMlpIn; ++c) f[c] = feat[(size_t)row * kMlpIn + c];
   }
 }
 
@@ -346,6 +369,150 @@ __global__ void k_mlp_pack(const float *__restrict__ theta, const float *__restr
   if (p == 0) W->b3 = theta[kOffB3];
 }
 
+// ------------------------------------------------------ tcgen05 MLP (128 rows)
+// One CTA of 128 threads scores 128 rows at a time on the fifth-generation tensor
+// cores: thread r writes row r's standardised BF16 inputs in the core-matrix
+// layout; one tcgen05.mma (M 128, N 64, K 16) puts layer 1 in tensor memory (64
+// FP32 columns); each thread loads its row back (tcgen05.ld), adds the bias,
+// applies ReLU, rounds to BF16 and writes the row of H1; four MMAs (K 64) give
+// layer 2; each thread finishes its row's logit in FP32.  Completion of the MMAs
+// is signalled through an mbarrier (bounded wait).
+struct __align__(1024) TcMlpSmem {
+  unsigned char x[128 * 16 * 2];   // inputs, core-matrix layout (K 16)
+  unsigned char h[128 * 64 * 2];   // first hidden layer (K 64)
+  unsigned char w1[64 * 16 * 2];   // W1 (N 64, K 16)
+  unsigned char w2[64 * 64 * 2];   // W2 (N 64, K 64)
+  float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ void tc_stage_weights(TcMlpSmem &sm, const MlpW *__restrict__ W) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kMlpH * 2; e += blockDim.x) {  // W1: 64 rows x 2 column groups of 16 B
+    const int n = e >> 1, g = e & 1;
+    *reinterpret_cast<uint4 *>(sm.w1 + core_offset(n, 8 * g, 16)) =
+        *reinterpret_cast<const uint4 *>(W->w1 + n * kXS + 8 * g);
+  }
+  for (int e = tid; e < kMlpH * 8; e += blockDim.x) {  // W2: 64 rows x 8 column groups
+    const int n = e >> 3, g = e & 7;
+    *reinterpret_cast<uint4 *>(sm.w2 + core_offset(n, 8 * g, 64)) =
+        *reinterpret_cast<const uint4 *>(W->w2 + n * kW2S + 8 * g);
+  }
+  for (int e = tid; e < kMlpH; e += blockDim.x) {
+    sm.b1[e] = W->b1[e];
+    sm.b2[e] = W->b2[e];
+    sm.w3[e] = W->w3[e];
+  }
+  for (int e = tid; e < kMlpIn; e += blockDim.x) {
+    sm.mean[e] = W->mean[e];
+    sm.inv_std[e] = W->inv_std[e];
+  }
+}
+
+// thread r's input row: 16 standardised BF16 values (12 + 4 zeros), or zeros
+__device__ __forceinline__ void tc_put_input(TcMlpSmem &sm, int r, const float *f, bool valid) {
+  __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    v[c] = (valid && c < kMlpIn) ? __float2bfloat16_rn(__fmul_rn(__fsub_rn(f[c], sm.mean[c]), sm.inv_std[c]))
+                                 : __float2bfloat16_rn(0.0f);
+  *reinterpret_cast<uint4 *>(sm.x + core_offset(r, 0, 16)) = reinterpret_cast<const uint4 *>(v)[0];
+  *reinterpret_cast<uint4 *>(sm.x + core_offset(r, 8, 16)) = reinterpret_cast<const uint4 *>(v)[1];
+}
+
+// The two tensor-core layers for the 128 rows staged in sm.x; returns thread r's
+// logit (false if a bounded wait gave up).
+__device__ __forceinline__ bool tc_mlp_rows(TcMlpSmem &sm, uint32_t tmem, float b3, float &logit) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {
+    tc_mma_bf16(tmem, tc_desc(smem_u32(sm.x), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), tc_idesc_bf16(128, 64),
+                false);
+    tc_commit(&sm.mbar);
+  }
+  bool ok = mbar_wait(&sm.mbar, 0, 1u << 22);
+  tc_fence_after();
+  float z[16];
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      tc_ld16(lane_base + 16 * q, z);
+      tc_wait_ld();
+      __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hv[c] = __float2bfloat16_rn(fmaxf(z[c] + sm.b1[16 * q + c], 0.f));
+      *reinterpret_cast<uint4 *>(sm.h + core_offset(tid, 16 * q, 64)) = reinterpret_cast<const uint4 *>(hv)[0];
+      *reinterpret_cast<uint4 *>(sm.h + core_offset(tid, 16 * q + 8, 64)) = reinterpret_cast<const uint4 *>(hv)[1];
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
+  tc_fence_after();
+  if (tid == 0 && ok) {
+    const uint32_t h0 = smem_u32(sm.h), w0 = smem_u32(sm.w2);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      tc_mma_bf16(tmem, tc_desc(h0 + 256 * s, 128, 1024), tc_desc(w0 + 256 * s, 128, 1024), tc_idesc_bf16(128, 64),
+                  s > 0);
+    tc_commit(&sm.mbar);
+  }
+  if (ok) ok = mbar_wait(&sm.mbar, 1, 1u << 22);
+  tc_fence_after();
+  float acc = b3;
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      tc_ld16(lane_base + 16 * q, z);
+      tc_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc = fmaf(fmaxf(z[c] + sm.b2[16 * q + c], 0.f), sm.w3[16 * q + c], acc);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();  // sm.x, sm.h and the accumulators are free again
+  logit = acc;
+  return __syncthreads_and(ok);
+}
+
+// logits of raw feature rows (float[m][12]) on the tcgen05 path
+__global__ void __launch_bounds__(128) k_mlp_score_tc(const MlpW *__restrict__ W, const float *__restrict__ feat,
+                                                      uint32_t m, float *__restrict__ logit, int *err) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  TcMlpSmem &sm = *reinterpret_cast<TcMlpSmem *>(smraw);
+  const int tid = threadIdx.x;
+  tc_stage_weights(sm, W);
+  if (tid == 0) mbar_init(&sm.mbar, 1);
+  if ((tid >> 5) == 0) tc_alloc(&sm.tmem, 64);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  const float b3 = W->b3;
+  const uint32_t tiles = (m + 127) / 128;
+  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const uint32_t row = t * 128 + tid;
+    float f[kMlpIn];
+    load_feature_row(feat, row, m, f);
+    tc_put_input(sm, tid, f, row < m);
+    float lg;
+    if (!tc_mlp_rows(sm, tmem, b3, lg)) {
+      if (tid == 0) atomicOr(err, (int)kErrTimeout);
+      break;
+    }
+    if (row < m) logit[row] = lg;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if ((tid >> 5) == 0) tc_dealloc(tmem, 64);
+}
+
 // ------------------------------------------------------------------ scoring
 // logits of raw feature rows (float[m][12]); one warp per 16 rows
 __global__ void __launch_bounds__(kPruneWarps * 32) k_mlp_score(const MlpW *__restrict__ W,
@@ -361,8 +528,7 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_mlp_score(const MlpW *__re
     if (lane < 16) {
       const uint32_t row = t * 16 + lane;
       float f[kMlpIn];
-#pragma unroll
-      for (int c = 0; c < kMlpIn; ++c) f[c] = row < m ? feat[(size_t)row * kMlpIn + c] : 0.0f;
+      load_feature_row(feat, row, m, f);
       store_input_row(xs + lane * kXS, f, sm.mean, sm.inv_std);
     }
     __syncwarp();
@@ -475,6 +641,28 @@ void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit
   const uint32_t tiles = (m + 15) / 16, blocks = (tiles + kPruneWarps - 1) / kPruneWarps;
   k_mlp_score<<<blocks < (uint32_t)sms * 8 ? blocks : (uint32_t)sms * 8, kPruneWarps * 32, 0, st>>>(w, feat, m,
                                                                                                     logit);
+}
+
+size_t mlp_score_tc_smem() { return sizeof(TcMlpSmem) + 1024; }
+
+int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *logit, int *err, int sms,
+                        cudaStream_t st) {
+  if (m == 0) return 0;
+  static bool configured[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    if (cudaFuncSetAttribute(k_mlp_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_score_tc_smem()) !=
+        cudaSuccess)
+      return -1;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  // at most 7 CTAs fit an SM (31 KB of shared memory each), so their 64-column
+  // tensor-memory allocations (512 columns per SM) never wait on each other
+  const uint32_t tiles = (m + 127) / 128;
+  const uint32_t grid = tiles < (uint32_t)sms * 4 ? tiles : (uint32_t)sms * 4;
+  k_mlp_score_tc<<<grid, 128, mlp_score_tc_smem(), st>>>(w, feat, m, logit, err);
+  return 0;
 }
 
 void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,

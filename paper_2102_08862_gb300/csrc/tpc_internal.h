@@ -56,6 +56,11 @@ void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaSt
 // FP32 parameters (blob order) + standardisation -> packed BF16 weights
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);
 void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit, int sms, cudaStream_t st);
+// the same on the tcgen05 tensor cores (128-row tiles, accumulators in tensor
+// memory); *err (device) is set if a bounded wait gave up; returns < 0 on a
+// launch-configuration failure
+int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *logit, int *err, int sms,
+                        cudaStream_t st);
 void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,
                         cudaStream_t st);
 // floor(sqrt(v)) for 0 <= v < 2^62, exact

@@ -26,6 +26,8 @@ TPC_MODE_PRUNED = 1
 TPC_INPUT_SORTED = 1
 TPC_FIT_THREAD = 0
 TPC_FIT_WARP = 1
+TPC_MMA_TCGEN05 = 0
+TPC_MMA_SYNC = 1
 ERROR_NAMES = {0: "TPC_OK", -1: "TPC_ERR_ARG", -2: "TPC_ERR_CAPACITY", -3: "TPC_ERR_CUDA", -4: "TPC_ERR_INPUT",
                -5: "TPC_ERR_TIMEOUT"}
 
@@ -137,6 +139,8 @@ def load():
     lib.tpc_mlp_load.restype = ctypes.c_int
     lib.tpc_mlp_score.argtypes = [c_vp, c_vp, c_u32, c_vp, c_vp]
     lib.tpc_mlp_score.restype = ctypes.c_int
+    lib.tpc_mlp_score_ex.argtypes = [c_vp, c_vp, c_u32, c_vp, ctypes.c_int, c_vp]
+    lib.tpc_mlp_score_ex.restype = ctypes.c_int
     lib.tpc_mlp_extract.argtypes = [c_vp, P(tpc_clusters), c_vp, c_vp, c_vp, c_u32, c_vp, c_vp]
     lib.tpc_mlp_extract.restype = ctypes.c_int
     lib.tpc_tf_pruned_clusters.argtypes = [c_vp, P(c_u32), P(c_u32), c_vp]
@@ -600,13 +604,13 @@ class TimeFrameTracker:
     def load_mlp(self, blob: bytes):
         _check(tpc_mlp_load(self.handle, blob))
 
-    def score(self, feat):
-        """Logits of raw feature rows (float32[m, 12] CUDA tensor)."""
+    def score(self, feat, engine=0):
+        """Logits of raw feature rows (float32[m, 12] CUDA tensor); engine 0 = tcgen05, 1 = mma.sync."""
         t = self.torch
         m = int(feat.shape[0])
         out = t.empty(max(m, 1), dtype=t.float32, device=self.device)
-        _check(tpc_mlp_score(self.handle, feat.data_ptr(), m, out.data_ptr(),
-                             t.cuda.current_stream(self.device).cuda_stream))
+        _check(load().tpc_mlp_score_ex(self.handle, feat.data_ptr(), m, out.data_ptr(), int(engine),
+                                       t.cuda.current_stream(self.device).cuda_stream))
         return out[:m]
 
     def extract(self, sector, row, pad, time, sorted_input=True, cap=None):

@@ -102,7 +102,8 @@ def test_extract_capacity_counts_all_rows(env, c1):
 
 
 # ------------------------------------------------------------------ scoring
-def test_scores_match_oracle_logits(env, c1):
+@pytest.mark.parametrize("engine", [0, 1])  # tcgen05 (tensor memory), mma.sync
+def test_scores_match_oracle_logits(env, c1, engine):
     tpcca, dev = env
     blob = _net()
     feat, _, _ = orc.training_triplets(c1.sector, c1.row, c1.pad, c1.time)
@@ -114,7 +115,9 @@ def test_scores_match_oracle_logits(env, c1):
     tr = tpcca.TimeFrameTracker(1024)
     try:
         tr.load_mlp(blob)
-        got = tr.score(_dev_tensor(feat, dev)).cpu().numpy().astype(np.float64)
+        got = tr.score(_dev_tensor(feat, dev), engine=engine).cpu().numpy().astype(np.float64)
+        torch.cuda.synchronize()
+        assert tpcca.tpc_tf_status(tr.handle, 0) == 0
     finally:
         tr.close()
     err = np.abs(got - want)
