@@ -38,8 +38,8 @@ ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a tr
 STAGED_BYTES_PER_CLUSTER = 48.0
 # DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "31cf8b2d74dd20dc4efd5a8b2b784cc2b7a959803470423233118dbac279c805",
-              "pruned": (204.053760e6 + 128.951808e6) / 16765809, "plain": (202.049792e6 + 100.518656e6) / 16765809}
+NB_TRAFFIC = {"sha256": "5458e593a63df8c2d20057a20176cbf8533f6958734497106e4c674bc8d8215d",
+              "pruned": (204.094464e6 + 129.071104e6) / 16765809, "plain": (202.566144e6 + 101.457408e6) / 16765809}
 
 
 def neighbours_traffic(mode, n):
@@ -127,6 +127,42 @@ def classifier():
     with open(WEIGHTS + ".json") as fh:
         tau = float(json.load(fh)["tau"])
     return blob, tau
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s (burst: the scorer is timed alone)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def dense_scorer(tr, torch, dev, stream, rows=5_200_000, reps=20):
+    """The classifier on a dense block of feature rows (tpc_mlp_score_ex), both
+    tensor-core engines: 5.2 M rows of 48 B (250 MB, larger than L2), seeded normal
+    features.  FLOP per row: 2 (16*64 + 64*64 + 64)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    feat = torch.randn(rows, 12, device=dev, generator=g)
+    flop = 2.0 * (16 * 64 + 64 * 64 + 64) * rows
+    bf16, kind = bf16_peak()
+    out = {"rows": rows, "flop_per_row": flop / rows, "peak_tflops": bf16, "peak_kind": kind}
+    logits = {}
+    with torch.cuda.stream(stream):
+        for eng, name in ((0, "tcgen05"), (1, "mma_sync")):
+            for _ in range(3):
+                logits[name] = tr.score(feat, engine=eng)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                tr.score(feat, engine=eng)
+            e1.record(stream)
+            stream.synchronize()
+            us = e0.elapsed_time(e1) / reps * 1e3
+            tf = flop / (us * 1e-6) / 1e12
+            out[name] = {"us": us, "tflops": tf, "frac_bf16": tf / bf16}
+    out["max_abs_diff"] = float((logits["tcgen05"] - logits["mma_sync"]).abs().max().item())
+    return out
 
 
 def gen_frame(workload, seed_offset=0):
@@ -349,6 +385,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default neighbour tile and fit kernel instead of letting the library's "
                          "autotuner pick them on the frame (untimed, before the warm-up; reported in config)")
+    ap.add_argument("--nb-tile", type=int, default=0, choices=[0, 512, 768, 1024],
+                    help="neighbour tile (clusters per CTA) instead of the autotuner's choice; 0 = autotune")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
@@ -390,12 +428,14 @@ def main():
 
     def make(name, **extra):
         opts = dict(fit_variant=args.fit_variant)
+        if args.nb_tile:
+            opts["nb_tile"] = args.nb_tile
         if name in tuned:
             opts.update(tuned[name])
         tr = tpcca.TimeFrameTracker(n, device=local, **opts, **modes[name], **extra)
         if name == "pruned":
             tr.load_mlp(blob)
-        if args.autotune and name not in tuned:
+        if args.autotune and not args.nb_tile and name not in tuned:
             with torch.cuda.stream(stream):
                 tile, fit = tr.autotune(sec, row, pad, tim, capacity=cap, trials=3)
             tuned[name] = dict(nb_tile=tile, fit_variant=fit)
@@ -581,6 +621,7 @@ def main():
     assert int(hcnt.item()) == n_kept and tpcca.tpc_tf_status(tr.handle, sh) == 0
     hr_ms = h0.elapsed_time(h1) / 10
     hr_bytes = 4 * n + 16 * n_kept + 16 * n_kept  # cluster_track read; kept fields read and written
+    scorer = dense_scorer(tr, torch, dev, stream) if head == "pruned" else None
     tr.close()
 
     if rank != 0:
@@ -617,6 +658,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "hit_removal": {"ms": hr_ms, "kept": n_kept, "kept_fraction": n_kept / n,
                         "achieved_gbs": hr_bytes / (hr_ms * 1e-3) / 1e9},
+        "dense_scorer": scorer,
         "gpu_launches": H["launches"] * args.steps,
         "clocks": H["clocks"].summary(),
     }
