@@ -30,7 +30,7 @@ TRACK_DTYPE = np.dtype([
 
 
 def build(force: bool = False) -> str:
-    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c")]
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "mlp.c", "follow.c")]
     hdr = os.path.join(_HERE, "oracle.h")
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= max(os.path.getmtime(p) for p in srcs + [hdr])):
@@ -45,6 +45,10 @@ def build(force: bool = False) -> str:
 class Params(ctypes.Structure):
     _fields_ = [("wy_q", ctypes.c_int32), ("wt_q", ctypes.c_int32),
                 ("cost_max_q", ctypes.c_int64), ("n_min", ctypes.c_int32)]
+
+
+class FollowParams(ctypes.Structure):
+    _fields_ = [("chi2_max", ctypes.c_double), ("max_miss", ctypes.c_int32), ("join_check", ctypes.c_int32)]
 
 
 class EvalOut(ctypes.Structure):
@@ -100,6 +104,10 @@ def _load():
             lib.or_track_ex.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, dbl, vp, vp, vp, vp, vp,
                                         vp, vp, i64, vp, vp, vp, vp]
             lib.or_track_ex.restype = ctypes.c_int
+            lib.or_default_follow.argtypes = [ctypes.POINTER(FollowParams)]
+            lib.or_track_follow.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, dbl,
+                                            ctypes.POINTER(FollowParams), vp, vp, i64, vp, vp, vp, vp, vp, vp]
+            lib.or_track_follow.restype = ctypes.c_int
             lib.or_training_triplets.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), i64, vp, vp, vp, vp]
             lib.or_training_triplets.restype = ctypes.c_int
             _lib = lib
@@ -231,6 +239,47 @@ def track(sector, row, pad, time, prm: Params | None = None, track_cap: int | No
         raise MemoryError("oracle: track failed")
     return dict(order=order, down=down, up=up, mdown=mdown, mup=mup, is_start=is_start.astype(bool),
                 cluster_track=ct, tracks=tracks[:min(nt.value, cap)], n_tracks=nt.value, **extra)
+
+
+def follow_params(**kw) -> FollowParams:
+    fp = FollowParams()
+    _load().or_default_follow(ctypes.byref(fp))
+    for k, v in kw.items():
+        setattr(fp, k, v)
+    return fp
+
+
+def track_follow(sector, row, pad, time, prm: Params | None = None, fp: FollowParams | None = None,
+                 track_cap: int | None = None, mlp: bytes | None = None, tau: float = 0.5):
+    """The whole path followed by track following and joining (follow.c).  Returns
+    `cluster_track` (caller order), `tracks` (TRACK_DTYPE), `n_tracks`, `margin`
+    (per final track; < 1 marks membership an FP32 follower may decide
+    differently), `old_to_new` (chain track -> final track), `n_chains` (tracks
+    before following) and `stats` (proposed pick-ups, accepted pick-ups, joins,
+    dropped inward pick-ups)."""
+    prm = prm or params()
+    fp = fp or follow_params()
+    sector, row = _c(sector, np.uint16), _c(row, np.uint16)
+    pad, time = _c(pad, np.float32), _c(time, np.float32)
+    n = sector.shape[0]
+    cap = track_cap if track_cap is not None else max(16, n // max(1, prm.n_min) + 1)
+    order = np.zeros(max(n, 1), np.int32)
+    ct = np.zeros(max(n, 1), np.int32)
+    tracks = np.zeros(cap, TRACK_DTYPE)
+    margin = np.zeros(cap, np.float64)
+    o2n = np.full(max(16, n // max(1, prm.n_min) + 1), -1, np.int32)
+    nt, nch = ctypes.c_int64(0), ctypes.c_int64(0)
+    stats = np.zeros(4, np.int64)
+    m = _mlp_struct(mlp) if mlp is not None else None
+    rc = _load().or_track_follow(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm),
+                                 _p(m) if m is not None else None, float(tau), ctypes.byref(fp), _p(order), _p(ct),
+                                 cap, _p(tracks), ctypes.byref(nt), _p(margin), _p(o2n), ctypes.byref(nch),
+                                 _p(stats))
+    if rc < 0:
+        raise MemoryError("oracle: track_follow failed")
+    k = min(nt.value, cap)
+    return dict(cluster_track=ct[:n], tracks=tracks[:k], n_tracks=nt.value, margin=margin[:k],
+                old_to_new=o2n[:nch.value], n_chains=nch.value, stats=stats, order=order[:n])
 
 
 # ------------------------------------------------------------ link classifier

@@ -323,7 +323,8 @@ static double or_asinc_d(double u) {
 }
 
 /* Transport the state p = (y, zeta, s = sin phi, t = dzeta/ds, Q = q/pT) by dx along
- * local x: helix in (x, y) with curvature c = -K Q, straight line in (arc, zeta).
+ * local x: helix in (x, y) with curvature c = -K Q, straight line in (arc, zeta); the
+ * arc length has the sign of dx.
  * F (row-major 5x5) receives d pout / d p.  Returns 1 (and leaves pout unset) when
  * |sin phi| would reach 0.999. */
 int or_propagate(const double *p, double dx, double *pout, double *F) {
@@ -334,9 +335,11 @@ int or_propagate(const double *p, double dx, double *pout, double *F) {
   double c1 = sqrt(1.0 - s1 * s1), c2 = sqrt(1.0 - s2 * s2);
   double A = s1 + s2, D = c1 + c2;
   double dy = dx * A / D;
+  /* the arc length is signed with dx: transport towards smaller x runs backwards */
+  double sg = dx < 0.0 ? -1.0 : 1.0;
   double l = sqrt(dx * dx + dy * dy);
   double u = 0.5 * c * l;
-  double ds = l * or_asinc(u);
+  double ds = sg * l * or_asinc(u);
   pout[0] = p[0] + dy;
   pout[1] = p[1] + t * ds;
   pout[2] = s2;
@@ -348,8 +351,8 @@ int or_propagate(const double *p, double dx, double *pout, double *F) {
     double ddy_dc = dx * dx * (D + A * s2 / c2) / (D * D);
     double g = 1.0 / sqrt(1.0 - u * u); /* d(arc)/d(chord) at fixed c */
     double dl_ds1 = dy / l * ddy_ds1, dl_dc = dy / l * ddy_dc;
-    double dds_ds1 = g * dl_ds1;
-    double dds_dc = g * dl_dc + 0.5 * l * l * or_asinc_d(u);
+    double dds_ds1 = sg * g * dl_ds1;
+    double dds_dc = sg * (g * dl_dc + 0.5 * l * l * or_asinc_d(u));
     for (int i = 0; i < 25; ++i) F[i] = 0.0;
     for (int i = 0; i < 5; ++i) F[i * 5 + i] = 1.0;
     F[0 * 5 + 2] = ddy_ds1;
@@ -488,10 +491,13 @@ int or_fit_chain(int32_t L, int32_t sector, const int32_t *rows, const float *pa
 }
 
 /* ------------------------------------------------------- the whole path */
-int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
-                const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down, int32_t *up,
-                int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track, int64_t track_cap,
-                or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats) {
+/* fp != NULL: the chains and their fits are followed and joined (follow.c) before
+ * the final records are written. */
+static int or_track_core(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                         const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down,
+                         int32_t *up, int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track,
+                         int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats,
+                         const or_follow_params *fp, double *fmargin, int32_t *old_to_new, int64_t *fstats) {
   *n_tracks = 0;
   if (n == 0) return 0;
   uint16_t *ss = (uint16_t *)malloc(sizeof(uint16_t) * n), *sr = (uint16_t *)malloc(sizeof(uint16_t) * n);
@@ -542,6 +548,12 @@ int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const fl
   int32_t *members = (int32_t *)malloc(sizeof(int32_t) * OR_NROWS);
   int64_t nt = 0;
   int rc = 0;
+  /* with following: every chain's start, length and fit, kept for the follower */
+  int64_t fcap = fp ? n / (prm->n_min > 0 ? prm->n_min : 1) + 1 : 0;
+  int32_t *tstart = fp ? (int32_t *)malloc(sizeof(int32_t) * fcap) : NULL;
+  int32_t *tlen = fp ? (int32_t *)malloc(sizeof(int32_t) * fcap) : NULL;
+  or_track_rec *trec = fp ? (or_track_rec *)malloc(sizeof(or_track_rec) * fcap) : NULL;
+  if (fp && (!tstart || !tlen || !trec)) return -1;
   for (int64_t i = 0; i < n; ++i) {
     is_start[i] = (uint8_t)(mdown[i] < 0 && mup[i] >= 0);
     if (!is_start[i]) continue;
@@ -554,7 +566,12 @@ int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const fl
       ++L;
     }
     if (L < prm->n_min) continue;
-    if (nt < track_cap) {
+    if (fp) {
+      tstart[nt] = (int32_t)i;
+      tlen[nt] = L;
+      or_fit_chain(L, ss[i], rows, pads, times, &trec[nt]);
+      trec[nt].first_cluster = order[i];
+    } else if (nt < track_cap) {
       or_fit_chain(L, ss[i], rows, pads, times, &tracks[nt]);
       tracks[nt].first_cluster = order[i];
     } else {
@@ -564,6 +581,19 @@ int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const fl
     ++nt;
   }
   *n_tracks = nt;
+  if (fp) {
+    int64_t *rf = (int64_t *)malloc(sizeof(int64_t) * (OR_NSECT * OR_NROWS + 1));
+    if (!rf) return -1;
+    or_row_ranges(n, ss, sr, rf);
+    int frc = or_follow_tracks(n, ss, sr, sp, st, rf, order, mup, nt, tstart, tlen, trec, fp, cluster_track,
+                               track_cap, tracks, n_tracks, fmargin, old_to_new, fstats);
+    if (frc < 0) return -1;
+    rc = frc;
+    free(rf);
+    free(tstart);
+    free(tlen);
+    free(trec);
+  }
   free(rows);
   free(pads);
   free(times);
@@ -574,6 +604,36 @@ int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const fl
   free(st);
   free(cost);
   free(claim);
+  return rc;
+}
+
+int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down, int32_t *up,
+                int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track, int64_t track_cap,
+                or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats) {
+  return or_track_core(n, sector, row, pad, time, prm, mlp, tau, order, down, up, mdown, mup, is_start, cluster_track,
+                       track_cap, tracks, n_tracks, band, stats, NULL, NULL, NULL, NULL);
+}
+
+int or_track_follow(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                    const or_params *prm, const or_mlp *mlp, double tau, const or_follow_params *fp,
+                    int32_t *order, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks,
+                    int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *n_chains, int64_t *fstats) {
+  int32_t *down = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *up = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+  int32_t *mdown = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *mup = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+  uint8_t *is_start = (uint8_t *)malloc(n + 1);
+  if (!down || !up || !mdown || !mup || !is_start) return -1;
+  int64_t st[4] = {0, 0, 0, 0};
+  int rc = or_track_core(n, sector, row, pad, time, prm, mlp, tau, order, down, up, mdown, mup, is_start,
+                         cluster_track, track_cap, tracks, n_tracks, NULL, mlp ? st : NULL, fp, margin, old_to_new,
+                         fstats);
+  /* chains before following = pick-ups and joins undone: n_tracks + joins */
+  if (n_chains) *n_chains = *n_tracks + (fstats ? fstats[2] : 0);
+  free(down);
+  free(up);
+  free(mdown);
+  free(mup);
+  free(is_start);
   return rc;
 }
 

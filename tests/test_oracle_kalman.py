@@ -47,13 +47,15 @@ def _truth_chain(qpt, phi0, eta, rows=range(152), sector=0, sy=0.0, st=0.0, rng=
 
 
 # ---------------------------------------------------------------- Jacobian
-@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("seed", range(9))
 def test_jacobian_matches_central_differences(seed):
+    """Forward transports (one row, 5 cm, 20 cm) and backward ones (towards smaller
+    x, as the inward track follow uses them)."""
     rng = np.random.default_rng(seed)
     for _ in range(50):
         p = np.array([rng.uniform(-30, 30), rng.uniform(-50, 50), rng.uniform(-0.8, 0.8),
                       rng.uniform(-1.2, 1.2), rng.uniform(-8, 8)])
-        dx = [160.0 / 151.0, 5.0, 20.0][seed % 3]
+        dx = [160.0 / 151.0, 5.0, 20.0, -160.0 / 151.0, -5.0, -20.0, -150.0, 7.0, -60.0][seed]
         res = orc.propagate(p, dx)
         if res is None:
             continue
@@ -67,6 +69,41 @@ def test_jacobian_matches_central_differences(seed):
                 continue
             num = (a[0] - b[0]) / (2 * h[j])
             assert np.allclose(F[:, j], num, rtol=1e-6, atol=1e-7), (j, F[:, j], num)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_transport_back_and_forth_is_the_identity(seed):
+    """The helix through a point is the same curve in both directions: transport by
+    dx then by -dx returns the state, and the two Jacobians are inverses."""
+    rng = np.random.default_rng(100 + seed)
+    done = 0
+    for _ in range(50):
+        p = np.array([rng.uniform(-30, 30), rng.uniform(-50, 50), rng.uniform(-0.8, 0.8),
+                      rng.uniform(-1.2, 1.2), rng.uniform(-8, 8)])
+        dx = rng.uniform(-160.0, 160.0)
+        a = orc.propagate(p, dx)
+        if a is None:
+            continue
+        b = orc.propagate(a[0], -dx)
+        if b is None:
+            continue
+        assert np.allclose(b[0], p, rtol=0, atol=1e-9 * (1 + abs(dx))), (p, b[0])
+        assert np.allclose(b[1] @ a[1], np.eye(5), atol=1e-7)
+        done += 1
+    assert done > 20
+
+
+def test_backward_transport_of_a_helix_reproduces_its_clusters():
+    """From the truth at the outermost row, transport back to every row: (y, zeta)
+    equal the generator's crossings (zeta relative to the outer row)."""
+    rows, pads, times, truth = _truth_chain(-0.8, math.radians(9.0), 0.3)
+    yl, tl, sl, tzl = truth[-1]
+    p_out = np.array([yl, 0.0, sl, tzl, -0.8])
+    for r, tr in zip(rows[::7], truth[::7]):
+        res = orc.propagate(p_out, X[r] - X[rows[-1]])
+        assert res is not None
+        assert res[0][0] == pytest.approx(tr[0], abs=1e-9)
+        assert res[0][1] == pytest.approx(0.516 * (tr[1] - tl), abs=1e-9)
 
 
 def test_propagation_stops_at_sin_phi_limit():
@@ -120,14 +157,20 @@ def _transport(p0, rows):
     return np.array(out)
 
 
+GAPPED_ROWS = [r for r in range(0, 75) if r not in (9, 10, 31, 47, 48, 49, 60)]
+
+
+@pytest.mark.parametrize("rows_sel", ["consecutive", "gapped"])
 @pytest.mark.parametrize("noise,tol,ctol", [(0.0, 1e-11, 1e-6), (2e-5, 2e-9, 5e-6), (2e-3, 2e-5, 5e-4)])
-def test_kalman_equals_batch_least_squares(noise, tol, ctol):
+def test_kalman_equals_batch_least_squares(noise, tol, ctol, rows_sel):
     """The filter linearises at its running estimate, the batch solution at the
     final one: states agree to second order in the deviations (which scale with the
     noise), covariances to first order.  Float rounding of the inputs is the only
-    noise in the first case."""
+    noise in the first case.  The gapped chain (rows missing, as in tracks that the
+    follower extended or joined) uses the same filter across the gaps."""
     rng = np.random.default_rng(4)
-    rows, pads, times, truth = _truth_chain(1.3, math.radians(11.0), 0.4, rows=range(0, 60),
+    sel = range(0, 60) if rows_sel == "consecutive" else GAPPED_ROWS
+    rows, pads, times, truth = _truth_chain(1.3, math.radians(11.0), 0.4, rows=sel,
                                             sy=noise, st=2 * noise, rng=rng)
     L = len(rows)
     ym = (pads.astype(np.float64) - 0.5 * (np.array([_npads(r) for r in rows]) - 1)) * \
