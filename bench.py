@@ -387,6 +387,9 @@ def main():
                          "autotuner pick them on the frame (untimed, before the warm-up; reported in config)")
     ap.add_argument("--nb-tile", type=int, default=0, choices=[0, 512, 768, 1024],
                     help="neighbour tile (clusters per CTA) instead of the autotuner's choice; 0 = autotune")
+    ap.add_argument("--follow", action="store_true",
+                    help="track following and joining on in every arm (profiler captures of its kernels); "
+                         "without it the default run times the headline arm with following as an extra line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
@@ -420,6 +423,9 @@ def main():
     sec, row, pad, tim = t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time)
     blob, tau = classifier()
     modes = {"pruned": dict(mode=tpcca.TPC_MODE_PRUNED, tau=tau), "plain": dict(mode=tpcca.TPC_MODE_PLAIN)}
+    if args.follow:
+        for v in modes.values():
+            v["follow"] = 1
     cap = n // 10 + 1
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
@@ -488,8 +494,8 @@ def main():
             total = float(tt.item())
         return total, per, clocks
 
-    def stages(name):
-        prof = make(name, profile_stages=1)
+    def stages(name, **extra):
+        prof = make(name, profile_stages=1, **extra)
         clp, outp, _, _ = prof.structs(sec, row, pad, tim, True, cap, host_count=None)
         acc = {}
         for k in range(args.warmup + 5):
@@ -499,7 +505,7 @@ def main():
                     acc.setdefault(nm, []).append(ms)
         ct = prof._out["cluster_track"][:n]
         in_tracks = int((ct >= 0).sum().item())
-        rescored = prof.pruned_split() if name == "pruned" else (0, 0)
+        rescored = prof.pruned_split() if name == "pruned" and not extra else (0, 0)
         prof.close()
         return {k: statistics.mean(v) for k, v in acc.items()}, in_tracks, rescored
 
@@ -541,6 +547,19 @@ def main():
             tr.close()
     head = arms[0]
     H = res[head]
+    # the headline arm with track following and joining (an extra line, not the headline)
+    follow_line = None
+    if not args.follow:
+        fol = make(head, follow=1)
+        fol_tracks = checked_call(fol)
+        fol_total, fol_per, _ = timed(fol, args.steps, False)
+        fol_q = quality(fol)
+        fol.close()
+        fol_stage, _, _ = stages(head, follow=1)
+        follow_line = {"mode": head + " + follow", "value": n_all * args.steps / (fol_total * 1e-3),
+                       "ms_per_step": fol_total / args.steps, "step_ms_median": statistics.median(fol_per),
+                       "n_tracks": fol_tracks, "quality": fol_q,
+                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit") if k in fol_stage}}
     total_ms, per = H["total_ms"], H["per"]
     value = n_all * args.steps / (total_ms * 1e-3)
     n_tracks = H["n_tracks"]
@@ -659,6 +678,7 @@ def main():
         "hit_removal": {"ms": hr_ms, "kept": n_kept, "kept_fraction": n_kept / n,
                         "achieved_gbs": hr_bytes / (hr_ms * 1e-3) / 1e9},
         "dense_scorer": scorer,
+        "follow": follow_line,
         "gpu_launches": H["launches"] * args.steps,
         "clocks": H["clocks"].summary(),
     }

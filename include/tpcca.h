@@ -23,6 +23,23 @@
  *                  tracks, numbered in the order of their start cluster;
  *   A5 fit         FP32 Kalman filter along each chain (helix in (x, y), straight
  *                  line in (arc length, zeta = 0.516 cm/bin * time)), 3-point seed.
+ *   F  follow      (config.follow = 1; the HLT tracker the paper's derives from
+ *                  prolongs and merges its tracklets, Sec. 1, without stated rules)
+ *                  each track whose fit did not stop early is followed outward from
+ *                  its fitted state, row by row in its sector, and inward from that
+ *                  state transported to its first row; in each row the free cluster
+ *                  (no track owns it) with the smallest chi2 <= follow_chi2 against
+ *                  the predicted (y, zeta) is picked up (Kalman update).  Outward,
+ *                  meeting another track's first cluster ends the follow and joins
+ *                  the two when that track's first follow_check clusters pass the
+ *                  gate in turn.  A follow ends after follow_miss rows without a
+ *                  cluster.  A cluster proposed by several tracks goes to the
+ *                  smallest track id, a join to the smallest proposer (a joined
+ *                  track's inward pick-ups are dropped); joined paths become one
+ *                  track (ids in the order of the first track of each path), and
+ *                  every track is fitted again over its clusters (rows may be
+ *                  skipped).  Membership is then decided in FP32: near ties can
+ *                  go either way.
  * With TPC_MODE_PRUNED a learned link classifier rescores the ambiguous clusters
  * of A1 (see the classifier section at the end of this file).
  *
@@ -91,6 +108,10 @@ typedef struct {
                             `sector` field of a cluster is then its instance id, < n_sectors <= 16384,
                             and a track's `sector` output is that id.  More than 36 needs sorted input. */
   int32_t nb_tile;       /* clusters per neighbour tile: 512, 768 or 1024 (0: 768); see tpc_tf_autotune */
+  int32_t follow;        /* 1: follow and join the tracks after the tracklet fit (see below); 0: off */
+  float follow_chi2;     /* follow: gate of a cluster against the predicted (y, zeta), 2 dof (default 16) */
+  int32_t follow_miss;   /* follow: consecutive rows without a cluster that end a follow (default 3) */
+  int32_t follow_check;  /* follow: clusters of another track that must pass the gate before a join (4) */
 } tpc_tf_config;
 
 typedef struct {      /* input clusters: device pointers, read only, caller owned */

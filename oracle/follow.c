@@ -36,12 +36,15 @@
  *   F6 each such track is fitted again with the tracklet fit (three-point seed
  *      and filter over its clusters, any row gaps), ids renumbered in the order of
  *      the roots' old ids, cluster_track rewritten.
- * Decisions that FP32 arithmetic could take differently are recorded: for each
- * final track the smallest margin met by any track of its path (a gated chi2
- * against chi2_max and the gap between the best and next chi2 of a row, in units
- * of 2 % of (1 + chi2); |sin phi| against 0.999, in units of 1e-3).  A margin
- * below 1 marks a track whose membership an FP32 follower may legitimately
- * decide differently.
+ * Decisions that FP32 arithmetic could take differently are recorded.  Each
+ * decision has a margin: a gated chi2 against chi2_max, and the gap between the
+ * best and next chi2 of a row, in units of 2 % of (1 + chi2); |sin phi| against
+ * 0.999, in units of 1e-3.  A cluster keeps the smallest margin of any decision
+ * about it (by any track).  A final track's margin is the smallest over the own
+ * decisions of the tracks of its path, its clusters and every cluster its path
+ * proposed.  A margin below 1 marks a track whose membership an FP32 follower
+ * may legitimately decide differently, or that such a decision elsewhere may
+ * reach (a cluster taken by another track in a near tie).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -132,6 +135,7 @@ typedef struct {
   const int32_t *first_of;  /* track whose first cluster this is, -1 */
   const int32_t *mup;       /* mutual up link (the next cluster of a chain), -1 */
   const or_follow_params *fp;
+  double *cmargin;          /* per sorted cluster: smallest margin of a decision about it */
 } fl_ctx;
 
 /* One row of a follow: the best cluster under the gate among the eligible ones
@@ -141,22 +145,34 @@ static int64_t fl_best(const fl_ctx *x, int sector, int r, int32_t self, int joi
   int64_t k = (int64_t)sector * OR_NROWS + r;
   int64_t best = -1;
   double b = 0.0, second = INFINITY;
+  int64_t second_c = -1;
   for (int64_t c = x->row_first[k]; c < x->row_first[k + 1]; ++c) {
     int eligible = x->own[c] < 0 || (joins && x->first_of[c] >= 0 && x->first_of[c] != self);
     if (!eligible) continue;
     double ym = fl_y(r, x->sp[c]), zm = FL_CM_PER_BIN * ((double)x->st[c] - t_ref);
     double q = fl_chi2(p, C, ym, zm);
-    fl_margin(margin, fabs(q - x->fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + x->fp->chi2_max)));
+    double g = fabs(q - x->fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + x->fp->chi2_max));
+    fl_margin(margin, g);
+    fl_margin(&x->cmargin[c], g);
     if (q > x->fp->chi2_max) continue;
     if (best < 0 || q < b) {
-      if (best >= 0) second = b;
+      if (best >= 0) {
+        second = b;
+        second_c = best;
+      }
       best = c;
       b = q;
     } else if (q < second) {
       second = q;
+      second_c = c;
     }
   }
-  if (best >= 0 && second < INFINITY) fl_margin(margin, (second - b) / (FL_TOL_CHI2 * (1.0 + b)));
+  if (best >= 0 && second_c >= 0) {
+    double g = (second - b) / (FL_TOL_CHI2 * (1.0 + b));
+    fl_margin(margin, g);
+    fl_margin(&x->cmargin[best], g);
+    fl_margin(&x->cmargin[second_c], g);
+  }
   *chi2_best = b;
   return best;
 }
@@ -200,7 +216,9 @@ static void fl_follow(const fl_ctx *x, int32_t t, const or_track_rec *rec, fl_tr
         }
         double ym = fl_y(rr, x->sp[cc]), zm = FL_CM_PER_BIN * ((double)x->st[cc] - rec->t_ref);
         double q2 = fl_chi2(p, C, ym, zm);
-        fl_margin(&ft->margin, fabs(q2 - fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + fp->chi2_max)));
+        double g = fabs(q2 - fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + fp->chi2_max));
+        fl_margin(&ft->margin, g);
+        fl_margin(&x->cmargin[cc], g);
         if (q2 > fp->chi2_max) { ok = 0; break; }
         fl_update(p, C, ym, zm);
         cc = x->mup[cc];
@@ -259,14 +277,18 @@ int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const fl
   int32_t *claim = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
   fl_track *ft = (fl_track *)malloc(sizeof(fl_track) * (nt + 1));
   int32_t *pred = (int32_t *)malloc(sizeof(int32_t) * (nt + 1));
-  if (!own || !first_of || !claim || !ft || !pred) return -1;
-  for (int64_t c = 0; c < n; ++c) own[c] = first_of[c] = claim[c] = -1;
+  double *cmargin = (double *)malloc(sizeof(double) * (n + 1));
+  if (!own || !first_of || !claim || !ft || !pred || !cmargin) return -1;
+  for (int64_t c = 0; c < n; ++c) {
+    own[c] = first_of[c] = claim[c] = -1;
+    cmargin[c] = INFINITY;
+  }
   for (int64_t t = 0; t < nt; ++t) {
     first_of[tstart[t]] = (int32_t)t;
     int32_t c = tstart[t];
     for (int m = 0; m < tlen[t]; ++m, c = mup[c]) own[c] = (int32_t)t;
   }
-  fl_ctx x = {ss, sr, sp, st, row_first, own, first_of, mup, fp};
+  fl_ctx x = {ss, sr, sp, st, row_first, own, first_of, mup, fp, cmargin};
   int64_t proposed = 0;
   for (int64_t t = 0; t < nt; ++t) {
     fl_follow(&x, (int32_t)t, &rec_in[t], &ft[t]);
@@ -311,12 +333,16 @@ int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const fl
       for (int m = 0; m < tlen[t]; ++m, c = mup[c]) mem[L++] = c;
       for (int m = 0; m < ft[t].n_out; ++m)
         if (claim[ft[t].out[m]] == t) mem[L++] = ft[t].out[m];
-      if (ft[t].margin < mg) mg = ft[t].margin;
+      /* the path's own decisions and those about every cluster it proposed */
+      fl_margin(&mg, ft[t].margin);
+      for (int m = 0; m < ft[t].n_out; ++m) fl_margin(&mg, cmargin[ft[t].out[m]]);
+      for (int m = 0; m < ft[t].n_in; ++m) fl_margin(&mg, cmargin[ft[t].in[m]]);
       if (old_to_new) old_to_new[t] = (int32_t)nn;
       int32_t u = ft[t].join;
       t = (u >= 0 && pred[u] == t) ? u : -1;
     }
     for (int m = 0; m < L; ++m) {
+      fl_margin(&mg, cmargin[mem[m]]);
       rows[m] = sr[mem[m]];
       pads[m] = sp[mem[m]];
       times[m] = st[mem[m]];
@@ -347,5 +373,6 @@ int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const fl
   free(claim);
   free(ft);
   free(pred);
+  free(cmargin);
   return rc;
 }

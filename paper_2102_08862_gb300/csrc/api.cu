@@ -92,6 +92,16 @@ struct tpc_tf {
   float *mlp_stage = nullptr; // FP32 blob body staged for packing
   bool mlp_ready = false;
   float logit_tau = 0.f;
+  // track follower (cfg.follow): the chain tracks' fit records, claims, joins and
+  // the followed tracks' membership (arena, follow mode only)
+  float *f_params = nullptr, *f_cov = nullptr, *f_tref = nullptr, *f_x = nullptr, *f_chi2 = nullptr;
+  int32_t *f_ndf = nullptr, *f_nhits = nullptr, *f_first = nullptr;
+  uint16_t *f_sec = nullptr, *f_rf = nullptr, *f_rl = nullptr;
+  uint8_t *f_status = nullptr;
+  uint32_t *f_pred_claim = nullptr;  // [track_list_cap] join proposals, then [N] cluster claims
+  int32_t *f_succ = nullptr;
+  uint32_t *f_npick = nullptr;
+  int32_t *f_chain2 = nullptr, *f_len2 = nullptr, *f_key2 = nullptr;
   // CUDA graph of one call (tpc_track_timeframe_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -112,6 +122,9 @@ extern "C" void tpc_default_config(tpc_tf_config *c) {
   c->tau = 0.5f;
   c->device = 0;
   c->fit_variant = TPC_FIT_THREAD;
+  c->follow_chi2 = 16.0f;
+  c->follow_miss = 3;
+  c->follow_check = 4;
 }
 
 extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
@@ -153,7 +166,10 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
   tf->track_list_cap = cfg->max_tracks ? cfg->max_tracks : tf->N / (uint32_t)cfg->n_min + 1;
 
   const size_t N = tf->N;
-  tf->reset_bytes_max = kNCounters * 4 + 8 * (link_tiles(tf->N) + walk_tiles(tf->N) + 2);
+  const bool fol = cfg->follow != 0;
+  const size_t TL = tf->track_list_cap;
+  tf->reset_bytes_max = kNCounters * 4 + 8 * (link_tiles(tf->N) + walk_tiles(tf->N) + 2 +
+                                              (fol ? follow_tiles(tf->N, cfg->n_min, tf->track_list_cap) : 0));
   std::vector<Part> parts = {
       {(void **)&tf->row_begin, (size_t)(tf->nkeys + 1) * 4},
       {(void **)&tf->tile_off, (size_t)(tf->nkeys + 1) * 4},
@@ -193,6 +209,24 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->q_rows,
        cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * sizeof(PruneRow) : 0},
       {(void **)&tf->q_count, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * 4 : 0},
+      {(void **)&tf->f_params, fol ? TL * 5 * 4 : 0},
+      {(void **)&tf->f_cov, fol ? TL * 15 * 4 : 0},
+      {(void **)&tf->f_tref, fol ? TL * 4 : 0},
+      {(void **)&tf->f_x, fol ? TL * 4 : 0},
+      {(void **)&tf->f_chi2, fol ? TL * 4 : 0},
+      {(void **)&tf->f_ndf, fol ? TL * 4 : 0},
+      {(void **)&tf->f_nhits, fol ? TL * 4 : 0},
+      {(void **)&tf->f_first, fol ? TL * 4 : 0},
+      {(void **)&tf->f_sec, fol ? TL * 2 : 0},
+      {(void **)&tf->f_rf, fol ? TL * 2 : 0},
+      {(void **)&tf->f_rl, fol ? TL * 2 : 0},
+      {(void **)&tf->f_status, fol ? TL : 0},
+      {(void **)&tf->f_pred_claim, fol ? (TL + N + 4) * 4 : 0},
+      {(void **)&tf->f_succ, fol ? TL * 4 : 0},
+      {(void **)&tf->f_npick, fol ? TL * 4 : 0},
+      {(void **)&tf->f_chain2, fol ? (size_t)kNRows * TL * 4 : 0},
+      {(void **)&tf->f_len2, fol ? (TL + 1) * 4 : 0},
+      {(void **)&tf->f_key2, fol ? (TL + 1) * 4 : 0},
   };
   return parts;
 }
@@ -219,6 +253,10 @@ static int validate_config(const tpc_tf_config *cfg) {
     return fail(TPC_ERR_ARG, "tpc_tf_create: n_sectors must be in [0, 16384]");
   if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
     return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
+  if (cfg->follow != 0 && cfg->follow != 1) return fail(TPC_ERR_ARG, "tpc_tf_create: follow must be 0 or 1");
+  if (cfg->follow && (!(cfg->follow_chi2 > 0.0f) || !(cfg->follow_chi2 < 1e6f) || cfg->follow_miss < 1 ||
+                      cfg->follow_miss > TPC_NROWS || cfg->follow_check < 1 || cfg->follow_check > TPC_NROWS))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: follow_chi2 must be in (0, 1e6), follow_miss and follow_check in [1, 152]");
   return TPC_OK;
 }
 
@@ -339,6 +377,23 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.logit_tau = tf->logit_tau;
   a.q_rows = tf->q_rows;
   a.q_count = tf->q_count;
+  if (tf->cfg.follow) {
+    a.fl.params = tf->f_params;
+    a.fl.cov = tf->f_cov;
+    a.fl.t_ref = tf->f_tref;
+    a.fl.status = tf->f_status;
+    a.fl.pred = tf->f_pred_claim;
+    a.fl.claim = tf->f_pred_claim + tf->track_list_cap;
+    a.fl.succ = tf->f_succ;
+    a.fl.npick = tf->f_npick;
+    a.fl.chain2 = tf->f_chain2;
+    a.fl.len2 = tf->f_len2;
+    a.fl.key2 = tf->f_key2;
+    a.fl.lb = a.lb_keep + walk_tiles(n);
+    a.fl.chi2_max = tf->cfg.follow_chi2;
+    a.fl.max_miss = tf->cfg.follow_miss;
+    a.fl.join_check = tf->cfg.follow_check;
+  }
   if (out) {
     a.cluster_track = out->cluster_track;
     a.track_capacity = out->track_capacity;
@@ -365,7 +420,11 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   tf->n_ev = 0;
   tf->launches = 0;
   if (tf->cfg.profile_stages) cudaEventRecord(tf->ev[0], st);
-  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 8 * (link_tiles(n) + walk_tiles(n)), st));
+  TPC_CK(cudaMemsetAsync(
+      tf->reset, 0,
+      kNCounters * 4 +
+          8 * (link_tiles(n) + walk_tiles(n) + (tf->cfg.follow ? follow_tiles(n, tf->cfg.n_min, tf->track_list_cap) : 0)),
+      st));
   ++tf->launches;
   if (sorted) {
     a.sector = cl->sector;
@@ -433,15 +492,51 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   }
   launch_links(a, tf->sms, st);
   stage(tf, st, "links");
-  launch_walk(a, tf->sms, st);
-  stage(tf, st, "walk");
-  launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
-  stage(tf, st, "fit");
-  tf->launches += 3;  // links, walk, fit
+  if (!tf->cfg.follow) {
+    launch_walk(a, tf->sms, st);
+    stage(tf, st, "walk");
+    launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+    stage(tf, st, "fit");
+    tf->launches += 3;  // links, walk, fit
+  } else {
+    // chains and their fit into the follower's records, then following and joining
+    // (cluster_track holds the chain ids in between), then the refit of the
+    // followed tracks into the caller's records
+    Args ac = a;
+    ac.track_capacity = tf->track_list_cap;
+    ac.params = tf->f_params;
+    ac.cov = tf->f_cov;
+    ac.t_ref = tf->f_tref;
+    ac.x = tf->f_x;
+    ac.chi2 = tf->f_chi2;
+    ac.ndf = tf->f_ndf;
+    ac.nhits = tf->f_nhits;
+    ac.first_cluster = tf->f_first;
+    ac.o_sector = tf->f_sec;
+    ac.o_row_first = tf->f_rf;
+    ac.o_row_last = tf->f_rl;
+    ac.o_status = tf->f_status;
+    ac.n_tracks_out = nullptr;
+    launch_walk(ac, tf->sms, st);
+    stage(tf, st, "walk");
+    launch_fit(ac, tf->sms, tf->cfg.fit_variant, st);
+    stage(tf, st, "fit");
+    TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, ((size_t)tf->track_list_cap + n) * 4, st));
+    launch_follow(a, tf->sms, st);
+    stage(tf, st, "follow");
+    Args ar = a;
+    ar.chain = tf->f_chain2;
+    ar.trk_len = tf->f_len2;
+    ar.trk_key = tf->f_key2;
+    launch_refit(ar, tf->sms, st);
+    stage(tf, st, "refit");
+    tf->launches += 7;  // links, walk, fit, claim reset, follow, paths, refit
+  }
   TPC_CK(cudaGetLastError());
   tf->last_args = a;
   if (out->n_tracks_host) {
-    TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + kCtrTracks, 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + (tf->cfg.follow ? kCtrFollowTracks : kCtrTracks), 4,
+                           cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaMemcpyAsync(tf->pinned + 1, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaStreamSynchronize(st));
     *out->n_tracks_host = tf->pinned[0];

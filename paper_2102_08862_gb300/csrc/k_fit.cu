@@ -29,28 +29,13 @@
 // This file is compiled with approximate FP32 division and square root (a few
 // ulp): the filter's error stays far inside the 1e-4 tolerance, and the stage
 // runs 16 % faster than with IEEE-rounded division.
+#include "kf_dev.cuh"
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
 namespace tpc {
 
 namespace {
-
-constexpr float kBz = 0.00149896229f;  // 1/cm per (GeV/c) at 0.5 T
-constexpr float kVy = 0.06f * 0.06f;
-constexpr float kVz = 0.0516f * 0.0516f;
-
-// asin(u)/u and its derivative (Taylor series of asin near 0)
-__device__ __forceinline__ float asinc(float u) {
-  const float u2 = u * u;
-  if (fabsf(u) < 0.05f) return 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
-  return asinf(u) / u;
-}
-__device__ __forceinline__ float asinc_d(float u) {
-  const float u2 = u * u;
-  if (fabsf(u) < 0.05f) return u * (1.0f / 3.0f + u2 * (0.3f + u2 * (15.0f / 56.0f + u2 * (35.0f / 144.0f))));
-  return (u / sqrtf((1.0f - u) * (1.0f + u)) - asinf(u)) / u2;
-}
 
 // index of U(i, j), i < j, in the packed strictly-upper triangle
 __host__ __device__ constexpr int ui(int i, int j) { return 4 * i - i * (i - 1) / 2 + (j - i - 1); }
@@ -191,20 +176,21 @@ __device__ __forceinline__ ff ff_y_um(float pad, int r, float yref_um) {
   return ff_norm(s.hi, s.lo + e);
 }
 
-// Seed at the first cluster; returns status bit 0 for a degenerate circle.  On a
-// short track the curvature rests on a sagitta of a few um over ~10 cm, and its
-// prior makes the seed's q/pT the fit's, so the circle's cross product
-// dx * (mid * (y_last - y0) - (L - 1) * (y_mid - y0)) is formed in float pairs
-// from y values that are exact in um; the rest is plain FP32.
-__device__ __forceinline__ int kf_seed(Kf &k, int L, int r0, float pad0, float pad1, float pad2, float dt2,
+// Seed at the first cluster (row r0) from the circle through it, the middle
+// cluster (row r1) and the last (row r2); returns status bit 0 for a degenerate
+// circle.  On a short track the curvature rests on a sagitta of a few um over
+// ~10 cm, and its prior makes the seed's q/pT the fit's, so the circle's cross
+// product dx * ((r1 - r0) (y_last - y0) - (r2 - r0) (y_mid - y0)) is formed in
+// float pairs from y values that are exact in um; the rest is plain FP32.
+__device__ __forceinline__ int kf_seed(Kf &k, int r0, int r1, int r2, float pad0, float pad1, float pad2, float dt2,
                                        float yref_um) {
-  const int mid = L / 2;
+  const int mid = r1 - r0, last = r2 - r0;
   const ff y0 = ff_y_um(pad0, r0, yref_um);
-  const ff ay = ff_sub(ff_y_um(pad1, r0 + mid, yref_um), y0);
-  const ff by = ff_sub(ff_y_um(pad2, r0 + L - 1, yref_um), y0);
-  const ff sag = ff_sub(ff_scale(by, (float)mid), ff_scale(ay, (float)(L - 1)));
+  const ff ay = ff_sub(ff_y_um(pad1, r1, yref_um), y0);
+  const ff by = ff_sub(ff_y_um(pad2, r2, yref_um), y0);
+  const ff sag = ff_sub(ff_scale(by, (float)mid), ff_scale(ay, (float)last));
   const float cross = kRowDx * (sag.hi + sag.lo) * 1e-4f;  // cm^2
-  const float ax = (float)mid * kRowDx, bx = (float)(L - 1) * kRowDx;
+  const float ax = (float)mid * kRowDx, bx = (float)last * kRowDx;
   const float ayc = (ay.hi + ay.lo) * 1e-4f, byc = (by.hi + by.lo) * 1e-4f;
   const float d01 = sqrtf(ax * ax + ayc * ayc), d02 = sqrtf(bx * bx + byc * byc);
   const float ex = bx - ax, ey = byc - ayc;
@@ -262,8 +248,12 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 
 }  // namespace
 
+// kGapped: the tracks of the follower (chain2, one cluster per row but rows may be
+// skipped): each cluster's row is read, transports span the row gaps, and the
+// track count is the follower's.
+template <bool kGapped>
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
-  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
+  const uint32_t nt = min(min(a.ctr[kGapped ? kCtrFollowTracks : kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     // the chain's clusters were recorded by the walk as chain[step][track]
@@ -272,6 +262,8 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     const int32_t start = ch[0], mid = ch[(size_t)(L / 2) * stride], last = ch[(size_t)(L - 1) * stride];
+    const int rmid = kGapped ? (int)a.row[mid] : r0 + L / 2;
+    const int rlast = kGapped ? (int)a.row[last] : r0 + L - 1;
     const float tref = a.time[start];
     const float pad0 = a.pad[start];
     // y reference: the first cluster's y (rounded to FP32, in um)
@@ -279,33 +271,37 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
     const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
     Kf k;
-    int status = kf_seed(k, L, r0, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
+    int status = kf_seed(k, r0, rmid, rlast, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
     // filter; the next cluster's (pad, time) and the one after's position are
     // loaded before the current step's arithmetic
     int used = 1, lastrow = r0;
     float pd = 0.f, tm = 0.f;
+    int rn = r0 + 1;
     int32_t c2 = -1;
     if (L > 1) {
       const int32_t c1 = ch[stride];
       pd = a.pad[c1];
       tm = a.time[c1];
+      if (kGapped) rn = a.row[c1];
     }
     if (L > 2) c2 = ch[2 * stride];
     for (int q = 1; q < L; ++q) {
       const float cpd = pd, ctm = tm;
+      const int cr = kGapped ? rn : r0 + q;
       if (q + 1 < L) {
         pd = a.pad[c2];
         tm = a.time[c2];
+        if (kGapped) rn = a.row[c2];
         if (q + 2 < L) c2 = ch[(size_t)(q + 2) * stride];
       }
-      if (!kf_transport(k, kRowDx)) {
+      if (!kf_transport(k, kGapped ? (float)(cr - lastrow) * kRowDx : kRowDx)) {
         status |= 2;
         break;
       }
-      kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
+      kf_measure<0>(k, y_local_um(cpd, cr, yref_um) * 1e-4f, kVy);
       kf_measure<1>(k, zeta_local(ctm, tref), kVz);
       ++used;
-      lastrow = r0 + q;
+      lastrow = cr;
     }
     float cov[15];
     kf_covariance(k, cov);
@@ -323,7 +319,7 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     a.first_cluster[t] = caller_index(a, start);
     a.o_sector[t] = (uint16_t)(key / kNRows);
     a.o_row_first[t] = (uint16_t)r0;
-    a.o_row_last[t] = (uint16_t)(r0 + L - 1);
+    a.o_row_last[t] = (uint16_t)rlast;
     a.o_status[t] = (uint8_t)status;
   }
 }
@@ -382,7 +378,8 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
     const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
     Kf k;
-    int status = kf_seed(k, L, r0, pad0, pad_at(L / 2), pad_at(L - 1), time_at(L - 1) - tref, yref_um);
+    int status = kf_seed(k, r0, r0 + L / 2, r0 + L - 1, pad0, pad_at(L / 2), pad_at(L - 1), time_at(L - 1) - tref,
+                         yref_um);
     int used = 1, lastrow = r0;
     for (int q = 1; q < L; ++q) {
       const float cpd = pad_at(q), ctm = time_at(q);
@@ -423,7 +420,9 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
 
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st) {
   if (variant == TPC_FIT_WARP) k_fit_warp<<<sms * 8, 256, 0, st>>>(a);
-  else k_fit_thread<<<sms * 8, 256, 0, st>>>(a);
+  else k_fit_thread<false><<<sms * 8, 256, 0, st>>>(a);
 }
+
+void launch_refit(const Args &a, int sms, cudaStream_t st) { k_fit_thread<true><<<sms * 8, 256, 0, st>>>(a); }
 
 }  // namespace tpc

@@ -1,0 +1,385 @@
+// k_follow.cu -- track following and joining after the tracklet fit.
+//
+// The paper's tracker descends from the Run-2 HLT tracker (Sec. 1), which
+// prolongs its tracklets along the fitted trajectory and merges broken pieces;
+// the paper gives no rules, so these are the readings this library takes:
+//  * every chain track whose fit did not stop early (status bit 1 clear) is
+//    followed outward from its fitted state, one row at a time in its sector, and
+//    inward from that state transported to its first row.  In each row the state
+//    and covariance are transported (helix in x-y, straight line in signed arc
+//    length and zeta) and every cluster of the (sector, row) that no track owns,
+//    or (outward only) that is another track's first cluster, is gated by
+//    chi2 = r^T (C_yz + V)^-1 r <= chi2_max; the smallest (chi2, sorted position)
+//    wins.  A free cluster is picked up (Kalman update, misses reset); another
+//    track's first cluster ends the follow and is a join proposal when that
+//    track's first join_check clusters all pass the gate in turn.  The follow
+//    ends after max_miss consecutive rows without a cluster, at the sector's
+//    first or last row, or at |sin phi| >= 0.999;
+//  * a free cluster proposed by several tracks goes to the smallest track id; a
+//    track proposed for joining by several goes to the smallest proposer; a
+//    joined track's inward pick-ups are dropped;
+//  * a path of joins from a root (a track nobody joined) becomes one track: the
+//    root's inward pick-ups, then each track's chain and outward pick-ups.  Roots
+//    are numbered in the order of their ids; every member gets the new id; the
+//    tracks are fitted again (k_fit_thread<true>, rows may be skipped).
+//
+// GB300 design: k_follow gives each chain track one thread.  Candidates of a row
+// are found by a binary search of its time-sorted clusters around the predicted
+// time, within the half-width that the chi2 gate implies for zeta alone, so the
+// scan is exact for the gate.  Pick-ups go into the unused top of the track's
+// own column of the chain buffer (outward above the chain, inward from row 151
+// down; a track's pick-ups and chain never exceed 152 rows), so no per-pick list
+// is allocated; claims and join proposals are atomicMin words.  k_follow_paths
+// numbers the roots by an ordered compaction (block scan + decoupled look-back
+// over 256-track tiles) and writes each root's members as chain2[step][id].
+#include "kf_dev.cuh"
+#include "tpc_dev.cuh"
+#include "tpc_internal.h"
+
+namespace tpc {
+
+namespace {
+
+constexpr uint32_t kNone = 0xffffffffu;
+constexpr int kThreads = 256;
+
+// index of (i, j) in a lower triangle stored row by row
+__host__ __device__ constexpr int lt(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+struct Fs {
+  float p[5];   // y (cm), zeta - zeta_ref (cm), sin phi, dzeta/ds, q/pT
+  float c[15];  // covariance, lower triangle
+};
+
+// Transport by dx (either sign); false (state untouched) when |sin phi| would
+// reach 0.999.  F = I + E with E nonzero at (0,2), (0,4), (1,2), (1,3), (1,4), (2,4).
+__device__ __forceinline__ bool fs_transport(Fs &f, float dx) {
+  const float s1 = f.p[2], t = f.p[3];
+  const float cv = -kBz * f.p[4];
+  const float s2 = s1 + cv * dx;
+  if (fabsf(s2) >= 0.999f || fabsf(s1) >= 0.999f) return false;
+  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1)), c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  const float A = s1 + s2, D = c1 + c2, iD = 1.0f / D;
+  const float dy = dx * A * iD;
+  const float sg = dx < 0.0f ? -1.0f : 1.0f;  // the arc length has the sign of dx
+  const float l = sqrtf(dx * dx + dy * dy);
+  const float u = 0.5f * cv * l;
+  const float ds = sg * l * asinc(u);
+  const float iD2 = iD * iD;
+  const float Fys = dx * (2.0f * D + A * (s1 / c1 + s2 / c2)) * iD2;  // dy/ds1
+  const float Fyc = dx * dx * (D + A * s2 / c2) * iD2;                // dy/dc
+  const float g = 1.0f / sqrtf((1.0f - u) * (1.0f + u));              // d(arc)/d(chord)
+  const float dyl = l > 0.0f ? dy / l : 0.0f;
+  float E[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) E[i][j] = 0.0f;
+  E[0][2] = Fys;
+  E[0][4] = -kBz * Fyc;
+  E[1][2] = sg * t * g * dyl * Fys;
+  E[1][3] = ds;
+  E[1][4] = -kBz * t * sg * (g * dyl * Fyc + 0.5f * l * l * asinc_d(u));
+  E[2][4] = -kBz * dx;
+  f.p[0] += dy;
+  f.p[1] += t * ds;
+  f.p[2] = s2;
+  // C' = F C F^T
+  float FC[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      float acc = f.c[lt(i, j)];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc = fmaf(E[i][k], f.c[lt(k, j)], acc);
+      FC[i][j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float acc = FC[i][j];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc = fmaf(FC[i][k], E[j][k], acc);
+      f.c[lt(i, j)] = acc;
+    }
+  return true;
+}
+
+// Kalman update with the measurement (ym, zm) of (y, zeta)
+__device__ __forceinline__ void fs_update(Fs &f, float ym, float zm) {
+  const float r0 = ym - f.p[0], r1 = zm - f.p[1];
+  const float S00 = f.c[0] + kVy, S01 = f.c[1], S11 = f.c[2] + kVz;
+  const float idet = 1.0f / (S00 * S11 - S01 * S01);
+  const float Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
+  float K0[5], K1[5], C0[5], C1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    C0[i] = f.c[lt(i, 0)];
+    C1[i] = f.c[lt(i, 1)];
+    K0[i] = C0[i] * Si00 + C1[i] * Si01;
+    K1[i] = C0[i] * Si01 + C1[i] * Si11;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f.p[i] += K0[i] * r0 + K1[i] * r1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) f.c[lt(i, j)] -= K0[i] * C0[j] + K1[i] * C1[j];
+}
+
+__device__ __forceinline__ float meas_y(float pad, int r) {
+  return (pad - 0.5f * (float)(row_npads(r) - 1)) * ((float)row_pitch_um(r) * 1e-4f);
+}
+
+// first e in [lo, hi) with time[e] >= x
+__device__ __forceinline__ int time_lower_bound(const float *time, int lo, int hi, float x) {
+  while (lo < hi) {
+    const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
+    if (time[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The best cluster of (sector, row r) under the gate among those no track owns or
+// (joins) that are another track's first cluster; -1 if none.  *first: the winner
+// is a track's first cluster.
+__device__ int32_t fs_best(const Args &a, const Fs &f, int sec, int r, uint32_t self, bool joins, float tref,
+                           bool *first) {
+  const int key = sec * kNRows + r;
+  const int rb = a.row_begin[key], re = a.row_begin[key + 1];
+  const float chi2_max = a.fl.chi2_max;
+  const float S00 = f.c[0] + kVy, S01 = f.c[1], S11 = f.c[2] + kVz;
+  const float idet = 1.0f / (S00 * S11 - S01 * S01);
+  // chi2 <= chi2_max implies |r_zeta| <= sqrt(chi2_max * S11): search that time
+  // window (widened a little so that rounding never drops a cluster)
+  const float tp = tref + f.p[1] * (1.0f / kCmPerBin);
+  const float w = sqrtf(chi2_max * S11) * (1.0f / kCmPerBin) * 1.001f + 0.01f;
+  const float half = 0.5f * (float)(row_npads(r) - 1), pitch = (float)row_pitch_um(r) * 1e-4f;
+  int32_t best = -1;
+  float bq = 0.0f;
+  bool bfirst = false;
+  for (int c = time_lower_bound(a.time, rb, re, tp - w); c < re; ++c) {
+    const float tc = a.time[c];
+    if (tc > tp + w) break;
+    const int32_t own = a.cluster_track[caller_index(a, c)];
+    bool is_first = false;
+    if (own >= 0) {
+      if (!joins || (uint32_t)own == self || a.chain[own] != c) continue;  // chain[0][own]
+      is_first = true;
+    }
+    const float r0 = (a.pad[c] - half) * pitch - f.p[0];
+    const float r1 = kCmPerBin * (tc - tref) - f.p[1];
+    const float q = (r0 * r0 * S11 - 2.0f * r0 * r1 * S01 + r1 * r1 * S00) * idet;
+    if (!(q <= chi2_max)) continue;
+    if (best < 0 || q < bq) {
+      best = c;
+      bq = q;
+      bfirst = is_first;
+    }
+  }
+  *first = bfirst;
+  return best;
+}
+
+__device__ __forceinline__ void fs_load(const Args &a, uint32_t t, Fs &f) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f.p[i] = a.fl.params[(size_t)t * 5 + i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) f.c[i] = a.fl.cov[(size_t)t * 15 + i];
+}
+
+// exclusive scan of v over the block; *total receives the block sum
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kThreads / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  *total = s_warp[kThreads / 32 - 1];
+  const uint32_t before = wid > 0 ? s_warp[wid - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_follow(Args a) {
+  const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
+  const size_t stride = a.track_list_cap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    uint32_t n_out = 0, n_in = 0;
+    int32_t join = -1;
+    if (!(a.fl.status[t] & 2)) {
+      const int L = a.trk_len[t], key = a.trk_key[t];
+      const int sec = key / kNRows, r0 = key % kNRows, rl = r0 + L - 1;
+      const float tref = a.fl.t_ref[t];
+      int32_t *col = a.chain + t;
+      Fs f;
+      fs_load(a, t, f);
+      // outward
+      int rcur = rl, miss = 0;
+      for (int r = rl + 1; r < kNRows; ++r) {
+        if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
+        rcur = r;
+        bool first;
+        const int32_t c = fs_best(a, f, sec, r, t, true, tref, &first);
+        if (c < 0) {
+          if (++miss >= a.fl.max_miss) break;
+          continue;
+        }
+        if (first) {  // another track's first cluster: its next clusters must follow
+          const int32_t u = a.cluster_track[caller_index(a, c)];
+          const int Lu = a.trk_len[u];
+          bool ok = true;
+          for (int v = 0; v < a.fl.join_check && v < Lu; ++v) {
+            const int32_t cc = a.chain[(size_t)v * stride + u];
+            const int rr = r + v;  // a chain holds consecutive rows
+            if (v > 0) {
+              if (!fs_transport(f, (float)(rr - rcur) * kRowDx)) {
+                ok = false;
+                break;
+              }
+              rcur = rr;
+            }
+            const float ym = meas_y(a.pad[cc], rr), zm = kCmPerBin * (a.time[cc] - tref);
+            const float r0v = ym - f.p[0], r1v = zm - f.p[1];
+            const float S00 = f.c[0] + kVy, S01 = f.c[1], S11 = f.c[2] + kVz;
+            const float q = (r0v * r0v * S11 - 2.0f * r0v * r1v * S01 + r1v * r1v * S00) / (S00 * S11 - S01 * S01);
+            if (!(q <= a.fl.chi2_max)) {
+              ok = false;
+              break;
+            }
+            fs_update(f, ym, zm);
+          }
+          if (ok) join = u;
+          break;
+        }
+        col[(size_t)(L + n_out) * stride] = c;
+        ++n_out;
+        atomicMin(&a.fl.claim[c], t);
+        fs_update(f, meas_y(a.pad[c], r), kCmPerBin * (a.time[c] - tref));
+        miss = 0;
+      }
+      // inward, from the fitted state transported to the first row
+      fs_load(a, t, f);
+      if (r0 > 0 && fs_transport(f, (float)(r0 - rl) * kRowDx)) {
+        rcur = r0;
+        miss = 0;
+        for (int r = r0 - 1; r >= 0; --r) {
+          if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
+          rcur = r;
+          bool first;
+          const int32_t c = fs_best(a, f, sec, r, t, false, tref, &first);
+          if (c < 0) {
+            if (++miss >= a.fl.max_miss) break;
+            continue;
+          }
+          col[(size_t)(kNRows - 1 - n_in) * stride] = c;
+          ++n_in;
+          atomicMin(&a.fl.claim[c], t);
+          fs_update(f, meas_y(a.pad[c], r), kCmPerBin * (a.time[c] - tref));
+          miss = 0;
+        }
+      }
+    }
+    a.fl.npick[t] = n_out | (n_in << 16);
+    a.fl.succ[t] = join;
+    if (join >= 0) atomicMin(&a.fl.pred[join], t);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_follow_paths(Args a) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t s_warp[kThreads / 32];
+  const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
+  const uint32_t n_tiles = (nt + kThreads - 1) / kThreads;
+  if (n_tiles == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.ctr[kCtrFollowTracks] = 0;
+      if (a.n_tracks_out) *a.n_tracks_out = 0;
+    }
+    return;
+  }
+  const size_t stride = a.track_list_cap;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrFollowTile], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const uint32_t t = tile * kThreads + threadIdx.x;
+    const bool root = t < nt && a.fl.pred[t] == kNone;
+    uint32_t total;
+    const uint32_t excl = block_scan(root ? 1u : 0u, s_warp, &total);
+    if (threadIdx.x < 32) {
+      const uint32_t pre = lookback_exclusive(a.fl.lb, tile, total, a.ctr);
+      if (threadIdx.x == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    if (root) {
+      const uint32_t id = s_prefix + excl;
+      int32_t *dst = a.fl.chain2 + id;
+      int m = 0;
+      bool over = false;
+      auto put = [&](int32_t c) {
+        if (m >= kNRows) {  // cannot happen: rows strictly increase along a path
+          over = true;
+          return;
+        }
+        dst[(size_t)m * stride] = c;
+        a.cluster_track[caller_index(a, c)] = (int32_t)id;
+        ++m;
+      };
+      const int nin = (int)(a.fl.npick[t] >> 16);
+      for (int q = nin - 1; q >= 0; --q) {
+        const int32_t c = a.chain[(size_t)(kNRows - 1 - q) * stride + t];
+        if (a.fl.claim[c] == t) put(c);
+      }
+      uint32_t u = t;
+      for (int hop = 0; hop < kNRows; ++hop) {
+        const int Lu = a.trk_len[u];
+        for (int v = 0; v < Lu; ++v) put(a.chain[(size_t)v * stride + u]);
+        const int nout = (int)(a.fl.npick[u] & 0xffffu);
+        for (int q = 0; q < nout; ++q) {
+          const int32_t c = a.chain[(size_t)(Lu + q) * stride + u];
+          if (a.fl.claim[c] == u) put(c);
+        }
+        const int32_t s = a.fl.succ[u];
+        if (s < 0 || a.fl.pred[s] != u) break;
+        u = (uint32_t)s;
+      }
+      if (over) raise(a.ctr, kErrInternal);
+      a.fl.len2[id] = m;
+      a.fl.key2[id] = (a.trk_key[t] / kNRows) * kNRows + (int)a.row[dst[0]];
+    }
+    if (tile == n_tiles - 1 && threadIdx.x == 0) {
+      const uint32_t nf = s_prefix + total;
+      a.ctr[kCtrFollowTracks] = nf;
+      if (a.n_tracks_out) *a.n_tracks_out = nf;
+      if (a.track_capacity > 0 && nf > a.track_capacity) raise(a.ctr, kErrCapacity);
+    }
+    __syncthreads();
+  }
+}
+
+void launch_follow(const Args &a, int sms, cudaStream_t st) {
+  k_follow<<<sms * 8, kThreads, 0, st>>>(a);
+  k_follow_paths<<<sms * 4, kThreads, 0, st>>>(a);
+}
+
+}  // namespace tpc

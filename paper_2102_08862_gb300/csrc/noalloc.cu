@@ -103,6 +103,7 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
   if (!(cl->flags & TPC_INPUT_SORTED))
     return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: input must be sorted (TPC_INPUT_SORTED)");
   if (c.mode != TPC_MODE_PLAIN) return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: only TPC_MODE_PLAIN");
+  if (c.follow) return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: follow needs a handle (tpc_tf_create)");
   if (c.n_min < 3 || c.n_min > TPC_NROWS || c.wy_q < 0 || c.wy_q > (1 << 28) || c.wt_q < 0 || c.wt_q > (1 << 17) ||
       c.cost_max_q < 0 || c.cost_max_q >= (1LL << 40))
     return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: configuration out of range");

@@ -75,6 +75,8 @@ enum : int {
   kCtrQueued = 11,  // clusters rescored from the tile regions (pruned mode)
   kCtrCompactTile = 12,  // hit removal: next tile
   kCtrCompactKept = 13,  // hit removal: clusters kept
+  kCtrFollowTile = 14,   // track follower: next tile of tracks
+  kCtrFollowTracks = 15, // track follower: tracks after joining
   kNCounters = 16
 };
 
@@ -131,6 +133,20 @@ struct Args {
   float logit_tau;         // a pair is kept when its logit >= logit_tau
   struct PruneRow *q_rows;  // per neighbour tile: kPruneRegionRows rows
   int32_t *q_count;         // per neighbour tile: rows used in its region
+  // track follower (follow mode): the chain tracks' fit records, claims and joins
+  struct Follow {
+    const float *params, *cov, *t_ref;  // fit of the chain tracks ([track][5], [track][15], [track])
+    const uint8_t *status;
+    uint32_t *claim;    // [n] smallest track proposing each free cluster, ~0u = none
+    uint32_t *pred;     // [track_list_cap] smallest track proposing to join each track, ~0u = none
+    int32_t *succ;      // [track_list_cap] track this one proposes to join, -1
+    uint32_t *npick;    // [track_list_cap] outward | inward << 16 pick-ups
+    int32_t *chain2;    // [152][track_list_cap] members of the followed tracks
+    int32_t *len2, *key2;
+    uint64_t *lb;       // look-back words, one per 256-track tile
+    float chi2_max;
+    int32_t max_miss, join_check;
+  } fl;
 };
 // rows of a neighbour tile's region in pruned mode
 constexpr int kPruneRegionRows = 128;

@@ -36,6 +36,15 @@ void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st);
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st);
+// track follower: pick-ups, claims and join proposals (k_follow), then the joined
+// tracks' membership in a.fl.chain2 (k_follow_paths); the refit reads chain2
+void launch_follow(const Args &a, int sms, cudaStream_t st);
+void launch_refit(const Args &a, int sms, cudaStream_t st);
+// look-back tiles of the follower (256 tracks each) for n clusters
+inline size_t follow_tiles(uint32_t n, int n_min, uint32_t track_list_cap) {
+  const size_t nt = (size_t)n / (size_t)(n_min > 0 ? n_min : 1) + 1;
+  return ((nt < track_list_cap ? nt : track_list_cap) + 255) / 256 + 1;
+}
 // unsorted input: stable sort by (sector, row, time, pad) into the sorted views
 int launch_sort(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                 uint16_t *s_sector, uint16_t *s_row, float *s_pad, float *s_time, int32_t *perm, void *scratch,

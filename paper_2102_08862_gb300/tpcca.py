@@ -36,7 +36,8 @@ class tpc_tf_config(ctypes.Structure):
     _fields_ = [("max_clusters", c_u32), ("max_tracks", c_u32), ("wy_q", c_i32), ("wt_q", c_i32),
                 ("cost_max_q", c_i64), ("n_min", c_i32), ("mode", c_i32), ("tau", c_f32), ("device", c_i32),
                 ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32), ("n_sectors", c_i32),
-                ("nb_tile", c_i32)]
+                ("nb_tile", c_i32), ("follow", c_i32), ("follow_chi2", c_f32), ("follow_miss", c_i32),
+                ("follow_check", c_i32)]
 
 
 class tpc_clusters(ctypes.Structure):
@@ -580,6 +581,35 @@ class TimeFrameTracker:
         _check(tpc_track_timeframe_graph(self.handle, cl, tr, st.cuda_stream))
         self._n = n
         return self._out["n_tracks"]
+
+    def track_host(self, sector, row, pad, time, sorted_input=True, capacity=None):
+        """tpc_track_timeframe_host on numpy arrays (host buffers): the call copies
+        them in, tracks, copies the results back and synchronises."""
+        import numpy as np
+        n = int(len(sector))
+        cap = int(capacity) if capacity is not None else n // 10 + 1
+        hs = np.ascontiguousarray(sector, np.uint16)
+        hr = np.ascontiguousarray(row, np.uint16)
+        hp = np.ascontiguousarray(pad, np.float32)
+        ht = np.ascontiguousarray(time, np.float32)
+        out = {"cluster_track": np.empty(max(n, 1), np.int32), "params": np.empty((cap, 5), np.float32),
+               "cov": np.empty((cap, 15), np.float32), "t_ref": np.empty(cap, np.float32),
+               "x": np.empty(cap, np.float32), "chi2": np.empty(cap, np.float32), "ndf": np.empty(cap, np.int32),
+               "nhits": np.empty(cap, np.int32), "first_cluster": np.empty(cap, np.int32),
+               "sector": np.empty(cap, np.uint16), "row_first": np.empty(cap, np.uint16),
+               "row_last": np.empty(cap, np.uint16), "status": np.empty(cap, np.uint8)}
+        cnt = np.zeros(1, np.uint32)
+        cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED if sorted_input else 0, sector=hs.ctypes.data,
+                          row=hr.ctypes.data, pad=hp.ctypes.data, time=ht.ctypes.data)
+        tr = tpc_tracks(cluster_track=out["cluster_track"].ctypes.data, track_capacity=cap,
+                        n_tracks=cnt.ctypes.data, **{k: v.ctypes.data for k, v in out.items() if k != "cluster_track"})
+        st = self.torch.cuda.current_stream(self.device).cuda_stream
+        _check(tpc_track_timeframe_host(self.handle, cl, tr, st))
+        self._n = n
+        res = {k: v for k, v in out.items()}
+        res["cluster_track"] = out["cluster_track"][:n]
+        res["n_tracks"] = int(cnt[0])
+        return res
 
     def autotune(self, sector, row, pad, time, sorted_input=True, capacity=None, trials=3):
         cl, tr, n, cap = self.structs(sector, row, pad, time, sorted_input, capacity, host_count=None)

@@ -39,7 +39,8 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("tpc_tf_config %zu\ntpc_clusters %zu\ntpc_tracks %zu\n", sizeof(tpc_tf_config), sizeof(tpc_clusters),
          sizeof(tpc_tracks));
-  F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap);
+  F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap); F(tpc_tf_config, follow_chi2);
+  F(tpc_tf_config, follow_check);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
   printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
   F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device);
@@ -71,6 +72,14 @@ def test_defaults_and_argument_errors(lib):
     c.n_min = 2
     assert lib.tpc_tf_create(ctypes.byref(c), ctypes.byref(h)) == tpcca.TPC_ERR_ARG
     assert lib.tpc_tf_create(None, ctypes.byref(h)) == tpcca.TPC_ERR_ARG
+    c.n_min = 10
+    for k, v in (("follow", 2), ("follow_chi2", 0.0), ("follow_miss", 0), ("follow_check", 153)):
+        d = tpcca.tpc_default_config()
+        d.max_clusters, d.follow = 100, 1
+        assert (d.follow_chi2, d.follow_miss, d.follow_check) == (16.0, 3, 4)
+        setattr(d, k, v)
+        assert lib.tpc_tf_create(ctypes.byref(d), ctypes.byref(h)) == tpcca.TPC_ERR_ARG, k
+        assert "follow" in tpcca.tpc_last_error()
     assert lib.tpc_track_timeframe(None, None, None, None) == tpcca.TPC_ERR_ARG
     assert lib.tpc_tf_status(None, None) == tpcca.TPC_ERR_ARG
     lib.tpc_tf_destroy(None)
