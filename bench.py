@@ -559,7 +559,7 @@ def main():
         follow_line = {"mode": head + " + follow", "value": n_all * args.steps / (fol_total * 1e-3),
                        "ms_per_step": fol_total / args.steps, "step_ms_median": statistics.median(fol_per),
                        "n_tracks": fol_tracks, "quality": fol_q,
-                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit") if k in fol_stage}}
+                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit", "relabel") if k in fol_stage}}
     total_ms, per = H["total_ms"], H["per"]
     value = n_all * args.steps / (total_ms * 1e-3)
     n_tracks = H["n_tracks"]

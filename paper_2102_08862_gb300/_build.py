@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # per translation unit: the Kalman fit uses approximate FP32 division and square
 # root (the fit's tolerance against the FP64 oracle is 1e-4; linking is integer)
-TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"], "k_follow.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc() -> str:

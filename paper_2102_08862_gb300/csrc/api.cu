@@ -101,7 +101,8 @@ struct tpc_tf {
   uint32_t *f_pred_claim = nullptr;  // [track_list_cap] join proposals, then [N] cluster claims
   int32_t *f_succ = nullptr;
   uint32_t *f_npick = nullptr;
-  int32_t *f_chain2 = nullptr, *f_len2 = nullptr, *f_key2 = nullptr;
+  uint32_t *f_map = nullptr;
+  float *f_t16 = nullptr;
   // CUDA graph of one call (tpc_track_timeframe_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -224,9 +225,8 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->f_pred_claim, fol ? (TL + N + 4) * 4 : 0},
       {(void **)&tf->f_succ, fol ? TL * 4 : 0},
       {(void **)&tf->f_npick, fol ? TL * 4 : 0},
-      {(void **)&tf->f_chain2, fol ? (size_t)kNRows * TL * 4 : 0},
-      {(void **)&tf->f_len2, fol ? (TL + 1) * 4 : 0},
-      {(void **)&tf->f_key2, fol ? (TL + 1) * 4 : 0},
+      {(void **)&tf->f_map, fol ? (TL + 1) * 4 : 0},
+      {(void **)&tf->f_t16, fol ? (N / 16 + 2) * 4 : 0},
   };
   return parts;
 }
@@ -386,9 +386,8 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
     a.fl.claim = tf->f_pred_claim + tf->track_list_cap;
     a.fl.succ = tf->f_succ;
     a.fl.npick = tf->f_npick;
-    a.fl.chain2 = tf->f_chain2;
-    a.fl.len2 = tf->f_len2;
-    a.fl.key2 = tf->f_key2;
+    a.fl.map = tf->f_map;
+    a.fl.t16 = tf->f_t16;
     a.fl.lb = a.lb_keep + walk_tiles(n);
     a.fl.chi2_max = tf->cfg.follow_chi2;
     a.fl.max_miss = tf->cfg.follow_miss;
@@ -524,13 +523,11 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, ((size_t)tf->track_list_cap + n) * 4, st));
     launch_follow(a, tf->sms, st);
     stage(tf, st, "follow");
-    Args ar = a;
-    ar.chain = tf->f_chain2;
-    ar.trk_len = tf->f_len2;
-    ar.trk_key = tf->f_key2;
-    launch_refit(ar, tf->sms, st);
+    launch_follow_fit(a, tf->sms, st);
     stage(tf, st, "refit");
-    tf->launches += 7;  // links, walk, fit, claim reset, follow, paths, refit
+    launch_follow_ct(a, tf->sms, st);
+    stage(tf, st, "relabel");
+    tf->launches += 8;  // links, walk, fit, claim reset, time samples, follow, refit, relabel
   }
   TPC_CK(cudaGetLastError());
   tf->last_args = a;

@@ -248,12 +248,8 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 
 }  // namespace
 
-// kGapped: the tracks of the follower (chain2, one cluster per row but rows may be
-// skipped): each cluster's row is read, transports span the row gaps, and the
-// track count is the follower's.
-template <bool kGapped>
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
-  const uint32_t nt = min(min(a.ctr[kGapped ? kCtrFollowTracks : kCtrTracks], a.track_list_cap), a.track_capacity);
+  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     // the chain's clusters were recorded by the walk as chain[step][track]
@@ -262,8 +258,7 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     const int32_t start = ch[0], mid = ch[(size_t)(L / 2) * stride], last = ch[(size_t)(L - 1) * stride];
-    const int rmid = kGapped ? (int)a.row[mid] : r0 + L / 2;
-    const int rlast = kGapped ? (int)a.row[last] : r0 + L - 1;
+    const int rlast = r0 + L - 1;
     const float tref = a.time[start];
     const float pad0 = a.pad[start];
     // y reference: the first cluster's y (rounded to FP32, in um)
@@ -271,37 +266,33 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
     const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
     Kf k;
-    int status = kf_seed(k, r0, rmid, rlast, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
+    int status = kf_seed(k, r0, r0 + L / 2, rlast, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
     // filter; the next cluster's (pad, time) and the one after's position are
     // loaded before the current step's arithmetic
     int used = 1, lastrow = r0;
     float pd = 0.f, tm = 0.f;
-    int rn = r0 + 1;
     int32_t c2 = -1;
     if (L > 1) {
       const int32_t c1 = ch[stride];
       pd = a.pad[c1];
       tm = a.time[c1];
-      if (kGapped) rn = a.row[c1];
     }
     if (L > 2) c2 = ch[2 * stride];
     for (int q = 1; q < L; ++q) {
       const float cpd = pd, ctm = tm;
-      const int cr = kGapped ? rn : r0 + q;
       if (q + 1 < L) {
         pd = a.pad[c2];
         tm = a.time[c2];
-        if (kGapped) rn = a.row[c2];
         if (q + 2 < L) c2 = ch[(size_t)(q + 2) * stride];
       }
-      if (!kf_transport(k, kGapped ? (float)(cr - lastrow) * kRowDx : kRowDx)) {
+      if (!kf_transport(k, kRowDx)) {
         status |= 2;
         break;
       }
-      kf_measure<0>(k, y_local_um(cpd, cr, yref_um) * 1e-4f, kVy);
+      kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
       kf_measure<1>(k, zeta_local(ctm, tref), kVz);
       ++used;
-      lastrow = cr;
+      lastrow = r0 + q;
     }
     float cov[15];
     kf_covariance(k, cov);
@@ -420,9 +411,247 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
 
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st) {
   if (variant == TPC_FIT_WARP) k_fit_warp<<<sms * 8, 256, 0, st>>>(a);
-  else k_fit_thread<false><<<sms * 8, 256, 0, st>>>(a);
+  else k_fit_thread<<<sms * 8, 256, 0, st>>>(a);
 }
 
-void launch_refit(const Args &a, int sms, cudaStream_t st) { k_fit_thread<true><<<sms * 8, 256, 0, st>>>(a); }
+// ------------------------------------------------------- followed tracks
+// The members of the path of joins that starts at root R, in row order: R's
+// accepted inward pick-ups (slots 151, 150, ... of its chain column, read in
+// reverse), then for every track u of the path its chain (slots 0 .. L_u - 1)
+// and its accepted outward pick-ups (slots L_u, L_u + 1, ...).  A pick-up is
+// accepted when the track holds its claim; the path continues from u to succ[u]
+// when u is the accepted proposer of that join.
+namespace {
+
+constexpr uint32_t kFolNone = 0xffffffffu;
+
+__device__ __forceinline__ bool fol_next(const Args &a, uint32_t &u) {
+  const int32_t s = a.fl.succ[u];
+  if (s < 0 || a.fl.pred[s] != u) return false;
+  u = (uint32_t)s;
+  return true;
+}
+
+// accepted pick-ups of track u among its n pick-up slots starting at slot s0,
+// stepping by ds (+1 outward, -1 inward)
+__device__ __forceinline__ int fol_accepted(const Args &a, uint32_t u, int s0, int ds, int n) {
+  int m = 0;
+  for (int q = 0; q < n; ++q) m += a.fl.claim[a.chain[(size_t)(s0 + ds * q) * a.track_list_cap + u]] == u;
+  return m;
+}
+
+// the k-th accepted pick-up of track u (slots from s0 by ds, n of them)
+__device__ __forceinline__ int32_t fol_pick(const Args &a, uint32_t u, int s0, int ds, int n, int k) {
+  for (int q = 0; q < n; ++q) {
+    const int32_t c = a.chain[(size_t)(s0 + ds * q) * a.track_list_cap + u];
+    if (a.fl.claim[c] == u && k-- == 0) return c;
+  }
+  return -1;
+}
+
+// Walks R's path member by member (the same order as fol_member).
+struct FolCursor {
+  uint32_t R, u;
+  int phase;  // 0: R's inward pick-ups, 1: chain of u, 2: outward pick-ups of u, 3: end
+  int q, n;   // position and count within the phase
+};
+
+__device__ __forceinline__ FolCursor fol_begin(const Args &a, uint32_t R) {
+  FolCursor k;
+  k.R = k.u = R;
+  k.phase = 0;
+  k.n = (int)(a.fl.npick[R] >> 16);
+  k.q = k.n - 1;  // inward slots are read from the last pick-up (lowest row) back
+  return k;
+}
+
+// next member, -1 at the end
+__device__ __forceinline__ int32_t fol_next_member(const Args &a, FolCursor &k) {
+  const size_t stride = a.track_list_cap;
+  for (int guard = 0; guard < 4 * kNRows + 8; ++guard) {
+    if (k.phase == 0) {
+      if (k.q >= 0) {
+        const int32_t c = a.chain[(size_t)(kNRows - 1 - k.q) * stride + k.R];
+        --k.q;
+        if (a.fl.claim[c] == k.R) return c;
+        continue;
+      }
+      k.phase = 1;
+      k.q = 0;
+      k.n = a.trk_len[k.u];
+    }
+    if (k.phase == 1) {
+      if (k.q < k.n) return a.chain[(size_t)(k.q++) * stride + k.u];
+      k.phase = 2;
+      k.q = 0;
+      k.n = (int)(a.fl.npick[k.u] & 0xffffu);
+    }
+    if (k.phase == 2) {
+      if (k.q < k.n) {
+        const int32_t c = a.chain[(size_t)(a.trk_len[k.u] + k.q) * stride + k.u];
+        ++k.q;
+        if (a.fl.claim[c] == k.u) return c;
+        continue;
+      }
+      if (!fol_next(a, k.u)) {
+        k.phase = 3;
+        return -1;
+      }
+      k.phase = 1;
+      k.q = 0;
+      k.n = a.trk_len[k.u];
+      continue;
+    }
+    return -1;
+  }
+  return -1;
+}
+
+// member k of R's path (0 <= k < the path's length)
+__device__ int32_t fol_member(const Args &a, uint32_t R, int k) {
+  const size_t stride = a.track_list_cap;
+  const int nin = (int)(a.fl.npick[R] >> 16);
+  const int ain = fol_accepted(a, R, kNRows - 1, -1, nin);
+  if (k < ain) return fol_pick(a, R, kNRows - 1, -1, nin, ain - 1 - k);  // increasing rows
+  k -= ain;
+  uint32_t u = R;
+  for (int hop = 0; hop < kNRows; ++hop) {
+    const int Lu = a.trk_len[u];
+    if (k < Lu) return a.chain[(size_t)k * stride + u];
+    k -= Lu;
+    const int nout = (int)(a.fl.npick[u] & 0xffffu);
+    const int aout = fol_accepted(a, u, Lu, 1, nout);
+    if (k < aout) return fol_pick(a, u, Lu, 1, nout, k);
+    k -= aout;
+    if (!fol_next(a, u)) break;
+  }
+  return -1;
+}
+
+}  // namespace
+
+// Tiles of 256 chain tracks in order: the roots of the tile are numbered by a
+// block scan and a decoupled look-back; each root's thread counts its path,
+// locates its middle and last members, and runs the tracklet fit over the path
+// (the same seed and filter as k_fit_thread, transported across row gaps); the
+// new id of every track on the path goes to map for the cluster pass.
+__global__ void __launch_bounds__(256) k_follow_fit(Args a) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t s_warp[8];
+  const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
+  const uint32_t n_tiles = (nt + 255) / 256;
+  if (n_tiles == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.ctr[kCtrFollowTracks] = 0;
+      if (a.n_tracks_out) *a.n_tracks_out = 0;
+    }
+    return;
+  }
+  const size_t stride = a.track_list_cap;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrFollowPathTile], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const uint32_t R = tile * 256 + threadIdx.x;
+    const bool root = R < nt && a.fl.pred[R] == kFolNone;
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<256>(root ? 1u : 0u, s_warp, &total);
+    if (threadIdx.x < 32) {
+      const uint32_t pre = lookback_exclusive(a.fl.lb, tile, total, a.ctr);
+      if (threadIdx.x == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    if (tile == n_tiles - 1 && threadIdx.x == 0) {
+      const uint32_t nf = s_prefix + total;
+      a.ctr[kCtrFollowTracks] = nf;
+      if (a.n_tracks_out) *a.n_tracks_out = nf;
+      if (a.track_capacity > 0 && nf > a.track_capacity) raise(a.ctr, kErrCapacity);
+    }
+    if (root) {
+      const uint32_t id = s_prefix + excl;
+      // length of the path (chain lengths and accepted pick-ups), map of its tracks
+      int L = fol_accepted(a, R, kNRows - 1, -1, (int)(a.fl.npick[R] >> 16));
+      {
+        uint32_t u = R;
+        for (int hop = 0; hop < kNRows; ++hop) {
+          const int Lu = a.trk_len[u];
+          L += Lu + fol_accepted(a, u, Lu, 1, (int)(a.fl.npick[u] & 0xffffu));
+          a.fl.map[u] = id;
+          if (!fol_next(a, u)) break;
+        }
+      }
+      if (L > kNRows) {  // cannot happen: rows strictly increase along a path
+        raise(a.ctr, kErrInternal);
+        L = kNRows;
+      }
+      if (id < a.track_capacity) {
+        const int32_t start = fol_member(a, R, 0), mid = fol_member(a, R, L / 2), last = fol_member(a, R, L - 1);
+        const int r0 = a.row[start], rlast = a.row[last];
+        const float tref = a.time[start];
+        const float pad0 = a.pad[start];
+        float h0, l0;
+        two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
+        const float yref_um = (h0 + l0) * (float)row_pitch_um(r0);
+        Kf k;
+        int status = kf_seed(k, r0, a.row[mid], rlast, pad0, a.pad[mid], a.pad[last], a.time[last] - tref, yref_um);
+        int used = 1, lastrow = r0;
+        // the filter over members 1 .. L-1 in path order; as in k_fit_thread the
+        // next member's (pad, time, row) and the one after's position are loaded
+        // before the current step's arithmetic
+        FolCursor cur = fol_begin(a, R);
+        fol_next_member(a, cur);  // the first member (it seeds)
+        int32_t c1 = L > 1 ? fol_next_member(a, cur) : -1;
+        float pd = 0.f, tm = 0.f;
+        int rw = 0;
+        if (c1 >= 0) {
+          pd = a.pad[c1];
+          tm = a.time[c1];
+          rw = a.row[c1];
+        }
+        int32_t c2 = L > 2 ? fol_next_member(a, cur) : -1;
+        for (int q = 1; q < L; ++q) {
+          const float cpd = pd, ctm = tm;
+          const int cr = rw;
+          if (q + 1 < L && c2 >= 0) {
+            pd = a.pad[c2];
+            tm = a.time[c2];
+            rw = a.row[c2];
+            c2 = q + 2 < L ? fol_next_member(a, cur) : -1;
+          }
+          if (!kf_transport(k, (float)(cr - lastrow) * kRowDx)) {
+            status |= 2;
+            break;
+          }
+          kf_measure<0>(k, y_local_um(cpd, cr, yref_um) * 1e-4f, kVy);
+          kf_measure<1>(k, zeta_local(ctm, tref), kVz);
+          ++used;
+          lastrow = cr;
+        }
+        float cov[15];
+        kf_covariance(k, cov);
+        float *po = a.params + (size_t)id * 5;
+        po[0] = fmaf(yref_um, 1e-4f, k.p[0]);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) po[i] = k.p[i];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) a.cov[(size_t)id * 15 + i] = cov[i];
+        a.t_ref[id] = tref;
+        a.x[id] = row_x(lastrow);
+        a.chi2[id] = k.chi2;
+        a.ndf[id] = 2 * used - 5;
+        a.nhits[id] = L;
+        a.first_cluster[id] = caller_index(a, start);
+        a.o_sector[id] = (uint16_t)(a.trk_key[R] / kNRows);
+        a.o_row_first[id] = (uint16_t)r0;
+        a.o_row_last[id] = (uint16_t)rlast;
+        a.o_status[id] = (uint8_t)status;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_follow_fit(const Args &a, int sms, cudaStream_t st) { k_follow_fit<<<sms * 8, 256, 0, st>>>(a); }
 
 }  // namespace tpc

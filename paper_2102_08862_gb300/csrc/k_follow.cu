@@ -21,17 +21,21 @@
 //  * a path of joins from a root (a track nobody joined) becomes one track: the
 //    root's inward pick-ups, then each track's chain and outward pick-ups.  Roots
 //    are numbered in the order of their ids; every member gets the new id; the
-//    tracks are fitted again (k_fit_thread<true>, rows may be skipped).
+//    tracks are fitted again over their clusters (rows may be skipped).
 //
-// GB300 design: k_follow gives each chain track one thread.  Candidates of a row
-// are found by a binary search of its time-sorted clusters around the predicted
-// time, within the half-width that the chi2 gate implies for zeta alone, so the
-// scan is exact for the gate.  Pick-ups go into the unused top of the track's
-// own column of the chain buffer (outward above the chain, inward from row 151
-// down; a track's pick-ups and chain never exceed 152 rows), so no per-pick list
-// is allocated; claims and join proposals are atomicMin words.  k_follow_paths
-// numbers the roots by an ordered compaction (block scan + decoupled look-back
-// over 256-track tiles) and writes each root's members as chain2[step][id].
+// GB300 design: in k_follow each lane follows one track at a time and takes the
+// next from a counter, one row per pass of its loop whichever direction it is
+// in, so the lanes of a warp stay busy and together although follows differ in
+// length.  Candidates of a row are found by a search of its time-sorted
+// clusters (binary over every 16th time, kept apart so that it stays in L2, then
+// one block of 16) around the predicted time, within the half-width that the
+// chi2 gate implies for zeta alone, so the scan is exact for the gate.  Pick-ups go into
+// the unused top of the track's own column of the chain buffer (outward above
+// the chain, inward from row 151 down; a track's pick-ups and chain never exceed
+// 152 rows), so no per-pick list is allocated; claims and join proposals are
+// atomicMin words.  k_follow_fit (in k_fit.cu, to share the tracklet fit's
+// arithmetic) numbers the roots and fits each joined path where it lies;
+// k_follow_ct then rewrites cluster_track in one coalesced pass.
 #include "kf_dev.cuh"
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
@@ -133,13 +137,27 @@ __device__ __forceinline__ float meas_y(float pad, int r) {
   return (pad - 0.5f * (float)(row_npads(r) - 1)) * ((float)row_pitch_um(r) * 1e-4f);
 }
 
-// first e in [lo, hi) with time[e] >= x
-__device__ __forceinline__ int time_lower_bound(const float *time, int lo, int hi, float x) {
+// first e in [rb, re) with time[e] >= x, the row's clusters sorted by time.  A
+// binary search over the row's entries of t16 (the time of every 16th sorted
+// cluster: 1/16 of the time array, which stays in L2) leaves a block of at most
+// 15 clusters, whose times are loaded together.
+__device__ __forceinline__ int time_lower_bound(const float *time, const float *t16, int rb, int re, float x) {
+  const int jlo = (rb + 15) >> 4, jhi = (re + 15) >> 4;  // samples 16 j inside [rb, re)
+  int lo = jlo, hi = jhi;
   while (lo < hi) {
     const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
-    if (time[mid] < x) lo = mid + 1; else hi = mid;
+    if (t16[mid] < x) lo = mid + 1; else hi = mid;
   }
-  return lo;
+  // every cluster before e0 is earlier than x; the one at e1 (if < re) is not
+  const int e0 = lo > jlo ? 16 * (lo - 1) + 1 : rb;
+  const int e1 = lo < jhi ? 16 * lo : re;
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < 15; ++q) {
+    const int e = e0 + q;
+    if (e < e1) cnt += time[e] < x;
+  }
+  return e0 + cnt;
 }
 
 // The best cluster of (sector, row r) under the gate among those no track owns or
@@ -160,7 +178,7 @@ __device__ int32_t fs_best(const Args &a, const Fs &f, int sec, int r, uint32_t 
   int32_t best = -1;
   float bq = 0.0f;
   bool bfirst = false;
-  for (int c = time_lower_bound(a.time, rb, re, tp - w); c < re; ++c) {
+  for (int c = time_lower_bound(a.time, a.fl.t16, rb, re, tp - w); c < re; ++c) {
     const float tc = a.time[c];
     if (tc > tp + w) break;
     const int32_t own = a.cluster_track[caller_index(a, c)];
@@ -190,60 +208,68 @@ __device__ __forceinline__ void fs_load(const Args &a, uint32_t t, Fs &f) {
   for (int i = 0; i < 15; ++i) f.c[i] = a.fl.cov[(size_t)t * 15 + i];
 }
 
-// exclusive scan of v over the block; *total receives the block sum
-__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = lane < kThreads / 32 ? s_warp[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < kThreads / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  *total = s_warp[kThreads / 32 - 1];
-  const uint32_t before = wid > 0 ? s_warp[wid - 1] : 0;
-  __syncthreads();
-  return before + x - v;
-}
-
 }  // namespace
 
+// One lane follows one track at a time and goes on to its next track (grid
+// stride) as soon as it is done; every pass of the loop is one row of whichever
+// direction and track the lane is in, with the same code for both directions, so
+// the lanes of a warp stay busy together although their follows differ in length.
 __global__ void __launch_bounds__(kThreads) k_follow(Args a) {
+  __shared__ int32_t s_rb[kNKeys + 1];
   const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
   const size_t stride = a.track_list_cap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    uint32_t n_out = 0, n_in = 0;
-    int32_t join = -1;
-    if (!(a.fl.status[t] & 2)) {
-      const int L = a.trk_len[t], key = a.trk_key[t];
-      const int sec = key / kNRows, r0 = key % kNRows, rl = r0 + L - 1;
-      const float tref = a.fl.t_ref[t];
-      int32_t *col = a.chain + t;
-      Fs f;
+  const bool smem_rb = a.nkeys <= kNKeys;
+  if (smem_rb)
+    for (int k = threadIdx.x; k <= a.nkeys; k += kThreads) s_rb[k] = a.row_begin[k];
+  __syncthreads();
+  Args la = a;
+  if (smem_rb) la.row_begin = s_rb;
+  enum { kOut = 0, kIn = 1, kDone = 2 };
+  int dir = kDone;
+  const uint32_t step = gridDim.x * blockDim.x;
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, n_out = 0, n_in = 0;
+  bool started = false;
+  int32_t join = -1;
+  int L = 0, sec = 0, r0 = 0, rl = 0, r = 0, rcur = 0, miss = 0;
+  float tref = 0.0f;
+  Fs f;
+  for (;;) {
+    if (dir == kDone) {
+      if (started) t += step;  // this lane's next track
+      started = true;
+      if (t >= nt) break;
+      n_out = n_in = 0;
+      join = -1;
+      if (a.fl.status[t] & 2) {  // the fit stopped early: not followed
+        a.fl.npick[t] = 0;
+        a.fl.succ[t] = -1;
+        continue;
+      }
+      L = a.trk_len[t];
+      const int key = a.trk_key[t];
+      sec = key / kNRows;
+      r0 = key % kNRows;
+      rl = r0 + L - 1;
+      tref = a.fl.t_ref[t];
       fs_load(a, t, f);
-      // outward
-      int rcur = rl, miss = 0;
-      for (int r = rl + 1; r < kNRows; ++r) {
-        if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
+      dir = kOut;
+      r = rl + 1;
+      rcur = rl;
+      miss = 0;
+    }
+    // end of a direction: outward -> inward (the fitted state transported to the
+    // first row), inward -> done
+    bool stop = dir == kOut ? r >= kNRows : r < 0;
+    if (!stop) {
+      if (!fs_transport(f, (float)(r - rcur) * kRowDx)) {
+        stop = true;
+      } else {
         rcur = r;
         bool first;
-        const int32_t c = fs_best(a, f, sec, r, t, true, tref, &first);
+        const int32_t c = fs_best(la, f, sec, r, t, dir == kOut, tref, &first);
         if (c < 0) {
-          if (++miss >= a.fl.max_miss) break;
-          continue;
-        }
-        if (first) {  // another track's first cluster: its next clusters must follow
+          stop = ++miss >= a.fl.max_miss;
+        } else if (first) {  // outward only: another track's first cluster, whose next clusters must follow
           const int32_t u = a.cluster_track[caller_index(a, c)];
           const int Lu = a.trk_len[u];
           bool ok = true;
@@ -268,118 +294,91 @@ __global__ void __launch_bounds__(kThreads) k_follow(Args a) {
             fs_update(f, ym, zm);
           }
           if (ok) join = u;
-          break;
-        }
-        col[(size_t)(L + n_out) * stride] = c;
-        ++n_out;
-        atomicMin(&a.fl.claim[c], t);
-        fs_update(f, meas_y(a.pad[c], r), kCmPerBin * (a.time[c] - tref));
-        miss = 0;
-      }
-      // inward, from the fitted state transported to the first row
-      fs_load(a, t, f);
-      if (r0 > 0 && fs_transport(f, (float)(r0 - rl) * kRowDx)) {
-        rcur = r0;
-        miss = 0;
-        for (int r = r0 - 1; r >= 0; --r) {
-          if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
-          rcur = r;
-          bool first;
-          const int32_t c = fs_best(a, f, sec, r, t, false, tref, &first);
-          if (c < 0) {
-            if (++miss >= a.fl.max_miss) break;
-            continue;
+          stop = true;
+        } else {
+          if (dir == kOut) {
+            a.chain[(size_t)(L + n_out) * stride + t] = c;
+            ++n_out;
+          } else {
+            a.chain[(size_t)(kNRows - 1 - n_in) * stride + t] = c;
+            ++n_in;
           }
-          col[(size_t)(kNRows - 1 - n_in) * stride] = c;
-          ++n_in;
           atomicMin(&a.fl.claim[c], t);
           fs_update(f, meas_y(a.pad[c], r), kCmPerBin * (a.time[c] - tref));
           miss = 0;
         }
       }
     }
+    if (!stop) {
+      r += dir == kOut ? 1 : -1;
+      continue;
+    }
+    if (dir == kOut) {
+      dir = kIn;
+      fs_load(a, t, f);
+      if (r0 > 0 && fs_transport(f, (float)(r0 - rl) * kRowDx)) {
+        rcur = r0;
+        r = r0 - 1;
+        miss = 0;
+        continue;
+      }
+    }
+    // done with this track
     a.fl.npick[t] = n_out | (n_in << 16);
     a.fl.succ[t] = join;
     if (join >= 0) atomicMin(&a.fl.pred[join], t);
+    dir = kDone;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_follow_paths(Args a) {
-  __shared__ uint32_t s_tile, s_prefix;
-  __shared__ uint32_t s_warp[kThreads / 32];
-  const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
-  const uint32_t n_tiles = (nt + kThreads - 1) / kThreads;
-  if (n_tiles == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.ctr[kCtrFollowTracks] = 0;
-      if (a.n_tracks_out) *a.n_tracks_out = 0;
+// cluster_track after joining, one cluster per thread in sorted order: a chain
+// member takes its track's new id; a cluster no chain held takes the new id of
+// the track that claimed it, unless the claim was an inward pick-up of a track
+// that was joined (rows below that track's first row), which is dropped.
+__global__ void __launch_bounds__(kThreads) k_follow_ct(Args a) {
+  constexpr int kPer = 4;  // clusters per thread and pass, loaded together
+  const uint32_t n = a.n;
+  const uint32_t span = gridDim.x * blockDim.x;
+  for (uint32_t c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < n; c0 += span * kPer) {
+    int32_t idx[kPer], old[kPer];
+    uint32_t cl[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const uint32_t c = c0 + j * span;
+      idx[j] = c < n ? caller_index(a, (int32_t)c) : -1;
     }
-    return;
-  }
-  const size_t stride = a.track_list_cap;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrFollowTile], 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= n_tiles) break;
-    const uint32_t t = tile * kThreads + threadIdx.x;
-    const bool root = t < nt && a.fl.pred[t] == kNone;
-    uint32_t total;
-    const uint32_t excl = block_scan(root ? 1u : 0u, s_warp, &total);
-    if (threadIdx.x < 32) {
-      const uint32_t pre = lookback_exclusive(a.fl.lb, tile, total, a.ctr);
-      if (threadIdx.x == 0) s_prefix = pre;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      old[j] = idx[j] >= 0 ? a.cluster_track[idx[j]] : 0;
+      cl[j] = idx[j] >= 0 ? a.fl.claim[c0 + j * span] : kNone;
     }
-    __syncthreads();
-    if (root) {
-      const uint32_t id = s_prefix + excl;
-      int32_t *dst = a.fl.chain2 + id;
-      int m = 0;
-      bool over = false;
-      auto put = [&](int32_t c) {
-        if (m >= kNRows) {  // cannot happen: rows strictly increase along a path
-          over = true;
-          return;
-        }
-        dst[(size_t)m * stride] = c;
-        a.cluster_track[caller_index(a, c)] = (int32_t)id;
-        ++m;
-      };
-      const int nin = (int)(a.fl.npick[t] >> 16);
-      for (int q = nin - 1; q >= 0; --q) {
-        const int32_t c = a.chain[(size_t)(kNRows - 1 - q) * stride + t];
-        if (a.fl.claim[c] == t) put(c);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (idx[j] < 0) continue;
+      int32_t v = -1;
+      if (old[j] >= 0) {
+        v = (int32_t)a.fl.map[old[j]];
+      } else if (cl[j] != kNone) {
+        const bool inward = (int)a.row[c0 + j * span] < a.trk_key[cl[j]] % kNRows;
+        if (!inward || a.fl.pred[cl[j]] == kNone) v = (int32_t)a.fl.map[cl[j]];
       }
-      uint32_t u = t;
-      for (int hop = 0; hop < kNRows; ++hop) {
-        const int Lu = a.trk_len[u];
-        for (int v = 0; v < Lu; ++v) put(a.chain[(size_t)v * stride + u]);
-        const int nout = (int)(a.fl.npick[u] & 0xffffu);
-        for (int q = 0; q < nout; ++q) {
-          const int32_t c = a.chain[(size_t)(Lu + q) * stride + u];
-          if (a.fl.claim[c] == u) put(c);
-        }
-        const int32_t s = a.fl.succ[u];
-        if (s < 0 || a.fl.pred[s] != u) break;
-        u = (uint32_t)s;
-      }
-      if (over) raise(a.ctr, kErrInternal);
-      a.fl.len2[id] = m;
-      a.fl.key2[id] = (a.trk_key[t] / kNRows) * kNRows + (int)a.row[dst[0]];
+      if (v != old[j]) a.cluster_track[idx[j]] = v;
     }
-    if (tile == n_tiles - 1 && threadIdx.x == 0) {
-      const uint32_t nf = s_prefix + total;
-      a.ctr[kCtrFollowTracks] = nf;
-      if (a.n_tracks_out) *a.n_tracks_out = nf;
-      if (a.track_capacity > 0 && nf > a.track_capacity) raise(a.ctr, kErrCapacity);
-    }
-    __syncthreads();
   }
+}
+
+// t16[j] = time of sorted cluster 16 j
+__global__ void __launch_bounds__(kThreads) k_time_samples(Args a) {
+  const uint32_t m = (a.n + 15) / 16;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+    a.fl.t16[j] = a.time[(size_t)j * 16];
 }
 
 void launch_follow(const Args &a, int sms, cudaStream_t st) {
-  k_follow<<<sms * 8, kThreads, 0, st>>>(a);
-  k_follow_paths<<<sms * 4, kThreads, 0, st>>>(a);
+  k_time_samples<<<sms * 4, kThreads, 0, st>>>(a);
+  k_follow<<<sms * 4, kThreads, 0, st>>>(a);
 }
+
+void launch_follow_ct(const Args &a, int sms, cudaStream_t st) { k_follow_ct<<<sms * 8, kThreads, 0, st>>>(a); }
 
 }  // namespace tpc

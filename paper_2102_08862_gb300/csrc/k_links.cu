@@ -28,30 +28,6 @@ constexpr int kItems = kLinkTileN / 256;         // consecutive clusters per thr
 constexpr int kLinkTile = kThreads * kItems;     // clusters per look-back tile
 constexpr uint16_t kNone16 = 0xffff;
 
-// exclusive scan of v over the block; *total receives the block sum
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int kWarps = kThreads / 32;
-  uint32_t x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t t = lane < kWarps ? s_warp[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < kWarps) s_warp[lane] = t;
-  }
-  __syncthreads();
-  *total = s_warp[kWarps - 1];
-  return (w > 0 ? s_warp[w - 1] : 0) + x - v;
-}
-
 // last key with rb[key] <= i
 __device__ __forceinline__ int key_of(const int32_t *rb, int i, int nkeys) {
   int lo = 0, hi = nkeys;
@@ -140,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
         if (i0 + q < (int)n) st_keep_u16(a.mup16 + i0 + q, m16[q], keep);
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan((uint32_t)__popc(flags), s_warp, &total);
+    const uint32_t excl = block_exclusive_scan<kThreads>((uint32_t)__popc(flags), s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(a.lb_links, tile, total, a.ctr);
       if (threadIdx.x == 0) s_prefix = pre;
@@ -231,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
       nkept += kept[q];
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan(nkept, s_warp, &total);
+    const uint32_t excl = block_exclusive_scan<kThreads>(nkept, s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(a.lb_keep, tile, total, a.ctr);
       if (threadIdx.x == 0) s_prefix = pre;
@@ -307,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(uint32_t n, const uint16_t
       if (t[q] >= 0) keep |= 1u << q;
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan((uint32_t)__popc(keep), s_warp, &total);
+    const uint32_t excl = block_exclusive_scan<kThreads>((uint32_t)__popc(keep), s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(lb, tile, total, ctr);
       if (threadIdx.x == 0) s_prefix = pre;

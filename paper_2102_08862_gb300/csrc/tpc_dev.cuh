@@ -75,9 +75,10 @@ enum : int {
   kCtrQueued = 11,  // clusters rescored from the tile regions (pruned mode)
   kCtrCompactTile = 12,  // hit removal: next tile
   kCtrCompactKept = 13,  // hit removal: clusters kept
-  kCtrFollowTile = 14,   // track follower: next tile of tracks
+  kCtrFollowTile = 14,   // track follower: next track to follow
   kCtrFollowTracks = 15, // track follower: tracks after joining
-  kNCounters = 16
+  kCtrFollowPathTile = 16,  // track follower: next tile of joined paths
+  kNCounters = 20
 };
 
 // A spin-wait gives up after this many polls (with a short sleep between polls,
@@ -141,8 +142,8 @@ struct Args {
     uint32_t *pred;     // [track_list_cap] smallest track proposing to join each track, ~0u = none
     int32_t *succ;      // [track_list_cap] track this one proposes to join, -1
     uint32_t *npick;    // [track_list_cap] outward | inward << 16 pick-ups
-    int32_t *chain2;    // [152][track_list_cap] members of the followed tracks
-    int32_t *len2, *key2;
+    uint32_t *map;      // [track_list_cap] id after joining of every chain track
+    float *t16;         // [n / 16 + 1] time of every 16th sorted cluster
     uint64_t *lb;       // look-back words, one per 256-track tile
     float chi2_max;
     int32_t max_miss, join_check;
@@ -182,6 +183,33 @@ __device__ __forceinline__ void st_keep_v4(void *addr, uint4 v, uint64_t pol) {
 }
 __device__ __forceinline__ void st_keep_u16(uint16_t *addr, uint16_t v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(addr), "h"(v), "l"(pol) : "memory");
+}
+
+// ------------------------------------------------- block scan
+// exclusive scan of v over a block of THREADS threads; *total receives the block
+// sum.  s_warp holds THREADS / 32 words; reusing it needs a barrier first.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int kWarps = THREADS / 32;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < kWarps ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kWarps) s_warp[lane] = t;
+  }
+  __syncthreads();
+  *total = s_warp[kWarps - 1];
+  return (w > 0 ? s_warp[w - 1] : 0) + x - v;
 }
 
 // ------------------------------------------------- ordered compaction

@@ -36,10 +36,12 @@ void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st);
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st);
-// track follower: pick-ups, claims and join proposals (k_follow), then the joined
-// tracks' membership in a.fl.chain2 (k_follow_paths); the refit reads chain2
+// track follower: pick-ups, claims and join proposals (k_follow); the joined
+// paths numbered and fitted into the caller's records (k_follow_fit); then
+// cluster_track rewritten with the new ids (k_follow_ct)
 void launch_follow(const Args &a, int sms, cudaStream_t st);
-void launch_refit(const Args &a, int sms, cudaStream_t st);
+void launch_follow_fit(const Args &a, int sms, cudaStream_t st);
+void launch_follow_ct(const Args &a, int sms, cudaStream_t st);
 // look-back tiles of the follower (256 tracks each) for n clusters
 inline size_t follow_tiles(uint32_t n, int n_min, uint32_t track_list_cap) {
   const size_t nt = (size_t)n / (size_t)(n_min > 0 ? n_min : 1) + 1;
