@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
 
 
 class FollowParams(ctypes.Structure):
-    _fields_ = [("chi2_max", ctypes.c_double), ("max_miss", ctypes.c_int32), ("join_check", ctypes.c_int32)]
+    _fields_ = [("chi2_max", ctypes.c_double), ("max_miss", ctypes.c_int32), ("join_check", ctypes.c_int32),
+                ("links", ctypes.c_int32), ("xs_rows", ctypes.c_int32), ("chi2_link", ctypes.c_double)]
 
 
 class EvalOut(ctypes.Structure):
@@ -106,7 +107,10 @@ def _load():
             lib.or_track_ex.restype = ctypes.c_int
             lib.or_default_follow.argtypes = [ctypes.POINTER(FollowParams)]
             lib.or_track_follow.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, dbl,
-                                            ctypes.POINTER(FollowParams), vp, vp, i64, vp, vp, vp, vp, vp, vp]
+                                            ctypes.POINTER(FollowParams), vp, vp, i64, vp, vp, vp, vp, vp, vp, vp,
+                                            vp]
+            lib.or_rotate.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
+            lib.or_rotate.restype = ctypes.c_int
             lib.or_track_follow.restype = ctypes.c_int
             lib.or_training_triplets.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), i64, vp, vp, vp, vp]
             lib.or_training_triplets.restype = ctypes.c_int
@@ -255,8 +259,9 @@ def track_follow(sector, row, pad, time, prm: Params | None = None, fp: FollowPa
     `cluster_track` (caller order), `tracks` (TRACK_DTYPE), `n_tracks`, `margin`
     (per final track; < 1 marks membership an FP32 follower may decide
     differently), `old_to_new` (chain track -> final track), `n_chains` (tracks
-    before following) and `stats` (proposed pick-ups, accepted pick-ups, joins,
-    dropped inward pick-ups)."""
+    before following), `stats` (proposed pick-ups, accepted pick-ups, joins,
+    dropped inward pick-ups) and, with fp.links = 1, `next` (the track continuing
+    each track in the neighbouring sector, -1) with its margin `xmargin`."""
     prm = prm or params()
     fp = fp or follow_params()
     sector, row = _c(sector, np.uint16), _c(row, np.uint16)
@@ -270,16 +275,30 @@ def track_follow(sector, row, pad, time, prm: Params | None = None, fp: FollowPa
     o2n = np.full(max(16, n // max(1, prm.n_min) + 1), -1, np.int32)
     nt, nch = ctypes.c_int64(0), ctypes.c_int64(0)
     stats = np.zeros(4, np.int64)
+    nxt = np.full(cap, -1, np.int32)
+    xmargin = np.full(cap, np.inf, np.float64)
     m = _mlp_struct(mlp) if mlp is not None else None
     rc = _load().or_track_follow(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm),
                                  _p(m) if m is not None else None, float(tau), ctypes.byref(fp), _p(order), _p(ct),
                                  cap, _p(tracks), ctypes.byref(nt), _p(margin), _p(o2n), ctypes.byref(nch),
-                                 _p(stats))
+                                 _p(stats), _p(nxt), _p(xmargin))
     if rc < 0:
         raise MemoryError("oracle: track_follow failed")
     k = min(nt.value, cap)
     return dict(cluster_track=ct[:n], tracks=tracks[:k], n_tracks=nt.value, margin=margin[:k],
-                old_to_new=o2n[:nch.value], n_chains=nch.value, stats=stats, order=order[:n])
+                old_to_new=o2n[:nch.value], n_chains=nch.value, stats=stats, order=order[:n], next=nxt[:k],
+                xmargin=xmargin[:k])
+
+
+def rotate(p, x, beta):
+    """Local frame rotated by beta: (p', x', J) or None (see follow.c)."""
+    p = _c(p, np.float64)
+    out = np.zeros(5, np.float64)
+    xo = np.zeros(1, np.float64)
+    J = np.zeros(25, np.float64)
+    if _load().or_rotate(_p(p), float(x), float(beta), _p(out), _p(xo), _p(J)):
+        return None
+    return out, float(xo[0]), J.reshape(5, 5)
 
 
 # ------------------------------------------------------------ link classifier

@@ -36,6 +36,21 @@
  *   F6 each such track is fitted again with the tracklet fit (three-point seed
  *      and filter over its clusters, any row gaps), ids renumbered in the order of
  *      the roots' old ids, cluster_track rewritten.
+ *   X  (cross-sector links, when asked) each final track with status 0 is
+ *      transported outward from its reported state for at most xs_rows rows
+ *      until its predicted y lies beyond the row's pad area (|y| > npads pitch
+ *      / 2); there the state is rotated into the frame of the neighbouring
+ *      sector of the same side (+20 deg for y > 0, -20 deg otherwise; position,
+ *      direction and the covariance through the rotation's Jacobian) and
+ *      transported row by row for at most xs_rows rows from the first row plane
+ *      at or beyond the rotated point.  In each row the first clusters of that
+ *      sector's tracks are gated as above; the best one (chi2, sorted position)
+ *      ends the search and links the two tracks when their states agree at that
+ *      row: the other track's reported state transported to its first row,
+ *      zeta shifted to the same reference, chi2 of the 5-parameter difference
+ *      with the summed covariances <= chi2_link.  A track linked from several
+ *      takes the smallest; next[track] is the track that continues it in the
+ *      neighbouring sector (membership and fits are unchanged).
  * Decisions that FP32 arithmetic could take differently are recorded.  Each
  * decision has a margin: a gated chi2 against chi2_max, and the gap between the
  * best and next chi2 of a row, in units of 2 % of (1 + chi2); |sin phi| against
@@ -59,6 +74,9 @@
  * decision that an FP32 implementation may take the other way */
 #define FL_TOL_CHI2 0.02 /* chi2 comparisons: 2 % of (1 + chi2) */
 #define FL_TOL_SIN 1e-3  /* |sin phi| against the 0.999 stop */
+#define FL_TOL_Y 1e-3    /* a predicted y against the edge of the pad area, cm */
+#define FL_K 0.00149896229
+#define FL_SECTOR_RAD (20.0 * 3.14159265358979323846 / 180.0)
 
 static double fl_x[OR_NROWS];
 static int32_t fl_npads[OR_NROWS], fl_pitch[OR_NROWS];
@@ -258,6 +276,203 @@ void or_default_follow(or_follow_params *fp) {
   fp->chi2_max = 16.0;
   fp->max_miss = 3;
   fp->join_check = 4;
+  fp->links = 0;
+  fp->xs_rows = 152;
+  fp->chi2_link = 80.0;
+}
+
+/* Rotate the local frame by beta: the point (x, y) with direction phi becomes
+ * x' = x cos b + y sin b, y' = -x sin b + y cos b, phi' = phi - b; zeta, dzeta/ds
+ * and q/pT are unchanged.  J (5x5 row-major, optional) is the Jacobian of the new
+ * parameters at fixed x' with respect to the old ones at fixed x: a change of y
+ * moves the point by (sin b, cos b) in the new frame, which is taken back to x'
+ * along the track (slope tan phi', arc dx'/cos phi', turning c ds).  Returns 1
+ * (nothing written) when the direction does not point to larger x' in the new
+ * frame or |sin phi| >= 0.999. */
+int or_rotate(const double *p, double x, double beta, double *pout, double *xout, double *J) {
+  double s = p[2];
+  if (fabs(s) >= 0.999) return 1;
+  double cp = sqrt(1.0 - s * s), cb = cos(beta), sb = sin(beta);
+  double s2 = s * cb - cp * sb, c2 = cp * cb + s * sb;
+  if (c2 <= 0.0 || fabs(s2) >= 0.999) return 1;
+  *xout = x * cb + p[0] * sb;
+  pout[0] = -x * sb + p[0] * cb;
+  pout[1] = p[1];
+  pout[2] = s2;
+  pout[3] = p[3];
+  pout[4] = p[4];
+  if (J) {
+    double c = -FL_K * p[4];
+    for (int i = 0; i < 25; ++i) J[i] = 0.0;
+    J[0 * 5 + 0] = cb - sb * s2 / c2;
+    J[1 * 5 + 0] = -p[3] * sb / c2;
+    J[1 * 5 + 1] = 1.0;
+    J[2 * 5 + 0] = -c * sb;
+    J[2 * 5 + 2] = c2 / cp;
+    J[3 * 5 + 3] = 1.0;
+    J[4 * 5 + 4] = 1.0;
+  }
+  return 0;
+}
+
+/* chi2 of the 5-parameter difference d with covariance S (Cholesky); -1 if S is
+ * not positive definite */
+static double fl_chi2_5(const double *d, const double *S) {
+  double L[25] = {0};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = S[i * 5 + j];
+      for (int k = 0; k < j; ++k) v -= L[i * 5 + k] * L[j * 5 + k];
+      if (i == j) {
+        if (v <= 0.0) return -1.0;
+        L[i * 5 + i] = sqrt(v);
+      } else {
+        L[i * 5 + j] = v / L[j * 5 + j];
+      }
+    }
+  double z[5], q = 0.0;
+  for (int i = 0; i < 5; ++i) {
+    double v = d[i];
+    for (int k = 0; k < i; ++k) v -= L[i * 5 + k] * z[k];
+    z[i] = v / L[i * 5 + i];
+    q += z[i] * z[i];
+  }
+  return q;
+}
+
+static void fl_full_cov(const double *lower, double *C) {
+  for (int i = 0, q = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j, ++q) C[i * 5 + j] = C[j * 5 + i] = lower[q];
+}
+
+/* X: links of the final tracks across sector boundaries (see the header).
+ * ct: final track of each sorted cluster; first_of: final track whose first
+ * cluster this sorted cluster is. */
+static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *first_of, const or_track_rec *tr,
+                            int64_t nf, int32_t *next, double *xmargin) {
+  const or_follow_params *fp = x->fp;
+  int32_t *pred = (int32_t *)malloc(sizeof(int32_t) * (nf + 1));
+  int32_t *prop = (int32_t *)malloc(sizeof(int32_t) * (nf + 1));
+  double *bmargin = (double *)malloc(sizeof(double) * (nf + 1));
+  if (!pred || !prop || !bmargin) return;
+  for (int64_t t = 0; t < nf; ++t) {
+    pred[t] = prop[t] = -1;
+    bmargin[t] = INFINITY;
+    xmargin[t] = INFINITY;
+  }
+  for (int64_t A = 0; A < nf; ++A) {
+    const or_track_rec *ra = &tr[A];
+    double mg = INFINITY;
+    if (ra->status != 0 || ra->row_last >= OR_NROWS - 1) continue;
+    double p[5], C[25];
+    for (int i = 0; i < 5; ++i) p[i] = ra->p[i];
+    fl_full_cov(ra->C, C);
+    int rcur = ra->row_last, exit_row = -1;
+    for (int r = ra->row_last + 1; r < OR_NROWS && r <= ra->row_last + fp->xs_rows; ++r) {
+      if (fl_transport(p, C, fl_x[r] - fl_x[rcur], &mg)) break;
+      rcur = r;
+      double edge = 0.5 * (double)fl_npads[r] * (double)fl_pitch[r] * 1e-4;
+      fl_margin(&mg, fabs(fabs(p[0]) - edge) / FL_TOL_Y);
+      if (fabs(p[0]) > edge) {
+        exit_row = r;
+        break;
+      }
+    }
+    if (exit_row < 0) {
+      xmargin[A] = mg;
+      continue;
+    }
+    int up = p[0] > 0.0;
+    double beta = up ? FL_SECTOR_RAD : -FL_SECTOR_RAD;
+    int side = ra->sector / 18, ls = ra->sector % 18;
+    int s2 = side * 18 + (up ? (ls + 1) % 18 : (ls + 17) % 18);
+    double q[5], Jr[25], xr;
+    if (or_rotate(p, fl_x[exit_row], beta, q, &xr, Jr)) {
+      xmargin[A] = mg;
+      continue;
+    }
+    double T[25], C2[25];
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 5; ++k) acc += Jr[i * 5 + k] * C[k * 5 + j];
+        T[i * 5 + j] = acc;
+      }
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < 5; ++k) acc += T[i * 5 + k] * Jr[j * 5 + k];
+        C2[i * 5 + j] = acc;
+      }
+    /* first row plane at or beyond the rotated point */
+    int r0 = 0;
+    while (r0 < OR_NROWS && fl_x[r0] < xr) ++r0;
+    double xcur = xr;
+    for (int r = r0; r < OR_NROWS && r < r0 + fp->xs_rows; ++r) {
+      if (fl_transport(q, C2, fl_x[r] - xcur, &mg)) break;
+      xcur = fl_x[r];
+      /* the first clusters of s2's tracks in this row under the gate */
+      int64_t k = (int64_t)s2 * OR_NROWS + r, best = -1, second = -1;
+      double b = 0.0, sec = INFINITY;
+      for (int64_t c = x->row_first[k]; c < x->row_first[k + 1]; ++c) {
+        if (first_of[c] < 0) continue;
+        double ym = fl_y(r, x->sp[c]), zm = FL_CM_PER_BIN * ((double)x->st[c] - ra->t_ref);
+        double g2 = fl_chi2(q, C2, ym, zm);
+        double g = fabs(g2 - fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + fp->chi2_max));
+        fl_margin(&mg, g);
+        fl_margin(&bmargin[first_of[c]], g);
+        if (g2 > fp->chi2_max) continue;
+        if (best < 0 || g2 < b) {
+          second = best;
+          sec = b;
+          best = c;
+          b = g2;
+        } else if (g2 < sec) {
+          second = c;
+          sec = g2;
+        }
+      }
+      if (best < 0) continue;
+      if (second >= 0) {
+        double g = (sec - b) / (FL_TOL_CHI2 * (1.0 + b));
+        fl_margin(&mg, g);
+        fl_margin(&bmargin[first_of[best]], g);
+        fl_margin(&bmargin[first_of[second]], g);
+      }
+      int32_t B = first_of[best];
+      const or_track_rec *rb = &tr[B];
+      if (rb->status == 0) {
+        double pb[5], Cb[25];
+        for (int i = 0; i < 5; ++i) pb[i] = rb->p[i];
+        fl_full_cov(rb->C, Cb);
+        double mgb = INFINITY;
+        if (!fl_transport(pb, Cb, fl_x[r] - rb->x, &mgb)) {
+          double d[5], S[25];
+          pb[1] += FL_CM_PER_BIN * (rb->t_ref - ra->t_ref);
+          for (int i = 0; i < 5; ++i) d[i] = q[i] - pb[i];
+          for (int i = 0; i < 25; ++i) S[i] = C2[i] + Cb[i];
+          double q5 = fl_chi2_5(d, S);
+          if (q5 >= 0.0) {
+            double g = fabs(q5 - fp->chi2_link) / (FL_TOL_CHI2 * (1.0 + fp->chi2_link));
+            fl_margin(&mg, g);
+            fl_margin(&bmargin[B], g);
+            if (q5 <= fp->chi2_link) prop[A] = B;
+          }
+        }
+        fl_margin(&mg, mgb);
+      }
+      break;
+    }
+    xmargin[A] = mg;
+    if (prop[A] >= 0 && pred[prop[A]] < 0) pred[prop[A]] = (int32_t)A;
+  }
+  for (int64_t A = 0; A < nf; ++A) {
+    next[A] = (prop[A] >= 0 && pred[prop[A]] == A) ? prop[A] : -1;
+    if (prop[A] >= 0) fl_margin(&xmargin[A], bmargin[prop[A]]);
+  }
+  free(pred);
+  free(prop);
+  free(bmargin);
 }
 
 /* See the file header.  Inputs: the sorted frame, its (sector, row) ranges, the
@@ -270,7 +485,8 @@ int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const fl
                      const int64_t *row_first, const int32_t *order, const int32_t *mup, int64_t nt,
                      const int32_t *tstart, const int32_t *tlen, const or_track_rec *rec_in,
                      const or_follow_params *fp, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks,
-                     int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *stats) {
+                     int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *stats, int32_t *next,
+                     double *xmargin) {
   fl_geom();
   int32_t *own = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
   int32_t *first_of = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
@@ -358,6 +574,22 @@ int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const fl
     ++nn;
   }
   *n_tracks = nn;
+  if (fp->links && next && xmargin && nn <= track_cap) {
+    /* final track of each sorted cluster, and whose first cluster it is */
+    int32_t *fct = own, *ffirst = first_of;
+    for (int64_t c = 0; c < n; ++c) {
+      fct[c] = cluster_track[order[c]];
+      ffirst[c] = -1;
+    }
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (n + 1)); /* caller index -> sorted position */
+    if (!pos) return -1;
+    for (int64_t c = 0; c < n; ++c) pos[order[c]] = (int32_t)c;
+    for (int64_t t = 0; t < nn; ++t) ffirst[pos[tracks[t].first_cluster]] = (int32_t)t;
+    free(pos);
+    fl_sector_links(&x, fct, ffirst, tracks, nn, next, xmargin);
+  } else if (next) {
+    for (int64_t t = 0; t < nn && t < track_cap; ++t) next[t] = -1;
+  }
   if (stats) {
     stats[0] = proposed;
     stats[1] = accepted;

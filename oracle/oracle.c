@@ -497,7 +497,8 @@ static int or_track_core(int64_t n, const uint16_t *sector, const uint16_t *row,
                          const or_params *prm, const or_mlp *mlp, double tau, int32_t *order, int32_t *down,
                          int32_t *up, int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track,
                          int64_t track_cap, or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats,
-                         const or_follow_params *fp, double *fmargin, int32_t *old_to_new, int64_t *fstats) {
+                         const or_follow_params *fp, double *fmargin, int32_t *old_to_new, int64_t *fstats,
+                         int32_t *fnext, double *fxmargin) {
   *n_tracks = 0;
   if (n == 0) return 0;
   uint16_t *ss = (uint16_t *)malloc(sizeof(uint16_t) * n), *sr = (uint16_t *)malloc(sizeof(uint16_t) * n);
@@ -586,7 +587,7 @@ static int or_track_core(int64_t n, const uint16_t *sector, const uint16_t *row,
     if (!rf) return -1;
     or_row_ranges(n, ss, sr, rf);
     int frc = or_follow_tracks(n, ss, sr, sp, st, rf, order, mup, nt, tstart, tlen, trec, fp, cluster_track,
-                               track_cap, tracks, n_tracks, fmargin, old_to_new, fstats);
+                               track_cap, tracks, n_tracks, fmargin, old_to_new, fstats, fnext, fxmargin);
     if (frc < 0) return -1;
     rc = frc;
     free(rf);
@@ -612,13 +613,14 @@ int or_track_ex(int64_t n, const uint16_t *sector, const uint16_t *row, const fl
                 int32_t *mdown, int32_t *mup, uint8_t *is_start, int32_t *cluster_track, int64_t track_cap,
                 or_track_rec *tracks, int64_t *n_tracks, uint8_t *band, int64_t *stats) {
   return or_track_core(n, sector, row, pad, time, prm, mlp, tau, order, down, up, mdown, mup, is_start, cluster_track,
-                       track_cap, tracks, n_tracks, band, stats, NULL, NULL, NULL, NULL);
+                       track_cap, tracks, n_tracks, band, stats, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 int or_track_follow(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                     const or_params *prm, const or_mlp *mlp, double tau, const or_follow_params *fp,
                     int32_t *order, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks,
-                    int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *n_chains, int64_t *fstats) {
+                    int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *n_chains, int64_t *fstats,
+                    int32_t *next, double *xmargin) {
   int32_t *down = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *up = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
   int32_t *mdown = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *mup = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
   uint8_t *is_start = (uint8_t *)malloc(n + 1);
@@ -626,7 +628,7 @@ int or_track_follow(int64_t n, const uint16_t *sector, const uint16_t *row, cons
   int64_t st[4] = {0, 0, 0, 0};
   int rc = or_track_core(n, sector, row, pad, time, prm, mlp, tau, order, down, up, mdown, mup, is_start,
                          cluster_track, track_cap, tracks, n_tracks, NULL, mlp ? st : NULL, fp, margin, old_to_new,
-                         fstats);
+                         fstats, next, xmargin);
   /* chains before following = pick-ups and joins undone: n_tracks + joins */
   if (n_chains) *n_chains = *n_tracks + (fstats ? fstats[2] : 0);
   free(down);

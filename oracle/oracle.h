@@ -106,22 +106,29 @@ typedef struct {
   double chi2_max;  /* gate of a cluster against the predicted (y, zeta), 2 dof (16) */
   int32_t max_miss; /* the follow ends after this many consecutive rows without a cluster (3) */
   int32_t join_check; /* clusters of the other track that must pass the gate before a join (4) */
+  int32_t links;      /* 1: also link tracks across sector boundaries (0) */
+  int32_t xs_rows;    /* rows searched on either side of a sector boundary (152: to the end) */
+  double chi2_link;   /* 5-parameter agreement of two linked tracks (80) */
 } or_follow_params;
 void or_default_follow(or_follow_params *fp);
+int or_rotate(const double *p, double x, double beta, double *pout, double *xout, double *J);
 int or_follow_tracks(int64_t n, const uint16_t *ss, const uint16_t *sr, const float *sp, const float *st,
                      const int64_t *row_first, const int32_t *order, const int32_t *mup, int64_t nt,
                      const int32_t *tstart, const int32_t *tlen, const or_track_rec *rec_in,
                      const or_follow_params *fp, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks,
-                     int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *stats);
+                     int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *stats, int32_t *next,
+                     double *xmargin);
 /* The whole path (A1 pruned by mlp when non-NULL) followed by following and
  * joining.  margin[final track] < 1 marks membership that FP32 arithmetic may
  * decide differently; old_to_new[chain track] = final track; *n_chains = tracks
  * before following; fstats = {proposed pick-ups, accepted pick-ups, joins,
- * dropped inward pick-ups}. */
+ * dropped inward pick-ups}; with fp->links, next[final track] = the track that
+ * continues it in the neighbouring sector (-1) and xmargin its decision margin. */
 int or_track_follow(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                     const or_params *prm, const or_mlp *mlp, double tau, const or_follow_params *fp,
                     int32_t *order, int32_t *cluster_track, int64_t track_cap, or_track_rec *tracks,
-                    int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *n_chains, int64_t *fstats);
+                    int64_t *n_tracks, double *margin, int32_t *old_to_new, int64_t *n_chains, int64_t *fstats,
+                    int32_t *next, double *xmargin);
 int or_eval(int64_t n, const int32_t *label, const uint16_t *sector, const int32_t *cluster_track, int64_t n_tracks,
             int64_t n_gen_tracks, int32_t min_findable, double match_frac, or_eval_out *out);
 #endif

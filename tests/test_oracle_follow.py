@@ -172,3 +172,157 @@ def test_empty_and_no_tracks():
     sec, row, pad, tim, _ = _helices(1, drop=set(range(5, 152, 6)))  # no chain of 10 survives
     res = orc.track_follow(sec, row, pad, tim)
     assert res["n_tracks"] == 0 and (res["cluster_track"] < 0).all()
+
+
+# ---------------------------------------------------------------- cross-sector links
+X = 85.0 + np.arange(152) * (160.0 / 151.0)
+BETA = np.radians(20.0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_rotation_jacobian_matches_finite_differences(seed):
+    """The rotation's Jacobian (new parameters at fixed x') against rotating a
+    perturbed state exactly and transporting it back to the nominal x'."""
+    rng = np.random.default_rng(300 + seed)
+    done = 0
+    for _ in range(40):
+        x = rng.uniform(90.0, 240.0)
+        p = np.array([rng.uniform(0.8, 1.0) * x * np.tan(np.radians(10.0)), rng.uniform(-20, 20),
+                      rng.uniform(-0.5, 0.5), rng.uniform(-1.0, 1.0), rng.uniform(-3, 3)])
+        beta = BETA if rng.uniform() < 0.5 else -BETA
+        res = orc.rotate(p, x, beta)
+        if res is None:
+            continue
+        q0, x0, J = res
+        h = np.array([1e-5, 1e-5, 1e-7, 1e-7, 1e-6])
+        num = np.zeros((5, 5))
+        ok = True
+        for j in range(5):
+            cols = []
+            for sgn in (1, -1):
+                e = np.zeros(5)
+                e[j] = sgn * h[j]
+                r = orc.rotate(p + e, x, beta)
+                back = orc.propagate(r[0], x0 - r[1]) if r is not None else None
+                if back is None:
+                    ok = False
+                    break
+                cols.append(back[0])
+            if not ok:
+                break
+            num[:, j] = (cols[0] - cols[1]) / (2 * h[j])
+        if not ok:
+            continue
+        assert np.allclose(J, num, rtol=1e-5, atol=1e-6), (J, num)
+        done += 1
+    assert done > 20
+
+
+def test_rotation_then_transport_reproduces_the_neighbouring_sector():
+    """A generator helix seen in sector 0 at row r, rotated into sector 1's frame and
+    transported to a row there, equals the generator's own crossing in sector 1."""
+    checked = 0
+    for qpt, phi0, eta in ((1.0, 17.0, 0.3), (-0.7, 21.0, 0.5), (2.5, 19.0, 0.1), (-1.5, 15.0, 0.7)):
+        phi0 = np.radians(phi0)
+        for r in (20, 60, 100):
+            a = ts.truth_at(qpt, phi0, eta, 0.0, 0, r)
+            if a is None:
+                continue
+            y, tb, sp, tz = a
+            res = orc.rotate(np.array([y, 0.0, sp, tz, qpt]), X[r], BETA)
+            if res is None:
+                continue
+            q, xq, _ = res
+            for r2 in range(152):
+                if X[r2] < xq:
+                    continue
+                b = ts.truth_at(qpt, phi0, eta, 0.0, 1, r2)
+                if b is None:
+                    continue
+                out = orc.propagate(q, X[r2] - xq)
+                if out is None:
+                    continue
+                assert out[0][0] == pytest.approx(b[0], abs=1e-8)
+                assert out[0][2] == pytest.approx(b[2], abs=1e-10)
+                assert out[0][1] == pytest.approx(0.516 * (b[1] - tb), abs=1e-8)
+                checked += 1
+                break
+    assert checked >= 6
+
+
+def _crossing_helices(n_tracks, seed=5):
+    """Noise-free helices of one collision that cross from sector 0 into sector 1
+    (or back), clusters in both sectors wherever they fall on the pad plane."""
+    rng = np.random.default_rng(seed)
+    sec, row, pad, tim, lab = [], [], [], [], []
+    for t in range(n_tracks):
+        eta = 0.05 + 0.8 * t / n_tracks
+        pt = rng.uniform(0.5, 2.0)
+        q = 1 if t % 2 else -1
+        # the position's azimuth at radius rho is phi0 -/+ asin(|c| rho / 2) for q = +/-1:
+        # cross the sector boundary (20 deg) at a radius between 115 and 215 cm
+        rho = rng.uniform(115.0, 215.0)
+        d = np.arcsin(0.00149896229 / pt * rho / 2.0)
+        phi0 = np.radians(20.0) + (d if q > 0 else -d)
+        for s in (0, 1):
+            for r in range(152):
+                res = ts.truth_at(q / pt, phi0, eta, 0.0, s, r)
+                if res is None:
+                    continue
+                y, tb, _, _ = res
+                p = y / _pitch_cm(r) + 0.5 * (_npads(r) - 1)
+                if not (-0.5 <= p < _npads(r) - 0.5) or not (0 <= tb < 500):
+                    continue
+                sec.append(s); row.append(r); pad.append(p); tim.append(tb); lab.append(t)
+    return (np.array(sec, np.uint16), np.array(row, np.uint16), np.array(pad, np.float32),
+            np.array(tim, np.float32), np.array(lab))
+
+
+def _labels(ct, lab, nt):
+    out = np.full(nt, -2)
+    for k in range(nt):
+        v, c = np.unique(lab[ct == k], return_counts=True)
+        out[k] = v[np.argmax(c)]
+    return out
+
+
+def test_crossing_helices_are_linked_across_the_boundary():
+    s, r, p, t, lab = _crossing_helices(10)
+    res = orc.track_follow(s, r, p, t, fp=orc.follow_params(links=1))
+    nt = res["n_tracks"]
+    labs = _labels(res["cluster_track"], lab, nt)
+    sec = res["tracks"]["sector"]
+    nxt = res["next"]
+    pairs = 0
+    for L in np.unique(labs):
+        ks = np.nonzero(labs == L)[0]
+        if len(ks) != 2 or sec[ks[0]] == sec[ks[1]]:
+            continue
+        pairs += 1
+        a, b = ks
+        assert nxt[a] == b or nxt[b] == a, (L, a, b, nxt[a], nxt[b])
+    linked = np.nonzero(nxt >= 0)[0]
+    assert pairs >= 5 and linked.size == pairs
+    assert np.all(labs[linked] == labs[nxt[linked]])
+    # without links nothing is reported
+    off = orc.track_follow(s, r, p, t)
+    assert np.all(off["next"] == -1)
+
+
+def test_links_on_a_dense_slice_are_pure(c2_slice):
+    f, _ = c2_slice
+    m = f.sector < 4
+    s, r, p, t, lab = f.sector[m], f.row[m], f.pad[m], f.time[m], f.label[m]
+    res = orc.track_follow(s, r, p, t, fp=orc.follow_params(links=1))
+    nt = res["n_tracks"]
+    nxt = res["next"]
+    linked = np.nonzero(nxt >= 0)[0]
+    sec = res["tracks"]["sector"].astype(int)
+    # a link goes to the neighbouring sector of the same side; each track has one predecessor at most
+    d = (sec[nxt[linked]] % 18 - sec[linked] % 18) % 18
+    assert np.all((d == 1) | (d == 17)) and np.all(sec[nxt[linked]] // 18 == sec[linked] // 18)
+    assert np.unique(nxt[linked]).size == linked.size
+    assert np.all(res["tracks"]["status"][linked] == 0)
+    labs = _labels(res["cluster_track"], lab, nt)
+    pure = np.mean(labs[linked] == labs[nxt[linked]])
+    assert linked.size > 500 and pure > 0.995
