@@ -425,7 +425,7 @@ def main():
     modes = {"pruned": dict(mode=tpcca.TPC_MODE_PRUNED, tau=tau), "plain": dict(mode=tpcca.TPC_MODE_PLAIN)}
     if args.follow:
         for v in modes.values():
-            v["follow"] = 1
+            v["follow"] = 2
     cap = n // 10 + 1
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
@@ -550,16 +550,19 @@ def main():
     # the headline arm with track following and joining (an extra line, not the headline)
     follow_line = None
     if not args.follow:
-        fol = make(head, follow=1)
+        fol = make(head, follow=2)
         fol_tracks = checked_call(fol)
         fol_total, fol_per, _ = timed(fol, args.steps, False)
         fol_q = quality(fol)
+        fol_links = int((fol._out["next_track"][:fol_tracks] >= 0).sum().item())
         fol.close()
-        fol_stage, _, _ = stages(head, follow=1)
-        follow_line = {"mode": head + " + follow", "value": n_all * args.steps / (fol_total * 1e-3),
+        fol_stage, _, _ = stages(head, follow=2)
+        follow_line = {"mode": head + " + follow, joins and sector links", "sector_links": fol_links,
+                       "value": n_all * args.steps / (fol_total * 1e-3),
                        "ms_per_step": fol_total / args.steps, "step_ms_median": statistics.median(fol_per),
                        "n_tracks": fol_tracks, "quality": fol_q,
-                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit", "relabel") if k in fol_stage}}
+                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit", "relabel",
+                                                              "sector_links") if k in fol_stage}}
     total_ms, per = H["total_ms"], H["per"]
     value = n_all * args.steps / (total_ms * 1e-3)
     n_tracks = H["n_tracks"]

@@ -40,6 +40,18 @@
  *                  every track is fitted again over its clusters (rows may be
  *                  skipped).  Membership is then decided in FP32: near ties can
  *                  go either way.
+ *   X  links       (config.follow = 2) each followed track with status 0 is
+ *                  transported outward until its predicted y leaves the pad area
+ *                  of a row (at most follow_link_rows rows), rotated into the frame
+ *                  of the neighbouring sector of the same side (+-20 deg; position,
+ *                  direction, covariance through the rotation's Jacobian) and
+ *                  transported row by row there; in the rows where the gate reaches
+ *                  the pad plane, the best first cluster of a track
+ *                  of that sector under the gate ends the search and links the two
+ *                  when their states agree at that row (the other track's state
+ *                  transported to its first row, chi2 of the 5 differences with the
+ *                  summed covariances <= follow_link_chi2).  A track linked from
+ *                  several takes the smallest; next_track[track] reports it.
  * With TPC_MODE_PRUNED a learned link classifier rescores the ambiguous clusters
  * of A1 (see the classifier section at the end of this file).
  *
@@ -108,10 +120,13 @@ typedef struct {
                             `sector` field of a cluster is then its instance id, < n_sectors <= 16384,
                             and a track's `sector` output is that id.  More than 36 needs sorted input. */
   int32_t nb_tile;       /* clusters per neighbour tile: 512, 768 or 1024 (0: 768); see tpc_tf_autotune */
-  int32_t follow;        /* 1: follow and join the tracks after the tracklet fit (see below); 0: off */
+  int32_t follow;        /* 1: follow and join the tracks after the tracklet fit (see below); 2: also link
+                            tracks across sector boundaries (tpc_tracks.next_track); 0: off */
   float follow_chi2;     /* follow: gate of a cluster against the predicted (y, zeta), 2 dof (default 16) */
   int32_t follow_miss;   /* follow: consecutive rows without a cluster that end a follow (default 3) */
   int32_t follow_check;  /* follow: clusters of another track that must pass the gate before a join (4) */
+  float follow_link_chi2;  /* follow 2: 5-parameter agreement of two linked tracks (default 80) */
+  int32_t follow_link_rows; /* follow 2: rows searched on either side of a sector boundary (default 152) */
 } tpc_tf_config;
 
 typedef struct {      /* input clusters: device pointers, read only, caller owned */
@@ -142,6 +157,9 @@ typedef struct {              /* outputs: device pointers, caller owned */
   uint32_t *n_tracks;         /* device scalar: number of tracks (also when it exceeds track_capacity) */
   uint32_t *n_tracks_host;    /* optional host scalar: when set, the call synchronises the stream,
                                  stores the count here and returns device-side errors directly */
+  int32_t *next_track;        /* optional [cap] (follow = 2): the track that continues this one in the
+                                 neighbouring sector, -1 = none; needs records of all tracks
+                                 (track_capacity >= n_tracks) */
 } tpc_tracks;
 
 /* Fill *cfg with the defaults listed above (max_clusters = 0 must be set by the caller). */

@@ -43,8 +43,9 @@
  *      sector of the same side (+20 deg for y > 0, -20 deg otherwise; position,
  *      direction and the covariance through the rotation's Jacobian) and
  *      transported row by row for at most xs_rows rows from the first row plane
- *      at or beyond the rotated point.  In each row the first clusters of that
- *      sector's tracks are gated as above; the best one (chi2, sorted position)
+ *      at or beyond the rotated point.  In each row where the gate reaches the
+ *      pad plane (|y| - npads pitch / 2 <= sqrt(chi2_max S_yy)) the first
+ *      clusters of that sector's tracks are gated as above; the best one (chi2, sorted position)
  *      ends the search and links the two tracks when their states agree at that
  *      row: the other track's reported state transported to its first row,
  *      zeta shifted to the same reference, chi2 of the 5-parameter difference
@@ -407,10 +408,18 @@ static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *f
     /* first row plane at or beyond the rotated point */
     int r0 = 0;
     while (r0 < OR_NROWS && fl_x[r0] < xr) ++r0;
+    if (r0 < OR_NROWS) fl_margin(&mg, (fl_x[r0] - xr) / FL_TOL_Y);
+    if (r0 > 0) fl_margin(&mg, (xr - fl_x[r0 - 1]) / FL_TOL_Y);
     double xcur = xr;
     for (int r = r0; r < OR_NROWS && r < r0 + fp->xs_rows; ++r) {
       if (fl_transport(q, C2, fl_x[r] - xcur, &mg)) break;
       xcur = fl_x[r];
+      /* a row is searched only where the gate reaches the pad plane (|y| up to
+       * npads pitch / 2): chi2 >= r_y^2 / S_yy */
+      double over = fabs(q[0]) - 0.5 * (double)fl_npads[r] * (double)fl_pitch[r] * 1e-4 -
+                    sqrt(fp->chi2_max * (C2[0] + FL_VY));
+      fl_margin(&mg, fabs(over) / FL_TOL_Y);
+      if (over > 0.0) continue;
       /* the first clusters of s2's tracks in this row under the gate */
       int64_t k = (int64_t)s2 * OR_NROWS + r, best = -1, second = -1;
       double b = 0.0, sec = INFINITY;

@@ -74,6 +74,7 @@ struct tpc_tf {
   int32_t *h_ndf = nullptr, *h_nhits = nullptr, *h_first = nullptr;
   uint16_t *h_sec = nullptr, *h_rf = nullptr, *h_rl = nullptr;
   uint8_t *h_status = nullptr;
+  int32_t *h_next = nullptr;  // follow = 2 only
   uint32_t *h_ntracks = nullptr;
   uint32_t *pinned = nullptr;  // [0] n_tracks, [1] error word
   cudaEvent_t ev[kMaxStages + 1];
@@ -126,6 +127,8 @@ extern "C" void tpc_default_config(tpc_tf_config *c) {
   c->follow_chi2 = 16.0f;
   c->follow_miss = 3;
   c->follow_check = 4;
+  c->follow_link_chi2 = 80.0f;
+  c->follow_link_rows = TPC_NROWS;
 }
 
 extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
@@ -205,6 +208,7 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->h_rf, (size_t)tf->track_list_cap * 2},
       {(void **)&tf->h_rl, (size_t)tf->track_list_cap * 2},
       {(void **)&tf->h_status, (size_t)tf->track_list_cap},
+      {(void **)&tf->h_next, cfg->follow == 2 ? (size_t)tf->track_list_cap * 4 : 0},
       {(void **)&tf->h_ntracks, 16},
       {(void **)&tf->amb, cfg->mode == TPC_MODE_PRUNED ? (N + 4) * 16 : 0},
       {(void **)&tf->q_rows,
@@ -253,7 +257,10 @@ static int validate_config(const tpc_tf_config *cfg) {
     return fail(TPC_ERR_ARG, "tpc_tf_create: n_sectors must be in [0, 16384]");
   if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
     return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
-  if (cfg->follow != 0 && cfg->follow != 1) return fail(TPC_ERR_ARG, "tpc_tf_create: follow must be 0 or 1");
+  if (cfg->follow < 0 || cfg->follow > 2) return fail(TPC_ERR_ARG, "tpc_tf_create: follow must be 0, 1 or 2");
+  if (cfg->follow == 2 && (!(cfg->follow_link_chi2 > 0.0f) || !(cfg->follow_link_chi2 < 1e6f) ||
+                           cfg->follow_link_rows < 1 || cfg->follow_link_rows > TPC_NROWS))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: follow_link_chi2 must be in (0, 1e6), follow_link_rows in [1, 152]");
   if (cfg->follow && (!(cfg->follow_chi2 > 0.0f) || !(cfg->follow_chi2 < 1e6f) || cfg->follow_miss < 1 ||
                       cfg->follow_miss > TPC_NROWS || cfg->follow_check < 1 || cfg->follow_check > TPC_NROWS))
     return fail(TPC_ERR_ARG, "tpc_tf_create: follow_chi2 must be in (0, 1e6), follow_miss and follow_check in [1, 152]");
@@ -392,6 +399,8 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
     a.fl.chi2_max = tf->cfg.follow_chi2;
     a.fl.max_miss = tf->cfg.follow_miss;
     a.fl.join_check = tf->cfg.follow_check;
+    a.fl.chi2_link = tf->cfg.follow_link_chi2;
+    a.fl.link_rows = tf->cfg.follow_link_rows;
   }
   if (out) {
     a.cluster_track = out->cluster_track;
@@ -409,6 +418,7 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
     a.o_row_last = out->row_last;
     a.o_status = out->status;
     a.n_tracks_out = out->n_tracks;
+    if (tf->cfg.follow == 2) a.fl.next = out->next_track;
   }
 }
 
@@ -528,6 +538,12 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     launch_follow_ct(a, tf->sms, st);
     stage(tf, st, "relabel");
     tf->launches += 8;  // links, walk, fit, claim reset, time samples, follow, refit, relabel
+    if (tf->cfg.follow == 2 && out->next_track && out->track_capacity > 0) {
+      TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, (size_t)tf->track_list_cap * 4, st));
+      launch_sector_links(a, tf->sms, st);
+      stage(tf, st, "sector_links");
+      tf->launches += 3;  // pred reset, links, resolve
+    }
   }
   TPC_CK(cudaGetLastError());
   tf->last_args = a;
@@ -589,6 +605,7 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   dt.row_first = tf->h_rf;
   dt.row_last = tf->h_rl;
   dt.status = tf->h_status;
+  dt.next_track = out->next_track ? tf->h_next : nullptr;
   dt.n_tracks = tf->h_ntracks;
   uint32_t nt = 0;
   dt.n_tracks_host = &nt;
@@ -610,6 +627,8 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
     TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
+    if (out->next_track && tf->h_next)
+      TPC_CK(cudaMemcpyAsync(out->next_track, tf->h_next, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
   }
   TPC_CK(cudaStreamSynchronize(st));
   if (out->n_tracks) *out->n_tracks = nt;

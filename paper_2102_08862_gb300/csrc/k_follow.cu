@@ -367,6 +367,203 @@ __global__ void __launch_bounds__(kThreads) k_follow_ct(Args a) {
   }
 }
 
+// ------------------------------------------------------ cross-sector links
+namespace {
+
+// the first cluster of a track (with a record) of (sector, row r) under the gate
+// with the smallest (chi2, sorted position); -1 if none.  *owner: its track.
+__device__ int32_t fs_best_first(const Args &a, const Fs &f, int sec, int r, float tref, int32_t *owner) {
+  const int key = sec * kNRows + r;
+  const float chi2_max = a.fl.chi2_max;
+  const float S00 = f.c[0] + kVy, S01 = f.c[1], S11 = f.c[2] + kVz;
+  const float half = 0.5f * (float)(row_npads(r) - 1), pitch = (float)row_pitch_um(r) * 1e-4f;
+  *owner = -1;
+  // the row is searched only where the gate reaches the pad plane (|y| up to
+  // npads pitch / 2; chi2 >= r_y^2 / S00)
+  if (fabsf(f.p[0]) - 0.5f * (float)row_npads(r) * pitch > sqrtf(chi2_max * S00)) return -1;
+  const int rb = a.row_begin[key], re = a.row_begin[key + 1];
+  const float idet = 1.0f / (S00 * S11 - S01 * S01);
+  const float tp = tref + f.p[1] * (1.0f / kCmPerBin);
+  const float w = sqrtf(chi2_max * S11) * (1.0f / kCmPerBin) * 1.001f + 0.01f;
+  const uint32_t ncap = min(a.ctr[kCtrFollowTracks], a.track_capacity);
+  int32_t best = -1, bown = -1;
+  float bq = 0.0f;
+  for (int c = time_lower_bound(a.time, a.fl.t16, rb, re, tp - w); c < re; ++c) {
+    const float tc = a.time[c];
+    if (tc > tp + w) break;
+    const int32_t i = caller_index(a, c);
+    const int32_t own = a.cluster_track[i];
+    if (own < 0 || (uint32_t)own >= ncap || a.first_cluster[own] != i) continue;
+    const float r0 = (a.pad[c] - half) * pitch - f.p[0];
+    const float r1 = kCmPerBin * (tc - tref) - f.p[1];
+    const float q = (r0 * r0 * S11 - 2.0f * r0 * r1 * S01 + r1 * r1 * S00) * idet;
+    if (!(q <= chi2_max)) continue;
+    if (best < 0 || q < bq) {
+      best = c;
+      bq = q;
+      bown = own;
+    }
+  }
+  *owner = bown;
+  return best;
+}
+
+// state of a track record (the caller's outputs)
+__device__ __forceinline__ void fs_load_record(const Args &a, uint32_t t, Fs &f) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f.p[i] = a.params[(size_t)t * 5 + i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) f.c[i] = a.cov[(size_t)t * 15 + i];
+}
+
+// chi2 of the 5-parameter difference d with covariance S (lower triangle), by
+// Cholesky; -1 when S is not positive definite
+__device__ __forceinline__ float chi2_5(const float *d, const float *S) {
+  float L[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float v = S[lt(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[lt(i, k)] * L[lt(j, k)];
+      if (i == j) {
+        if (!(v > 0.0f)) return -1.0f;
+        L[lt(i, i)] = sqrtf(v);
+      } else {
+        L[lt(i, j)] = v / L[lt(j, j)];
+      }
+    }
+  float z[5], q = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float v = d[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) v -= L[lt(i, k)] * z[k];
+    z[i] = v / L[lt(i, i)];
+    q += z[i] * z[i];
+  }
+  return q;
+}
+
+}  // namespace
+
+// One thread per followed track: the link proposal to the track continuing it in
+// the neighbouring sector (succ reused), claimed with atomicMin in pred (reset).
+__global__ void __launch_bounds__(kThreads) k_sector_links(Args a) {
+  const uint32_t nf = min(a.ctr[kCtrFollowTracks], a.track_capacity);
+  const float kCb = 0.93969262f, kSb = 0.34202014f;  // cos, sin of 20 deg
+  for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < nf; A += gridDim.x * blockDim.x) {
+    int32_t prop = -1;
+    const int rl = a.o_row_last[A];
+    if (a.o_status[A] == 0 && rl < kNRows - 1) {
+      const int sec = a.o_sector[A];
+      const float tref = a.t_ref[A];
+      Fs f;
+      fs_load_record(a, A, f);
+      int rcur = rl, exit_row = -1;
+      for (int r = rl + 1; r < kNRows && r <= rl + a.fl.link_rows; ++r) {
+        if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
+        rcur = r;
+        const float edge = 0.5f * (float)row_npads(r) * (float)row_pitch_um(r) * 1e-4f;
+        if (fabsf(f.p[0]) > edge) {
+          exit_row = r;
+          break;
+        }
+      }
+      // rotation into the neighbouring sector's frame
+      const float s = f.p[2];
+      if (exit_row >= 0 && fabsf(s) < 0.999f) {
+        const bool up = f.p[0] > 0.0f;
+        const float sb = up ? kSb : -kSb;
+        const float cp = sqrtf((1.0f - s) * (1.0f + s));
+        const float s2 = s * kCb - cp * sb, c2 = cp * kCb + s * sb;
+        const float x0 = row_x(exit_row);
+        if (c2 > 0.0f && fabsf(s2) < 0.999f) {
+          const float xr = x0 * kCb + f.p[0] * sb;
+          const float cv = -kBz * f.p[4];
+          float J[5][5];
+#pragma unroll
+          for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) J[i][j] = i == j && i != 0 && i != 2 ? 1.0f : 0.0f;
+          J[0][0] = kCb - sb * s2 / c2;
+          J[1][0] = -f.p[3] * sb / c2;
+          J[2][0] = -cv * sb;
+          J[2][2] = c2 / cp;
+          Fs g;
+          g.p[0] = -x0 * sb + f.p[0] * kCb;
+          g.p[1] = f.p[1];
+          g.p[2] = s2;
+          g.p[3] = f.p[3];
+          g.p[4] = f.p[4];
+          float JC[5][5];
+#pragma unroll
+          for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+              float acc = 0.0f;
+#pragma unroll
+              for (int k = 0; k < 5; ++k) acc = fmaf(J[i][k], f.c[lt(k, j)], acc);
+              JC[i][j] = acc;
+            }
+#pragma unroll
+          for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+              float acc = 0.0f;
+#pragma unroll
+              for (int k = 0; k < 5; ++k) acc = fmaf(JC[i][k], J[j][k], acc);
+              g.c[lt(i, j)] = acc;
+            }
+          const int side = sec / 18, ls = sec % 18;
+          const int s2ec = side * 18 + (up ? (ls + 1) % 18 : (ls + 17) % 18);
+          int r0 = 0;
+          while (r0 < kNRows && row_x(r0) < xr) ++r0;
+          float xcur = xr;
+          for (int r = r0; r < kNRows && r < r0 + a.fl.link_rows; ++r) {
+            if (!fs_transport(g, row_x(r) - xcur)) break;
+            xcur = row_x(r);
+            int32_t B;
+            const int32_t c = fs_best_first(a, g, s2ec, r, tref, &B);
+            if (c < 0) continue;
+            if (a.o_status[B] == 0) {
+              Fs h;
+              fs_load_record(a, B, h);
+              if (fs_transport(h, row_x(r) - a.x[B])) {
+                h.p[1] += kCmPerBin * (a.t_ref[B] - tref);
+                float d[5], S[15];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) d[i] = g.p[i] - h.p[i];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) S[i] = g.c[i] + h.c[i];
+                const float q5 = chi2_5(d, S);
+                if (q5 >= 0.0f && q5 <= a.fl.chi2_link) prop = B;
+              }
+            }
+            break;
+          }
+        }
+      }
+    }
+    a.fl.succ[A] = prop;
+    if (prop >= 0) atomicMin(&a.fl.pred[prop], A);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sector_links_resolve(Args a) {
+  const uint32_t nf = min(a.ctr[kCtrFollowTracks], a.track_capacity);
+  for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < nf; A += gridDim.x * blockDim.x) {
+    const int32_t B = a.fl.succ[A];
+    a.fl.next[A] = (B >= 0 && a.fl.pred[B] == A) ? B : -1;
+  }
+}
+
+void launch_sector_links(const Args &a, int sms, cudaStream_t st) {
+  k_sector_links<<<sms * 4, kThreads, 0, st>>>(a);
+  k_sector_links_resolve<<<sms * 4, kThreads, 0, st>>>(a);
+}
+
 // t16[j] = time of sorted cluster 16 j
 __global__ void __launch_bounds__(kThreads) k_time_samples(Args a) {
   const uint32_t m = (a.n + 15) / 16;

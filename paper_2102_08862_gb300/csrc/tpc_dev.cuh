@@ -147,6 +147,9 @@ struct Args {
     uint64_t *lb;       // look-back words, one per 256-track tile
     float chi2_max;
     int32_t max_miss, join_check;
+    float chi2_link;    // cross-sector links (follow = 2)
+    int32_t link_rows;
+    int32_t *next;      // [track_capacity] caller's next_track, nullptr when not asked
   } fl;
 };
 // rows of a neighbour tile's region in pruned mode

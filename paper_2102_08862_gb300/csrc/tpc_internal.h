@@ -42,6 +42,9 @@ void launch_fit(const Args &a, int sms, int variant, cudaStream_t st);
 void launch_follow(const Args &a, int sms, cudaStream_t st);
 void launch_follow_fit(const Args &a, int sms, cudaStream_t st);
 void launch_follow_ct(const Args &a, int sms, cudaStream_t st);
+// cross-sector links of the followed tracks into a.fl.next (a.fl.pred reset to ~0
+// before; a.fl.succ is reused)
+void launch_sector_links(const Args &a, int sms, cudaStream_t st);
 // look-back tiles of the follower (256 tracks each) for n clusters
 inline size_t follow_tiles(uint32_t n, int n_min, uint32_t track_list_cap) {
   const size_t nt = (size_t)n / (size_t)(n_min > 0 ? n_min : 1) + 1;

@@ -37,7 +37,7 @@ class tpc_tf_config(ctypes.Structure):
                 ("cost_max_q", c_i64), ("n_min", c_i32), ("mode", c_i32), ("tau", c_f32), ("device", c_i32),
                 ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32), ("n_sectors", c_i32),
                 ("nb_tile", c_i32), ("follow", c_i32), ("follow_chi2", c_f32), ("follow_miss", c_i32),
-                ("follow_check", c_i32)]
+                ("follow_check", c_i32), ("follow_link_chi2", c_f32), ("follow_link_rows", c_i32)]
 
 
 class tpc_clusters(ctypes.Structure):
@@ -48,7 +48,7 @@ class tpc_tracks(ctypes.Structure):
     _fields_ = [("cluster_track", c_vp), ("track_capacity", c_u32), ("params", c_vp), ("cov", c_vp),
                 ("t_ref", c_vp), ("x", c_vp), ("chi2", c_vp), ("ndf", c_vp), ("nhits", c_vp),
                 ("first_cluster", c_vp), ("sector", c_vp), ("row_first", c_vp), ("row_last", c_vp),
-                ("status", c_vp), ("n_tracks", c_vp), ("n_tracks_host", c_vp)]
+                ("status", c_vp), ("n_tracks", c_vp), ("n_tracks_host", c_vp), ("next_track", c_vp)]
 
 
 class tpc_mlp_train_config(ctypes.Structure):
@@ -491,6 +491,7 @@ class Tracks:
     row_first: "object"
     row_last: "object"
     status: "object"
+    next_track: "object" = None  # int32[n_tracks] with follow = 2
 
 
 class TimeFrameTracker:
@@ -536,6 +537,7 @@ class TimeFrameTracker:
                 nhits=t.empty(cap, dtype=t.int32, device=d), first_cluster=t.empty(cap, dtype=t.int32, device=d),
                 sector=t.empty(cap, dtype=t.int16, device=d), row_first=t.empty(cap, dtype=t.int16, device=d),
                 row_last=t.empty(cap, dtype=t.int16, device=d), status=t.empty(cap, dtype=t.uint8, device=d),
+                next_track=t.empty(cap, dtype=t.int32, device=d),
                 n_tracks=t.zeros(1, dtype=t.int32, device=d))
             self._cap = cap
         return self._out
@@ -554,7 +556,8 @@ class TimeFrameTracker:
                         sector=o["sector"].data_ptr(), row_first=o["row_first"].data_ptr(),
                         row_last=o["row_last"].data_ptr(), status=o["status"].data_ptr(),
                         n_tracks=o["n_tracks"].data_ptr(),
-                        n_tracks_host=ctypes.addressof(host_count) if host_count is not None else None)
+                        n_tracks_host=ctypes.addressof(host_count) if host_count is not None else None,
+                        next_track=o["next_track"].data_ptr() if self.cfg.follow == 2 else None)
         return cl, tr, n, cap
 
     def track(self, sector, row, pad, time, sorted_input=True, capacity=None, stream=None) -> Tracks:
@@ -570,7 +573,8 @@ class TimeFrameTracker:
         return Tracks(cluster_track=o["cluster_track"][:n], n_tracks=nt, params=o["params"][:m], cov=o["cov"][:m],
                       t_ref=o["t_ref"][:m], x=o["x"][:m], chi2=o["chi2"][:m], ndf=o["ndf"][:m],
                       nhits=o["nhits"][:m], first_cluster=o["first_cluster"][:m], sector=o["sector"][:m],
-                      row_first=o["row_first"][:m], row_last=o["row_last"][:m], status=o["status"][:m])
+                      row_first=o["row_first"][:m], row_last=o["row_last"][:m], status=o["status"][:m],
+                      next_track=o["next_track"][:m] if self.cfg.follow == 2 else None)
 
     def track_graph(self, sector, row, pad, time, sorted_input=True, capacity=None, stream=None):
         """tpc_track_timeframe_graph on device tensors; returns the device track count
@@ -598,6 +602,8 @@ class TimeFrameTracker:
                "nhits": np.empty(cap, np.int32), "first_cluster": np.empty(cap, np.int32),
                "sector": np.empty(cap, np.uint16), "row_first": np.empty(cap, np.uint16),
                "row_last": np.empty(cap, np.uint16), "status": np.empty(cap, np.uint8)}
+        if self.cfg.follow == 2:
+            out["next_track"] = np.empty(cap, np.int32)
         cnt = np.zeros(1, np.uint32)
         cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED if sorted_input else 0, sector=hs.ctypes.data,
                           row=hr.ctypes.data, pad=hp.ctypes.data, time=ht.ctypes.data)

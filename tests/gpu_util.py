@@ -21,6 +21,8 @@ def run_gpu(tracker, torch, dev, sector, row, pad, time, sorted_input=True, capa
                                                     "nhits", "first_cluster", "sector", "row_first", "row_last",
                                                     "status")}
     out["n_tracks"] = res.n_tracks
+    if res.next_track is not None:
+        out["next_track"] = res.next_track.cpu().numpy()
     if debug:
         dbg = tracker.debug_links()
         out.update({k: v.cpu().numpy() for k, v in dbg.items()})

@@ -40,7 +40,7 @@ int main(void) {
   printf("tpc_tf_config %zu\ntpc_clusters %zu\ntpc_tracks %zu\n", sizeof(tpc_tf_config), sizeof(tpc_clusters),
          sizeof(tpc_tracks));
   F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap); F(tpc_tf_config, follow_chi2);
-  F(tpc_tf_config, follow_check);
+  F(tpc_tf_config, follow_check); F(tpc_tf_config, follow_link_rows); F(tpc_tracks, next_track);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
   printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
   F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device);
@@ -73,10 +73,12 @@ def test_defaults_and_argument_errors(lib):
     assert lib.tpc_tf_create(ctypes.byref(c), ctypes.byref(h)) == tpcca.TPC_ERR_ARG
     assert lib.tpc_tf_create(None, ctypes.byref(h)) == tpcca.TPC_ERR_ARG
     c.n_min = 10
-    for k, v in (("follow", 2), ("follow_chi2", 0.0), ("follow_miss", 0), ("follow_check", 153)):
+    for k, v in (("follow", 3), ("follow_chi2", 0.0), ("follow_miss", 0), ("follow_check", 153),
+                 ("follow_link_chi2", -1.0), ("follow_link_rows", 0)):
         d = tpcca.tpc_default_config()
-        d.max_clusters, d.follow = 100, 1
+        d.max_clusters, d.follow = 100, 2
         assert (d.follow_chi2, d.follow_miss, d.follow_check) == (16.0, 3, 4)
+        assert (d.follow_link_chi2, d.follow_link_rows) == (80.0, 152)
         setattr(d, k, v)
         assert lib.tpc_tf_create(ctypes.byref(d), ctypes.byref(h)) == tpcca.TPC_ERR_ARG, k
         assert "follow" in tpcca.tpc_last_error()

@@ -30,7 +30,8 @@ def env():
 
 
 def _gpu_follow(tpcca, dev, s, r, p, t, sorted_input=True, **kw):
-    tr = tpcca.TimeFrameTracker(len(s) + 16, follow=1, **kw)
+    kw.setdefault("follow", 1)
+    tr = tpcca.TimeFrameTracker(len(s) + 16, **kw)
     try:
         return run_gpu(tr, torch, dev, s, r, p, t, sorted_input=sorted_input, debug=False)
     finally:
@@ -244,3 +245,41 @@ def test_pruned_mode_follow_keeps_every_chain_whole(env, slice2):
     assert np.all(rs[1:][same] > rs[:-1][same])
     nh = np.bincount(b[b >= 0], minlength=outs[1]["n_tracks"])
     assert np.array_equal(outs[1]["nhits"][:outs[1]["n_tracks"]], nh)
+
+
+# ---------------------------------------------------------------- cross-sector links
+def test_crossing_helices_are_linked_as_in_the_oracle(env):
+    from test_oracle_follow import _crossing_helices
+    tpcca, dev = env
+    s, r, p, t, _ = _crossing_helices(10)  # not sorted
+    o = orc.track_follow(s, r, p, t, fp=orc.follow_params(links=1))
+    g = _gpu_follow(tpcca, dev, s, r, p, t, sorted_input=False, follow=2)
+    assert np.all(o["margin"] >= 1) and np.all(o["xmargin"] >= 1)
+    assert np.array_equal(g["cluster_track"], o["cluster_track"])
+    assert np.array_equal(g["next_track"][:g["n_tracks"]], o["next"])
+    assert (o["next"] >= 0).sum() >= 5
+
+
+@pytest.mark.parametrize("sorted_input", [True, False])
+def test_dense_slice_links_match_the_oracle(env, slice2, sorted_input):
+    tpcca, dev = env
+    s, r, p, t, _ = slice2
+    o = orc.track_follow(s, r, p, t, fp=orc.follow_params(links=1))
+    if sorted_input:
+        g = _gpu_follow(tpcca, dev, s, r, p, t, follow=2)
+        ct_g = g["cluster_track"]
+    else:
+        perm = np.random.default_rng(6).permutation(len(s))
+        g = _gpu_follow(tpcca, dev, s[perm], r[perm], p[perm], t[perm], sorted_input=False, follow=2)
+        ct_g = np.empty_like(g["cluster_track"])
+        ct_g[perm] = g["cluster_track"]
+    n_o = o["n_tracks"]
+    clear = (o["margin"] >= 1) & (o["xmargin"] >= 1)
+    gid = ct_g[o["tracks"]["first_cluster"]]  # the GPU track of each oracle track
+    nxt_o = o["next"]
+    want = np.where(nxt_o >= 0, gid[np.maximum(nxt_o, 0)], -1)
+    both = clear & ((nxt_o < 0) | clear[np.maximum(nxt_o, 0)])
+    got = g["next_track"][gid[both]]
+    assert np.array_equal(got, want[both]), f"{(got != want[both]).sum()} links differ"
+    assert (~both).sum() <= 0.10 * n_o  # the long search beyond a boundary meets many gates
+    assert (nxt_o >= 0).sum() > 1000
