@@ -111,6 +111,23 @@ __device__ __forceinline__ bool fs_transport(Fs &f, float dx) {
   return true;
 }
 
+// the state alone transported by dx (as fs_transport, without the covariance);
+// false (untouched) when |sin phi| would reach 0.999
+__device__ __forceinline__ bool fs_transport_state(float *p, float dx) {
+  const float s1 = p[2], t = p[3];
+  const float cv = -kBz * p[4];
+  const float s2 = s1 + cv * dx;
+  if (fabsf(s2) >= 0.999f || fabsf(s1) >= 0.999f) return false;
+  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1)), c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  const float dy = dx * (s1 + s2) / (c1 + c2);
+  const float sg = dx < 0.0f ? -1.0f : 1.0f;
+  const float l = sqrtf(dx * dx + dy * dy);
+  p[0] += dy;
+  p[1] += t * (sg * l * asinc(0.5f * cv * l));
+  p[2] = s2;
+  return true;
+}
+
 // Kalman update with the measurement (ym, zm) of (y, zeta)
 __device__ __forceinline__ void fs_update(Fs &f, float ym, float zm) {
   const float r0 = ym - f.p[0], r1 = zm - f.p[1];
@@ -461,14 +478,28 @@ __global__ void __launch_bounds__(kThreads) k_sector_links(Args a) {
       const float tref = a.t_ref[A];
       Fs f;
       fs_load_record(a, A, f);
+      // the exit row: the state alone is transported row by row; at the exit the
+      // covariance is transported from the record in one step (the Jacobian of
+      // the composed transport is the product of the per-row ones)
+      float ps[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) ps[i] = f.p[i];
       int rcur = rl, exit_row = -1;
       for (int r = rl + 1; r < kNRows && r <= rl + a.fl.link_rows; ++r) {
-        if (!fs_transport(f, (float)(r - rcur) * kRowDx)) break;
+        if (!fs_transport_state(ps, (float)(r - rcur) * kRowDx)) break;
         rcur = r;
         const float edge = 0.5f * (float)row_npads(r) * (float)row_pitch_um(r) * 1e-4f;
-        if (fabsf(f.p[0]) > edge) {
+        if (fabsf(ps[0]) > edge) {
           exit_row = r;
           break;
+        }
+      }
+      if (exit_row >= 0) {
+        if (fs_transport(f, (float)(exit_row - rl) * kRowDx)) {
+#pragma unroll
+          for (int i = 0; i < 5; ++i) f.p[i] = ps[i];
+        } else {
+          exit_row = -1;
         }
       }
       // rotation into the neighbouring sector's frame
