@@ -220,6 +220,17 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def init_dist(world, local):
+    """torch.distributed over NCCL for N > 1 ranks (None for one)."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist
+
+
 def run_batched(args, rank, world):
     """c4: 256 sector x time-frame instances of uneven size (log-uniform 1e4-2e6
     clusters, 0.2-10 ms) in one batched call, replayed from a CUDA graph, with the
@@ -227,8 +238,10 @@ def run_batched(args, rank, world):
     import torch
     import tpcsynth as ts
     from paper_2102_08862_gb300 import _build, tpcca
+    from paper_2102_08862_gb300.multigpu import job_totals
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    dist = init_dist(world, dev.index)
     _build.build()
     b = ts.batched(256, seed=4 + 1000 * rank)
     f, n_inst = b.frame, b.offsets.size - 1
@@ -257,15 +270,17 @@ def run_batched(args, rank, world):
                 e1.record(stream)
             stream.synchronize()
         assert tpcca.tpc_tf_status(tr.handle, stream.cuda_stream) == 0, tpcca.tpc_last_error()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms, n_all = job_totals(dist, e0.elapsed_time(e1) / args.steps, n, dev)
         res[name] = dict(ms=ms, tile=tile, fit=["thread", "warp"][fit], launches=tr.launches_per_call(),
                          n_tracks=int(tr._out["n_tracks"].item()), clocks=clocks)
         tr.close()
+    if dist:
+        dist.destroy_process_group()
     if rank != 0:
         return
     P, Q = res["pruned"], res["plain"]
     sizes = np.diff(b.offsets)
-    out = {"metric": METRIC, "value": n / (P["ms"] * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": METRIC, "value": n_all / (P["ms"] * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": P["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int64+bf16+f32", "data": "synthetic",
            "config": {"workload": f"c4: {n_inst} sector x time-frame instances in one batched call, {n} clusters "
@@ -275,7 +290,7 @@ def run_batched(args, rank, world):
                       "autotuned": {"nb_tile": P["tile"], "fit": P["fit"]}, "parallelism": f"replicas x{world}"},
            "n_tracks": P["n_tracks"], "gpu_launches": P["launches"] * args.steps, "graph_launches": args.steps,
            "clocks": P["clocks"].summary(),
-           "plain": {"value": n / (Q["ms"] * 1e-3), "ms_per_step": Q["ms"], "n_tracks": Q["n_tracks"],
+           "plain": {"value": n_all / (Q["ms"] * 1e-3), "ms_per_step": Q["ms"], "n_tracks": Q["n_tracks"],
                      "autotuned": {"nb_tile": Q["tile"], "fit": Q["fit"]}}}
     print(json.dumps(out), flush=True)
 
@@ -287,8 +302,10 @@ def run_serving(args, rank, world):
     import torch
     import tpcsynth as ts
     from paper_2102_08862_gb300 import _build, tpcca
+    from paper_2102_08862_gb300.multigpu import job_totals
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
+    dist = init_dist(world, dev)
     _build.build()
     rng = np.random.default_rng(5 + 1000 * rank)
     lengths = rng.uniform(2.0, 12.0, 6)
@@ -345,12 +362,16 @@ def run_serving(args, rank, world):
     drain(n_req, done)
     st = srv.stats()
     srv.close()
+    span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done)
+    span_all, clusters_all = job_totals(dist, span, clusters, torch.device("cuda", dev))
+    if dist:
+        dist.destroy_process_group()
     if rank != 0:
         return
     lat = np.array([r["t_done"] - r["t_submit"] for r in done]) * 1e3
     queue = np.array([r["t_start"] - r["t_submit"] for r in done]) * 1e3
-    span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done)
-    out = {"metric": METRIC, "value": clusters / span, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": len(pool),
+    out = {"metric": METRIC, "value": clusters_all / span_all, "unit": UNIT, "n_gpus": world, "steps": n_req,
+           "warmup": len(pool),
            "ms_per_step": 1e3 * span / n_req, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "int64+bf16+f32", "data": "synthetic",
            "config": {"workload": f"c5: {n_req} requests, frames of 2-12 ms ({', '.join(f'{x:.1f}' for x in lengths)} ms "
@@ -362,7 +383,7 @@ def run_serving(args, rank, world):
                           "mean": float(lat.mean()), "queue_p50": float(np.percentile(queue, 50))},
            "capacity": {"frames_per_s": cap_fps, "clusters_per_s": cap_cps},
            "arrival_rate_per_s": lam, "slots": st["slots"], "slot_bytes": st["bytes"],
-           "e2e": {"value": clusters / span, "unit": UNIT, "h2d_bytes_per_step": int(12 * clusters / n_req),
+           "e2e": {"value": clusters_all / span_all, "unit": UNIT, "h2d_bytes_per_step": int(12 * clusters / n_req),
                    "d2h_bytes_per_step": int(4 * clusters / n_req)}}
     print(json.dumps(out), flush=True)
 
@@ -408,11 +429,8 @@ def main():
 
     import torch
     from paper_2102_08862_gb300 import _build, tpcca
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    from paper_2102_08862_gb300.multigpu import job_totals
+    dist = init_dist(world, local)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     _build.build()
@@ -488,10 +506,7 @@ def main():
         assert tpcca.tpc_tf_status(tr.handle, sh) == 0, tpcca.tpc_last_error()
         total = ev[0].elapsed_time(ev[-1])
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-        if dist:
-            tt = torch.tensor([total], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = float(tt.item())
+        total, _ = job_totals(dist, total, 0, dev)  # the slowest rank's time
         return total, per, clocks
 
     def stages(name, **extra):
@@ -515,12 +530,7 @@ def main():
         e = evaluate(f.label, f.sector, res.cluster_track.cpu().numpy(), res.n_tracks, f.trk_qpt.shape[0])
         return {k: e[k] for k in ("efficiency", "clone_rate", "fake_rate", "n_tracks", "n_findable")}
 
-    if dist:
-        nn = torch.tensor([float(n)], device=dev)
-        dist.all_reduce(nn)
-        n_all = float(nn.item())
-    else:
-        n_all = float(n)
+    _, n_all = job_totals(dist, 0.0, n, dev)  # clusters of all ranks
 
     if args.kernel_only:
         name = args.mode if args.mode != "both" else "pruned"
@@ -613,11 +623,7 @@ def main():
     e1.record(stream)
     stream.synchronize()
     wall = time.perf_counter() - t0
-    e2e_ms = max(e0.elapsed_time(e1), 1e3 * wall) / e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms, _ = job_totals(dist, max(e0.elapsed_time(e1), 1e3 * wall) / e2e_steps, 0, dev)
     d2h = 4 * n + 4 + int(hn[0]) * (20 + 60 + 4 * 6 + 2 * 3 + 1)
     # hit removal (compression consumer of cluster_track): the tracked clusters, in input order
     ct_dev = tr._out["cluster_track"][:n]
