@@ -38,8 +38,8 @@ ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a tr
 STAGED_BYTES_PER_CLUSTER = 48.0
 # DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "5458e593a63df8c2d20057a20176cbf8533f6958734497106e4c674bc8d8215d",
-              "pruned": (204.094464e6 + 129.071104e6) / 16765809, "plain": (202.566144e6 + 101.457408e6) / 16765809}
+NB_TRAFFIC = {"sha256": "a9cc4b2577cf67dc06130af08960c7c000aae2386e40552062a440f88a6abbe8",
+              "pruned": (207.316480e6 + 145.654528e6) / 16765809, "plain": (203.861504e6 + 104.378368e6) / 16765809}
 
 
 def neighbours_traffic(mode, n):

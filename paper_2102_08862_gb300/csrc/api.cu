@@ -106,6 +106,11 @@ struct tpc_tf {
   float *f_t16 = nullptr;
   // CUDA graph of one call (tpc_track_timeframe_graph)
   cudaStream_t cap_stream = nullptr;
+  // host-buffer calls: cluster_track is copied back on aux_stream as soon as it is
+  // final (after the walk; after relabelling in follow mode), while the fit runs
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_ct = nullptr;
+  bool record_ct = false;
   cudaGraphExec_t graph_exec = nullptr;
   tpc_clusters graph_cl;
   tpc_tracks graph_out;
@@ -143,6 +148,8 @@ static void free_all(tpc_tf *tf) {
   if (!tf) return;
   if (tf->graph_exec) cudaGraphExecDestroy(tf->graph_exec);
   if (tf->cap_stream) cudaStreamDestroy(tf->cap_stream);
+  if (tf->aux_stream) cudaStreamDestroy(tf->aux_stream);
+  if (tf->ev_ct) cudaEventDestroy(tf->ev_ct);
   if (tf->arena) cudaFree(tf->arena);
   if (tf->mlp) cudaFree(tf->mlp);
   if (tf->pinned) cudaFreeHost(tf->pinned);
@@ -503,6 +510,7 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   stage(tf, st, "links");
   if (!tf->cfg.follow) {
     launch_walk(a, tf->sms, st);
+    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "walk");
     launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
     stage(tf, st, "fit");
@@ -536,6 +544,7 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     launch_follow_fit(a, tf->sms, st);
     stage(tf, st, "refit");
     launch_follow_ct(a, tf->sms, st);
+    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "relabel");
     tf->launches += 8;  // links, walk, fit, claim reset, time samples, follow, refit, relabel
     if (tf->cfg.follow == 2 && out->next_track && out->track_capacity > 0) {
@@ -607,36 +616,55 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   dt.status = tf->h_status;
   dt.next_track = out->next_track ? tf->h_next : nullptr;
   dt.n_tracks = tf->h_ntracks;
-  uint32_t nt = 0;
-  dt.n_tracks_host = &nt;
-  int rc = tpc_track_timeframe(tf, &dcl, &dt, stream);
-  if (rc != TPC_OK && rc != TPC_ERR_CAPACITY) return rc;
+  dt.n_tracks_host = nullptr;
+  if (!tf->aux_stream) TPC_CK(cudaStreamCreateWithFlags(&tf->aux_stream, cudaStreamNonBlocking));
+  if (!tf->ev_ct) TPC_CK(cudaEventCreateWithFlags(&tf->ev_ct, cudaEventDisableTiming));
+  tf->record_ct = true;
+  const int rc0 = tpc_track_timeframe(tf, &dcl, &dt, stream);
+  tf->record_ct = false;
+  if (rc0 != TPC_OK) return rc0;
+  // cluster_track back while the fit runs; then the count, then exactly that many records
+  if (n > 0) {
+    TPC_CK(cudaStreamWaitEvent(tf->aux_stream, tf->ev_ct, 0));
+    TPC_CK(cudaMemcpyAsync(out->cluster_track, tf->h_ct, (size_t)n * 4, cudaMemcpyDeviceToHost, tf->aux_stream));
+  }
+  TPC_CK(cudaMemcpyAsync(tf->pinned, tf->reset + (tf->cfg.follow ? kCtrFollowTracks : kCtrTracks), 4,
+                         cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(tf->pinned + 1, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaStreamSynchronize(st));
+  const uint32_t nt = tf->pinned[0];
+  int rc = map_err(tf->pinned[1]);
   const std::string msg = g_err;
-  if (n > 0) TPC_CK(cudaMemcpyAsync(out->cluster_track, tf->h_ct, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
   const uint32_t m = nt < out->track_capacity ? nt : out->track_capacity;
-  if (m > 0 && out->params) {
-    TPC_CK(cudaMemcpyAsync(out->params, tf->h_params, (size_t)m * 20, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->cov, tf->h_cov, (size_t)m * 60, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->t_ref, tf->h_tref, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->x, tf->h_x, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->chi2, tf->h_chi2, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->ndf, tf->h_ndf, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->nhits, tf->h_nhits, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->first_cluster, tf->h_first, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->sector, tf->h_sec, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-    TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
-    if (out->next_track && tf->h_next)
-      TPC_CK(cudaMemcpyAsync(out->next_track, tf->h_next, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  if (rc == TPC_OK || rc == TPC_ERR_CAPACITY) {
+    if (m > 0 && out->params) {
+      TPC_CK(cudaMemcpyAsync(out->params, tf->h_params, (size_t)m * 20, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->cov, tf->h_cov, (size_t)m * 60, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->t_ref, tf->h_tref, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->x, tf->h_x, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->chi2, tf->h_chi2, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->ndf, tf->h_ndf, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->nhits, tf->h_nhits, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->first_cluster, tf->h_first, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->sector, tf->h_sec, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+      TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
+      if (out->next_track && tf->h_next)
+        TPC_CK(cudaMemcpyAsync(out->next_track, tf->h_next, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    }
   }
   TPC_CK(cudaStreamSynchronize(st));
+  TPC_CK(cudaStreamSynchronize(tf->aux_stream));
   if (out->n_tracks) *out->n_tracks = nt;
   if (out->n_tracks_host) *out->n_tracks_host = nt;
-  if (rc != TPC_OK) g_err = msg;
-  if (rc == TPC_OK && out->track_capacity > 0 && nt > out->track_capacity)
+  if (rc != TPC_OK) {
+    g_err = msg;
+    return rc;
+  }
+  if (out->track_capacity > 0 && nt > out->track_capacity)
     return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
-  return rc;
+  return TPC_OK;
 }
 
 extern "C" int tpc_tf_debug_links(tpc_tf *tf, int32_t *order, int32_t *down, int32_t *up, int32_t *mup,
