@@ -283,3 +283,49 @@ def test_dense_slice_links_match_the_oracle(env, slice2, sorted_input):
     assert np.array_equal(got, want[both]), f"{(got != want[both]).sum()} links differ"
     assert (~both).sum() <= 0.10 * n_o  # the long search beyond a boundary meets many gates
     assert (nxt_o >= 0).sum() > 1000
+
+
+def test_full_size_10ms_frame_follow_sampled_sectors(env):
+    """The 10 ms frame (~32M clusters) with follow = 2, as the benchmark's follow line
+    runs it.  Whole frame: the chains of the follow-free call each lie inside one
+    followed track, rows strictly increase along every track, links join tracks of
+    neighbouring sectors of one side.  Two sectors (sectors follow independently;
+    links, which cross sectors, are checked structurally) are recomputed by the
+    oracle: every oracle track clear of the band is a GPU track with exactly its
+    clusters and the same refit."""
+    tpcca, dev = env
+    f = ts.generate(ts.c3())
+    outs = {}
+    for fol in (0, 2):
+        tr = tpcca.TimeFrameTracker(f.n, follow=fol)
+        try:
+            outs[fol] = run_gpu(tr, torch, dev, f.sector, f.row, f.pad, f.time, debug=False)
+        finally:
+            tr.close()
+    a, g = outs[0]["cluster_track"], outs[2]
+    b = g["cluster_track"]
+    nt = g["n_tracks"]
+    assert np.all(b[a >= 0] >= 0)
+    pairs = np.unique(np.stack([a[a >= 0], b[a >= 0]], 1), axis=0)
+    assert np.unique(pairs[:, 0]).size == pairs.shape[0], "a chain split over two followed tracks"
+    order = np.lexsort((f.row, b))
+    bs, rs = b[order], f.row[order].astype(np.int64)
+    keep = bs >= 0
+    same = bs[keep][1:] == bs[keep][:-1]
+    assert np.all(rs[keep][1:][same] > rs[keep][:-1][same])
+    nxt = g["next_track"][:nt]
+    linked = np.nonzero(nxt >= 0)[0]
+    sec = g["sector"][:nt].astype(np.int64)
+    d = (sec[nxt[linked]] % 18 - sec[linked] % 18) % 18
+    assert linked.size > 50000 and np.all((d == 1) | (d == 17))
+    assert np.all(sec[nxt[linked]] // 18 == sec[linked] // 18)
+    assert np.unique(nxt[linked]).size == linked.size
+    for s in (5, 27):
+        idx = np.where(f.sector == s)[0]
+        o = orc.track_follow(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx])
+        sub = dict(g)
+        sub["cluster_track"] = b[idx]
+        inv = np.full(f.n, -1, np.int64)
+        inv[idx] = np.arange(len(idx))
+        sub["first_cluster"] = np.where(g["first_cluster"] >= 0, inv[np.maximum(g["first_cluster"], 0)], -1)
+        compare_followed(sub, o, sector=s)
