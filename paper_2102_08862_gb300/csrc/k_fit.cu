@@ -248,10 +248,36 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 
 }  // namespace
 
+// Each block takes 256 consecutive tracks and sorts them by chain length in
+// shared memory (bitonic), so that the lanes of a warp fit chains of similar
+// length and finish together; the chain reads of a step stay inside the block's
+// 256 columns (1 KB, cached in L1).
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
+  __shared__ uint32_t s_key[256];
   const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+  for (uint32_t t0 = blockIdx.x * 256; t0 < nt; t0 += gridDim.x * 256) {
+    {
+      const uint32_t tt = t0 + threadIdx.x;
+      const uint32_t len = tt < nt ? (uint32_t)a.trk_len[tt] : 0u;
+      s_key[threadIdx.x] = (len << 8) | threadIdx.x;
+      __syncthreads();
+      for (int k = 2; k <= 256; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int i = threadIdx.x, ixj = i ^ j;
+          if (ixj > i) {
+            const uint32_t x = s_key[i], y = s_key[ixj];
+            if ((x > y) == ((i & k) == 0)) {
+              s_key[i] = y;
+              s_key[ixj] = x;
+            }
+          }
+          __syncthreads();
+        }
+    }
+    const uint32_t t = t0 + (s_key[threadIdx.x] & 255u);
+    __syncthreads();  // s_key is rewritten by the next round
+    if (t >= nt) continue;
     // the chain's clusters were recorded by the walk as chain[step][track]
     const int32_t *ch = a.chain + t;
     const int L = a.trk_len[t];
