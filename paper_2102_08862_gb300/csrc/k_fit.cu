@@ -564,6 +564,7 @@ __device__ int32_t fol_member(const Args &a, uint32_t R, int k) {
 __global__ void __launch_bounds__(256) k_follow_fit(Args a) {
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_key[256], s_excl[256];
   const uint32_t nt = min(a.ctr[kCtrTracks], a.track_list_cap);
   const uint32_t n_tiles = (nt + 255) / 256;
   if (n_tiles == 0) {
@@ -594,23 +595,46 @@ __global__ void __launch_bounds__(256) k_follow_fit(Args a) {
       if (a.n_tracks_out) *a.n_tracks_out = nf;
       if (a.track_capacity > 0 && nf > a.track_capacity) raise(a.ctr, kErrCapacity);
     }
+    // length of each root's path (chain lengths and accepted pick-ups), map of its
+    // tracks; then the roots of the tile sorted by length (bitonic, in shared
+    // memory), so that a warp's lanes fit paths of similar length
+    int Lr = 0;
     if (root) {
       const uint32_t id = s_prefix + excl;
-      // length of the path (chain lengths and accepted pick-ups), map of its tracks
-      int L = fol_accepted(a, R, kNRows - 1, -1, (int)(a.fl.npick[R] >> 16));
-      {
-        uint32_t u = R;
-        for (int hop = 0; hop < kNRows; ++hop) {
-          const int Lu = a.trk_len[u];
-          L += Lu + fol_accepted(a, u, Lu, 1, (int)(a.fl.npick[u] & 0xffffu));
-          a.fl.map[u] = id;
-          if (!fol_next(a, u)) break;
-        }
+      Lr = fol_accepted(a, R, kNRows - 1, -1, (int)(a.fl.npick[R] >> 16));
+      uint32_t u = R;
+      for (int hop = 0; hop < kNRows; ++hop) {
+        const int Lu = a.trk_len[u];
+        Lr += Lu + fol_accepted(a, u, Lu, 1, (int)(a.fl.npick[u] & 0xffffu));
+        a.fl.map[u] = id;
+        if (!fol_next(a, u)) break;
       }
-      if (L > kNRows) {  // cannot happen: rows strictly increase along a path
+      if (Lr > kNRows) {  // cannot happen: rows strictly increase along a path
         raise(a.ctr, kErrInternal);
-        L = kNRows;
+        Lr = kNRows;
       }
+    }
+    s_key[threadIdx.x] = root ? ((uint32_t)Lr << 9) | (1u << 8) | threadIdx.x : threadIdx.x;
+    s_excl[threadIdx.x] = excl;
+    __syncthreads();
+    for (int k2 = 2; k2 <= 256; k2 <<= 1)
+      for (int j = k2 >> 1; j > 0; j >>= 1) {
+        const int i = threadIdx.x, ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t x = s_key[i], y = s_key[ixj];
+          if ((x > y) == ((i & k2) == 0)) {
+            s_key[i] = y;
+            s_key[ixj] = x;
+          }
+        }
+        __syncthreads();
+      }
+    const uint32_t key = s_key[threadIdx.x];
+    if (key & (1u << 8)) {
+      const uint32_t src = key & 255u;
+      const uint32_t R = tile * 256 + src;
+      const uint32_t id = s_prefix + s_excl[src];
+      const int L = (int)(key >> 9);
       if (id < a.track_capacity) {
         const int32_t start = fol_member(a, R, 0), mid = fol_member(a, R, L / 2), last = fol_member(a, R, L - 1);
         const int r0 = a.row[start], rlast = a.row[last];
