@@ -258,50 +258,88 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
 }
 
 // Hit removal: the clusters attached to a track, in caller order (an ordered
-// compaction: block scan plus decoupled look-back over 2048-cluster tiles taken
-// in order from a counter).  Inputs and outputs are in caller order.
+// compaction over 2048-cluster tiles taken in order from a counter, with a
+// decoupled look-back across tiles).  Inputs and outputs are in caller order.
+// Thread t of a tile holds elements t + 256 q (q = 0..7), so every load is
+// coalesced; positions inside the tile come from warp ballots per q and one scan
+// of the 64 (q, warp) counts (the element order is q-major, then warp, then
+// lane); the kept clusters are staged in shared memory at their tile positions
+// and written out coalesced.
 __global__ void __launch_bounds__(kThreads) k_compact(uint32_t n, const uint16_t *__restrict__ sector,
                                                       const uint16_t *__restrict__ row, const float *__restrict__ pad,
                                                       const float *__restrict__ time, const int32_t *__restrict__ ct,
                                                       uint16_t *o_sector, uint16_t *o_row, float *o_pad,
                                                       float *o_time, int32_t *o_track, uint32_t *o_count,
                                                       uint64_t *lb, uint32_t *ctr) {
-  __shared__ uint32_t s_tile, s_prefix;
-  __shared__ uint32_t s_warp[kThreads / 32];
+  constexpr int kWarps = kThreads / 32;
+  static_assert(kItems * kWarps == 64, "two (q, warp) counts per lane of the scanning warp");
+  __shared__ uint32_t s_tile, s_prefix, s_total;
+  __shared__ uint32_t s_cnt[kItems * kWarps];  // kept per (q, warp), then their offsets
+  __shared__ uint16_t s_sec[kLinkTile], s_row[kLinkTile];
+  __shared__ float s_pad[kLinkTile], s_time[kLinkTile];
+  __shared__ int32_t s_trk[kLinkTile];
   const uint32_t n_tiles = (n + kLinkTile - 1) / kLinkTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[kCtrCompactTile], 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const uint32_t i0 = tile * kLinkTile + threadIdx.x * kItems;
+    const uint32_t base = tile * kLinkTile;
     int32_t t[kItems];
-    uint32_t keep = 0;
+    uint32_t mask[kItems];
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
-      t[q] = i0 + q < n ? __ldcs(ct + i0 + q) : -1;
-      if (t[q] >= 0) keep |= 1u << q;
-    }
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan<kThreads>((uint32_t)__popc(keep), s_warp, &total);
-    if (threadIdx.x < 32) {
-      const uint32_t pre = lookback_exclusive(lb, tile, total, ctr);
-      if (threadIdx.x == 0) s_prefix = pre;
+      const uint32_t i = base + threadIdx.x + q * kThreads;
+      t[q] = i < n ? __ldcs(ct + i) : -1;
+      mask[q] = __ballot_sync(0xffffffffu, t[q] >= 0);
+      if (lane == 0) s_cnt[q * kWarps + warp] = (uint32_t)__popc(mask[q]);
     }
     __syncthreads();
-    uint32_t pos = s_prefix + excl;
+    if (warp == 0) {  // exclusive scan of the 64 counts in element order, then the look-back
+      const uint32_t v0 = s_cnt[lane], v1 = s_cnt[lane + 32];
+      uint32_t x0 = v0, x1 = v1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, o), y1 = __shfl_up_sync(0xffffffffu, x1, o);
+        if (lane >= o) {
+          x0 += y0;
+          x1 += y1;
+        }
+      }
+      const uint32_t half = __shfl_sync(0xffffffffu, x0, 31);
+      s_cnt[lane] = x0 - v0;
+      s_cnt[lane + 32] = half + x1 - v1;
+      const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
+      const uint32_t pre = lookback_exclusive(lb, tile, total, ctr);
+      if (lane == 0) {
+        s_prefix = pre;
+        s_total = total;
+      }
+    }
+    __syncthreads();
+    const uint32_t below = (1u << lane) - 1u;
 #pragma unroll
     for (int q = 0; q < kItems; ++q)
-      if ((keep >> q) & 1u) {
-        const uint32_t i = i0 + q;
-        o_sector[pos] = sector[i];
-        o_row[pos] = row[i];
-        o_pad[pos] = pad[i];
-        o_time[pos] = time[i];
-        if (o_track) o_track[pos] = t[q];
-        ++pos;
+      if (t[q] >= 0) {
+        const uint32_t i = base + threadIdx.x + q * kThreads;
+        const uint32_t p = s_cnt[q * kWarps + warp] + (uint32_t)__popc(mask[q] & below);
+        s_sec[p] = sector[i];
+        s_row[p] = row[i];
+        s_pad[p] = pad[i];
+        s_time[p] = time[i];
+        s_trk[p] = t[q];
       }
-    if (tile == n_tiles - 1 && threadIdx.x == 0) *o_count = s_prefix + total;
+    __syncthreads();
+    const uint32_t total = s_total, out0 = s_prefix;
+    for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+      o_sector[out0 + k] = s_sec[k];
+      o_row[out0 + k] = s_row[k];
+      o_pad[out0 + k] = s_pad[k];
+      o_time[out0 + k] = s_time[k];
+      if (o_track) o_track[out0 + k] = s_trk[k];
+    }
+    if (tile == n_tiles - 1 && threadIdx.x == 0) *o_count = out0 + total;
     __syncthreads();
   }
   if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) *o_count = 0;
@@ -311,7 +349,8 @@ void launch_compact(const Args &a, const uint16_t *sector, const uint16_t *row, 
                     const int32_t *ct, uint16_t *o_sector, uint16_t *o_row, float *o_pad, float *o_time,
                     int32_t *o_track, uint32_t *o_count, int sms, cudaStream_t st) {
   const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
-  const uint32_t grid = tiles < (uint32_t)sms * 4u ? (tiles ? tiles : 1u) : (uint32_t)sms * 4u;
+  // 6 CTAs per SM fit (40 registers, 33 KB of shared memory each)
+  const uint32_t grid = tiles < (uint32_t)sms * 6u ? (tiles ? tiles : 1u) : (uint32_t)sms * 6u;
   k_compact<<<grid, kThreads, 0, st>>>(a.n, sector, row, pad, time, ct, o_sector, o_row, o_pad, o_time, o_track,
                                        o_count, a.lb_links, a.ctr);
 }
