@@ -372,7 +372,8 @@ __global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
 
 void launch_links(const Args &a, int sms, cudaStream_t st) {
   const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
-  const uint32_t grid = tiles < (uint32_t)sms * 4u ? (tiles ? tiles : 1u) : (uint32_t)sms * 4u;
+  // 5 CTAs per SM (the register limit at 48 per thread): their look-back waits overlap
+  const uint32_t grid = tiles < (uint32_t)sms * 5u ? (tiles ? tiles : 1u) : (uint32_t)sms * 5u;
   if (a.nkeys <= kNKeys) k_links<true><<<grid, kThreads, 0, st>>>(a);
   else k_links<false><<<grid, kThreads, 0, st>>>(a);
 }

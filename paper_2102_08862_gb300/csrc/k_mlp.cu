@@ -625,7 +625,8 @@ __global__ void __launch_bounds__(256) k_mlp_extract(Args a, float *__restrict__
 
 // ------------------------------------------------------------------ launchers
 void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
-  k_prune_tiles<<<sms * 3, kPtWarps * 32, 0, st>>>(a, w, logit_tau);
+  // 4 CTAs per SM: the register limit (64 per thread), below the shared-memory one
+  k_prune_tiles<<<sms * 4, kPtWarps * 32, 0, st>>>(a, w, logit_tau);
 }
 
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
