@@ -437,7 +437,13 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
 
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st) {
   if (variant == TPC_FIT_WARP) k_fit_warp<<<sms * 8, 256, 0, st>>>(a);
-  else k_fit_thread<<<sms * 8, 256, 0, st>>>(a);
+  else {
+    // one block per 256-track group of the list (blocks past the track count exit at
+    // once; the grid-stride loop covers lists of more than 65535 groups), so that
+    // the hardware hands groups to SMs as they free up
+    const size_t groups = ((size_t)a.track_list_cap + 255) / 256;
+    k_fit_thread<<<(unsigned)(groups < 65535 ? (groups ? groups : 1) : 65535), 256, 0, st>>>(a);
+  }
 }
 
 // ------------------------------------------------------- followed tracks
