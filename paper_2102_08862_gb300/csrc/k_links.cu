@@ -7,7 +7,7 @@
 // mutual down link; chains of at least n_min clusters become tracks, numbered in
 // the order of their start cluster.
 //
-// GB300 design.  k_links streams the link array in 4096-cluster tiles (16
+// GB300 design.  k_links streams the link array in 2048-cluster tiles (8
 // consecutive clusters per thread), stores each mutual up link as a 16-bit index
 // inside row r+1 (a 32M-cluster frame's links then take 64 MB and stay in L2 for
 // the walk) and compacts the start hits in cluster order with a block scan plus a
@@ -135,10 +135,11 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
   if (bad) raise(a.ctr, kErrRowCap);
 }
 
-// A4: kWalkChains start hits per thread, walked interleaved so that as many
-// dependent load chains are in flight.  Chains that reach n_min clusters become tracks (ids in
-// start order); their clusters get the track id and are recorded in the chain
-// buffer; the clusters of shorter chains get -1.
+// A4: one start hit per thread (kWalkChains; walking two or four chains per
+// thread interleaved was slower: more threads hide the pointer chase better).
+// Chains that reach n_min clusters become tracks (ids in start order); their
+// clusters get the track id and are recorded in the chain buffer; the clusters of
+// shorter chains get -1.
 template <bool kSmemRb>
 __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
