@@ -11,8 +11,10 @@
 // C0 = diag(0.06^2, 0.0516^2, 0.01, 0.01, 0.01).
 //
 // GB300 design: one thread per track.  The walk recorded each track's clusters as
-// chain[step][track], so consecutive threads read consecutive words; the next
-// cluster's (pad, time) is loaded before the current step's arithmetic.
+// chain[step][track], so the threads of a block read words of the same 1 KB span;
+// each block sorts its 256 tracks by chain length first, so that the lanes of a
+// warp finish together; the next cluster's (pad, time) is loaded before the
+// current step's arithmetic.
 //
 // FP32 accuracy.  Three choices keep the FP32 filter within 1e-4 of an FP64 one:
 //  * the covariance is carried as C = U D U^T (U unit upper triangular, D

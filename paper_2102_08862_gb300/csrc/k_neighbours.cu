@@ -13,8 +13,9 @@
 // tile-window kernel finds, for each tile, the clusters of rows r-1 and r+1 whose
 // time lies within wt of the tile's time span (binary searches, all tiles in
 // parallel).  The neighbour kernel gives each tile one CTA: it validates and
-// quantises its tile and stages both windows in shared memory (27 KB, so several
-// CTAs share an SM and hide each other's memory latency); each thread then links
+// quantises its tile and stages both windows in shared memory (18 KB at the
+// 512-cluster tile, so that 8 CTAs share an SM and hide each other's memory
+// latency); each thread then links
 // a contiguous run of clusters, moving its window pointers forward only.  Windows
 // larger than the staging buffers are read from global memory with the same
 // arithmetic.
