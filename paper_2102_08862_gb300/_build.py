@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpcca.so")
 SOURCES = ["api.cu", "k_index.cu", "k_neighbours.cu", "k_links.cu", "k_fit.cu", "k_sort.cu", "noalloc.cu", "k_mlp.cu",
-           "train.cu", "serve.cu", "k_follow.cu"]
+           "train.cu", "serve.cu", "k_follow.cu", "k_append.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # per translation unit: the Kalman fit uses approximate FP32 division and square

@@ -39,6 +39,9 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 constexpr int kMaxStages = 12;
+constexpr int kMaxRanges = 8;             // sector ranges of a pipelined host-buffer call
+constexpr uint32_t kRangeMinClusters = 1u << 22;  // smaller frames are copied in one piece
+constexpr int kRanges = 4;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -76,7 +79,7 @@ struct tpc_tf {
   uint8_t *h_status = nullptr;
   int32_t *h_next = nullptr;  // follow = 2 only
   uint32_t *h_ntracks = nullptr;
-  uint32_t *pinned = nullptr;  // [0] n_tracks, [1] error word
+  uint32_t *pinned = nullptr;  // [0] n_tracks, [1] error word, [4 + k] / [16 + k] a range's error word / running track count
   cudaEvent_t ev[kMaxStages + 1];
   const char *ev_name[kMaxStages];
   int n_ev = 0;
@@ -111,6 +114,14 @@ struct tpc_tf {
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_ct = nullptr;
   bool record_ct = false;
+  // host-buffer calls on large sorted frames: sector ranges copied in on copy_stream
+  // while the previous range is tracked; each range's records go to r_* first
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_in[kMaxRanges] = {}, ev_out[kMaxRanges] = {};
+  float *r_params = nullptr, *r_cov = nullptr, *r_tref = nullptr, *r_x = nullptr, *r_chi2 = nullptr;
+  int32_t *r_ndf = nullptr, *r_nhits = nullptr, *r_first = nullptr;
+  uint16_t *r_sec = nullptr, *r_rf = nullptr, *r_rl = nullptr;
+  uint8_t *r_status = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   tpc_clusters graph_cl;
   tpc_tracks graph_out;
@@ -150,6 +161,11 @@ static void free_all(tpc_tf *tf) {
   if (tf->cap_stream) cudaStreamDestroy(tf->cap_stream);
   if (tf->aux_stream) cudaStreamDestroy(tf->aux_stream);
   if (tf->ev_ct) cudaEventDestroy(tf->ev_ct);
+  if (tf->copy_stream) cudaStreamDestroy(tf->copy_stream);
+  for (int k = 0; k < kMaxRanges; ++k) {
+    if (tf->ev_in[k]) cudaEventDestroy(tf->ev_in[k]);
+    if (tf->ev_out[k]) cudaEventDestroy(tf->ev_out[k]);
+  }
   if (tf->arena) cudaFree(tf->arena);
   if (tf->mlp) cudaFree(tf->mlp);
   if (tf->pinned) cudaFreeHost(tf->pinned);
@@ -216,6 +232,18 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->h_rl, (size_t)tf->track_list_cap * 2},
       {(void **)&tf->h_status, (size_t)tf->track_list_cap},
       {(void **)&tf->h_next, cfg->follow == 2 ? (size_t)tf->track_list_cap * 4 : 0},
+      {(void **)&tf->r_params, (size_t)tf->track_list_cap * 5 * 4},
+      {(void **)&tf->r_cov, (size_t)tf->track_list_cap * 15 * 4},
+      {(void **)&tf->r_tref, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_x, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_chi2, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_ndf, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_nhits, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_first, (size_t)tf->track_list_cap * 4},
+      {(void **)&tf->r_sec, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->r_rf, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->r_rl, (size_t)tf->track_list_cap * 2},
+      {(void **)&tf->r_status, (size_t)tf->track_list_cap},
       {(void **)&tf->h_ntracks, 16},
       {(void **)&tf->amb, cfg->mode == TPC_MODE_PRUNED ? (N + 4) * 16 : 0},
       {(void **)&tf->q_rows,
@@ -306,7 +334,7 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     off += align_up(p.bytes, 256);
   }
   tf->sort_scratch_bytes = sort_scratch_bytes(tf->N);
-  e = cudaMallocHost(&tf->pinned, 64);
+  e = cudaMallocHost(&tf->pinned, 256);
   if (e != cudaSuccess) {
     free_all(tf);
     return fail(TPC_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
@@ -577,6 +605,169 @@ extern "C" int tpc_tf_status(tpc_tf *tf, void *stream) {
   return map_err(tf->pinned[1]);
 }
 
+// The records of the first m tracks of the staging buffers back to the caller.
+static int copy_records_back(tpc_tf *tf, const tpc_tracks *out, uint32_t m, cudaStream_t st) {
+  if (m == 0 || !out->params) return TPC_OK;
+  TPC_CK(cudaMemcpyAsync(out->params, tf->h_params, (size_t)m * 20, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->cov, tf->h_cov, (size_t)m * 60, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->t_ref, tf->h_tref, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->x, tf->h_x, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->chi2, tf->h_chi2, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->ndf, tf->h_ndf, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->nhits, tf->h_nhits, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->first_cluster, tf->h_first, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->sector, tf->h_sec, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
+  TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
+  if (out->next_track && tf->h_next)
+    TPC_CK(cudaMemcpyAsync(out->next_track, tf->h_next, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  return TPC_OK;
+}
+
+// Records [running count before range k, after it) back to the caller, on the
+// copy-back stream, once range k is done (its running count is in pinned[16 + k]).
+static int copy_range_records(tpc_tf *tf, const tpc_tracks *out, int k) {
+  TPC_CK(cudaEventSynchronize(tf->ev_out[k]));
+  const uint32_t cap = out->track_capacity;
+  const uint32_t lo = k > 0 ? tf->pinned[16 + k - 1] : 0u, hi = tf->pinned[16 + k];
+  const uint32_t a = lo < cap ? lo : cap, b = hi < cap ? hi : cap;
+  if (b <= a || !out->params) return TPC_OK;
+  const size_t m = b - a;
+  cudaStream_t s = tf->aux_stream;
+  TPC_CK(cudaMemcpyAsync(out->params + (size_t)a * 5, tf->h_params + (size_t)a * 5, m * 20, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->cov + (size_t)a * 15, tf->h_cov + (size_t)a * 15, m * 60, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->t_ref + a, tf->h_tref + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->x + a, tf->h_x + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->chi2 + a, tf->h_chi2 + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->ndf + a, tf->h_ndf + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->nhits + a, tf->h_nhits + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->first_cluster + a, tf->h_first + a, m * 4, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->sector + a, tf->h_sec + a, m * 2, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->row_first + a, tf->h_rf + a, m * 2, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->row_last + a, tf->h_rl + a, m * 2, cudaMemcpyDeviceToHost, s));
+  TPC_CK(cudaMemcpyAsync(out->status + a, tf->h_status + a, m, cudaMemcpyDeviceToHost, s));
+  return TPC_OK;
+}
+
+// Host-buffer call on a large sorted frame, pipelined over sector ranges: range
+// k + 1 is copied in (copy_stream) while range k is tracked (the caller's stream);
+// each range's cluster_track goes back (aux_stream) as soon as its ids are
+// offset.  Sectors are independent and track ids follow the sector-major order
+// of the start clusters, so the result is the one-call result.
+static int track_host_ranges(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, cudaStream_t st,
+                             int nr) {
+  const uint32_t n = cl->n;
+  if (!tf->copy_stream) TPC_CK(cudaStreamCreateWithFlags(&tf->copy_stream, cudaStreamNonBlocking));
+  if (!tf->aux_stream) TPC_CK(cudaStreamCreateWithFlags(&tf->aux_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < nr; ++k) {
+    if (!tf->ev_in[k]) TPC_CK(cudaEventCreateWithFlags(&tf->ev_in[k], cudaEventDisableTiming));
+    if (!tf->ev_out[k]) TPC_CK(cudaEventCreateWithFlags(&tf->ev_out[k], cudaEventDisableTiming));
+  }
+  // range boundaries where the (sorted) sector reaches k * nsect / nr
+  uint32_t b[kMaxRanges + 1];
+  b[0] = 0;
+  b[nr] = n;
+  for (int k = 1; k < nr; ++k) {
+    const uint16_t target = (uint16_t)((k * tf->nsect) / nr);
+    uint32_t lo = b[k - 1], hi = n;
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if (cl->sector[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    b[k] = lo;
+  }
+  const TrackRecords rec_r = {tf->r_params, tf->r_cov, tf->r_tref, tf->r_x, tf->r_chi2, tf->r_ndf, tf->r_nhits,
+                              tf->r_first, tf->r_sec, tf->r_rf, tf->r_rl, tf->r_status};
+  const TrackRecords rec_h = {tf->h_params, tf->h_cov, tf->h_tref, tf->h_x, tf->h_chi2, tf->h_ndf, tf->h_nhits,
+                              tf->h_first, tf->h_sec, tf->h_rf, tf->h_rl, tf->h_status};
+  TPC_CK(cudaMemsetAsync(tf->h_ntracks, 0, 16, st));  // [0] a range's tracks, [1] the running total
+  for (int k = 0; k < nr; ++k) tf->pinned[4 + k] = tf->pinned[16 + k] = 0;
+  // every range's copy in is queued first, so that the host's waits below never
+  // delay one
+  for (int k = 0; k < nr; ++k) {
+    const uint32_t a0 = b[k], m = b[k + 1] - b[k];
+    if (m > 0) {
+      TPC_CK(cudaMemcpyAsync(tf->h_sector + a0, cl->sector + a0, (size_t)m * 2, cudaMemcpyHostToDevice,
+                             tf->copy_stream));
+      TPC_CK(cudaMemcpyAsync(tf->h_row + a0, cl->row + a0, (size_t)m * 2, cudaMemcpyHostToDevice, tf->copy_stream));
+      TPC_CK(cudaMemcpyAsync(tf->h_pad + a0, cl->pad + a0, (size_t)m * 4, cudaMemcpyHostToDevice, tf->copy_stream));
+      TPC_CK(cudaMemcpyAsync(tf->h_time + a0, cl->time + a0, (size_t)m * 4, cudaMemcpyHostToDevice,
+                             tf->copy_stream));
+    }
+    TPC_CK(cudaEventRecord(tf->ev_in[k], tf->copy_stream));
+  }
+  for (int k = 0; k < nr; ++k) {
+    const uint32_t a0 = b[k], m = b[k + 1] - b[k];
+    TPC_CK(cudaStreamWaitEvent(st, tf->ev_in[k], 0));
+    tpc_clusters dcl = *cl;
+    dcl.n = m;
+    dcl.flags = TPC_INPUT_SORTED;
+    dcl.sector = tf->h_sector + a0;
+    dcl.row = tf->h_row + a0;
+    dcl.pad = tf->h_pad + a0;
+    dcl.time = tf->h_time + a0;
+    tpc_tracks dt;
+    std::memset(&dt, 0, sizeof(dt));
+    dt.cluster_track = tf->h_ct + a0;
+    dt.track_capacity = tf->track_list_cap;
+    dt.params = tf->r_params;
+    dt.cov = tf->r_cov;
+    dt.t_ref = tf->r_tref;
+    dt.x = tf->r_x;
+    dt.chi2 = tf->r_chi2;
+    dt.ndf = tf->r_ndf;
+    dt.nhits = tf->r_nhits;
+    dt.first_cluster = tf->r_first;
+    dt.sector = tf->r_sec;
+    dt.row_first = tf->r_rf;
+    dt.row_last = tf->r_rl;
+    dt.status = tf->r_status;
+    dt.n_tracks = tf->h_ntracks;
+    const int rc = tpc_track_timeframe(tf, &dcl, &dt, st);
+    if (rc != TPC_OK) {  // nothing may still be copying into the caller's buffers
+      cudaStreamSynchronize(tf->copy_stream);
+      cudaStreamSynchronize(tf->aux_stream);
+      return rc;
+    }
+    launch_append_range(tf->h_ntracks, tf->h_ntracks + 1, tf->track_list_cap, (int32_t)a0, m, tf->h_ct + a0, rec_r,
+                        rec_h, tf->sms, st);
+    TPC_CK(cudaMemcpyAsync(tf->pinned + 4 + k, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaMemcpyAsync(tf->pinned + 16 + k, tf->h_ntracks + 1, 4, cudaMemcpyDeviceToHost, st));
+    TPC_CK(cudaEventRecord(tf->ev_out[k], st));
+    if (m > 0) {
+      TPC_CK(cudaStreamWaitEvent(tf->aux_stream, tf->ev_out[k], 0));
+      TPC_CK(cudaMemcpyAsync(out->cluster_track + a0, tf->h_ct + a0, (size_t)m * 4, cudaMemcpyDeviceToHost,
+                             tf->aux_stream));
+    }
+    // the previous range's records go back while this one is tracked
+    if (k > 0) {
+      const int rc2 = copy_range_records(tf, out, k - 1);
+      if (rc2 != TPC_OK) return rc2;
+    }
+  }
+  {
+    const int rc2 = copy_range_records(tf, out, nr - 1);
+    if (rc2 != TPC_OK) return rc2;
+  }
+  TPC_CK(cudaStreamSynchronize(st));
+  const uint32_t nt = tf->pinned[16 + nr - 1];
+  uint32_t err = 0;
+  for (int k = 0; k < nr; ++k) err |= tf->pinned[4 + k];
+  int rc = map_err(err);
+  const std::string msg = g_err;
+  TPC_CK(cudaStreamSynchronize(tf->aux_stream));
+  if (out->n_tracks) *out->n_tracks = nt;
+  if (out->n_tracks_host) *out->n_tracks_host = nt;
+  if (rc != TPC_OK) {
+    g_err = msg;
+    return rc;
+  }
+  if (out->track_capacity > 0 && nt > out->track_capacity)
+    return fail(TPC_ERR_CAPACITY, "more tracks than the track capacity");
+  return TPC_OK;
+}
+
 extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
   g_err.clear();
   if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null argument");
@@ -586,6 +777,9 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
     return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null array");
   TPC_CK(cudaSetDevice(tf->device));
   cudaStream_t st = (cudaStream_t)stream;
+  // large sorted frames without cross-sector links: pipelined over sector ranges
+  if ((cl->flags & TPC_INPUT_SORTED) && tf->cfg.follow != 2 && n >= kRangeMinClusters && tf->nsect >= kRanges)
+    return track_host_ranges(tf, cl, out, st, kRanges);
   if (n > 0) {
     TPC_CK(cudaMemcpyAsync(tf->h_sector, cl->sector, (size_t)n * 2, cudaMemcpyHostToDevice, st));
     TPC_CK(cudaMemcpyAsync(tf->h_row, cl->row, (size_t)n * 2, cudaMemcpyHostToDevice, st));
@@ -637,22 +831,8 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   const std::string msg = g_err;
   const uint32_t m = nt < out->track_capacity ? nt : out->track_capacity;
   if (rc == TPC_OK || rc == TPC_ERR_CAPACITY) {
-    if (m > 0 && out->params) {
-      TPC_CK(cudaMemcpyAsync(out->params, tf->h_params, (size_t)m * 20, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->cov, tf->h_cov, (size_t)m * 60, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->t_ref, tf->h_tref, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->x, tf->h_x, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->chi2, tf->h_chi2, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->ndf, tf->h_ndf, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->nhits, tf->h_nhits, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->first_cluster, tf->h_first, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->sector, tf->h_sec, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->row_first, tf->h_rf, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->row_last, tf->h_rl, (size_t)m * 2, cudaMemcpyDeviceToHost, st));
-      TPC_CK(cudaMemcpyAsync(out->status, tf->h_status, (size_t)m, cudaMemcpyDeviceToHost, st));
-      if (out->next_track && tf->h_next)
-        TPC_CK(cudaMemcpyAsync(out->next_track, tf->h_next, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
-    }
+    const int rc2 = copy_records_back(tf, out, m, st);
+    if (rc2 != TPC_OK) return rc2;
   }
   TPC_CK(cudaStreamSynchronize(st));
   TPC_CK(cudaStreamSynchronize(tf->aux_stream));

@@ -60,6 +60,19 @@ size_t sort_scratch_bytes(uint32_t max_n);
 void launch_compact(const Args &a, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
                     const int32_t *ct, uint16_t *o_sector, uint16_t *o_row, float *o_pad, float *o_time,
                     int32_t *o_track, uint32_t *o_count, int sms, cudaStream_t st);
+// track records (device arrays, as in tpc_tracks)
+struct TrackRecords {
+  float *params, *cov, *t_ref, *x, *chi2;
+  int32_t *ndf, *nhits, *first_cluster;
+  uint16_t *sector, *row_first, *row_last;
+  uint8_t *status;
+};
+// a frame tracked as sector ranges: offset one range's cluster_track by the running
+// track count *acc and append its records (from src) behind the earlier ranges'
+// (in dst, up to cap); then *acc += *range_tracks
+void launch_append_range(const uint32_t *range_tracks, uint32_t *acc, uint32_t cap, int32_t first_off,
+                         uint32_t n_range, int32_t *ct, const TrackRecords &src, const TrackRecords &dst, int sms,
+                         cudaStream_t st);
 // link classifier (k_mlp.cu)
 struct MlpW;
 size_t mlp_weights_bytes();

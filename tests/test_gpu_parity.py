@@ -225,6 +225,45 @@ def test_host_entry_point_matches_device_path(dev, tracker, c1):
     compare_tracks(g, o)
 
 
+@pytest.mark.parametrize("mode", ["plain", "pruned"])
+def test_host_entry_point_pipelined_over_sector_ranges(dev, mode):
+    """A frame of more than 4M sorted clusters through the host-buffer entry point is
+    copied in and tracked as sector ranges (a range copied while the previous one
+    is tracked); the result must be the device path's, byte for byte."""
+    import json
+    import os
+    from paper_2102_08862_gb300 import tpcca
+    f = ts.generate(ts.c2())
+    assert f.n >= 1 << 22
+    kw = {}
+    blob = None
+    if mode == "pruned":
+        w = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2102_08862_gb300",
+                         "weights", "link_classifier")
+        blob = open(w + ".bin", "rb").read()
+        kw = dict(mode=tpcca.TPC_MODE_PRUNED, tau=json.load(open(w + ".json"))["tau"])
+    tr = tpcca.TimeFrameTracker(f.n + 16, **kw)
+    try:
+        if blob:
+            tr.load_mlp(blob)
+        cap = f.n // 10 + 1
+        direct = run_gpu(tr, torch, dev, f.sector, f.row, f.pad, f.time, capacity=cap, debug=False)
+        for _ in range(2):
+            host = tr.track_host(f.sector, f.row, f.pad, f.time, capacity=cap)
+            assert host["n_tracks"] == direct["n_tracks"]
+            assert np.array_equal(host["cluster_track"], direct["cluster_track"])
+            m = direct["n_tracks"]
+            for k in ("params", "cov", "t_ref", "x", "chi2", "ndf", "nhits", "first_cluster", "row_first",
+                      "row_last", "status"):
+                assert np.array_equal(host[k][:m], direct[k][:m]), k
+            assert np.array_equal(host["sector"][:m].astype(np.int64), direct["sector"][:m].astype(np.int64))
+        with pytest.raises(tpcca.TpcError) as ei:  # the capacity error and count survive the ranges
+            tr.track_host(f.sector, f.row, f.pad, f.time, capacity=direct["n_tracks"] - 1)
+        assert ei.value.code == tpcca.TPC_ERR_CAPACITY
+    finally:
+        tr.close()
+
+
 def test_repeated_calls_are_identical_and_allocate_nothing(dev, tracker, c1):
     s, r, p, t = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
                   (c1.sector.view(np.int16), c1.row.view(np.int16), c1.pad, c1.time))
