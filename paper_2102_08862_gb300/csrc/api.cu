@@ -41,7 +41,7 @@ int fail(int code, const std::string &msg) {
 constexpr int kMaxStages = 12;
 constexpr int kMaxRanges = 8;             // sector ranges of a pipelined host-buffer call
 constexpr uint32_t kRangeMinClusters = 1u << 22;  // smaller frames are copied in one piece
-constexpr int kRanges = 4;
+constexpr int kRanges = 3;  // measured on the 10 ms frame: 3 ranges 7.45e9 clusters/s end to end, 4: 7.30e9, 6: 6.66e9, 8: 6.15e9
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
