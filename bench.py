@@ -38,8 +38,8 @@ ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a tr
 STAGED_BYTES_PER_CLUSTER = 48.0
 # DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "a9cc4b2577cf67dc06130af08960c7c000aae2386e40552062a440f88a6abbe8",
-              "pruned": (207.316480e6 + 145.654528e6) / 16765809, "plain": (203.861504e6 + 104.378368e6) / 16765809}
+NB_TRAFFIC = {"sha256": "4fcf5ccfc435803b1d1aac5ac0fcf5fafcc45df543a695dbfb61726de2f26a85",
+              "pruned": (207.212544e6 + 145.546496e6) / 16765809, "plain": (204.066560e6 + 103.926784e6) / 16765809}
 
 
 def neighbours_traffic(mode, n):

@@ -180,8 +180,11 @@ int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *ou
 /* Same with HOST input and output pointers (pageable or pinned): the call copies
  * the clusters into the arena, tracks them, copies cluster_track and the track
  * records back and synchronises the stream.  cluster_track is copied back on an
- * internal stream of the handle as soon as it is final (while the fit runs).  out->n_tracks and
- * out->n_tracks_host are host pointers here (either may be NULL). */
+ * internal stream of the handle as soon as it is final (while the fit runs).  A
+ * sorted frame of at least 4 Mi clusters (without cross-sector links) whose host
+ * arrays are all page-locked goes through as three sector ranges whose copies in,
+ * tracking and copies back overlap; the results are those of the one-piece call.
+ * out->n_tracks and out->n_tracks_host are host pointers here (either may be NULL). */
 int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
 
 /* Track one small time frame without allocating any device memory (the paper

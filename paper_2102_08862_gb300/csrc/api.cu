@@ -677,6 +677,8 @@ static int track_host_ranges(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
     }
     b[k] = lo;
   }
+  // no records wanted: none are fitted (as in the one-piece call), only the ids offset
+  const uint32_t rcap = out->track_capacity > 0 ? tf->track_list_cap : 0u;
   const TrackRecords rec_r = {tf->r_params, tf->r_cov, tf->r_tref, tf->r_x, tf->r_chi2, tf->r_ndf, tf->r_nhits,
                               tf->r_first, tf->r_sec, tf->r_rf, tf->r_rl, tf->r_status};
   const TrackRecords rec_h = {tf->h_params, tf->h_cov, tf->h_tref, tf->h_x, tf->h_chi2, tf->h_ndf, tf->h_nhits,
@@ -710,7 +712,7 @@ static int track_host_ranges(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
     tpc_tracks dt;
     std::memset(&dt, 0, sizeof(dt));
     dt.cluster_track = tf->h_ct + a0;
-    dt.track_capacity = tf->track_list_cap;
+    dt.track_capacity = rcap;
     dt.params = tf->r_params;
     dt.cov = tf->r_cov;
     dt.t_ref = tf->r_tref;
@@ -730,8 +732,8 @@ static int track_host_ranges(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
       cudaStreamSynchronize(tf->aux_stream);
       return rc;
     }
-    launch_append_range(tf->h_ntracks, tf->h_ntracks + 1, tf->track_list_cap, (int32_t)a0, m, tf->h_ct + a0, rec_r,
-                        rec_h, tf->sms, st);
+    launch_append_range(tf->h_ntracks, tf->h_ntracks + 1, rcap, (int32_t)a0, m, tf->h_ct + a0, rec_r, rec_h, tf->sms,
+                        st);
     TPC_CK(cudaMemcpyAsync(tf->pinned + 4 + k, tf->reset + kCtrErr, 4, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaMemcpyAsync(tf->pinned + 16 + k, tf->h_ntracks + 1, 4, cudaMemcpyDeviceToHost, st));
     TPC_CK(cudaEventRecord(tf->ev_out[k], st));
@@ -768,6 +770,28 @@ static int track_host_ranges(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
   return TPC_OK;
 }
 
+// True when every host array of the call is page-locked.  A copy to or from
+// pageable memory returns only once it has completed, so over pageable buffers
+// the range pipeline would serialise: each range's copy back would hold the
+// host until that range is tracked, before the next range is enqueued.
+static bool host_arrays_pinned(const tpc_clusters *cl, const tpc_tracks *out) {
+  const void *p[] = {cl->sector,   cl->row,   cl->pad,           cl->time,      out->cluster_track,
+                     out->params,  out->cov,  out->t_ref,        out->x,        out->chi2,
+                     out->ndf,     out->nhits, out->first_cluster, out->sector, out->row_first,
+                     out->row_last, out->status};
+  const int np = out->track_capacity > 0 ? 17 : 5;
+  for (int i = 0; i < np; ++i) {
+    if (!p[i]) continue;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeHost) return false;
+  }
+  return true;
+}
+
 extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
   g_err.clear();
   if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null argument");
@@ -777,8 +801,10 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
     return fail(TPC_ERR_ARG, "tpc_track_timeframe_host: null array");
   TPC_CK(cudaSetDevice(tf->device));
   cudaStream_t st = (cudaStream_t)stream;
-  // large sorted frames without cross-sector links: pipelined over sector ranges
-  if ((cl->flags & TPC_INPUT_SORTED) && tf->cfg.follow != 2 && n >= kRangeMinClusters && tf->nsect >= kRanges)
+  // large sorted frames without cross-sector links, in page-locked buffers:
+  // pipelined over sector ranges
+  if ((cl->flags & TPC_INPUT_SORTED) && tf->cfg.follow != 2 && n >= kRangeMinClusters && tf->nsect >= kRanges &&
+      host_arrays_pinned(cl, out))
     return track_host_ranges(tf, cl, out, st, kRanges);
   if (n > 0) {
     TPC_CK(cudaMemcpyAsync(tf->h_sector, cl->sector, (size_t)n * 2, cudaMemcpyHostToDevice, st));

@@ -586,24 +586,43 @@ class TimeFrameTracker:
         self._n = n
         return self._out["n_tracks"]
 
-    def track_host(self, sector, row, pad, time, sorted_input=True, capacity=None):
+    def track_host(self, sector, row, pad, time, sorted_input=True, capacity=None, pinned=False):
         """tpc_track_timeframe_host on numpy arrays (host buffers): the call copies
-        them in, tracks, copies the results back and synchronises."""
+        them in, tracks, copies the results back and synchronises.  pinned: the
+        inputs and outputs are staged in page-locked memory (the returned arrays
+        are views of it), which lets a large sorted frame go through as
+        overlapping sector ranges."""
         import numpy as np
         n = int(len(sector))
         cap = int(capacity) if capacity is not None else n // 10 + 1
-        hs = np.ascontiguousarray(sector, np.uint16)
-        hr = np.ascontiguousarray(row, np.uint16)
-        hp = np.ascontiguousarray(pad, np.float32)
-        ht = np.ascontiguousarray(time, np.float32)
-        out = {"cluster_track": np.empty(max(n, 1), np.int32), "params": np.empty((cap, 5), np.float32),
-               "cov": np.empty((cap, 15), np.float32), "t_ref": np.empty(cap, np.float32),
-               "x": np.empty(cap, np.float32), "chi2": np.empty(cap, np.float32), "ndf": np.empty(cap, np.int32),
-               "nhits": np.empty(cap, np.int32), "first_cluster": np.empty(cap, np.int32),
-               "sector": np.empty(cap, np.uint16), "row_first": np.empty(cap, np.uint16),
-               "row_last": np.empty(cap, np.uint16), "status": np.empty(cap, np.uint8)}
+        t = self.torch
+
+        def empty(shape, dt):
+            if not pinned:
+                return np.empty(shape, dt)
+            tdt = {np.uint16: t.int16, np.uint8: t.uint8, np.int32: t.int32, np.float32: t.float32}[dt]
+            return t.empty(shape, dtype=tdt, pin_memory=True).numpy().view(dt)
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dt)
+            if not pinned:
+                return a
+            b = empty(a.shape, dt)
+            b[...] = a
+            return b
+
+        hs = host(sector, np.uint16)
+        hr = host(row, np.uint16)
+        hp = host(pad, np.float32)
+        ht = host(time, np.float32)
+        out = {"cluster_track": empty(max(n, 1), np.int32), "params": empty((cap, 5), np.float32),
+               "cov": empty((cap, 15), np.float32), "t_ref": empty(cap, np.float32),
+               "x": empty(cap, np.float32), "chi2": empty(cap, np.float32), "ndf": empty(cap, np.int32),
+               "nhits": empty(cap, np.int32), "first_cluster": empty(cap, np.int32),
+               "sector": empty(cap, np.uint16), "row_first": empty(cap, np.uint16),
+               "row_last": empty(cap, np.uint16), "status": empty(cap, np.uint8)}
         if self.cfg.follow == 2:
-            out["next_track"] = np.empty(cap, np.int32)
+            out["next_track"] = empty(cap, np.int32)
         cnt = np.zeros(1, np.uint32)
         cl = tpc_clusters(n=n, flags=TPC_INPUT_SORTED if sorted_input else 0, sector=hs.ctypes.data,
                           row=hr.ctypes.data, pad=hp.ctypes.data, time=ht.ctypes.data)

@@ -227,9 +227,10 @@ def test_host_entry_point_matches_device_path(dev, tracker, c1):
 
 @pytest.mark.parametrize("mode", ["plain", "pruned"])
 def test_host_entry_point_pipelined_over_sector_ranges(dev, mode):
-    """A frame of more than 4M sorted clusters through the host-buffer entry point is
-    copied in and tracked as sector ranges (a range copied while the previous one
-    is tracked); the result must be the device path's, byte for byte."""
+    """A frame of more than 4M sorted clusters through the host-buffer entry point:
+    in page-locked buffers it is copied in and tracked as sector ranges (a range
+    copied while the previous one is tracked), in pageable ones in one piece; both
+    results must be the device path's, byte for byte."""
     import json
     import os
     from paper_2102_08862_gb300 import tpcca
@@ -248,8 +249,8 @@ def test_host_entry_point_pipelined_over_sector_ranges(dev, mode):
             tr.load_mlp(blob)
         cap = f.n // 10 + 1
         direct = run_gpu(tr, torch, dev, f.sector, f.row, f.pad, f.time, capacity=cap, debug=False)
-        for _ in range(2):
-            host = tr.track_host(f.sector, f.row, f.pad, f.time, capacity=cap)
+        for pinned in (True, True, False):
+            host = tr.track_host(f.sector, f.row, f.pad, f.time, capacity=cap, pinned=pinned)
             assert host["n_tracks"] == direct["n_tracks"]
             assert np.array_equal(host["cluster_track"], direct["cluster_track"])
             m = direct["n_tracks"]
@@ -258,8 +259,12 @@ def test_host_entry_point_pipelined_over_sector_ranges(dev, mode):
                 assert np.array_equal(host[k][:m], direct[k][:m]), k
             assert np.array_equal(host["sector"][:m].astype(np.int64), direct["sector"][:m].astype(np.int64))
         with pytest.raises(tpcca.TpcError) as ei:  # the capacity error and count survive the ranges
-            tr.track_host(f.sector, f.row, f.pad, f.time, capacity=direct["n_tracks"] - 1)
+            tr.track_host(f.sector, f.row, f.pad, f.time, capacity=direct["n_tracks"] - 1, pinned=True)
         assert ei.value.code == tpcca.TPC_ERR_CAPACITY
+        # no records wanted (capacity 0): the same assignment, the count still reported
+        none = tr.track_host(f.sector, f.row, f.pad, f.time, capacity=0, pinned=True)
+        assert none["n_tracks"] == direct["n_tracks"]
+        assert np.array_equal(none["cluster_track"], direct["cluster_track"])
     finally:
         tr.close()
 
