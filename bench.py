@@ -40,6 +40,8 @@ STAGED_BYTES_PER_CLUSTER = 48.0
 # valid while k_neighbours.cu is the file captured (its SHA-256)
 NB_TRAFFIC = {"sha256": "4fcf5ccfc435803b1d1aac5ac0fcf5fafcc45df543a695dbfb61726de2f26a85",
               "pruned": (207.212544e6 + 145.546496e6) / 16765809, "plain": (204.066560e6 + 103.926784e6) / 16765809}
+# warp instructions per cluster of the same captures (smsp__inst_executed.sum / clusters)
+NB_INST = {"pruned": 616386918 / 16765809, "plain": 539628699 / 16765809}
 
 
 def neighbours_traffic(mode, n):
@@ -50,6 +52,20 @@ def neighbours_traffic(mode, n):
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != NB_TRAFFIC["sha256"]:
         return None
     return NB_TRAFFIC[mode] * n
+
+
+def neighbours_issue(mode, n, ms, sm_mhz, sms):
+    """The neighbour kernel against the SMs' instruction issue peak (one warp
+    instruction per cycle per scheduler, four schedulers per SM): its warp
+    instructions per cluster from the capture, times n, over the live CUDA-event
+    time.  None when the kernel source changed since the capture."""
+    if neighbours_traffic(mode, n) is None or not sm_mhz:
+        return None
+    achieved = NB_INST[mode] * n / (ms * 1e-3) / 1e9
+    peak = 4.0 * sms * sm_mhz * 1e6 / 1e9
+    return {"kernel": "neighbours", "bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "G warp-instructions/s", "frac": achieved / peak, "inst_per_cluster": NB_INST[mode],
+            "peak_from": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median SM clock under load)"}
 
 
 def peaks():
@@ -592,6 +608,8 @@ def main():
                 "alg_bytes": dom_alg}
     step_ms = statistics.median(per)
     step_gbs = STAGED_BYTES_PER_CLUSTER * n / (step_ms * 1e-3) / 1e9
+    roof_issue = neighbours_issue(head, n, stage_ms["neighbours"], (H["clocks"].summary() or {}).get("sm_mhz"),
+                                  torch.cuda.get_device_properties(dev).multi_processor_count)
 
     # end to end through the host-buffer entry point (pinned host memory)
     tr = head_tr
@@ -681,6 +699,7 @@ def main():
         "roofline": roof,
         "roofline_step": {"bytes_per_cluster": STAGED_BYTES_PER_CLUSTER, "achieved": step_gbs, "peak": hbm,
                           "unit": "GB/s", "frac": step_gbs / hbm},
+        "roofline_issue": roof_issue,
         "cpu_baseline": cpu,
         "e2e": {"value": n_all / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},
