@@ -36,6 +36,9 @@ UNIT = "clusters/s"
 # algorithmic bytes per cluster of each stage (read once + written once)
 ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a track
 STAGED_BYTES_PER_CLUSTER = 48.0
+IO_FLOOR_BYTES_PER_CLUSTER = 16.0  # 12 B of cluster fields in, 4 B of cluster_track out
+NOMINAL_HBM_GBS = 8000.0
+FIT_FLOP_PER_CLUSTER = 200.0  # transport + 2-D update per cluster in a track (algorithmic)
 # DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
 # valid while k_neighbours.cu is the file captured (its SHA-256)
 NB_TRAFFIC = {"sha256": "4fcf5ccfc435803b1d1aac5ac0fcf5fafcc45df543a695dbfb61726de2f26a85",
@@ -66,6 +69,18 @@ def neighbours_issue(mode, n, ms, sm_mhz, sms):
     return {"kernel": "neighbours", "bound": "issue", "achieved": achieved, "peak": peak,
             "unit": "G warp-instructions/s", "frac": achieved / peak, "inst_per_cluster": NB_INST[mode],
             "peak_from": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median SM clock under load)"}
+
+
+def fit_fp32(in_tracks, ms, sm_mhz, sms):
+    """The Kalman fit against the FP32 peak (128 FMA lanes per SM, 2 flop each):
+    200 algorithmic flop per cluster in a track over the live stage time."""
+    if not ms or not sm_mhz:
+        return None
+    achieved = FIT_FLOP_PER_CLUSTER * in_tracks / (ms * 1e-3) / 1e12
+    peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return {"kernel": "fit", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flop_per_cluster": FIT_FLOP_PER_CLUSTER, "clusters_in_tracks": in_tracks,
+            "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
 
 
 def peaks():
@@ -203,6 +218,67 @@ def cpu_oracle_rate(f, budget_s=10.0, mlp=None, tau=0.5):
             break
     dt = time.perf_counter() - t0
     return done / dt, f"sectors {used[0]}-{used[-1]} of the frame ({done} clusters), {dt:.1f} s", done
+
+
+def _oracle_warm(_):
+    """Start a worker: load the oracle's library (and give the pool time to start
+    every worker before the timed jobs)."""
+    import oracle
+    oracle.params()
+    time.sleep(0.2)
+    return os.getpid()
+
+
+def _oracle_sector_job(names, n, lo, hi, mlp, tau):
+    """One sector [lo, hi) of the frame held in shared memory through the oracle."""
+    from multiprocessing import shared_memory
+    import oracle
+    handles = [shared_memory.SharedMemory(name=nm) for nm in names]
+    try:
+        arrs = [np.ndarray((n,), dt, buffer=h.buf)[lo:hi]
+                for h, dt in zip(handles, (np.uint16, np.uint16, np.float32, np.float32))]
+        res = oracle.track(*arrs, mlp=mlp, tau=tau)
+        del res, arrs
+    finally:
+        for h in handles:
+            h.close()
+    return hi - lo
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def cpu_oracle_rate_parallel(f, mlp=None, tau=0.5, cores=None):
+    """The oracle as it stands on the whole frame as 36 independent sector jobs over
+    the host cores (spawned worker processes, the frame in shared memory, largest
+    sectors first): clusters/s of the frame, the cores used and the sample."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    cores = cores or host_cores()
+    shms = []
+    try:
+        for a in (f.sector, f.row, f.pad, f.time):
+            a = np.ascontiguousarray(a)
+            h = shared_memory.SharedMemory(create=True, size=max(a.nbytes, 1))
+            shms.append(h)
+            np.ndarray(a.shape, a.dtype, buffer=h.buf)[:] = a
+        bounds = np.searchsorted(np.asarray(f.sector), np.arange(37))
+        jobs = sorted((s for s in range(36) if bounds[s + 1] > bounds[s]), key=lambda s: bounds[s] - bounds[s + 1])
+        names = [h.name for h in shms]
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_oracle_warm, range(cores)))
+            t0 = time.perf_counter()
+            futs = [ex.submit(_oracle_sector_job, names, int(f.n), int(bounds[s]), int(bounds[s + 1]), mlp, tau)
+                    for s in jobs]
+            done = sum(x.result() for x in futs)
+            dt = time.perf_counter() - t0
+    finally:
+        for h in shms:
+            h.close()
+            h.unlink()
+    return done / dt, cores, f"the whole frame ({done} clusters) as {len(jobs)} sector jobs on {cores} cores, {dt:.1f} s"
 
 
 def run_reference(args, rank, world):
@@ -605,9 +681,12 @@ def main():
         traffic = neighbours_traffic(head, n) if dom == "neighbours" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                "alg_bytes": dom_alg}
+                "alg_bytes": dom_alg, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS}
     step_ms = statistics.median(per)
     step_gbs = STAGED_BYTES_PER_CLUSTER * n / (step_ms * 1e-3) / 1e9
+    sm_mhz = (H["clocks"].summary() or {}).get("sm_mhz")
+    roof_fit = fit_fp32(in_tracks, stage_ms.get("fit"), sm_mhz,
+                        torch.cuda.get_device_properties(dev).multi_processor_count)
     roof_issue = neighbours_issue(head, n, stage_ms["neighbours"], (H["clocks"].summary() or {}).get("sm_mhz"),
                                   torch.cuda.get_device_properties(dev).multi_processor_count)
 
@@ -674,10 +753,12 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu = cpu_par = None
     if not args.no_cpu_baseline and world == 1:
         v, sample, _ = cpu_oracle_rate(f, args.cpu_budget, mlp=blob if head == "pruned" else None, tau=tau)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        vp, cores, sample_p = cpu_oracle_rate_parallel(f, mlp=blob if head == "pruned" else None, tau=tau)
+        cpu_par = {"value": vp, "unit": UNIT, "cores": cores, "kind": "oracle, sector-parallel", "sample": sample_p}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -698,9 +779,14 @@ def main():
         "stage_ms": stage_ms,
         "roofline": roof,
         "roofline_step": {"bytes_per_cluster": STAGED_BYTES_PER_CLUSTER, "achieved": step_gbs, "peak": hbm,
-                          "unit": "GB/s", "frac": step_gbs / hbm},
+                          "unit": "GB/s", "frac": step_gbs / hbm, "frac_of_nominal_8tbs": step_gbs / NOMINAL_HBM_GBS,
+                          "io_floor": {"bytes_per_cluster": IO_FLOOR_BYTES_PER_CLUSTER,
+                                       "achieved": step_gbs * IO_FLOOR_BYTES_PER_CLUSTER / STAGED_BYTES_PER_CLUSTER,
+                                       "frac": step_gbs * IO_FLOOR_BYTES_PER_CLUSTER / STAGED_BYTES_PER_CLUSTER / hbm}},
+        "roofline_fit": roof_fit,
         "roofline_issue": roof_issue,
         "cpu_baseline": cpu,
+        "cpu_baseline_parallel": cpu_par,
         "e2e": {"value": n_all / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},
         "hit_removal": {"ms": hr_ms, "kept": n_kept, "kept_fraction": n_kept / n,
