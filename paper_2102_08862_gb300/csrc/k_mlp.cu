@@ -89,11 +89,16 @@ __device__ __forceinline__ int2 ty_of(const Args &a, int e, int r) {
 }  // namespace
 
 // ------------------------------------------------------------------ rescoring
-// One warp per listed cluster: lanes scan the windows 32 candidates at a time,
-// the pairs under the cut come out in (j, k) order through ballots and are
-// staged (features as BF16) 64 at a time for the tensor-core MLP; the kept pair
-// is the warp-wide minimum of (cost, sequence number in (j, k) order).
+// One warp per listed cluster: lanes scan the windows 32 candidates at a time and
+// keep each row's candidates (in window order, up to kListCand) in shared memory;
+// the pairs are then one flat (j, k)-ordered index over the two lists, so a dense
+// window is read once instead of once per j candidate.  The pairs under the cut
+// come out in (j, k) order through ballots and are staged (features as BF16) 64
+// at a time for the tensor-core MLP; the kept pair is the warp-wide minimum of
+// (cost, sequence number in (j, k) order).  A row with more candidates than the
+// lists hold is enumerated again from global memory for every j candidate.
 constexpr int kListRows = 64;
+constexpr int kListCand = 64;
 struct __align__(16) ListSmem {
   __nv_bfloat16 w1[kMlpH * kXS];
   __nv_bfloat16 w2[kMlpH * kW2S];
@@ -103,6 +108,8 @@ struct __align__(16) ListSmem {
   uint64_t key[kPruneWarps][kListRows];  // cost << 24 | sequence number
   int32_t jj[kPruneWarps][kListRows], kk[kPruneWarps][kListRows];
   float lg[kPruneWarps][kListRows];
+  int2 qj[kPruneWarps][kListCand], qk[kPruneWarps][kListCand];  // quantised (t, y) of the candidates
+  int32_t cj[kPruneWarps][kListCand], ck[kPruneWarps][kListCand];  // their sorted positions
 };
 static_assert(sizeof(ListSmem) <= 48 * 1024, "static shared memory");
 
@@ -134,6 +141,8 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
   uint64_t *key = sm.key[warp];
   int32_t *jj = sm.jj[warp], *kk = sm.kk[warp];
   float *lg = sm.lg[warp];
+  int2 *qjs = sm.qj[warp], *qks = sm.qk[warp];
+  int32_t *cjs = sm.cj[warp], *cks = sm.ck[warp];
   for (uint32_t e = blockIdx.x * kPruneWarps + warp; e < n_amb; e += gridDim.x * kPruneWarps) {
     const int4 en = a.amb[e];
     const int i = en.x, jlo = en.y, klo = en.z;
@@ -141,22 +150,39 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
     const int2 ci = ty_of(a, i, r);
     const int ti = ci.x, yi = ci.y;
     const int jend = a.row_begin[s * kNRows + r], kend = a.row_begin[s * kNRows + r + 2];
-    // candidate counts inside the windows
+    // the candidates inside the windows, in window order (their counts are
+    // features); the first kListCand of each row go to the warp's lists
     int nj = 0, nk = 0;
+    __syncwarp();  // the previous cluster's lists have been read
     for (int j0 = jlo; j0 < jend; j0 += 32) {
       const int j = j0 + lane;
-      const int2 q = j < jend ? ty_of(a, j, r - 1) : make_int2(INT32_MAX, 0);
-      const bool in_t = q.x - ti <= a.wt;
-      nj += __popc(__ballot_sync(0xffffffffu, in_t && abs(q.y - yi) <= a.wy));
+      const int2 q = j < jend ? ty_of(a, j, r - 1) : make_int2(0, 0);
+      const bool in_t = j < jend && q.x - ti <= a.wt;
+      const bool cand = in_t && abs(q.y - yi) <= a.wy;
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      const int slot = nj + __popc(m & below);
+      if (cand && slot < kListCand) {
+        qjs[slot] = q;
+        cjs[slot] = j;
+      }
+      nj += __popc(m);
       if (!__all_sync(0xffffffffu, in_t)) break;
     }
     for (int k0 = klo; k0 < kend; k0 += 32) {
       const int k = k0 + lane;
-      const int2 q = k < kend ? ty_of(a, k, r + 1) : make_int2(INT32_MAX, 0);
-      const bool in_t = q.x - ti <= a.wt;
-      nk += __popc(__ballot_sync(0xffffffffu, in_t && abs(q.y - yi) <= a.wy));
+      const int2 q = k < kend ? ty_of(a, k, r + 1) : make_int2(0, 0);
+      const bool in_t = k < kend && q.x - ti <= a.wt;
+      const bool cand = in_t && abs(q.y - yi) <= a.wy;
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      const int slot = nk + __popc(m & below);
+      if (cand && slot < kListCand) {
+        qks[slot] = q;
+        cks[slot] = k;
+      }
+      nk += __popc(m);
       if (!__all_sync(0xffffffffu, in_t)) break;
     }
+    __syncwarp();
     uint64_t best = ~0ull;
     int bj = -1, bk = -1, staged = 0;
     uint32_t seq = 0;
@@ -187,10 +213,46 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
       __syncwarp();
       staged = 0;
     };
-    for (int j0 = jlo; j0 < jend; j0 += 32) {
+    // stage the pair (j, k) if it is under the cut (lanes with take set, in lane order)
+    auto stage_pairs = [&](bool take, int j, int k, int32_t tj, int32_t yj, int32_t tk, int32_t yk, int64_t c) {
+      const unsigned tm = __ballot_sync(0xffffffffu, take);
+      if (__popc(tm) + staged > kListRows) flush();
+      if (take) {
+        const int slot = staged + __popc(tm & below);
+        float f[kMlpIn];
+        triplet_features(r, yj, yi, yk, tj, ti, tk, c, nj, nk, a.cost_max, f);
+        store_input_row(xs + slot * kXS, f, sm.mean, sm.inv_std);
+        key[slot] = ((uint64_t)c << 24) | (uint64_t)(seq + __popc(tm & below));
+        jj[slot] = j;
+        kk[slot] = k;
+      }
+      staged += __popc(tm);
+      seq += __popc(tm);
+    };
+    const bool listed = nj <= kListCand && nk <= kListCand;
+    if (listed) {  // every pair from the two lists, j-major
+      const int npair = nj * nk;
+      for (int p0 = 0; p0 < npair; p0 += 32) {
+        const int p = p0 + lane;
+        bool take = false;
+        int x = 0, z = 0;
+        int2 qa = make_int2(0, 0), qb = make_int2(0, 0);
+        int64_t c = 0;
+        if (p < npair) {
+          x = p / nk;
+          z = p - x * nk;
+          qa = qjs[x];
+          qb = qks[z];
+          c = triplet_cost(qa.y - yi, qb.y - yi, qa.x - ti, qb.x - ti);
+          take = c <= a.cost_max;
+        }
+        stage_pairs(take, take ? cjs[x] : 0, take ? cks[z] : 0, qa.x, qa.y, qb.x, qb.y, c);
+      }
+    }
+    for (int j0 = jlo; !listed && j0 < jend; j0 += 32) {  // a row beyond the lists
       const int jl = j0 + lane;
-      const int2 qj = jl < jend ? ty_of(a, jl, r - 1) : make_int2(INT32_MAX, 0);
-      const bool in_t = qj.x - ti <= a.wt;
+      const int2 qj = jl < jend ? ty_of(a, jl, r - 1) : make_int2(0, 0);
+      const bool in_t = jl < jend && qj.x - ti <= a.wt;
       unsigned cand = __ballot_sync(0xffffffffu, in_t && abs(qj.y - yi) <= a.wy);
       while (cand) {  // this chunk's j candidates in order
         const int src = __ffs(cand) - 1;
@@ -199,25 +261,12 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
         const int tj = __shfl_sync(0xffffffffu, qj.x, src), yj = __shfl_sync(0xffffffffu, qj.y, src);
         for (int k0 = klo; k0 < kend; k0 += 32) {
           const int k = k0 + lane;
-          const int2 qk = k < kend ? ty_of(a, k, r + 1) : make_int2(INT32_MAX, 0);
-          const bool kin_t = qk.x - ti <= a.wt;
+          const int2 qk = k < kend ? ty_of(a, k, r + 1) : make_int2(0, 0);
+          const bool kin_t = k < kend && qk.x - ti <= a.wt;
           const bool kin = kin_t && abs(qk.y - yi) <= a.wy;
           int64_t c = 0;
           if (kin) c = triplet_cost(yj - yi, qk.y - yi, tj - ti, qk.x - ti);
-          const bool take = kin && c <= a.cost_max;
-          const unsigned tm = __ballot_sync(0xffffffffu, take);
-          if (__popc(tm) + staged > kListRows) flush();
-          if (take) {
-            const int slot = staged + __popc(tm & below);
-            float f[kMlpIn];
-            triplet_features(r, yj, yi, qk.y, tj, ti, qk.x, c, nj, nk, a.cost_max, f);
-            store_input_row(xs + slot * kXS, f, sm.mean, sm.inv_std);
-            key[slot] = ((uint64_t)c << 24) | (uint64_t)(seq + __popc(tm & below));
-            jj[slot] = j;
-            kk[slot] = k;
-          }
-          staged += __popc(tm);
-          seq += __popc(tm);
+          stage_pairs(kin && c <= a.cost_max, j, k, tj, yj, qk.x, qk.y, c);
           if (!__all_sync(0xffffffffu, kin_t)) break;
         }
       }
