@@ -89,14 +89,17 @@ __device__ __forceinline__ int2 ty_of(const Args &a, int e, int r) {
 }  // namespace
 
 // ------------------------------------------------------------------ rescoring
-// One warp per listed cluster: lanes scan the windows 32 candidates at a time and
-// keep each row's candidates (in window order, up to kListCand) in shared memory;
-// the pairs are then one flat (j, k)-ordered index over the two lists, so a dense
-// window is read once instead of once per j candidate.  The pairs under the cut
-// come out in (j, k) order through ballots and are staged (features as BF16) 64
-// at a time for the tensor-core MLP; the kept pair is the warp-wide minimum of
-// (cost, sequence number in (j, k) order).  A row with more candidates than the
-// lists hold is enumerated again from global memory for every j candidate.
+// Each warp takes listed clusters in turn: lanes scan the windows 32 candidates at
+// a time and keep each row's candidates (in window order, up to kListCand) in
+// shared memory; the pairs are then one flat (j, k)-ordered index over the two
+// lists, so a dense window is read once instead of once per j candidate (a row
+// with more candidates is enumerated again from global memory for every j
+// candidate).  The pairs under the cut come out in (j, k) order through ballots
+// and are staged (features as BF16, tagged with their cluster's pending slot) for
+// the tensor-core MLP; the staged rows of several clusters are scored together
+// whenever the 64-row buffer fills, and each passing row folds into its cluster's
+// smallest (cost, sequence number in (j, k) order) key.  The pending clusters'
+// links are written when all 64 slots are taken and when the warp is done.
 constexpr int kListRows = 64;
 constexpr int kListCand = 64;
 struct __align__(16) ListSmem {
@@ -110,6 +113,9 @@ struct __align__(16) ListSmem {
   float lg[kPruneWarps][kListRows];
   int2 qj[kPruneWarps][kListCand], qk[kPruneWarps][kListCand];  // quantised (t, y) of the candidates
   int32_t cj[kPruneWarps][kListCand], ck[kPruneWarps][kListCand];  // their sorted positions
+  uint8_t own[kPruneWarps][kListRows];  // pending cluster of each staged row
+  unsigned long long pbest[kPruneWarps][kListRows];  // per pending cluster: smallest passing key
+  int32_t pi[kPruneWarps][kListRows], pbj[kPruneWarps][kListRows], pbk[kPruneWarps][kListRows];
 };
 static_assert(sizeof(ListSmem) <= 48 * 1024, "static shared memory");
 
@@ -143,6 +149,46 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
   float *lg = sm.lg[warp];
   int2 *qjs = sm.qj[warp], *qks = sm.qk[warp];
   int32_t *cjs = sm.cj[warp], *cks = sm.ck[warp];
+  uint8_t *own = sm.own[warp];
+  unsigned long long *pbest = sm.pbest[warp];
+  int32_t *pi = sm.pi[warp], *pbj = sm.pbj[warp], *pbk = sm.pbk[warp];
+  int staged = 0, npend = 0;
+  // score the staged rows and fold the passing ones into their clusters' keys;
+  // complete: then write the pending clusters' links and free their slots
+  auto flush = [&](bool complete) {
+    const int ntile = (staged + 15) >> 4;
+    for (int rr = staged + lane; rr < ntile * 16; rr += 32) {
+      reinterpret_cast<uint4 *>(xs + rr * kXS)[0] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4 *>(xs + rr * kXS)[1] = make_uint4(0, 0, 0, 0);
+    }
+    __syncwarp();
+    for (int tt = 0; tt < ntile; ++tt) {
+      float l0, l1;
+      mlp_forward_tile(xs + tt * 16 * kXS, sm.w1, sm.w2, sm.b1, sm.b2, sm.w3, b3, l0, l1);
+      const int g = lane >> 2;
+      if ((lane & 3) == 0) {
+        if (tt * 16 + g < staged) lg[tt * 16 + g] = l0;
+        if (tt * 16 + g + 8 < staged) lg[tt * 16 + g + 8] = l1;
+      }
+    }
+    __syncwarp();
+    for (int rr = lane; rr < staged; rr += 32)
+      if (lg[rr] >= logit_tau) atomicMin(&pbest[own[rr]], (unsigned long long)key[rr]);
+    __syncwarp();
+    for (int rr = lane; rr < staged; rr += 32)  // keys are unique within a cluster
+      if (lg[rr] >= logit_tau && key[rr] == pbest[own[rr]]) {
+        pbj[own[rr]] = jj[rr];
+        pbk[own[rr]] = kk[rr];
+      }
+    __syncwarp();
+    staged = 0;
+    if (complete) {
+      for (int q = lane; q < npend; q += 32)
+        if (pbest[q] != ~0ull) a.link[pi[q]] = make_int2(pbj[q], pbk[q]);
+      __syncwarp();
+      npend = 0;
+    }
+  };
   for (uint32_t e = blockIdx.x * kPruneWarps + warp; e < n_amb; e += gridDim.x * kPruneWarps) {
     const int4 en = a.amb[e];
     const int i = en.x, jlo = en.y, klo = en.z;
@@ -182,41 +228,19 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
       nk += __popc(m);
       if (!__all_sync(0xffffffffu, in_t)) break;
     }
+    // this cluster's pending slot
+    if (npend == kListRows) flush(true);
+    const int pslot = npend++;
+    if (lane == 0) {
+      pbest[pslot] = ~0ull;
+      pi[pslot] = i;
+    }
     __syncwarp();
-    uint64_t best = ~0ull;
-    int bj = -1, bk = -1, staged = 0;
     uint32_t seq = 0;
-    // score the staged rows and fold the kept ones into (best, bj, bk)
-    auto flush = [&]() {
-      const int ntile = (staged + 15) >> 4;
-      for (int rr = staged + lane; rr < ntile * 16; rr += 32) {
-        reinterpret_cast<uint4 *>(xs + rr * kXS)[0] = make_uint4(0, 0, 0, 0);
-        reinterpret_cast<uint4 *>(xs + rr * kXS)[1] = make_uint4(0, 0, 0, 0);
-      }
-      __syncwarp();
-      for (int tt = 0; tt < ntile; ++tt) {
-        float l0, l1;
-        mlp_forward_tile(xs + tt * 16 * kXS, sm.w1, sm.w2, sm.b1, sm.b2, sm.w3, b3, l0, l1);
-        const int g = lane >> 2;
-        if ((lane & 3) == 0) {
-          if (tt * 16 + g < staged) lg[tt * 16 + g] = l0;
-          if (tt * 16 + g + 8 < staged) lg[tt * 16 + g + 8] = l1;
-        }
-      }
-      __syncwarp();
-      for (int rr = lane; rr < staged; rr += 32)
-        if (lg[rr] >= logit_tau && key[rr] < best) {
-          best = key[rr];
-          bj = jj[rr];
-          bk = kk[rr];
-        }
-      __syncwarp();
-      staged = 0;
-    };
     // stage the pair (j, k) if it is under the cut (lanes with take set, in lane order)
     auto stage_pairs = [&](bool take, int j, int k, int32_t tj, int32_t yj, int32_t tk, int32_t yk, int64_t c) {
       const unsigned tm = __ballot_sync(0xffffffffu, take);
-      if (__popc(tm) + staged > kListRows) flush();
+      if (__popc(tm) + staged > kListRows) flush(false);
       if (take) {
         const int slot = staged + __popc(tm & below);
         float f[kMlpIn];
@@ -225,6 +249,7 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
         key[slot] = ((uint64_t)c << 24) | (uint64_t)(seq + __popc(tm & below));
         jj[slot] = j;
         kk[slot] = k;
+        own[slot] = (uint8_t)pslot;
       }
       staged += __popc(tm);
       seq += __popc(tm);
@@ -272,19 +297,8 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
       }
       if (!__all_sync(0xffffffffu, in_t)) break;
     }
-    if (staged) flush();
-    // warp-wide minimum of (cost, sequence number)
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, bj, o), ok = __shfl_xor_sync(0xffffffffu, bk, o);
-      if (ob < best) {
-        best = ob;
-        bj = oj;
-        bk = ok;
-      }
-    }
-    if (lane == 0 && best != ~0ull) a.link[i] = make_int2(bj, bk);
   }
+  flush(true);
 }
 
 // Rows of the neighbour tiles' regions: one warp per tile region, features
