@@ -196,6 +196,18 @@ def dense_scorer(tr, torch, dev, stream, rows=5_200_000, reps=20):
     return out
 
 
+WORKLOAD_TEXT = {"c1": "one sector, one collision, 200 tracks", "c2": "2 ms continuous frame, 36 sectors",
+                 "c3": "10 ms continuous frame, 36 sectors", "c3half": "5 ms continuous frame, 36 sectors"}
+WORKLOAD_SEED = {"c1": 1, "c2": 2, "c3": 3, "c3half": 3}
+
+
+def workload_text(name, f, per_rank_seed=False):
+    """The workload of a frame generated by gen_frame, with its sizes."""
+    coll = "" if name == "c1" else f", {f.n_collisions} collisions at 50 kHz"
+    seed = f"seed {WORKLOAD_SEED[name]}" + (" (+1000*rank)" if per_rank_seed else "")
+    return f"{name}: {WORKLOAD_TEXT[name]}{coll}, {f.n} clusters, {seed}"
+
+
 def gen_frame(workload, seed_offset=0):
     import tpcsynth as ts
     cfg = {"c1": ts.c1, "c2": ts.c2, "c3": ts.c3, "c3half": lambda: ts.continuous(5.0, 3)}[workload]()
@@ -288,11 +300,11 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     blob, tau = classifier()
-    # warm-up and timed steps; each step is a bounded sample (one sector) of the frame
-    secs = [np.where(f.sector == s)[0] for s in range(36)]
+    # warm-up and timed steps; each step is a bounded sample (one non-empty sector) of the frame
+    secs = [idx for idx in (np.where(f.sector == s)[0] for s in range(36)) if idx.size]
     total, t_all = 0, 0.0
     for k in range(args.warmup + args.steps):
-        idx = secs[k % 36]
+        idx = secs[k % len(secs)]
         t0 = time.perf_counter()
         oracle.track(f.sector[idx], f.row[idx], f.pad[idx], f.time[idx], mlp=blob, tau=tau)
         dt = time.perf_counter() - t0
@@ -303,8 +315,9 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
-           "data": "synthetic", "config": {"workload": f"{args.workload}: 10 ms frame, {f.n} clusters, seed 3",
-                                           "model": "CPU oracle (plain single-threaded C), learned-pruned CA",
+           "data": "synthetic", "config": {"workload": workload_text(args.workload, f),
+                                           "mode": f"learned-pruned CA (tau {tau})",
+                                           "program": "CPU oracle (plain single-threaded C)",
                                            "parallelism": "1 core"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": "one sector of the frame per step"},
@@ -487,7 +500,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3half", "c4", "c5"],
-                    help="c3: the 10 ms frame; c3half: its first 5 ms (profiler captures); c1, c2: smaller "
+                    help="c3: the 10 ms frame; c3half: a 5 ms frame, same generator and seed (profiler captures); c1, c2: smaller "
                          "cases; c4: 256 sector x time-frame instances in one batched, graph-replayed call; "
                          "c5: the serving loop under Poisson arrivals")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -763,8 +776,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64+bf16+f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 10 ms continuous frame, 36 sectors, {f.n_collisions} collisions "
-                               f"at 50 kHz, {n} clusters, seed 3 (+1000*rank)",
+        "config": {"workload": workload_text(args.workload, f, per_rank_seed=world > 1),
                    "mode": {"pruned": f"learned-pruned CA (tau {tau})", "plain": "plain CA"}[head],
                    "fit": ["thread per track", "warp per track"][tuned.get(head, {}).get("fit_variant",
                                                                                    args.fit_variant)],

@@ -38,3 +38,24 @@ def test_issue_roofline_arithmetic():
         pytest.skip("capture stale")
     assert r["peak"] == pytest.approx(4 * 152 * 2.0)  # G warp instructions/s
     assert r["achieved"] == pytest.approx(539628699 / 1e-3 / 1e9)
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` prints one JSON line with the contract's keys and
+    samples only non-empty sectors (the one-sector workload gives a rate > 0)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "c1",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [x for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "clusters/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("c1: one sector") and "model" not in d["config"]
