@@ -1,4 +1,4 @@
-"""The host side of runs on several GPUs, with two or three gloo ranks on the CPU.
+"""The host side of runs on several GPUs, with two or five gloo ranks on the CPU.
 
 Each rank tracks its own contiguous block of sectors of one frame (the oracle
 stands in for the rank's GPU: the library's result for a sector subset equals
@@ -72,7 +72,7 @@ def _worker(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 5])  # 18/18 and 8/7/7/7/7 sectors
 def test_ranks_merge_to_the_whole_frame(tmp_path, world):
     import torch.multiprocessing as mp
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
