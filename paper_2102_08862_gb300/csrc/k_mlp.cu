@@ -693,7 +693,7 @@ void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, 
 }
 
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
-  k_prune<<<sms * 4, kPruneWarps * 32, 0, st>>>(a, w, logit_tau);
+  k_prune<<<sms * 5, kPruneWarps * 32, 0, st>>>(a, w, logit_tau);  // 5 CTAs per SM: its registers and shared memory allow 5
 }
 
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st) {
