@@ -76,6 +76,8 @@ def _load():
             lib.or_neighbours_sorted.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp]
             lib.or_neighbours_sorted.restype = ctypes.c_int
             lib.or_bruteforce_neighbours.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp]
+            lib.or_bruteforce_links.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp]
+            lib.or_bruteforce_links.restype = ctypes.c_int
             lib.or_propagate.argtypes = [vp, ctypes.c_double, vp, vp]
             lib.or_propagate.restype = ctypes.c_int
             lib.or_seed_chain.argtypes = [i32, vp, vp, vp, vp]
@@ -177,6 +179,18 @@ def bruteforce_neighbours(sector, row, pad, time, prm: Params | None = None):
     down, up = np.zeros(n, np.int32), np.zeros(n, np.int32)
     _load().or_bruteforce_neighbours(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm),
                                      _p(down), _p(up))
+    return down, up
+
+
+def bruteforce_links(sector, row, pad, time, prm: Params | None = None):
+    """Brute-force A1 choice followed by the A2 edge-row claims (caller indices)."""
+    prm = prm or params()
+    sector, row = _c(sector, np.uint16), _c(row, np.uint16)
+    pad, time = _c(pad, np.float32), _c(time, np.float32)
+    n = sector.shape[0]
+    down, up = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    if _load().or_bruteforce_links(n, _p(sector), _p(row), _p(pad), _p(time), ctypes.byref(prm), _p(down), _p(up)):
+        raise MemoryError("oracle: brute-force links failed")
     return down, up
 
 

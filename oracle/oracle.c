@@ -308,6 +308,57 @@ int or_bruteforce_neighbours(int64_t n, const uint16_t *sector, const uint16_t *
   return 0;
 }
 
+/* Brute force of A1 followed by the A2 edge-row claims, for tiny inputs only.
+ * After the brute-force neighbour choice, every row-0 cluster e looks at every
+ * cluster i of row 1 in its sector whose down link is e, recomputes the cost of
+ * i's chosen triplet from the quantised coordinates, counts i's row-local
+ * position from scratch, and adopts as up link the i of smallest (cost,
+ * position); a row-151 cluster does the same over row 150 with the up links.
+ * Outputs are caller indices (or -1) for every cluster. */
+int or_bruteforce_links(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                        const or_params *prm, int32_t *down, int32_t *up) {
+  if (or_bruteforce_neighbours(n, sector, row, pad, time, prm, down, up)) return -1;
+  int32_t *d1 = (int32_t *)malloc(sizeof(int32_t) * (n + 1)), *u1 = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+  if (!d1 || !u1) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    d1[i] = down[i];
+    u1[i] = up[i];
+  }
+  for (int64_t e = 0; e < n; ++e) {
+    int re = row[e];
+    if (re != 0 && re != OR_NROWS - 1) continue;
+    int rc = re == 0 ? 1 : OR_NROWS - 2; /* row of the claimants */
+    int64_t best = -1, bloc = 0;
+    int32_t bi = -1;
+    for (int64_t i = 0; i < n; ++i) {
+      if (sector[i] != sector[e] || row[i] != rc) continue;
+      int32_t toward = re == 0 ? d1[i] : u1[i];
+      if (toward != (int32_t)e) continue;
+      int32_t j = d1[i], k = u1[i];
+      int64_t yj = (or_q64(pad[j]) - 32 * (or_npads(rc - 1) - 1)) * (int64_t)or_pitch_um(rc - 1);
+      int64_t yi = (or_q64(pad[i]) - 32 * (or_npads(rc) - 1)) * (int64_t)or_pitch_um(rc);
+      int64_t yk = (or_q64(pad[k]) - 32 * (or_npads(rc + 1) - 1)) * (int64_t)or_pitch_um(rc + 1);
+      int64_t dy = yj + yk - 2 * yi;
+      int64_t dz = ((int64_t)or_q64(time[j]) + or_q64(time[k]) - 2 * (int64_t)or_q64(time[i])) * OR_UM_PER_BIN_Q;
+      int64_t c = dy * dy + dz * dz;
+      int64_t loc = 0;
+      for (int64_t m = 0; m < n; ++m) {
+        if (m == i || sector[m] != sector[i] || row[m] != rc) continue;
+        if (time[m] < time[i] || (time[m] == time[i] && (pad[m] < pad[i] || (pad[m] == pad[i] && m < i)))) ++loc;
+      }
+      if (bi < 0 || c < best || (c == best && loc < bloc)) {
+        best = c;
+        bloc = loc;
+        bi = (int32_t)i;
+      }
+    }
+    if (re == 0) up[e] = bi; else down[e] = bi;
+  }
+  free(d1);
+  free(u1);
+  return 0;
+}
+
 /* ------------------------------------------------------------ A5: Kalman fit */
 /* asin(u)/u and its derivative; series near 0 (Taylor series of asin). */
 static double or_asinc(double u) {

@@ -49,6 +49,8 @@ int or_neighbours_sorted(int64_t n, const uint16_t *sector, const uint16_t *row,
                          const or_params *prm, int32_t *down, int32_t *up, int64_t *cost);
 int or_bruteforce_neighbours(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad,
                              const float *time, const or_params *prm, int32_t *down, int32_t *up);
+int or_bruteforce_links(int64_t n, const uint16_t *sector, const uint16_t *row, const float *pad, const float *time,
+                        const or_params *prm, int32_t *down, int32_t *up);
 int or_propagate(const double *p, double dx, double *pout, double *F);
 int or_seed_chain(int32_t L, const int32_t *rows, const float *pads, const float *times, double *p0);
 int or_fit_chain(int32_t L, int32_t sector, const int32_t *rows, const float *pads, const float *times,

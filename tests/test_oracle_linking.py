@@ -254,3 +254,163 @@ def test_exact_recovery_of_separated_noise_free_helices():
             assert np.array_equal(np.sort(np.where(ct == ids[0])[0]), np.sort(members))
             found += 1
     assert found == res["n_tracks"] and found >= 8
+
+
+# ---------------------------------------------------------------- A2 edge-row claims
+GOLDEN_A2 = os.path.join(os.path.dirname(__file__), "golden", "a2_edge_claims.txt")
+
+
+def _read_golden_a2():
+    cases, cur = {}, None
+    for line in open(GOLDEN_A2):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tok = line.split()
+        if tok[0] == "case":
+            cur = cases.setdefault(tok[1], {"cl": [], "expect": [], "mutual": []})
+        elif tok[0] in ("expect", "mutual"):
+            cur[tok[0]].append(tok[1:])
+        else:
+            cur["cl"].append((tok[0], int(tok[1]), int(tok[2]), float(tok[3]), float(tok[4])))
+    return cases
+
+
+@pytest.mark.parametrize("name", ["bottom", "bottom_tie", "top_tie"])
+def test_golden_edge_claims(name):
+    """Hand-worked claims: several claimants of different cost per edge cluster,
+    a cost tie at equal time (pad decides the row-local order) and a tie between
+    clusters at different times."""
+    case = _read_golden_a2()[name]
+    ids = [c[0] for c in case["cl"]]
+    sec = np.array([c[1] for c in case["cl"]], np.uint16)
+    row = np.array([c[2] for c in case["cl"]], np.uint16)
+    pad = np.array([c[3] for c in case["cl"]], np.float32)
+    tim = np.array([c[4] for c in case["cl"]], np.float32)
+    res = orc.track(sec, row, pad, tim)
+    order = res["order"]
+    pos = {ids[order[p]]: p for p in range(len(ids))}
+    nm = lambda p: "-" if p < 0 else ids[order[p]]
+    bd, bu = orc.bruteforce_links(sec, row, pad, tim)
+    nmc = lambda c: "-" if c < 0 else ids[c]
+    for cid, ed, eu in case["expect"]:
+        p = pos[cid]
+        assert (nm(res["down"][p]), nm(res["up"][p])) == (ed, eu), cid
+        assert (nmc(bd[ids.index(cid)]), nmc(bu[ids.index(cid)])) == (ed, eu), cid
+    for cid, ed, eu in case["mutual"]:
+        p = pos[cid]
+        assert (nm(res["mdown"][p]), nm(res["mup"][p])) == (ed, eu), cid
+
+
+def _random_edge_tiny(rng, ties):
+    """Tiny frames around the first or last pad rows: few edge clusters, crowded
+    claimant rows, so that edge clusters have several claimants (and, with
+    `ties`, equal costs from coordinates snapped to a coarse grid)."""
+    secs, rows, pads, times = [], [], [], []
+    for s in range(int(rng.integers(1, 3))):
+        top = bool(rng.integers(0, 2))
+        edge_rows = [151, 150, 149, 148] if top else [0, 1, 2, 3]
+        counts = [int(rng.integers(1, 4)), int(rng.integers(3, 13)), int(rng.integers(1, 7)), int(rng.integers(0, 4))]
+        for r, m in zip(edge_rows, counts):
+            for _ in range(m):
+                secs.append(s)
+                rows.append(r)
+                pads.append(rng.uniform(20.0, 23.0))
+                times.append(rng.uniform(100.0, 104.0))
+    pads = np.array(pads, np.float32)
+    times = np.array(times, np.float32)
+    if ties:
+        pads = (np.round(pads * 2) / 2).astype(np.float32)
+        times = (np.round(times * 2) / 2).astype(np.float32)
+    perm = rng.permutation(len(rows))
+    return (np.array(secs, np.uint16)[perm], np.array(rows, np.uint16)[perm], pads[perm], times[perm])
+
+
+def _claims_by_rule(sec, row, pad, tim, down, up, rule):
+    """Edge-row claims recomputed in Python from the brute-force A1 links (caller
+    indices) under a selectable rule; 'min' is the reading, the others are
+    plausible mistakes the tests must be able to tell apart."""
+    npads = lambda r: 66 + (144 * r + 151) // 302
+    pitch = lambda r: 4000 + (4000 * r + 151) // 302
+    q = lambda v: int(np.rint(np.float64(v) * 64.0))
+    yq = lambda c: (q(pad[c]) - 32 * (npads(int(row[c])) - 1)) * pitch(int(row[c]))
+    n = len(sec)
+    key = lambda c: (float(tim[c]), float(pad[c]), c)        # row-local order
+    d, u = down.copy(), up.copy()
+    for e in range(n):
+        re_ = int(row[e])
+        if re_ not in (0, 151):
+            continue
+        rc = 1 if re_ == 0 else 150
+        cl = [i for i in range(n) if sec[i] == sec[e] and row[i] == rc and (down[i] if re_ == 0 else up[i]) == e]
+        if not cl:
+            win = -1
+        else:
+            def cost(i):
+                j, k = int(down[i]), int(up[i])
+                d2y = yq(j) + yq(k) - 2 * yq(i)
+                d2z = (q(tim[j]) + q(tim[k]) - 2 * q(tim[i])) * 5160
+                return d2y * d2y + d2z * d2z
+            cl.sort(key=key)
+            if rule == "min":
+                win = min(cl, key=lambda i: (cost(i), key(i)))
+            elif rule == "last_of_equal":
+                win = min(cl, key=lambda i: (cost(i), tuple(-x for x in key(i))))
+            elif rule == "first":
+                win = cl[0]
+            elif rule == "last":
+                win = cl[-1]
+            elif rule == "max":
+                win = max(cl, key=lambda i: (cost(i), tuple(-x for x in key(i))))
+        if re_ == 0:
+            u[e] = win
+        else:
+            d[e] = win
+    return d, u
+
+
+def _edge_corpus():
+    out = []
+    for seed in range(40):
+        rng = np.random.default_rng(7000 + seed)
+        out.append(_random_edge_tiny(rng, ties=seed % 2 == 1))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_edge_claims_match_bruteforce(seed):
+    sec, row, pad, tim = _edge_corpus()[seed]
+    res = orc.track(sec, row, pad, tim)
+    order = res["order"]
+    od = np.where(res["down"] >= 0, order[np.maximum(res["down"], 0)], -1)
+    ou = np.where(res["up"] >= 0, order[np.maximum(res["up"], 0)], -1)
+    bd, bu = orc.bruteforce_links(sec, row, pad, tim)
+    assert np.array_equal(od, bd[order])
+    assert np.array_equal(ou, bu[order])
+
+
+def test_edge_claim_corpus_tells_the_rules_apart():
+    """The random corpus exercises several claimants and cost ties, and every
+    plausible wrong claim rule disagrees with the oracle on it somewhere, while the
+    reading agrees everywhere."""
+    wrong = {"first": 0, "last": 0, "max": 0, "last_of_equal": 0}
+    multi = ties = 0
+    for sec, row, pad, tim in _edge_corpus():
+        bd, bu = orc.bruteforce_neighbours(sec, row, pad, tim)
+        res = orc.track(sec, row, pad, tim)
+        order = res["order"]
+        od = np.where(res["down"] >= 0, order[np.maximum(res["down"], 0)], -1)[np.argsort(order)]
+        ou = np.where(res["up"] >= 0, order[np.maximum(res["up"], 0)], -1)[np.argsort(order)]
+        d, u = _claims_by_rule(sec, row, pad, tim, bd, bu, "min")
+        assert np.array_equal(d, od) and np.array_equal(u, ou)
+        for rule in wrong:
+            d2, u2 = _claims_by_rule(sec, row, pad, tim, bd, bu, rule)
+            wrong[rule] += int(not (np.array_equal(d2, od) and np.array_equal(u2, ou)))
+        d_last, u_last = _claims_by_rule(sec, row, pad, tim, bd, bu, "last_of_equal")
+        ties += int(not (np.array_equal(d_last, d) and np.array_equal(u_last, u)))
+        for e in np.where((row == 0) | (row == 151))[0]:
+            rc = 1 if row[e] == 0 else 150
+            link = bd if row[e] == 0 else bu
+            multi += int(np.sum((row == rc) & (sec == sec[e]) & (link == e)) >= 3)
+    assert multi >= 10 and ties >= 2, (multi, ties)
+    assert all(v > 0 for v in wrong.values()), wrong
