@@ -39,7 +39,7 @@ STAGED_BYTES_PER_CLUSTER = 48.0
 IO_FLOOR_BYTES_PER_CLUSTER = 16.0  # 12 B of cluster fields in, 4 B of cluster_track out
 NOMINAL_HBM_GBS = 8000.0
 FIT_FLOP_PER_CLUSTER = 200.0  # transport + 2-D update per cluster in a track (algorithmic)
-# DRAM bytes per cluster of k_neighbours from one full ncu capture (profiles/neighbours_c3half.md),
+# DRAM bytes per cluster of k_neighbours from one full ncu capture of the 5 ms frame,
 # valid while k_neighbours.cu is the file captured (its SHA-256)
 NB_TRAFFIC = {"sha256": "4fcf5ccfc435803b1d1aac5ac0fcf5fafcc45df543a695dbfb61726de2f26a85",
               "pruned": (207.212544e6 + 145.546496e6) / 16765809, "plain": (204.066560e6 + 103.926784e6) / 16765809}

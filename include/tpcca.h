@@ -201,7 +201,12 @@ int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, const tpc_track
  * address (with that device current); make that first call before any stream
  * capture.  Every call uses the same array, so calls must not overlap on the GPU:
  * two calls in flight at once on different streams race and corrupt each other.
- * Errors as for tpc_track_timeframe. */
+ * Host-side errors as for tpc_track_timeframe (TPC_ERR_ARG for null or misaligned
+ * arrays, before anything is enqueued).  Device-side errors (invalid input, more
+ * tracks than track_capacity, a wait that gave up) are returned only when
+ * out->n_tracks_host is set, which synchronises the stream and therefore cannot be
+ * used during stream capture; with n_tracks_host NULL the call is asynchronous,
+ * the count arrives in out->n_tracks and device-side errors are not reported. */
 int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_clusters *cl, const tpc_tracks *out,
                                 void *stream);
 
@@ -266,6 +271,30 @@ int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int cap);
 
 /* Number of kernel launches (and memset nodes) one call enqueues on its stream. */
 int tpc_tf_launches_per_call(const tpc_tf *tf);
+
+/* The device's fixed-point conversion of the A1 coordinates, for checking the
+ * bit-exactness contract of the seeding step (Sec. 1: seeding in native pad and
+ * time coordinates; the fixed-point reading is this library's): q[i] =
+ * rint(64 v[i]) with ties to even, exactly as the neighbour kernels convert pad
+ * and time.  v and q are device arrays of n entries (4-byte aligned), enqueued on
+ * `stream`.  Values outside the validated input range (|pad| <= 1024, time in
+ * [-65536, 131072]) are converted but never reach the tracker.  Errors:
+ * TPC_ERR_ARG (null or misaligned pointer), TPC_ERR_CUDA. */
+int tpc_debug_quantize(const float *v, uint32_t n, int32_t *q, void *stream);
+
+/* Polls after which a device-side look-back wait of this handle gives up and
+ * records TPC_ERR_TIMEOUT (the kernel then finishes with a zero prefix, so the
+ * context stays usable).  0 restores the default (4194304 polls with a short
+ * sleep each).  For tests of the failure path; lower limits can make regular calls
+ * report TPC_ERR_TIMEOUT under load.  Errors: TPC_ERR_ARG. */
+int tpc_tf_set_spin_limit(tpc_tf *tf, uint32_t polls);
+
+/* Failure-path check of the bounded waits: enqueues on `stream` one look-back
+ * wait (as used by the ordered compactions) whose predecessor never publishes,
+ * with the handle's spin limit.  The wait gives up after that many polls and the
+ * handle's status word reports TPC_ERR_TIMEOUT (tpc_tf_status); the next tracking
+ * call clears it.  Errors: TPC_ERR_ARG, TPC_ERR_CUDA. */
+int tpc_tf_debug_wait(tpc_tf *tf, void *stream);
 
 /* ----------------------------------------------------------------------------
  * Learned link classifier (an extension: the paper has no learned component).

@@ -23,8 +23,8 @@
  *       tracks, numbered in the order of their start cluster;
  *   A5 Kalman fit (FP64):  3-point seed, helix propagation in (x, y), straight
  *       line in (arc length, zeta = 0.516 cm/bin * time), 2-D measurement update.
- * Every reading of a point where the paper is silent is listed in the project's
- * design notes and pinned by the oracle's tests.
+ * Every point where the paper is silent is a reading stated beside the code that
+ * implements it, and the oracle's tests pin each one.
  */
 #include "oracle.h"
 

@@ -127,6 +127,7 @@ struct tpc_tf {
   tpc_tracks graph_out;
   int graph_nb_tile = 0;
   int graph_launches = 0;
+  uint32_t spin_limit = kSpinLimit;  // polls before a look-back wait gives up
 };
 
 extern "C" void tpc_default_config(tpc_tf_config *c) {
@@ -413,6 +414,7 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.nsect = tf->nsect;
   a.nkeys = tf->nkeys;
   a.nb_tile = tf->nb_tile;
+  a.spin_limit = tf->spin_limit;
   a.amb = tf->amb;
   a.amb_cap = tf->amb ? tf->N + 4 : 0;
   a.mlp = tf->mlp;
@@ -525,7 +527,8 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
       (!out->params || !out->cov || !out->t_ref || !out->x || !out->chi2 || !out->ndf || !out->nhits ||
        !out->first_cluster || !out->sector || !out->row_first || !out->row_last || !out->status))
     return fail(TPC_ERR_ARG, "tpc_track_timeframe: null track array");
-  if ((uintptr_t)out->cluster_track & 3) return fail(TPC_ERR_ARG, "tpc_track_timeframe: misaligned array");
+  if (((uintptr_t)out->cluster_track & 3) || !records_aligned(out))
+    return fail(TPC_ERR_ARG, "tpc_track_timeframe: misaligned array");
   TPC_CK(cudaSetDevice(tf->device));
   cudaStream_t st = (cudaStream_t)stream;
   Args a;
@@ -906,6 +909,36 @@ extern "C" int tpc_tf_stage_times(tpc_tf *tf, float *ms, const char **names, int
 }
 
 extern "C" int tpc_tf_launches_per_call(const tpc_tf *tf) { return tf ? tf->launches : 0; }
+
+extern "C" int tpc_debug_quantize(const float *v, uint32_t n, int32_t *q, void *stream) {
+  g_err.clear();
+  if (n > 0 && (!v || !q)) return fail(TPC_ERR_ARG, "tpc_debug_quantize: null array");
+  if (((uintptr_t)v & 3) || ((uintptr_t)q & 3)) return fail(TPC_ERR_ARG, "tpc_debug_quantize: misaligned array");
+  if (n == 0) return TPC_OK;
+  launch_debug_quantize(v, n, q, (cudaStream_t)stream);
+  TPC_CK(cudaGetLastError());
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_set_spin_limit(tpc_tf *tf, uint32_t polls) {
+  g_err.clear();
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_set_spin_limit: null handle");
+  tf->spin_limit = polls ? polls : kSpinLimit;
+  return TPC_OK;
+}
+
+extern "C" int tpc_tf_debug_wait(tpc_tf *tf, void *stream) {
+  g_err.clear();
+  if (!tf) return fail(TPC_ERR_ARG, "tpc_tf_debug_wait: null handle");
+  TPC_CK(cudaSetDevice(tf->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  // counters and the first two look-back words start at zero: tile 0 never publishes
+  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 16, st));
+  uint64_t *lb = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(tf->reset) + kNCounters * 4);
+  launch_debug_wait(lb, tf->reset, tf->spin_limit, st);
+  TPC_CK(cudaGetLastError());
+  return TPC_OK;
+}
 
 // ================================================================ classifier
 extern "C" size_t tpc_mlp_blob_bytes(void);

@@ -1,8 +1,9 @@
 // k_append.cu -- joining the results of a frame tracked as several sector ranges.
 //
-// The sectors of a frame are independent (Sec. 1: the tracker processes a whole
-// time frame; nothing links clusters of different sectors before the fit), and
-// track ids follow the start cluster's order, which is sector-major.  A frame
+// In this tracker the sectors of a frame are independent until the fit: the
+// seeding, the mutual links and the chains never connect clusters of different
+// sectors (cross-sector links come only from the optional follower, which keeps
+// one range).  Track ids follow the start cluster's order, which is sector-major.  A frame
 // tracked as consecutive sector ranges therefore gives the one-call result when
 // each range's track ids are offset by the tracks of the ranges before it and
 // its track records are appended in order.  The host-buffer entry point uses this

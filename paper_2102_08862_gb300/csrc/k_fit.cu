@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(256) k_follow_fit(Args a) {
     uint32_t total;
     const uint32_t excl = block_exclusive_scan<256>(root ? 1u : 0u, s_warp, &total);
     if (threadIdx.x < 32) {
-      const uint32_t pre = lookback_exclusive(a.fl.lb, tile, total, a.ctr);
+      const uint32_t pre = lookback_exclusive(a.fl.lb, tile, total, a.ctr, a.spin_limit);
       if (threadIdx.x == 0) s_prefix = pre;
     }
     __syncthreads();

@@ -104,6 +104,17 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
   }
 }
 
+// The neighbour kernels' fixed-point conversion, element by element (tests of
+// the quantisation contract).
+__global__ void __launch_bounds__(256) k_debug_quantize(const float *__restrict__ v, uint32_t n, int32_t *q) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) q[i] = q64(v[i]);
+}
+
+void launch_debug_quantize(const float *v, uint32_t n, int32_t *q, cudaStream_t st) {
+  const uint32_t blocks = (n + 255) / 256;
+  k_debug_quantize<<<blocks < 8192u ? blocks : 8192u, 256, 0, st>>>(v, n, q);
+}
+
 void launch_row_index(const Args &a, cudaStream_t st) {
   const int warps = a.nkeys + 1;
   const int blocks = (warps * 32 + 255) / 256;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
     uint32_t total;
     const uint32_t excl = block_exclusive_scan<kThreads>((uint32_t)__popc(flags), s_warp, &total);
     if (threadIdx.x < 32) {
-      const uint32_t pre = lookback_exclusive(a.lb_links, tile, total, a.ctr);
+      const uint32_t pre = lookback_exclusive(a.lb_links, tile, total, a.ctr, a.spin_limit);
       if (threadIdx.x == 0) s_prefix = pre;
     }
     __syncthreads();
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
     uint32_t total;
     const uint32_t excl = block_exclusive_scan<kThreads>(nkept, s_warp, &total);
     if (threadIdx.x < 32) {
-      const uint32_t pre = lookback_exclusive(a.lb_keep, tile, total, a.ctr);
+      const uint32_t pre = lookback_exclusive(a.lb_keep, tile, total, a.ctr, a.spin_limit);
       if (threadIdx.x == 0) s_prefix = pre;
     }
     __syncthreads();
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(uint32_t n, const uint16_t
                                                       const float *__restrict__ time, const int32_t *__restrict__ ct,
                                                       uint16_t *o_sector, uint16_t *o_row, float *o_pad,
                                                       float *o_time, int32_t *o_track, uint32_t *o_count,
-                                                      uint64_t *lb, uint32_t *ctr) {
+                                                      uint64_t *lb, uint32_t *ctr, uint32_t spin_limit) {
   constexpr int kWarps = kThreads / 32;
   static_assert(kItems * kWarps == 64, "two (q, warp) counts per lane of the scanning warp");
   __shared__ uint32_t s_tile, s_prefix, s_total;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(uint32_t n, const uint16_t
       s_cnt[lane] = x0 - v0;
       s_cnt[lane + 32] = half + x1 - v1;
       const uint32_t total = half + __shfl_sync(0xffffffffu, x1, 31);
-      const uint32_t pre = lookback_exclusive(lb, tile, total, ctr);
+      const uint32_t pre = lookback_exclusive(lb, tile, total, ctr, spin_limit);
       if (lane == 0) {
         s_prefix = pre;
         s_total = total;
@@ -353,7 +353,7 @@ void launch_compact(const Args &a, const uint16_t *sector, const uint16_t *row, 
   // 6 CTAs per SM fit (40 registers, 33 KB of shared memory each)
   const uint32_t grid = tiles < (uint32_t)sms * 6u ? (tiles ? tiles : 1u) : (uint32_t)sms * 6u;
   k_compact<<<grid, kThreads, 0, st>>>(a.n, sector, row, pad, time, ct, o_sector, o_row, o_pad, o_time, o_track,
-                                       o_count, a.lb_links, a.ctr);
+                                       o_count, a.lb_links, a.ctr, a.spin_limit);
 }
 
 // inspection: the mutual up link as a sorted position, and the start flag
@@ -382,6 +382,18 @@ void launch_links(const Args &a, int sms, cudaStream_t st) {
 void launch_walk(const Args &a, int sms, cudaStream_t st) {
   if (a.nkeys <= kNKeys) k_walk<true><<<sms * 8, kThreads, 0, st>>>(a);
   else k_walk<false><<<sms * 8, kThreads, 0, st>>>(a);
+}
+
+// Failure path of the bounded waits: tile 1 of a look-back whose tile 0 never
+// publishes (one warp).  The wait gives up after spin_limit polls, records
+// kErrTimeout and finishes with a zero prefix.
+__global__ void k_debug_wait(uint64_t *lb, uint32_t *ctr, uint32_t spin_limit) {
+  const uint32_t pre = lookback_exclusive(lb, 1u, 1u, ctr, spin_limit);
+  if (threadIdx.x == 0) ctr[kCtrStarts] = pre;
+}
+
+void launch_debug_wait(uint64_t *lb, uint32_t *ctr, uint32_t spin_limit, cudaStream_t st) {
+  k_debug_wait<<<1, 32, 0, st>>>(lb, ctr, spin_limit);
 }
 
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st) {

@@ -111,6 +111,11 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
     return report(TPC_ERR_CAPACITY, "tpc_track_timeframe_noalloc: more than 65536 clusters (the static scratch limit)");
   if (n > 0 && (!cl->sector || !cl->row || !cl->pad || !cl->time || !out->cluster_track))
     return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: null array");
+  // the kernels load sector/row as 2-byte and pad/time/cluster_track as 4-byte
+  // words: a misaligned array is an argument error, never a device fault
+  if (((uintptr_t)cl->sector & 1) || ((uintptr_t)cl->row & 1) || ((uintptr_t)cl->pad & 3) ||
+      ((uintptr_t)cl->time & 3) || ((uintptr_t)out->cluster_track & 3) || !records_aligned(out))
+    return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: misaligned array");
   if (!out->n_tracks) return report(TPC_ERR_ARG, "tpc_track_timeframe_noalloc: null n_tracks");
   if (out->track_capacity > 0 &&
       (!out->params || !out->cov || !out->t_ref || !out->x || !out->chi2 || !out->ndf || !out->nhits ||
@@ -142,6 +147,7 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
   a.cost_max = c.cost_max_q;
   a.cost_rmax = isqrt64(c.cost_max_q);
   a.n_min = c.n_min;
+  a.spin_limit = kSpinLimit;
   a.cluster_track = out->cluster_track;
   a.track_capacity = out->track_capacity;
   a.params = out->params;

@@ -83,7 +83,8 @@ enum : int {
 
 // A spin-wait gives up after this many polls (with a short sleep between polls,
 // far longer than any legitimate wait), records kErrTimeout and lets the kernel
-// finish so that the context stays usable.
+// finish so that the context stays usable.  This is the default of Args::spin_limit;
+// a handle may lower it (tpc_tf_set_spin_limit) to exercise the give-up path.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ void raise(uint32_t *ctr, uint32_t bits) { atomicOr(&ctr[kCtrErr], bits); }
@@ -118,6 +119,7 @@ struct Args {
   int32_t nsect, nkeys;  // independent sectors of this call (36 for one TPC frame; one per instance
                          // in a batched call) and their (sector, row) keys, nsect * 152
   int32_t nb_tile;       // clusters per neighbour tile
+  uint32_t spin_limit;   // polls before a look-back wait gives up (kSpinLimit unless lowered)
   // outputs
   int32_t *cluster_track;
   uint32_t track_capacity;
@@ -230,7 +232,8 @@ __device__ __forceinline__ void lb_store(uint64_t *p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, uint32_t tile, uint32_t aggregate, uint32_t *ctr) {
+__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, uint32_t tile, uint32_t aggregate, uint32_t *ctr,
+                                                       uint32_t spin_limit) {
   const int lane = threadIdx.x & 31;
   const uint64_t kA = 1ull << 62, kP = 2ull << 62, kMask = (1ull << 62) - 1;
   if (tile == 0) {
@@ -253,7 +256,7 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *status, uint32_
     const int first_p = pref ? __ffs(pref) - 1 : 32;
     const unsigned before_p = (first_p >= 31) ? 0xffffffffu : ((2u << first_p) - 1u);
     if (empty & before_p) {  // a predecessor has not published yet: poll again
-      if (++polls > kSpinLimit) {
+      if (++polls > spin_limit) {
         gave_up = true;
         if (lane == 0) raise(ctr, kErrTimeout);
       }

@@ -97,8 +97,21 @@ inline int32_t isqrt64(int64_t v) {
     if ((r + b) * (r + b) <= v) r += b;
   return (int32_t)r;
 }
+// true when every track-record array of `out` is aligned to its element size
+// (the kernels store records element by element; null arrays are not checked)
+inline bool records_aligned(const tpc_tracks *out) {
+  auto al = [](const void *p, uintptr_t m) { return ((uintptr_t)p & m) == 0; };
+  return al(out->params, 3) && al(out->cov, 3) && al(out->t_ref, 3) && al(out->x, 3) && al(out->chi2, 3) &&
+         al(out->ndf, 3) && al(out->nhits, 3) && al(out->first_cluster, 3) && al(out->sector, 1) &&
+         al(out->row_first, 1) && al(out->row_last, 1) && al(out->n_tracks, 3) && al(out->next_track, 3);
+}
 // sets the message returned by tpc_last_error() (cleared for TPC_OK); returns code
 int report(int code, const char *msg);
+// device fixed-point conversion q[i] = rint(64 v[i]) (tests of the quantisation contract)
+void launch_debug_quantize(const float *v, uint32_t n, int32_t *q, cudaStream_t st);
+// one look-back wait on lb[1] whose predecessor lb[0] never publishes; gives up
+// after spin_limit polls and records kErrTimeout in ctr (tests of the failure path)
+void launch_debug_wait(uint64_t *lb, uint32_t *ctr, uint32_t spin_limit, cudaStream_t st);
 // order[] of the last call (inspection)
 void launch_debug_order(const int32_t *perm, uint32_t n, int32_t *order, cudaStream_t st);
 

@@ -1,8 +1,11 @@
 """Host-side logic of runs on several GPUs of one node (one process per GPU).
 
 The tracking path shards with no collective on the data path: time frames are
-independent, and so are the 36 sectors of one frame (no cluster of one sector is
-linked to another's by the seeding, the chains or the fit).  Every rank tracks
+independent, and so are the 36 sectors of one frame as long as cross-sector
+links are off (no cluster of one sector is linked to another's by the seeding,
+the chains or the fit).  With follow = 2 the follower links tracks across sector
+boundaries, so a sector-sharded frame would lose the links that cross a shard
+boundary: `sector_shard` refuses that mode, and such frames are sharded whole.  Every rank tracks
 its own frames, or its own contiguous block of sectors of a shared frame; the
 only exchange is on the host:
   * step times reduced by maximum and unit counts by sum (whole-job throughput
@@ -20,10 +23,14 @@ import numpy as np
 NSECT = 36
 
 
-def sector_shard(rank: int, world: int, nsect: int = NSECT) -> tuple[int, int]:
-    """Contiguous block [lo, hi) of sectors for this rank (sizes differ by one at most)."""
+def sector_shard(rank: int, world: int, nsect: int = NSECT, follow: int = 0) -> tuple[int, int]:
+    """Contiguous block [lo, hi) of sectors for this rank (sizes differ by one at
+    most).  `follow` is the tracker's follow mode: with cross-sector links
+    (follow = 2) sectors are not independent and a frame cannot be split."""
     if world < 1 or not 0 <= rank < world:
         raise ValueError("rank must be in [0, world)")
+    if follow == 2 and world > 1:
+        raise ValueError("cross-sector links (follow = 2) join neighbouring sectors: shard whole frames instead")
     base, extra = divmod(nsect, world)
     lo = rank * base + min(rank, extra)
     return lo, lo + base + (1 if rank < extra else 0)

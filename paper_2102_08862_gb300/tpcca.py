@@ -110,6 +110,12 @@ def load():
     lib.tpc_tf_stage_times.restype = ctypes.c_int
     lib.tpc_tf_launches_per_call.argtypes = [c_vp]
     lib.tpc_tf_launches_per_call.restype = ctypes.c_int
+    lib.tpc_debug_quantize.argtypes = [c_vp, c_u32, c_vp, c_vp]
+    lib.tpc_debug_quantize.restype = ctypes.c_int
+    lib.tpc_tf_set_spin_limit.argtypes = [c_vp, c_u32]
+    lib.tpc_tf_set_spin_limit.restype = ctypes.c_int
+    lib.tpc_tf_debug_wait.argtypes = [c_vp, c_vp]
+    lib.tpc_tf_debug_wait.restype = ctypes.c_int
     lib.tpc_tf_remove_unassigned.argtypes = [c_vp, P(tpc_clusters), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]
     lib.tpc_tf_remove_unassigned.restype = ctypes.c_int
     lib.tpc_tf_arena_bytes.argtypes = [P(tpc_tf_config), P(ctypes.c_size_t)]
@@ -231,6 +237,18 @@ def tpc_tf_stage_times(handle, cap: int = 16):
 
 def tpc_tf_launches_per_call(handle) -> int:
     return load().tpc_tf_launches_per_call(handle)
+
+
+def tpc_debug_quantize(v_ptr, n: int, q_ptr, stream: int = 0) -> int:
+    return load().tpc_debug_quantize(v_ptr, n, q_ptr, stream)
+
+
+def tpc_tf_set_spin_limit(handle, polls: int) -> int:
+    return load().tpc_tf_set_spin_limit(handle, polls)
+
+
+def tpc_tf_debug_wait(handle, stream: int = 0) -> int:
+    return load().tpc_tf_debug_wait(handle, stream)
 
 
 def tpc_track_timeframe_graph(handle, clusters: tpc_clusters, tracks: tpc_tracks, stream: int = 0) -> int:

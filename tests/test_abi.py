@@ -139,3 +139,37 @@ def test_arena_estimate_grows_with_clusters(lib):
     assert big > 10 * small
     c.mode = tpcca.TPC_MODE_PRUNED
     assert tpcca.tpc_tf_arena_bytes(c) > big  # the pair regions and the overflow list
+
+
+def test_noalloc_rejects_misaligned_arrays_before_any_launch(lib):
+    """The allocation-free entry point checks the alignment of every array on the
+    host and returns TPC_ERR_ARG without touching the device (this runs without a
+    GPU: any device call here would fail with TPC_ERR_CUDA instead)."""
+    base = 0x10000
+    good = dict(sector=base, row=base + 0x1000, pad=base + 0x2000, time=base + 0x3000)
+    cases = [("sector", 1), ("row", 1), ("pad", 2), ("time", 1)]
+    for field, off in cases:
+        kw = dict(good)
+        kw[field] += off
+        cl = tpcca.tpc_clusters(n=100, flags=tpcca.TPC_INPUT_SORTED, **kw)
+        tr = tpcca.tpc_tracks(cluster_track=base + 0x4000, track_capacity=0, n_tracks=base + 0x5000)
+        assert lib.tpc_track_timeframe_noalloc(None, ctypes.byref(cl), ctypes.byref(tr), None) == tpcca.TPC_ERR_ARG
+        assert "misaligned" in tpcca.tpc_last_error(), field
+    cl = tpcca.tpc_clusters(n=100, flags=tpcca.TPC_INPUT_SORTED, **good)
+    for field in ("cluster_track", "params", "sector", "n_tracks"):
+        kw = dict(cluster_track=base + 0x4000, track_capacity=16, n_tracks=base + 0x5000,
+                  **{k: base + 0x6000 + 0x100 * i for i, k in enumerate(
+                      ("params", "cov", "t_ref", "x", "chi2", "ndf", "nhits", "first_cluster", "sector",
+                       "row_first", "row_last", "status"))})
+        kw[field] += 1 if field == "sector" else 2
+        tr = tpcca.tpc_tracks(**kw)
+        assert lib.tpc_track_timeframe_noalloc(None, ctypes.byref(cl), ctypes.byref(tr), None) == tpcca.TPC_ERR_ARG
+        assert "misaligned" in tpcca.tpc_last_error(), field
+
+
+def test_debug_entry_points_check_arguments(lib):
+    assert lib.tpc_tf_set_spin_limit(None, 4) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_tf_debug_wait(None, None) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_debug_quantize(0x10002, 8, 0x20000, None) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_debug_quantize(None, 8, 0x20000, None) == tpcca.TPC_ERR_ARG
+    assert lib.tpc_debug_quantize(None, 0, None, None) == tpcca.TPC_OK

@@ -26,6 +26,9 @@ def test_sector_shards_cover_the_sectors_once():
         assert max(sizes) - min(sizes) <= 1
     with pytest.raises(ValueError):
         mg.sector_shard(2, 2)
+    with pytest.raises(ValueError):
+        mg.sector_shard(0, 2, follow=2)
+    assert mg.sector_shard(0, 1, follow=2) == (0, 36)
 
 
 def test_track_id_offsets_are_the_exclusive_scan():
@@ -75,5 +78,9 @@ def _worker(rank, world, port, out_dir):
 @pytest.mark.parametrize("world", [2, 5])  # 18/18 and 8/7/7/7/7 sectors
 def test_ranks_merge_to_the_whole_frame(tmp_path, world):
     import torch.multiprocessing as mp
+    import oracle
+    import tpcsynth as ts
+    oracle.build()  # built once here, not raced by the spawned ranks
+    ts.build()
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     assert (tmp_path / "ok").read_text().endswith(f"from {world} shards\n")

@@ -98,3 +98,52 @@ def test_noalloc_rejects_oversized_frames(env):
     cl, tr = _structs(tpcca, ins, outs, 16, count)
     assert tpcca.tpc_track_timeframe_noalloc(None, cl, tr, 0) == tpcca.TPC_ERR_CAPACITY
     assert "65536" in tpcca.tpc_last_error()
+
+
+def test_noalloc_async_count_and_error_then_clean_call(env):
+    """Without n_tracks_host the call is asynchronous and the count arrives in
+    out->n_tracks; an invalid frame (flagged sorted, two times swapped) reports
+    TPC_ERR_INPUT through n_tracks_host, and the next clean call returns TPC_OK
+    with the regular entry point's results (the static array keeps state between
+    calls, so the error word must be cleared by the call itself)."""
+    import ctypes
+    tpcca = env
+    dev = torch.device("cuda", 0)
+    f = ts.generate(ts.c1(seed=7))
+    cap = 4096
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ins = (t(f.sector.view(np.int16)), t(f.row.view(np.int16)), t(f.pad), t(f.time))
+    cfg = tpcca.tpc_default_config()
+    cfg.max_clusters = f.n
+    handle = tpcca.tpc_tf_create(cfg)
+    try:
+        ref_out = _outputs(dev, f.n, cap)
+        c_ref = ctypes.c_uint32(0)
+        cl, tr = _structs(tpcca, ins, ref_out, cap, c_ref)
+        assert tpcca.tpc_track_timeframe(handle, cl, tr, 0) == tpcca.TPC_OK, tpcca.tpc_last_error()
+        # asynchronous: no host count
+        na_out = _outputs(dev, f.n, cap)
+        cl, tr = _structs(tpcca, ins, na_out, cap, ctypes.c_uint32(0))
+        tr.n_tracks_host = None
+        assert tpcca.tpc_track_timeframe_noalloc(None, cl, tr, 0) == tpcca.TPC_OK, tpcca.tpc_last_error()
+        torch.cuda.synchronize()
+        assert int(na_out["n_tracks"][0].item()) == c_ref.value > 0
+        assert torch.equal(na_out["cluster_track"], ref_out["cluster_track"])
+        # invalid input flagged as sorted: reported through n_tracks_host
+        swapped = f.time.copy()
+        same = (f.sector[1:] == f.sector[:-1]) & (f.row[1:] == f.row[:-1])
+        i = int(np.nonzero(same & (np.diff(swapped) > 0))[0][0])
+        swapped[[i, i + 1]] = swapped[[i + 1, i]]
+        bad = (ins[0], ins[1], ins[2], t(swapped))
+        c_bad = ctypes.c_uint32(0)
+        cl, tr = _structs(tpcca, bad, _outputs(dev, f.n, cap), cap, c_bad)
+        assert tpcca.tpc_track_timeframe_noalloc(None, cl, tr, 0) == tpcca.TPC_ERR_INPUT
+        # a clean call afterwards
+        again = _outputs(dev, f.n, cap)
+        c2 = ctypes.c_uint32(0)
+        cl, tr = _structs(tpcca, ins, again, cap, c2)
+        assert tpcca.tpc_track_timeframe_noalloc(None, cl, tr, 0) == tpcca.TPC_OK, tpcca.tpc_last_error()
+        assert c2.value == c_ref.value
+        assert torch.equal(again["cluster_track"], ref_out["cluster_track"])
+    finally:
+        tpcca.tpc_tf_destroy(handle)
