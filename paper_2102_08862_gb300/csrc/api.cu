@@ -59,6 +59,7 @@ struct tpc_tf {
   size_t arena_bytes = 0;
   int32_t *row_begin = nullptr;
   int2 *link = nullptr;
+  int2 *tq = nullptr;  // quantised (t, y) of every sorted cluster
   uint16_t *mup16 = nullptr;
   int2 *starts = nullptr;
   int32_t *trk_key = nullptr, *trk_len = nullptr, *chain = nullptr;
@@ -203,6 +204,7 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->tile_off, (size_t)(tf->nkeys + 1) * 4},
       {(void **)&tf->tile_win, (size_t)tf->tile_cap * 2 * 16},
       {(void **)&tf->link, (N + 4) * 8},
+      {(void **)&tf->tq, (N + 8) * 8},
       {(void **)&tf->mup16, (N + 16) * 2},
       {(void **)&tf->starts, (N / 2 + 2) * 8},
       {(void **)&tf->trk_key, (size_t)(tf->track_list_cap + 1) * 4},
@@ -395,6 +397,7 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.tile_win = tf->tile_win;
   a.tile_cap = tf->tile_cap;
   a.link = tf->link;
+  a.tq = tf->tq;
   a.mup16 = tf->mup16;
   a.starts = tf->starts;
   a.trk_key = tf->trk_key;
@@ -490,12 +493,13 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
     tf->launches += nl;
     stage(tf, st, "sort");
   }
+  launch_quantize(a, tf->sms, st);
   launch_row_index(a, st);
   launch_tile_windows(a, st);
   stage(tf, st, "ingest");
-  launch_neighbours(a, tf->cfg.row_cap, st, prune);
+  launch_neighbours(a, tf->cfg.row_cap, tf->sms, st, prune);
   stage(tf, st, "neighbours");
-  tf->launches += 3;
+  tf->launches += 4;
   if (prune) {
     launch_prune_tiles(a, tf->mlp, tf->logit_tau, tf->sms, st);
     stage(tf, st, "prune_tiles");

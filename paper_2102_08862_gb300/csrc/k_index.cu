@@ -104,6 +104,99 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
   }
 }
 
+// A0 validation and quantisation, one pass over the sorted clusters: every
+// cluster must have sector < nsect, row < 152, a pad and a time inside the
+// validated range, and follow its predecessor in (sector, row, time, pad) order;
+// anything else raises kErrInput (the cluster then gets the coordinates of pad
+// 0, time 0 so that later stages stay in range).  The pass writes each cluster's
+// fixed-point (t_q, y_q) = (rint(64 time), (rint(64 pad) - 32 (npads - 1)) *
+// pitch_um) once, so that the neighbour, window and claim kernels read 8
+// quantised bytes per cluster instead of converting the same clusters again
+// for every tile whose windows hold them.  A thread takes 8 consecutive clusters
+// with 16-byte loads (arrays on a 16-byte boundary; otherwise, and for the
+// tail, one cluster per thread); the predecessor of its first cluster comes
+// from the lane below (a shuffle) or, for lane 0, from global memory.
+struct QCheck {
+  int kp;
+  float tp, pp;
+  bool bad;
+  __device__ __forceinline__ void step(int key, float t, float p, bool first_of_array) {
+    if (!first_of_array && !(kp < key || (kp == key && (tp < t || (tp == t && pp <= p))))) bad = true;
+    kp = key;
+    tp = t;
+    pp = p;
+  }
+};
+__device__ __forceinline__ int2 quant_checked(int sec, int row, float p, float t, int nsect, bool &bad) {
+  if (sec >= nsect || row >= kNRows) bad = true;
+  if (!pad_ok(p) || !time_ok(t)) {
+    bad = true;
+    p = 0.0f;
+    t = 0.0f;
+  }
+  return make_int2(q64(t), y_quant(p, min(row, kNRows - 1)));
+}
+
+__global__ void __launch_bounds__(256) k_quantize(Args a, int vec) {
+  const uint32_t n = a.n;
+  const int lane = threadIdx.x & 31;
+  const int nsect = a.nsect;
+  QCheck ck;
+  ck.bad = false;
+  const uint32_t nvec = vec ? n / 256u * 256u : 0u;  // clusters handled 8 per thread (whole warps of 256)
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t w0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 8u; w0 < nvec; w0 += stride * 8u) {
+    const uint32_t i0 = w0 + (uint32_t)lane * 8u;
+    const uint4 sv = *reinterpret_cast<const uint4 *>(a.sector + i0);
+    const uint4 rv = *reinterpret_cast<const uint4 *>(a.row + i0);
+    const float4 p0 = *reinterpret_cast<const float4 *>(a.pad + i0), p1 = *reinterpret_cast<const float4 *>(a.pad + i0 + 4);
+    const float4 t0 = *reinterpret_cast<const float4 *>(a.time + i0), t1 = *reinterpret_cast<const float4 *>(a.time + i0 + 4);
+    const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w}, rw[4] = {rv.x, rv.y, rv.z, rv.w};
+    const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+    const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+    // the predecessor of the first cluster: the last one of the lane below
+    const int klast = (int)(sw[3] >> 16) * kNRows + (int)(rw[3] >> 16);
+    ck.kp = __shfl_up_sync(0xffffffffu, klast, 1);
+    ck.tp = __shfl_up_sync(0xffffffffu, tv[7], 1);
+    ck.pp = __shfl_up_sync(0xffffffffu, pv[7], 1);
+    if (lane == 0 && i0 > 0) {
+      ck.kp = (int)a.sector[i0 - 1] * kNRows + a.row[i0 - 1];
+      ck.tp = a.time[i0 - 1];
+      ck.pp = a.pad[i0 - 1];
+    }
+    int2 q[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int sec = (int)((sw[e >> 1] >> (16 * (e & 1))) & 0xffffu), row = (int)((rw[e >> 1] >> (16 * (e & 1))) & 0xffffu);
+      const int key = sec * kNRows + row;
+      ck.step(key, tv[e], pv[e], i0 + e == 0);
+      q[e] = quant_checked(sec, row, pv[e], tv[e], nsect, ck.bad);
+    }
+    int4 *dst = reinterpret_cast<int4 *>(a.tq + i0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[e] = make_int4(q[2 * e].x, q[2 * e].y, q[2 * e + 1].x, q[2 * e + 1].y);
+  }
+  for (uint32_t i = nvec + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {  // the rest
+    const int sec = a.sector[i], row = a.row[i];
+    const float p = a.pad[i], t = a.time[i];
+    if (i > 0) {
+      ck.kp = (int)a.sector[i - 1] * kNRows + a.row[i - 1];
+      ck.tp = a.time[i - 1];
+      ck.pp = a.pad[i - 1];
+    }
+    ck.step(sec * kNRows + row, t, p, i == 0);
+    a.tq[i] = quant_checked(sec, row, p, t, nsect, ck.bad);
+  }
+  if (ck.bad) raise(a.ctr, kErrInput);
+}
+
+void launch_quantize(const Args &a, int sms, cudaStream_t st) {
+  const bool vec = ((((uintptr_t)a.pad | (uintptr_t)a.time | (uintptr_t)a.sector | (uintptr_t)a.row) & 15) == 0);
+  const uint32_t blocks = (a.n / 8 + 255) / 256 + 1;
+  const uint32_t cap = (uint32_t)sms * 8u;
+  k_quantize<<<blocks < cap ? blocks : cap, 256, 0, st>>>(a, vec ? 1 : 0);
+}
+
 // The neighbour kernels' fixed-point conversion, element by element (tests of
 // the quantisation contract).
 __global__ void __launch_bounds__(256) k_debug_quantize(const float *__restrict__ v, uint32_t n, int32_t *q) {

@@ -9,16 +9,19 @@
 // when the residual is <= cost_max; ties go to the smaller row-local j, then k.
 // All of it is integer arithmetic in 1/64 um units, so results are exact.
 //
-// GB300 design: every (sector, row) is cut into tiles of nb_tile clusters.  The
-// tile-window kernel finds, for each tile, the clusters of rows r-1 and r+1 whose
-// time lies within wt of the tile's time span (binary searches, all tiles in
-// parallel).  The neighbour kernel gives each tile one CTA: it validates and
-// quantises its tile and stages both windows in shared memory (18 KB at the
-// 512-cluster tile, so that 8 CTAs share an SM and hide each other's memory
-// latency); each thread then links
-// a contiguous run of clusters, moving its window pointers forward only.  Windows
-// larger than the staging buffers are read from global memory with the same
-// arithmetic.
+// GB300 design: the ingest pass has validated every cluster and written its
+// quantised (t, y) once into an 8-byte array, sorted like the clusters.  Every
+// (sector, row) is cut into tiles of nb_tile clusters; the tile-window kernel
+// finds, for each tile, the clusters of rows r-1 and r+1 whose time lies within
+// wt of the tile's time span (binary searches, all tiles in parallel).  The
+// neighbour kernel gives each tile one CTA: the bulk-copy (TMA) engine copies the
+// tile and both windows from the quantised array into shared memory, completion
+// on an mbarrier; each thread then links a contiguous run of clusters, moving its
+// window pointers forward only.  Its scans of the two windows only collect
+// candidates (indices in a 16-bit shift register); the pairs are scored after
+// both scans, so that lanes with longer windows do not drag the pair arithmetic
+// through every iteration.  Windows larger than the staging buffers are read
+// from global memory with the same arithmetic.
 #include "mlp_dev.cuh"
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
@@ -37,29 +40,21 @@ constexpr int kMaxCand = 4;  // candidates per neighbour row kept in registers
 // do not fit, go to the global list.
 constexpr int kPruneMaxPairs = 32;
 struct NbQueue {
-  uint32_t pairs[4][256];  // a thread's first four pairs under the cut (j | k << 11); <= 256 threads
   int count, end;
-  unsigned warps_done;     // the last warp to finish publishes the region's row count
+  unsigned warps_done;  // the last warp to finish publishes the region's row count
 };
 template <bool kPrune> struct NbExtra {};
 template <> struct NbExtra<true> { NbQueue q; };
 
-// first e in [lo, hi) with q64(time[e]) >= x
-__device__ __forceinline__ int gm_lower_bound(const float *time, int lo, int hi, int x) {
+// first e in [lo, hi) with tq[e].x >= x
+__device__ __forceinline__ int tq_lower_bound(const int2 *tq, int lo, int hi, int x) {
   while (lo < hi) {
     const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
-    if (q64(time[mid]) < x) lo = mid + 1; else hi = mid;
+    if (tq[mid].x < x) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-__device__ __forceinline__ float sane_pad(float p) { return pad_ok(p) ? p : 0.0f; }
-__device__ __forceinline__ float sane_time(float t) { return time_ok(t) ? t : 0.0f; }
-
-// quantised (t, y) of a cluster of row r: y_q = (rint(64 pad) - half) * pitch
-__device__ __forceinline__ int2 quant_ty(float pad, float time, int half, int pitch) {
-  return make_int2(q64(time), (q64(pad) - half) * pitch);
-}
 
 // Pruned mode: append a cluster with >= 2 pairs under the cost cut to the list
 // the classifier rescores.  The lanes that append together share one atomic.
@@ -109,7 +104,7 @@ __device__ __forceinline__ int gallop_lower_bound(T t, int n, int x, int guess) 
 // (np entries) and r+1 (nn entries).  Links are written as sorted positions
 // (window base + window-local index).
 template <bool kPrune, class CT, class PT, class NT_>
-__device__ __forceinline__ void link_run(const Args &a, int li0, int li1, int cnt, CT C, PT P, int np, NT_ N, int nn,
+__device__ __noinline__ void link_run(const Args &a, int li0, int li1, int cnt, CT C, PT P, int np, NT_ N, int nn,
                                          int wy, int wt, int64_t cost_max, int2 *out, int base_p, int base_n,
                                          int base_c) {
   if (li0 >= li1) return;
@@ -198,17 +193,25 @@ __device__ __forceinline__ void link_run(const Args &a, int li0, int li1, int cn
 }
 
 // The same linking for staged windows (fewer than 2048 entries each), on
-// shared-memory arrays of (t, y).  Every candidate pair is scored as one 64-bit
-// key (min(cost, cost_max + 1) << 22 | j << 11 | k): the smallest key is the
-// lexicographic minimum of (cost, j, k), so the scan order does not matter and
-// costs above cost_max (which never link) cannot overflow the key.
+// shared-memory arrays of (t, y) that end with a sentinel entry of t = INT_MAX,
+// so that no scan needs a bounds check.  The scans of both windows only collect
+// the in-window candidates (their window-local indices, up to four per row, in
+// two registers used as a shift register of 16-bit entries); the pairs are scored
+// afterwards, so that the divergent scans stay cheap.  The best pair is the
+// smallest key (cost << 22 | j << 11 | k) over the pairs of cost <= cost_max:
+// the lexicographic minimum of (cost, j, k) whatever the order of scoring.  A
+// window test is one unsigned compare: |d| <= w  <=>  (unsigned)(d + w) <= 2 w.
+// A cluster with more than four candidates in a row (0.2 % on the synthetic
+// frames) scores every pair of its windows instead.
 template <bool kPrune>
 __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, int cnt, const int2 *__restrict__ sc,
                                               const int2 *__restrict__ sp, int np, const int2 *__restrict__ sn,
                                               int nn, int wy, int wt, int64_t cost_max, int2 *out, int base_p,
-                                              int base_n, int base_c, NbQueue *q, PruneRow *region) {
+                                              int base_n, int base_c, NbQueue *q, uint32_t *pairs,
+                                              PruneRow *region) {
   if (li0 >= li1) return;
-  const uint64_t capc = (uint64_t)cost_max + 1;
+  const uint32_t wy2 = 2u * (uint32_t)wy;
+  const uint64_t cmax = (uint64_t)cost_max;
   const float frac = (float)li0 / (float)cnt;
   const int t0 = sc[li0].x;
   int jlo = gallop_lower_bound([&](int j) { return sp[j].x; }, np, t0 - wt, (int)(frac * (float)np));
@@ -216,80 +219,86 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
   for (int li = li0; li < li1; ++li) {
     const int2 ci = sc[li];
     const int32_t ti = ci.x, yi = ci.y, tlo = ti - wt, thi = ti + wt;
-    while (jlo < np && sp[jlo].x < tlo) ++jlo;
-    while (klo < nn && sn[klo].x < tlo) ++klo;
-    // candidates in row r-1 (at most kMaxCand kept in registers)
-    int nj = 0;
-    int2 ej0 = make_int2(0, 0), ej1 = ej0, ej2 = ej0, ej3 = ej0;
-    int cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
-    for (int j = jlo; j < np; ++j) {
+    while (sp[jlo].x < tlo) ++jlo;  // the sentinel stops both advances
+    while (sn[klo].x < tlo) ++klo;
+    // candidates: newest in the low half of c01, then the high half, then c23
+    uint32_t cj01 = 0, cj23 = 0, ck01 = 0, ck23 = 0;
+    int nj = 0, nk = 0;
+    for (int j = jlo;; ++j) {
       const int2 e = sp[j];
       if (e.x > thi) break;
-      if (abs(e.y - yi) > wy) continue;
-      if (nj == 0) { cj0 = j; ej0 = e; }
-      else if (nj == 1) { cj1 = j; ej1 = e; }
-      else if (nj == 2) { cj2 = j; ej2 = e; }
-      else if (nj == 3) { cj3 = j; ej3 = e; }
-      ++nj;
-    }
-    // pruned mode: pairs under the cost cut, the first four kept (j | k << 11) in
-    // the thread's shared-memory slots
-    int nc = 0, nkc = 0;
-    auto keep_pair = [&](uint32_t v) {
-      if (nc < 4) q->pairs[nc][threadIdx.x] = v;
-      ++nc;
-    };
-    // best pair under the cut as (cost, j, k); a pair whose y or z kink alone
-    // exceeds floor(sqrt(cost_max)) costs more than cost_max and is skipped with
-    // two 32-bit compares (most pairs of a window are not on a straight line)
-    uint64_t bc = ~0ull;
-    int bj = 2047, bk = 2047;
-    const int32_t rmax = a.cost_rmax;
-    auto consider = [&](int j, int k, int32_t d2y, int32_t d2t) {
-      const int32_t d2z = d2t * kUmPerBin;
-      if (abs(d2y) > rmax || abs(d2z) > rmax) return;
-      const uint64_t c = (uint64_t)((int64_t)d2y * d2y) + (uint64_t)((int64_t)d2z * d2z);
-      if (c >= capc) return;
-      if (kPrune) keep_pair((uint32_t)j | ((uint32_t)k << 11));
-      if (c < bc || (c == bc && (j < bj || (j == bj && k < bk)))) {
-        bc = c;
-        bj = j;
-        bk = k;
+      if ((uint32_t)(e.y - yi + wy) <= wy2) {
+        cj23 = __byte_perm(cj23, cj01, 0x1076);  // (c23 << 16) | (c01 >> 16)
+        cj01 = __byte_perm(cj01, (uint32_t)j, 0x1054);  // (c01 << 16) | j
+        ++nj;
       }
-    };
-    if (nj > 0 && nj <= kMaxCand) {
-      const int cj[4] = {cj0, cj1, cj2, cj3};
-      const int32_t dyj[4] = {ej0.y - yi, ej1.y - yi, ej2.y - yi, ej3.y - yi};
-      const int32_t dtj[4] = {ej0.x - ti, ej1.x - ti, ej2.x - ti, ej3.x - ti};
-      for (int k = klo; k < nn; ++k) {
+    }
+    if (nj > 0)
+      for (int k = klo;; ++k) {
         const int2 e = sn[k];
         if (e.x > thi) break;
-        const int32_t dyk = e.y - yi;
-        if (abs(dyk) > wy) continue;
-        if (kPrune) ++nkc;
-        const int32_t dtk = e.x - ti;
-#pragma unroll
-        for (int x = 0; x < kMaxCand; ++x) {
-          if (x >= nj) break;
-          consider(cj[x], k, dyj[x] + dyk, dtj[x] + dtk);
+        if ((uint32_t)(e.y - yi + wy) <= wy2) {
+          ck23 = __byte_perm(ck23, ck01, 0x1076);
+          ck01 = __byte_perm(ck01, (uint32_t)k, 0x1054);
+          ++nk;
         }
       }
-    } else if (nj > kMaxCand) {  // crowded windows: every pair
-      for (int j = jlo; j < np; ++j) {
+    uint64_t best = ~0ull;
+    int nc = 0;
+    auto score = [&](int j, int k, int2 ej, int2 ek) {
+      const int32_t d2y = ej.y + ek.y - 2 * yi;
+      const int32_t d2z = (ej.x + ek.x - 2 * ti) * kUmPerBin;
+      const uint64_t c = (uint64_t)((int64_t)d2y * d2y) + (uint64_t)((int64_t)d2z * d2z);
+      if (c <= cmax) {
+        if (kPrune) {
+          if (nc < 4) pairs[nc * 256 + threadIdx.x] = (uint32_t)j | ((uint32_t)k << 11);
+          ++nc;
+        }
+        const uint64_t key = (c << 22) | ((uint64_t)j << 11) | (uint64_t)k;
+        best = key < best ? key : best;
+      }
+    };
+    if (nj <= 4 && nk <= 4) {
+      // the newest two candidates of each row (unused ones read entry 0 and are not taken)
+      if (nk > 0) {
+        const int ja = (int)(cj01 & 0xffffu), jb = (int)(cj01 >> 16);
+        const int ka = (int)(ck01 & 0xffffu), kb = (int)(ck01 >> 16);
+        const int2 eja = sp[ja], eka = sn[ka];
+        score(ja, ka, eja, eka);
+        if (nj > 1) score(jb, ka, sp[jb], eka);
+        if (nk > 1) {
+          const int2 ekb = sn[kb];
+          score(ja, kb, eja, ekb);
+          if (nj > 1) score(jb, kb, sp[jb], ekb);
+        }
+      }
+      {
+        if (nj > 2 || nk > 2) {  // pairs with an older candidate (positions 2, 3 from the newest)
+          auto at = [](uint32_t c01, uint32_t c23, int pos) {
+            return (int)(((pos & 2 ? c23 : c01) >> ((pos & 1) * 16)) & 0xffffu);
+          };
+          for (int x = 0; x < nj; ++x)
+            for (int z = (x < 2 ? 2 : 0); z < nk; ++z) {
+              const int j = at(cj01, cj23, x), k = at(ck01, ck23, z);
+              score(j, k, sp[j], sn[k]);
+            }
+        }
+      }
+    } else {  // crowded: every pair of the windows
+      for (int j = jlo;; ++j) {
         const int2 ej = sp[j];
         if (ej.x > thi) break;
-        const int32_t dyj = ej.y - yi;
-        if (abs(dyj) > wy) continue;
-        for (int k = klo; k < nn; ++k) {
+        if ((uint32_t)(ej.y - yi + wy) > wy2) continue;
+        for (int k = klo;; ++k) {
           const int2 ek = sn[k];
           if (ek.x > thi) break;
-          const int32_t dyk = ek.y - yi;
-          if (abs(dyk) > wy) continue;
-          consider(j, k, dyj + dyk, (ej.x - ti) + (ek.x - ti));
+          if ((uint32_t)(ek.y - yi + wy) > wy2) continue;
+          score(j, k, ej, ek);
         }
       }
     }
-    out[li] = bc != ~0ull ? make_int2(base_p + bj, base_n + bk) : make_int2(-1, -1);
+    out[li] = best != ~0ull ? make_int2(base_p + (int)((best >> 11) & 2047u), base_n + (int)(best & 2047u))
+                            : make_int2(-1, -1);
     if (kPrune && nc >= 2) {
       // the pairs go to the tile's region (rows in any order: the rescoring
       // compares (cost, j, k) explicitly); a cluster that does not fit goes to the list
@@ -297,15 +306,7 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
       if (nc <= kPruneMaxPairs) old = atomicAdd(&q->count, nc);
       if (old + nc <= kPruneRegionRows) {
         atomicMax(&q->end, old + nc);  // reservations that fit form a prefix of the region
-        if (nj > kMaxCand) {           // crowded path: count the row r+1 candidates
-          nkc = 0;
-          for (int k = klo; k < nn; ++k) {
-            const int2 e = sn[k];
-            if (e.x > thi) break;
-            nkc += abs(e.y - yi) <= wy;
-          }
-        }
-        const int cn = nj | (nkc << 16), ci_ = base_c + li;
+        const int cn = nj | (nk << 16), ci_ = base_c + li;
         auto put = [&](int slot, uint32_t jk) {
           const int j = (int)(jk & 2047u), k = (int)(jk >> 11);
           const int2 ej = sp[j], ek = sn[k];
@@ -315,18 +316,18 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
           reinterpret_cast<int4 *>(&w)[2] = make_int4(ek.x, ek.y, 0, 0);
         };
         if (nc <= 4) {
-          for (int e = 0; e < nc; ++e) put(old + e, q->pairs[e][threadIdx.x]);
+          for (int e = 0; e < nc; ++e) put(old + e, pairs[e * 256 + threadIdx.x]);
         } else {  // more than four pairs (rare): enumerate them again from the windows
           int slot = old;
-          for (int j = jlo; j < np; ++j) {
+          for (int j = jlo;; ++j) {
             const int2 ej = sp[j];
             if (ej.x > thi) break;
-            if (abs(ej.y - yi) > wy) continue;
-            for (int k = klo; k < nn; ++k) {
+            if ((uint32_t)(ej.y - yi + wy) > wy2) continue;
+            for (int k = klo;; ++k) {
               const int2 ek = sn[k];
               if (ek.x > thi) break;
-              if (abs(ek.y - yi) > wy) continue;
-              if ((uint64_t)triplet_cost(ej.y - yi, ek.y - yi, ej.x - ti, ek.x - ti) < capc)
+              if ((uint32_t)(ek.y - yi + wy) > wy2) continue;
+              if ((uint64_t)triplet_cost(ej.y - yi, ek.y - yi, ej.x - ti, ek.x - ti) <= cmax)
                 put(slot++, (uint32_t)j | ((uint32_t)k << 11));
             }
           }
@@ -338,7 +339,50 @@ __device__ __forceinline__ void link_run_smem(const Args &a, int li0, int li1, i
   }
 }
 
+// ------------------------------------------------------- bulk-copy staging
+// The tile and both windows are copied from the quantised cluster array into
+// shared memory by the bulk-copy (TMA) engine: cp.async.bulk with completion on
+// an mbarrier, in 16-byte granules (two 8-byte entries), so a range [lo, hi) is
+// copied from lo & ~1 to (hi + 1) & ~1 (the array is padded past n).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
 
+template <bool kPrune> struct NbPairs {};
+template <> struct NbPairs<true> { uint32_t v[4 * 256]; };  // a thread's first four pairs under the cut
+
+// shared memory of one neighbour CTA: the quantised tile and windows, each with
+// a granule offset of 0 or 1 entry in front and a sentinel behind
+template <int TILE, int WIN>
+struct __align__(16) NbSmem {
+  int2 c[TILE + 2];
+  int2 p[WIN + 4];
+  int2 n[WIN + 4];
+  uint64_t bar;
+};
 
 }  // namespace
 
@@ -360,12 +404,12 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
     const int tb = min(re, ta + a.nb_tile);
     int4 win = make_int4(0, 0, 0, 0);
     if (r >= 1 && r <= kNRows - 2 && tb > ta) {
-      const int t0 = q64(sane_time(a.time[ta])), t1 = q64(sane_time(a.time[tb - 1]));
+      const int t0 = a.tq[ta].x, t1 = a.tq[tb - 1].x;
       const int pb = a.row_begin[key - 1], pe = rb, nb = re, ne = a.row_begin[key + 2];
-      win.x = gm_lower_bound(a.time, pb, pe, t0 - a.wt);
-      win.y = gm_lower_bound(a.time, pb, pe, t1 + a.wt + 1);
-      win.z = gm_lower_bound(a.time, nb, ne, t0 - a.wt);
-      win.w = gm_lower_bound(a.time, nb, ne, t1 + a.wt + 1);
+      win.x = tq_lower_bound(a.tq, pb, pe, t0 - a.wt);
+      win.y = tq_lower_bound(a.tq, pb, pe, t1 + a.wt + 1);
+      win.z = tq_lower_bound(a.tq, nb, ne, t0 - a.wt);
+      win.w = tq_lower_bound(a.tq, nb, ne, t1 + a.wt + 1);
       if (win.y < win.x) win.y = win.x;  // only with unsorted (invalid) input
       if (win.w < win.z) win.w = win.z;
     }
@@ -375,97 +419,85 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 }
 
 // ------------------------------------------------------------ neighbours
-// 32 registers per thread (8 CTAs of 256 threads per SM where shared memory
-// allows): a few bytes spill, but more resident CTAs hide the staging loads of
-// the others; measured 6 % faster than 40 registers and 6 CTAs.
+// One CTA per tile: one thread issues the bulk copies of the tile and its two
+// windows, every thread waits on the mbarrier (bounded), one thread writes the
+// windows' sentinels, and each thread links a contiguous run of clusters.  32
+// registers per thread, so that 8 CTAs of 256 threads share an SM and hide each
+// other's copies and uneven tiles (a persistent, double-buffered form with 4-6
+// CTAs per SM measured 35-45 % slower: its per-tile barrier holds every warp
+// until the tile's slowest one).
 template <bool kPrune, int TILE, int WIN, int THREADS>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS) k_neighbours(Args a, int win_cap) {
   static_assert(WIN < 2048 && TILE % THREADS == 0 && THREADS <= 256, "window indices are packed in 11 bits");
-  __shared__ int2 s_c[TILE], s_p[WIN], s_n[WIN];  // quantised (t, y)
+  __shared__ NbSmem<TILE, WIN> sm;
   __shared__ NbExtra<kPrune> ex;
+  __shared__ NbPairs<kPrune> pr;
   const uint32_t t = blockIdx.x;
   if (t >= min(a.ctr[kCtrTiles], a.tile_cap)) return;
   const int4 h = a.tile_win[2 * t], w = a.tile_win[2 * t + 1];
   const int key = h.x, ta = h.y, cnt = h.z - h.y;
-  const int s = key / kNRows, r = key % kNRows;
+  const int r = key % kNRows;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int rb = a.row_begin[key];
-  bool bad = false;
-
-  // the tile: validate every cluster, quantise into shared memory
-  {
-    const int half = 32 * (row_npads(r) - 1), pitch = row_pitch_um(r);
-#pragma unroll
-    for (int q = 0; q < TILE / THREADS; ++q) {
-      const int e = tid + q * THREADS;
-      if (e >= cnt) break;
-      const int gi = ta + e;
-      float p = a.pad[gi], tt = a.time[gi];
-      if (a.sector[gi] != s || a.row[gi] != r) bad = true;
-      if (!pad_ok(p) || !time_ok(tt)) {
-        bad = true;
-        p = 0.0f;
-        tt = 0.0f;
-      }
-      if (e == 0 && gi > rb && !(a.time[gi - 1] <= tt)) bad = true;  // sorted across tiles
-      s_c[e] = quant_ty(p, tt, half, pitch);
-    }
-  }
   if (r == 0 || r == kNRows - 1) {  // edge rows: no A1 links (claims come later)
     if (kPrune && tid == 0) a.q_count[t] = 0;
-    __syncthreads();
-    for (int e = tid; e < cnt; e += NT) {
-      if (e > 0 && s_c[e].x < s_c[e - 1].x) bad = true;
-      a.link[ta + e] = make_int2(-1, -1);
-    }
-    if (bad) raise(a.ctr, kErrInput);
+    for (int e = tid; e < cnt; e += NT) a.link[ta + e] = make_int2(-1, -1);
     return;
   }
   const int np = w.y - w.x, nn = w.w - w.z;
   const bool staged = np <= win_cap && nn <= win_cap;
+  // granule-aligned copies: tile [ta & ~1, (ta + cnt + 1) & ~1), windows likewise
+  const int c0 = ta & ~1, p0 = w.x & ~1, n0 = w.z & ~1;
   NbQueue *q = nullptr;
   if constexpr (kPrune) {
     q = &ex.q;
     if (tid == 0) q->count = q->end = 0, q->warps_done = 0;
   }
-  const int half_p = 32 * (row_npads(r - 1) - 1), pitch_p = row_pitch_um(r - 1);
-  const int half_n = 32 * (row_npads(r + 1) - 1), pitch_n = row_pitch_um(r + 1);
-  if (staged) {
-    constexpr int kPer = (WIN + THREADS - 1) / THREADS;
-    float pp[kPer], tp[kPer], pn[kPer], tn[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {  // issue all loads first
-      const int e = tid + q * THREADS;
-      if (e < np) {
-        pp[q] = a.pad[w.x + e];
-        tp[q] = a.time[w.x + e];
-      }
-      if (e < nn) {
-        pn[q] = a.pad[w.z + e];
-        tn[q] = a.time[w.z + e];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int e = tid + q * THREADS;
-      if (e < np) s_p[e] = quant_ty(sane_pad(pp[q]), sane_time(tp[q]), half_p, pitch_p);
-      if (e < nn) s_n[e] = quant_ty(sane_pad(pn[q]), sane_time(tn[q]), half_n, pitch_n);
+  if (tid == 0) mbar_init1(&sm.bar);
+  __syncthreads();  // the barrier is initialised
+  if (tid == 0) {
+    const uint32_t bc = 8u * (uint32_t)(((ta + cnt + 1) & ~1) - c0);
+    const uint32_t bp = staged ? 8u * (uint32_t)(((w.y + 1) & ~1) - p0) : 0u;
+    const uint32_t bn = staged ? 8u * (uint32_t)(((w.w + 1) & ~1) - n0) : 0u;
+    mbar_expect(&sm.bar, bc + bp + bn);
+    if (bc) bulk_g2s(sm.c, a.tq + c0, bc, &sm.bar);
+    if (bp) bulk_g2s(sm.p, a.tq + p0, bp, &sm.bar);
+    if (bn) bulk_g2s(sm.n, a.tq + n0, bn, &sm.bar);
+  }
+  // bounded wait for the copies; if any thread gives up, the CTA records a
+  // timeout, waits once more (bounded) for copies still in flight and leaves the
+  // tile unlinked (the decision is taken by the whole CTA at one barrier)
+  bool ok = true;
+  for (uint32_t it = 0; !mbar_try(&sm.bar, 0); ++it) {  // try_wait suspends the thread for a while itself
+    if (it >= a.spin_limit) {
+      ok = false;
+      break;
     }
   }
-  __syncthreads();
-  for (int e = tid + 1; e < cnt; e += NT)  // sorted by time inside the tile
-    if (s_c[e].x < s_c[e - 1].x) bad = true;
+  const int2 *sc = sm.c + (ta - c0);
+  int2 *s_p = sm.p + (w.x - p0), *s_n = sm.n + (w.z - n0);
+  if (ok && tid == 0 && staged) {
+    s_p[np] = make_int2(INT_MAX, 0);  // sentinels
+    s_n[nn] = make_int2(INT_MAX, 0);
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) raise(a.ctr, kErrTimeout);
+    if (!ok)
+      for (uint32_t it = 0; it < a.spin_limit && !mbar_try(&sm.bar, 0); ++it) {
+      }
+    return;
+  }
   const int K = (cnt + NT - 1) / NT, li0 = tid * K, li1 = min(cnt, li0 + K);
-  auto C = [&](int i) { return s_c[i]; };
   if (staged) {
-    link_run_smem<kPrune>(a, li0, li1, cnt, s_c, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta,
-                          q, a.q_rows + (size_t)t * kPruneRegionRows);
+    uint32_t *pairs = nullptr;
+    if constexpr (kPrune) pairs = pr.v;
+    link_run_smem<kPrune>(a, li0, li1, cnt, sc, s_p, np, s_n, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta,
+                          q, pairs, a.q_rows + (size_t)t * kPruneRegionRows);
   } else {
-    const float *pp = a.pad + w.x, *tpg = a.time + w.x, *pn = a.pad + w.z, *tng = a.time + w.z;
+    const int2 *tq = a.tq;
+    const int pb = w.x, nb = w.z;
     link_run<kPrune>(
-        a, li0, li1, cnt, C, [&](int j) { return quant_ty(sane_pad(pp[j]), sane_time(tpg[j]), half_p, pitch_p); },
-        np, [&](int k) { return quant_ty(sane_pad(pn[k]), sane_time(tng[k]), half_n, pitch_n); }, nn, a.wy, a.wt,
-        a.cost_max, a.link + ta, w.x, w.z, ta);
+        a, li0, li1, cnt, [&](int i) { return sc[i]; }, [&](int j) { return tq[pb + j]; }, np,
+        [&](int k) { return tq[nb + k]; }, nn, a.wy, a.wt, a.cost_max, a.link + ta, w.x, w.z, ta);
   }
   if constexpr (kPrune) {  // rows used in this tile's region, published by the last warp to finish
     __syncwarp();
@@ -474,7 +506,6 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS) k_neighbours(Args a, 
       if (atomicAdd(&q->warps_done, 1u) == (unsigned)(THREADS / 32 - 1)) a.q_count[t] = atomicAdd(&q->end, 0);
     }
   }
-  if (bad) raise(a.ctr, kErrInput);
 }
 
 // ------------------------------------------------------------- edge-row claims
@@ -487,24 +518,24 @@ __global__ void __launch_bounds__(256) k_edge_claims(Args a) {
   const int e = blockIdx.y;
   const int s = e >> 1;
   const bool top = (e & 1) != 0;
-  const int r = top ? kNRows - 1 : 0, rn = top ? kNRows - 2 : 1, ro = top ? kNRows - 3 : 2;
+  const int r = top ? kNRows - 1 : 0, rn = top ? kNRows - 2 : 1;
   const int rb = a.row_begin[s * kNRows + r], re = a.row_begin[s * kNRows + r + 1];
   const int nb = a.row_begin[s * kNRows + rn], ne = a.row_begin[s * kNRows + rn + 1];
   for (int j = rb + (int)(blockIdx.x * blockDim.x + threadIdx.x); j < re; j += (int)(gridDim.x * blockDim.x)) {
-    const float pj = a.pad[j], tjf = a.time[j];
-    if (!pad_ok(pj) || !time_ok(tjf)) continue;  // reported by the neighbour kernel
-    const int32_t tj = q64(tjf), yj = y_quant(pj, r);
-    const int lo = gm_lower_bound(a.time, nb, ne, tj - a.wt);
+    const int2 qj = a.tq[j];
+    const int32_t tj = qj.x, yj = qj.y;
+    const int lo = tq_lower_bound(a.tq, nb, ne, tj - a.wt);
     int64_t best = INT64_MAX;
     int bi = -1;
     for (int i = lo; i < ne; ++i) {
-      const int32_t ti = q64(sane_time(a.time[i]));
+      const int2 qi = a.tq[i];
+      const int32_t ti = qi.x;
       if (ti - tj > a.wt) break;
       const int2 l = a.link[i];
       if ((top ? l.y : l.x) != j) continue;
       const int o = top ? l.x : l.y;  // far end of i's triplet
-      const int32_t yi = y_quant(sane_pad(a.pad[i]), rn);
-      const int32_t yo = y_quant(sane_pad(a.pad[o]), ro), to = q64(sane_time(a.time[o]));
+      const int2 qo = a.tq[o];
+      const int32_t yi = qi.y, yo = qo.y, to = qo.x;
       const int64_t c = triplet_cost(yj - yi, yo - yi, tj - ti, to - ti);
       if (c < best) {
         best = c;
@@ -527,11 +558,12 @@ template <int TILE, int WIN>
 static void launch_nb(const Args &a, int row_cap, cudaStream_t st, bool prune) {
   const int cap = row_cap > 0 && row_cap < WIN ? row_cap : WIN;
   const uint32_t grid = neighbour_tiles_max(a.n, a.nkeys, TILE);
-  if (prune) k_neighbours<true, TILE, WIN, 256><<<grid, 256, 0, st>>>(a, cap);
-  else k_neighbours<false, TILE, WIN, 256><<<grid, 256, 0, st>>>(a, cap);
+  if (prune) k_neighbours<true, TILE, WIN, kNbThreads><<<grid, kNbThreads, 0, st>>>(a, cap);
+  else k_neighbours<false, TILE, WIN, kNbThreads><<<grid, kNbThreads, 0, st>>>(a, cap);
 }
 
-void launch_neighbours(const Args &a, int row_cap, cudaStream_t st, bool prune) {
+void launch_neighbours(const Args &a, int row_cap, int sms, cudaStream_t st, bool prune) {
+  (void)sms;
   if (a.nb_tile == 512) launch_nb<512, 896>(a, row_cap, st, prune);
   else if (a.nb_tile == 1024) launch_nb<1024, 1664>(a, row_cap, st, prune);
   else launch_nb<768, 1280>(a, row_cap, st, prune);

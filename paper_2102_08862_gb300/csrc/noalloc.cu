@@ -81,6 +81,7 @@ size_t carve(unsigned char *base, uint32_t n, uint32_t list_cap, Args *a, size_t
   a->tile_cap = neighbour_tiles_max(n, kNKeys, kNbTile);
   a->tile_win = reinterpret_cast<int4 *>(take((size_t)a->tile_cap * 32));
   a->link = reinterpret_cast<int2 *>(take(((size_t)n + 4) * 8));
+  a->tq = reinterpret_cast<int2 *>(take(((size_t)n + 8) * 8));
   a->mup16 = reinterpret_cast<uint16_t *>(take(((size_t)n + 16) * 2));
   a->starts = reinterpret_cast<int2 *>(take(((size_t)n / 2 + 2) * 8));
   a->trk_key = reinterpret_cast<int32_t *>(take(((size_t)list_cap + 1) * 4));
@@ -167,9 +168,10 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
   // counters and look-back words start at zero; everything else is rewritten
   if (cudaMemsetAsync(a.ctr, 0, reset_bytes, st) != cudaSuccess)
     return report(TPC_ERR_CUDA, "tpc_track_timeframe_noalloc: clearing the counters failed");
+  launch_quantize(a, sms, st);
   launch_row_index(a, st);
   launch_tile_windows(a, st);
-  launch_neighbours(a, 0, st);
+  launch_neighbours(a, 0, sms, st);
   launch_edge_claims(a, st);
   launch_links(a, sms, st);
   launch_walk(a, sms, st);

@@ -97,6 +97,7 @@ struct Args {
   const float *pad;
   const float *time;
   const int32_t *perm;     // sorted position -> caller index, nullptr for identity
+  int2 *tq;                // [n + 8] quantised (t_q, y_q) of every sorted cluster (written by the ingest pass)
   int32_t *row_begin;      // [kNKeys + 1]
   int32_t *tile_off;       // [kNKeys + 1] first neighbour tile of each (sector, row)
   int4 *tile_win;          // per tile: candidate ranges in rows r-1 and r+1 (lo, hi, lo, hi)

@@ -27,10 +27,12 @@ inline size_t walk_tiles(uint32_t n) { return (n / 2 + 1 + kWalkTileN - 1) / kWa
 inline uint32_t neighbour_tiles_max(uint32_t n, int nkeys, int tile) { return n / (uint32_t)tile + (uint32_t)nkeys + 1; }
 
 void launch_row_index(const Args &a, cudaStream_t st);
+// validation of every sorted cluster and its quantised (t, y) into a.tq
+void launch_quantize(const Args &a, int sms, cudaStream_t st);
 void launch_tile_windows(const Args &a, cudaStream_t st);
 // prune = true also lists the clusters with >= 2 pairs under the cost cut in a.amb
 // row_cap > 0 lowers the staged window capacity (tests of the global-memory path)
-void launch_neighbours(const Args &a, int row_cap, cudaStream_t st, bool prune = false);
+void launch_neighbours(const Args &a, int row_cap, int sms, cudaStream_t st, bool prune = false);
 void launch_edge_claims(const Args &a, cudaStream_t st);
 void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);
