@@ -337,9 +337,16 @@ def init_dist(world, local):
 
 
 def run_batched(args, rank, world):
+    out = batched_line(args, rank, world)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def batched_line(args, rank, world):
     """c4: 256 sector x time-frame instances of uneven size (log-uniform 1e4-2e6
     clusters, 0.2-10 ms) in one batched call, replayed from a CUDA graph, with the
-    neighbour tile and fit kernel chosen by the autotuner on the batch itself."""
+    neighbour tile and fit kernel chosen by the autotuner on the batch itself.
+    Returns the JSON line's dict on rank 0 (None elsewhere)."""
     import torch
     import tpcsynth as ts
     from paper_2102_08862_gb300 import _build, tpcca
@@ -379,10 +386,10 @@ def run_batched(args, rank, world):
         res[name] = dict(ms=ms, tile=tile, fit=["thread", "warp"][fit], launches=tr.launches_per_call(),
                          n_tracks=int(tr._out["n_tracks"].item()), clocks=clocks)
         tr.close()
-    if dist:
+    if dist and not getattr(args, "keep_dist", False):
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     P, Q = res["pruned"], res["plain"]
     sizes = np.diff(b.offsets)
     out = {"metric": METRIC, "value": n_all / (P["ms"] * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -397,13 +404,20 @@ def run_batched(args, rank, world):
            "clocks": P["clocks"].summary(),
            "plain": {"value": n_all / (Q["ms"] * 1e-3), "ms_per_step": Q["ms"], "n_tracks": Q["n_tracks"],
                      "autotuned": {"nb_tile": Q["tile"], "fit": Q["fit"]}}}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_serving(args, rank, world):
+    out = serving_line(args, rank, world)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def serving_line(args, rank, world):
     """c5: time frames of 2-12 ms arriving Poisson at 80 % of the measured capacity,
     served by the library's runtime (slots admitted by free HBM within 180 GiB,
-    state device-resident, learned-pruned CA); p50/p99 latency and clusters/s."""
+    state device-resident, learned-pruned CA); p50/p99 latency and clusters/s.
+    Returns the JSON line's dict on rank 0 (None elsewhere)."""
     import torch
     import tpcsynth as ts
     from paper_2102_08862_gb300 import _build, tpcca
@@ -469,10 +483,10 @@ def run_serving(args, rank, world):
     srv.close()
     span = max(r["t_done"] for r in done) - min(r["t_submit"] for r in done)
     span_all, clusters_all = job_totals(dist, span, clusters, torch.device("cuda", dev))
-    if dist:
+    if dist and not getattr(args, "keep_dist", False):
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     lat = np.array([r["t_done"] - r["t_submit"] for r in done]) * 1e3
     queue = np.array([r["t_start"] - r["t_submit"] for r in done]) * 1e3
     out = {"metric": METRIC, "value": clusters_all / span_all, "unit": UNIT, "n_gpus": world, "steps": n_req,
@@ -490,7 +504,7 @@ def run_serving(args, rank, world):
            "arrival_rate_per_s": lam, "slots": st["slots"], "slot_bytes": st["bytes"],
            "e2e": {"value": clusters_all / span_all, "unit": UNIT, "h2d_bytes_per_step": int(12 * clusters / n_req),
                    "d2h_bytes_per_step": int(4 * clusters / n_req)}}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -516,6 +530,8 @@ def main():
     ap.add_argument("--follow", action="store_true",
                     help="track following and joining on in every arm (profiler captures of its kernels); "
                          "without it the default run times the headline arm with following as an extra line")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batched (c4) and serving (c5) summaries that the default one-GPU c3 run appends")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the warm-up and timed tracking calls (for profiler captures); prints ms/step")
     args = ap.parse_args()
@@ -662,22 +678,25 @@ def main():
             tr.close()
     head = arms[0]
     H = res[head]
-    # the headline arm with track following and joining (an extra line, not the headline)
-    follow_line = None
+    # every arm with track following, joining and sector links (extra lines, not the headline)
+    follow_lines = {}
     if not args.follow:
-        fol = make(head, follow=2)
-        fol_tracks = checked_call(fol)
-        fol_total, fol_per, _ = timed(fol, args.steps, False)
-        fol_q = quality(fol)
-        fol_links = int((fol._out["next_track"][:fol_tracks] >= 0).sum().item())
-        fol.close()
-        fol_stage, _, _ = stages(head, follow=2)
-        follow_line = {"mode": head + " + follow, joins and sector links", "sector_links": fol_links,
-                       "value": n_all * args.steps / (fol_total * 1e-3),
-                       "ms_per_step": fol_total / args.steps, "step_ms_median": statistics.median(fol_per),
-                       "n_tracks": fol_tracks, "quality": fol_q,
-                       "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit", "relabel",
-                                                              "sector_links") if k in fol_stage}}
+        for name in arms:
+            fol = make(name, follow=2)
+            fol_tracks = checked_call(fol)
+            fol_total, fol_per, _ = timed(fol, args.steps, False)
+            fol_q = quality(fol)
+            fol_links = int((fol._out["next_track"][:fol_tracks] >= 0).sum().item())
+            fol.close()
+            fol_stage, _, _ = stages(name, follow=2)
+            follow_lines[name] = {
+                "mode": name + " + follow, joins and sector links", "sector_links": fol_links,
+                "value": n_all * args.steps / (fol_total * 1e-3),
+                "ms_per_step": fol_total / args.steps, "step_ms_median": statistics.median(fol_per),
+                "n_tracks": fol_tracks, "quality": fol_q,
+                "stage_ms": {k: fol_stage[k] for k in ("walk", "fit", "follow", "refit", "relabel", "sector_links")
+                             if k in fol_stage}}
+    follow_line = follow_lines.get(head)
     total_ms, per = H["total_ms"], H["per"]
     value = n_all * args.steps / (total_ms * 1e-3)
     n_tracks = H["n_tracks"]
@@ -812,7 +831,18 @@ def main():
         R = res[name]
         out[name] = {"value": n_all * args.steps / (R["total_ms"] * 1e-3), "ms_per_step": R["total_ms"] / args.steps,
                      "step_ms_median": statistics.median(R["per"]), "n_tracks": R["n_tracks"],
-                     "quality": R["quality"]}
+                     "quality": R["quality"], "follow": follow_lines.get(name)}
+    # the batched (c4) and serving (c5) workloads of the same run, one GPU: summaries
+    if args.extras and world == 1 and args.workload == "c3" and not args.follow:
+        del sec, row, pad, tim
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**{**vars(args), "steps": min(args.steps, 10), "warmup": 3})
+        b = batched_line(sub, rank, world)
+        out["c4"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "n_tracks", "plain", "config")}
+        torch.cuda.empty_cache()
+        c5 = serving_line(argparse.Namespace(**{**vars(args), "steps": 300}), rank, world)
+        out["c5"] = {k: c5[k] for k in ("value", "unit", "latency_ms", "capacity", "arrival_rate_per_s", "steps",
+                                        "slots", "config")}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -1,7 +1,10 @@
 """The serving runtime (tpc_server_*) on the GPU: frames of differing length
 submitted together run concurrently on several slots, and every result is the
-same as the frame tracked alone through the library's direct entry point.  Also
-the memory budget (it limits the slots) and a request no budget can hold."""
+same as the frame tracked alone through the library's direct entry point and as
+the CPU oracle's assignment (exactly in plain mode; in pruned mode outside the
+tracks touched by a classifier score within 1e-3 of tau, where FP32 and FP64 may
+decide differently).  Also the memory budget (it limits the slots) and a request
+no budget can hold."""
 import json
 import os
 import time
@@ -9,6 +12,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle as orc
 import tpcsynth as ts
 from gpu_util import run_gpu
 
@@ -78,6 +82,29 @@ def test_results_equal_alone_and_in_the_mix(env, frames, mode):
             ct, nt = got[rid]
             assert nt == alone[k][1]
             assert np.array_equal(ct, alone[k][0])
+        # every served frame against the oracle
+        for k, f in enumerate(frames):
+            ct = next(got[rid][0] for rid, kk in ids.items() if kk == k)
+            if mode == "plain":
+                ref = orc.track(f.sector, f.row, f.pad, f.time)
+                assert np.array_equal(ct, ref["cluster_track"]), k
+            else:
+                ref = orc.track(f.sector, f.row, f.pad, f.time, mlp=kw["blob"], tau=tau)
+                rct = ref["cluster_track"]
+                band = ref["order"][np.nonzero(ref["band"])[0]]  # caller indices near the threshold
+                excl = np.zeros(f.n, bool)
+                for ids_ in (rct, ct):  # tracks that hold a band cluster, on either side
+                    hit = np.unique(ids_[band][ids_[band] >= 0])
+                    excl |= np.isin(ids_, hit)
+                assert excl.mean() < 0.02, (k, excl.mean())
+                if band.size == 0:
+                    assert np.array_equal(ct, rct), k
+                    continue
+                # elsewhere the same partition into tracks (ids may shift by the tracks that differ)
+                g, o = ct[~excl], rct[~excl]
+                assert np.array_equal(g < 0, o < 0), k
+                pairs = np.unique(np.stack([g[g >= 0], o[o >= 0]]), axis=1)
+                assert np.unique(pairs[0]).size == pairs.shape[1] == np.unique(pairs[1]).size, k
         st = srv.stats()
         assert 2 <= st["slots"] <= 3 and st["queued"] == 0
     finally:
