@@ -34,17 +34,19 @@ sys.path.insert(0, ROOT)
 METRIC = "TPC clusters tracked/s on a 10 ms TF, learned-pruned vs plain CA at equal efficiency"
 UNIT = "clusters/s"
 # algorithmic bytes per cluster of each stage (read once + written once)
-ALG_BYTES = {"neighbours": 20.0, "links": 12.0}  # fit: 16 B per cluster in a track
+# neighbours: 8 B of quantised (t, y) in + 8 B of links out; ingest: 12 B of cluster fields in + 8 B of
+# quantised (t, y) out (its validation-and-quantisation pass; the row index and tile windows are ~0)
+ALG_BYTES = {"neighbours": 16.0, "links": 12.0, "ingest": 20.0}  # fit: 16 B per cluster in a track
 STAGED_BYTES_PER_CLUSTER = 48.0
 IO_FLOOR_BYTES_PER_CLUSTER = 16.0  # 12 B of cluster fields in, 4 B of cluster_track out
 NOMINAL_HBM_GBS = 8000.0
 FIT_FLOP_PER_CLUSTER = 200.0  # transport + 2-D update per cluster in a track (algorithmic)
 # DRAM bytes per cluster of k_neighbours from one full ncu capture of the 5 ms frame,
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "4fcf5ccfc435803b1d1aac5ac0fcf5fafcc45df543a695dbfb61726de2f26a85",
-              "pruned": (207.212544e6 + 145.546496e6) / 16765809, "plain": (204.066560e6 + 103.926784e6) / 16765809}
+NB_TRAFFIC = {"sha256": "c370aa988f7203e7d09dc7afe1f1d3befdd79a3e8bee3f59227246e8649e27c6",
+              "pruned": (135.789568e6 + 129.231616e6) / 16765809, "plain": (135.306240e6 + 93.925376e6) / 16765809}
 # warp instructions per cluster of the same captures (smsp__inst_executed.sum / clusters)
-NB_INST = {"pruned": 616386918 / 16765809, "plain": 539628699 / 16765809}
+NB_INST = {"pruned": 426533997 / 16765809, "plain": 366935837 / 16765809}
 
 
 def neighbours_traffic(mode, n):
@@ -370,6 +372,7 @@ def batched_line(args, rank, world):
         cap = n // 10 + 1
         with torch.cuda.stream(stream):
             tile, fit = tr.autotune(sec, row, pad, tim, capacity=cap, trials=3)
+            engine = tr.mlp_engine
             for _ in range(args.warmup):
                 tr.track_graph(sec, row, pad, tim, capacity=cap, stream=stream)
         stream.synchronize()
@@ -383,7 +386,8 @@ def batched_line(args, rank, world):
             stream.synchronize()
         assert tpcca.tpc_tf_status(tr.handle, stream.cuda_stream) == 0, tpcca.tpc_last_error()
         ms, n_all = job_totals(dist, e0.elapsed_time(e1) / args.steps, n, dev)
-        res[name] = dict(ms=ms, tile=tile, fit=["thread", "warp"][fit], launches=tr.launches_per_call(),
+        res[name] = dict(ms=ms, tile=tile, fit=["thread", "warp"][fit], engine=["tcgen05", "mma.sync"][engine],
+                         launches=tr.launches_per_call(),
                          n_tracks=int(tr._out["n_tracks"].item()), clocks=clocks)
         tr.close()
     if dist and not getattr(args, "keep_dist", False):
@@ -399,7 +403,8 @@ def batched_line(args, rank, world):
                                   f"(per instance {int(sizes.min())}-{int(sizes.max())}, median {int(np.median(sizes))}), "
                                   f"frames 0.2-10 ms, seed 4",
                       "mode": f"learned-pruned CA (tau {tau})", "launch": "CUDA graph replay of one batched call",
-                      "autotuned": {"nb_tile": P["tile"], "fit": P["fit"]}, "parallelism": f"replicas x{world}"},
+                      "autotuned": {"nb_tile": P["tile"], "fit": P["fit"], "mlp_engine": P["engine"]},
+                      "parallelism": f"replicas x{world}"},
            "n_tracks": P["n_tracks"], "gpu_launches": P["launches"] * args.steps, "graph_launches": args.steps,
            "clocks": P["clocks"].summary(),
            "plain": {"value": n_all / (Q["ms"] * 1e-3), "ms_per_step": Q["ms"], "n_tracks": Q["n_tracks"],
@@ -527,6 +532,8 @@ def main():
                          "autotuner pick them on the frame (untimed, before the warm-up; reported in config)")
     ap.add_argument("--nb-tile", type=int, default=0, choices=[0, 512, 768, 1024],
                     help="neighbour tile (clusters per CTA) instead of the autotuner's choice; 0 = autotune")
+    ap.add_argument("--mlp-engine", default=None, choices=["tcgen05", "mma.sync"],
+                    help="tensor-core engine of the pruned arm's region rescoring instead of the autotuner's choice")
     ap.add_argument("--follow", action="store_true",
                     help="track following and joining on in every arm (profiler captures of its kernels); "
                          "without it the default run times the headline arm with following as an extra line")
@@ -577,13 +584,15 @@ def main():
             opts["nb_tile"] = args.nb_tile
         if name in tuned:
             opts.update(tuned[name])
+        if args.mlp_engine:
+            opts["mlp_engine"] = {"tcgen05": tpcca.TPC_MMA_TCGEN05, "mma.sync": tpcca.TPC_MMA_SYNC}[args.mlp_engine]
         tr = tpcca.TimeFrameTracker(n, device=local, **opts, **modes[name], **extra)
         if name == "pruned":
             tr.load_mlp(blob)
         if args.autotune and not args.nb_tile and name not in tuned:
             with torch.cuda.stream(stream):
                 tile, fit = tr.autotune(sec, row, pad, tim, capacity=cap, trials=3)
-            tuned[name] = dict(nb_tile=tile, fit_variant=fit)
+            tuned[name] = dict(nb_tile=tile, fit_variant=fit, mlp_engine=tr.mlp_engine)
         return tr
 
     def checked_call(tr):
@@ -704,7 +713,8 @@ def main():
     # stage timing (CUDA events between the stages of a call, on the call's stream)
     stage_ms, in_tracks, rescored = stages(head)
     hbm, peak_kind = peaks()
-    alg = {"neighbours": ALG_BYTES["neighbours"] * n, "links": ALG_BYTES["links"] * n, "fit": 16.0 * in_tracks}
+    alg = {"neighbours": ALG_BYTES["neighbours"] * n, "links": ALG_BYTES["links"] * n, "fit": 16.0 * in_tracks,
+           "ingest": ALG_BYTES["ingest"] * n}
     dom = max(stage_ms, key=stage_ms.get)
     dom_alg = alg.get(dom)
     roof = None

@@ -91,6 +91,9 @@ extern "C" {
 
 #define TPC_INPUT_SORTED 1u /* clusters are sorted by (sector, row, time, pad) */
 
+#define TPC_MMA_TCGEN05 0 /* fifth-generation tensor cores: tcgen05.mma into tensor memory */
+#define TPC_MMA_SYNC 1    /* warp-level mma.sync m16n8k16 tiles in registers */
+
 #define TPC_FIT_THREAD 0 /* one thread per tracklet in the Kalman fit (default, fastest) */
 #define TPC_FIT_WARP 1   /* one warp per tracklet: the lanes load the chain's clusters together and run
                             the same filter in lockstep (identical arithmetic, slower) */
@@ -127,6 +130,10 @@ typedef struct {
   int32_t follow_check;  /* follow: clusters of another track that must pass the gate before a join (4) */
   float follow_link_chi2;  /* follow 2: 5-parameter agreement of two linked tracks (default 80) */
   int32_t follow_link_rows; /* follow 2: rows searched on either side of a sector boundary (default 152) */
+  int32_t mlp_engine;    /* TPC_MODE_PRUNED: tensor-core engine of the region rescoring, TPC_MMA_TCGEN05
+                            (fifth-generation tensor cores, batches of 256 rows) or TPC_MMA_SYNC (warp-level
+                            16-row tiles; the default, faster on the 10 ms frame); both give the same logits
+                            to FP32 rounding; tpc_tf_autotune picks one by timing */
 } tpc_tf_config;
 
 typedef struct {      /* input clusters: device pointers, read only, caller owned */
@@ -221,14 +228,16 @@ int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_clusters *cl
 int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream);
 
 /* The project's autotuner (the paper has no counterpart): times the neighbour
- * tile variants (512, 768, 1024 clusters per tile) and the two fit kernels on
- * calls with `cl` and `out` (one untimed call, then the median of `trials`
- * timed calls per variant), keeps the fastest choice in the handle and returns
- * it in *nb_tile and *fit_variant (either may be NULL).  The results of a call
- * do not depend on the choice.  Synchronises `stream`.  Errors as for
+ * tile variants (512, 768, 1024 clusters per tile), the two fit kernels and, in
+ * TPC_MODE_PRUNED, the two tensor-core engines of the rescoring on calls with
+ * `cl` and `out` (one untimed call, then the median of `trials` timed calls per
+ * variant), keeps the fastest choice in the handle and returns it in *nb_tile,
+ * *fit_variant and *mlp_engine (any may be NULL; *mlp_engine is the handle's
+ * engine in plain mode).  The results of a call do not depend on the choice up to
+ * FP32 rounding of the logits.  Synchronises `stream`.  Errors as for
  * tpc_track_timeframe; TPC_ERR_ARG for trials outside [1, 100]. */
 int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
-                    int32_t *nb_tile, int32_t *fit_variant);
+                    int32_t *nb_tile, int32_t *fit_variant, int32_t *mlp_engine);
 
 /* Hit removal for compression (the consumer of cluster_track in the paper's
  * synchronous chain, Sec. 1): copies the clusters with cluster_track[i] >= 0 to
@@ -337,8 +346,6 @@ int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes);
  * bounded wait that gave up surfaces through tpc_tf_status as TPC_ERR_TIMEOUT. */
 int tpc_mlp_score(tpc_tf *tf, const float *feat, uint32_t m, float *logit, void *stream);
 
-#define TPC_MMA_TCGEN05 0 /* fifth-generation tensor cores: tcgen05.mma into tensor memory */
-#define TPC_MMA_SYNC 1    /* warp-level mma.sync m16n8k16 tiles in registers */
 
 /* tpc_mlp_score with the tensor-core engine chosen (TPC_MMA_TCGEN05 or
  * TPC_MMA_SYNC); both compute the same network and agree to FP32 rounding. */

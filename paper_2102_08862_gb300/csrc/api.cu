@@ -147,6 +147,7 @@ extern "C" void tpc_default_config(tpc_tf_config *c) {
   c->follow_check = 4;
   c->follow_link_chi2 = 80.0f;
   c->follow_link_rows = TPC_NROWS;
+  c->mlp_engine = TPC_MMA_SYNC;
 }
 
 extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
@@ -296,6 +297,8 @@ static int validate_config(const tpc_tf_config *cfg) {
   if (cfg->nb_tile != 0 && !nb_tile_ok(cfg->nb_tile))
     return fail(TPC_ERR_ARG, "tpc_tf_create: nb_tile must be 512, 768 or 1024");
   if (cfg->follow < 0 || cfg->follow > 2) return fail(TPC_ERR_ARG, "tpc_tf_create: follow must be 0, 1 or 2");
+  if (cfg->mlp_engine != TPC_MMA_TCGEN05 && cfg->mlp_engine != TPC_MMA_SYNC)
+    return fail(TPC_ERR_ARG, "tpc_tf_create: mlp_engine must be TPC_MMA_TCGEN05 or TPC_MMA_SYNC");
   if (cfg->follow == 2 && (!(cfg->follow_link_chi2 > 0.0f) || !(cfg->follow_link_chi2 < 1e6f) ||
                            cfg->follow_link_rows < 1 || cfg->follow_link_rows > TPC_NROWS))
     return fail(TPC_ERR_ARG, "tpc_tf_create: follow_link_chi2 must be in (0, 1e6), follow_link_rows in [1, 152]");
@@ -501,7 +504,7 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   stage(tf, st, "neighbours");
   tf->launches += 4;
   if (prune) {
-    launch_prune_tiles(a, tf->mlp, tf->logit_tau, tf->sms, st);
+    launch_prune_tiles(a, tf->mlp, tf->logit_tau, tf->sms, tf->cfg.mlp_engine, st);
     stage(tf, st, "prune_tiles");
     launch_prune(a, tf->mlp, tf->logit_tau, tf->sms, st);
     stage(tf, st, "prune_list");
@@ -967,6 +970,7 @@ extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
   launch_mlp_pack(body + 24, body, body + 12, tf->mlp, 0);
   TPC_CK(cudaGetLastError());
   TPC_CK(cudaDeviceSynchronize());
+  if (prune_tiles_prepare() != 0) return fail(TPC_ERR_CUDA, "tpc_mlp_load: cannot configure the region scorer");
   tf->mlp_ready = true;
   return TPC_OK;
 }
@@ -1072,7 +1076,7 @@ extern "C" int tpc_track_timeframe_graph(tpc_tf *tf, const tpc_clusters *cl, con
 
 // ================================================================ autotuner
 extern "C" int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, int trials, void *stream,
-                               int32_t *nb_tile, int32_t *fit_variant) {
+                               int32_t *nb_tile, int32_t *fit_variant, int32_t *mlp_engine) {
   g_err.clear();
   if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_tf_autotune: null argument");
   if (trials < 1 || trials > 100) return fail(TPC_ERR_ARG, "tpc_tf_autotune: trials must be in [1, 100]");
@@ -1125,11 +1129,22 @@ extern "C" int tpc_tf_autotune(tpc_tf *tf, const tpc_clusters *cl, const tpc_tra
     best_fit = fit_ms[1] < fit_ms[0] ? TPC_FIT_WARP : TPC_FIT_THREAD;
     tf->cfg.fit_variant = best_fit;
   }
+  int best_engine = tf->cfg.mlp_engine;
+  if (rc == TPC_OK && tf->cfg.mode == TPC_MODE_PRUNED) {  // the region scorer's tensor-core engine
+    float eng_ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2 && rc == TPC_OK; ++v) {
+      tf->cfg.mlp_engine = v;
+      rc = time_calls(&eng_ms[v]);
+    }
+    best_engine = eng_ms[TPC_MMA_SYNC] < eng_ms[TPC_MMA_TCGEN05] ? TPC_MMA_SYNC : TPC_MMA_TCGEN05;
+    tf->cfg.mlp_engine = best_engine;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != TPC_OK) return rc;
   if (nb_tile) *nb_tile = best_tile;
   if (fit_variant) *fit_variant = best_fit;
+  if (mlp_engine) *mlp_engine = best_engine;
   return TPC_OK;
 }
 

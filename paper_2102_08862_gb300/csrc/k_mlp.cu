@@ -543,6 +543,213 @@ __device__ __forceinline__ bool tc_mlp_rows(TcMlpSmem &sm, uint32_t tmem, float 
   return __syncthreads_and(ok);
 }
 
+// Rows of the neighbour tiles' regions on the tcgen05 path.  A CTA of 256
+// threads takes 32 consecutive tile regions at a time and packs their rows,
+// region after region, into batches of at most 256 rows (a region holds at most
+// 128 rows and never straddles two batches): thread r computes row r's features
+// into the core-matrix layout; each layer is two M = 128 MMAs (rows 0-127 into
+// tensor-memory columns 0-63, rows 128-255 into columns 64-127) sharing the
+// weights; and the thread holding a cluster's first row picks the smallest
+// passing (cost, j, k) among the cluster's contiguous rows (a cluster's rows all
+// sit in one region).  Regions hold ~17 rows on the 10 ms frame: the batches are
+// short chains of staging, MMA and epilogue, bound by their latency, so a CTA
+// takes 256 rows per step rather than 128.
+constexpr int kTcRegions = 32;  // regions examined per step
+constexpr int kTcRows = 256;    // rows per batch (two M = 128 halves)
+struct __align__(1024) TcPruneSmem {
+  unsigned char x[kTcRows * 16 * 2];   // inputs, core-matrix layout (K 16), half h at h * 4096
+  unsigned char h[kTcRows * 64 * 2];   // first hidden layer (K 64), half h at h * 16384
+  unsigned char w1[64 * 16 * 2];
+  unsigned char w2[64 * 64 * 2];
+  float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
+  int64_t pc[kTcRows];
+  int32_t pi[kTcRows], pj[kTcRows], pk[kTcRows];
+  float lg[kTcRows];
+  int32_t off[kTcRegions + 1];  // region row offsets inside the group (regions with < 2 rows count 0)
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *__restrict__ W, float logit_tau) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  TcPruneSmem &sm = *reinterpret_cast<TcPruneSmem *>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int half = tid >> 7, hr = tid & 127;  // the thread's MMA half and row (= tensor-memory lane) in it
+  for (int e = tid; e < kMlpH * 2; e += blockDim.x) {
+    const int n = e >> 1, g = e & 1;
+    *reinterpret_cast<uint4 *>(sm.w1 + core_offset(n, 8 * g, 16)) =
+        *reinterpret_cast<const uint4 *>(W->w1 + n * kXS + 8 * g);
+  }
+  for (int e = tid; e < kMlpH * 8; e += blockDim.x) {
+    const int n = e >> 3, g = e & 7;
+    *reinterpret_cast<uint4 *>(sm.w2 + core_offset(n, 8 * g, 64)) =
+        *reinterpret_cast<const uint4 *>(W->w2 + n * kW2S + 8 * g);
+  }
+  for (int e = tid; e < kMlpH; e += blockDim.x) {
+    sm.b1[e] = W->b1[e];
+    sm.b2[e] = W->b2[e];
+    sm.w3[e] = W->w3[e];
+  }
+  for (int e = tid; e < kMlpIn; e += blockDim.x) {
+    sm.mean[e] = W->mean[e];
+    sm.inv_std[e] = W->inv_std[e];
+  }
+  if (tid == 0) mbar_init(&sm.mbar, 1);
+  if (warp == 0) tc_alloc(&sm.tmem, 128);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  // warp w reads tensor-memory lanes 32 (w % 4) ..; its half's columns start at 64 * half
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)half;
+  const float b3 = W->b3;
+  const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
+  const uint32_t idesc = tc_idesc_bf16(128, 64);
+  uint32_t clusters = 0, phase = 0;
+  bool ok = true;
+  for (uint32_t g0 = blockIdx.x * kTcRegions; g0 < ntiles && ok; g0 += gridDim.x * kTcRegions) {
+    const int nreg = (int)min((uint32_t)kTcRegions, ntiles - g0);
+    if (tid < 32) {  // row offsets of the group's regions
+      int c = lane < nreg ? min(a.q_count[g0 + lane], kPruneRegionRows) : 0;
+      if (c < 2) c = 0;
+      int x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      sm.off[lane + 1] = x;
+      if (lane == 0) sm.off[0] = 0;
+    }
+    __syncthreads();
+    for (int s = 0; s < nreg && ok;) {
+      int e = s;  // regions [s, e) fill the batch
+      while (e < nreg && sm.off[e + 1] - sm.off[s] <= kTcRows) ++e;
+      const int rows = sm.off[e] - sm.off[s];
+      if (rows > 0) {
+        const bool mine = tid < rows;
+        float f[kMlpIn];
+        if (mine) {
+          const int gr = sm.off[s] + tid;
+          int g = s;
+          while (sm.off[g + 1] <= gr) ++g;
+          const uint32_t tile = g0 + (uint32_t)g;
+          const int4 *pr =
+              reinterpret_cast<const int4 *>(a.q_rows + (size_t)tile * kPruneRegionRows + (gr - sm.off[g]));
+          const int4 q = pr[0], c1 = pr[1], c2 = pr[2];  // (i, j, k, cn), (ti, yi, tj, yj), (tk, yk, -, -)
+          const int r = a.tile_win[2 * tile].x % kNRows;
+          const int64_t c = triplet_cost(c1.w - c1.y, c2.y - c1.y, c1.z - c1.x, c2.x - c1.x);
+          triplet_features(r, c1.w, c1.y, c2.y, c1.z, c1.x, c2.x, c, q.w & 0xffff, (int)((unsigned)q.w >> 16),
+                           a.cost_max, f);
+          sm.pc[tid] = c;
+          sm.pi[tid] = q.x;
+          sm.pj[tid] = q.y;
+          sm.pk[tid] = q.z;
+        }
+        {  // input row (zeros past the batch)
+          __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc)
+            v[cc] = (mine && cc < kMlpIn)
+                        ? __float2bfloat16_rn(__fmul_rn(__fsub_rn(f[cc], sm.mean[cc]), sm.inv_std[cc]))
+                        : __float2bfloat16_rn(0.0f);
+          unsigned char *xb = sm.x + 4096 * half;
+          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 0, 16)) = reinterpret_cast<const uint4 *>(v)[0];
+          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 8, 16)) = reinterpret_cast<const uint4 *>(v)[1];
+        }
+        const bool two = rows > 128;  // second half in use
+        // layer 1
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+          for (int hh = 0; hh < (two ? 2 : 1); ++hh)
+            tc_mma_bf16(tmem + 64u * hh, tc_desc(smem_u32(sm.x) + 4096 * hh, 128, 256),
+                        tc_desc(smem_u32(sm.w1), 128, 256), idesc, false);
+          tc_commit(&sm.mbar);
+        }
+        ok = mbar_wait(&sm.mbar, phase, a.spin_limit);
+        phase ^= 1u;
+        tc_fence_after();
+        float z[16];
+        if (ok && (half == 0 || two)) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            tc_ld16(lane_base + 16 * qq, z);
+            tc_wait_ld();
+            __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) hv[cc] = __float2bfloat16_rn(fmaxf(z[cc] + sm.b1[16 * qq + cc], 0.f));
+            unsigned char *hb = sm.h + 16384 * half;
+            *reinterpret_cast<uint4 *>(hb + core_offset(hr, 16 * qq, 64)) = reinterpret_cast<const uint4 *>(hv)[0];
+            *reinterpret_cast<uint4 *>(hb + core_offset(hr, 16 * qq + 8, 64)) =
+                reinterpret_cast<const uint4 *>(hv)[1];
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
+        tc_fence_after();
+        if (!ok) break;
+        if (tid == 0) {
+          for (int hh = 0; hh < (two ? 2 : 1); ++hh) {
+            const uint32_t h0 = smem_u32(sm.h) + 16384 * hh, w0 = smem_u32(sm.w2);
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4)
+              tc_mma_bf16(tmem + 64u * hh, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024),
+                          idesc, k4 > 0);
+          }
+          tc_commit(&sm.mbar);
+        }
+        ok = mbar_wait(&sm.mbar, phase, a.spin_limit);
+        phase ^= 1u;
+        tc_fence_after();
+        float acc = b3;
+        if (ok && (half == 0 || two)) {
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            tc_ld16(lane_base + 16 * qq, z);
+            tc_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) acc = fmaf(fmaxf(z[cc] + sm.b2[16 * qq + cc], 0.f), sm.w3[16 * qq + cc], acc);
+          }
+        }
+        sm.lg[tid] = acc;
+        tc_fence_before();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        // a cluster's rows are contiguous: the thread holding its first row decides
+        if (mine && (tid == 0 || sm.pi[tid - 1] != sm.pi[tid])) {
+          const int i = sm.pi[tid];
+          ++clusters;
+          int64_t bestc = INT64_MAX;
+          int bj = 0x7fffffff, bk = 0x7fffffff;
+          for (int m = tid; m < rows && sm.pi[m] == i; ++m) {
+            if (!(sm.lg[m] >= logit_tau)) continue;
+            const int qj = sm.pj[m], qk = sm.pk[m];
+            if (sm.pc[m] < bestc || (sm.pc[m] == bestc && (qj < bj || (qj == bj && qk < bk)))) {
+              bestc = sm.pc[m];
+              bj = qj;
+              bk = qk;
+            }
+          }
+          if (bestc != INT64_MAX) a.link[i] = make_int2(bj, bk);
+        }
+        __syncthreads();  // the batch's rows are free again
+      }
+      s = e;
+    }
+    __syncthreads();  // sm.off is rewritten for the next group
+  }
+  if (!ok && tid == 0) raise(a.ctr, kErrTimeout);
+  for (int o = 16; o > 0; o >>= 1) clusters += __shfl_xor_sync(0xffffffffu, clusters, o);
+  if (lane == 0 && clusters) atomicAdd(&a.ctr[kCtrQueued], clusters);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 128);
+}
+
 // logits of raw feature rows (float[m][12]) on the tcgen05 path
 __global__ void __launch_bounds__(128) k_mlp_score_tc(const MlpW *__restrict__ W, const float *__restrict__ feat,
                                                       uint32_t m, float *__restrict__ logit, int *err) {
@@ -687,9 +894,16 @@ __global__ void __launch_bounds__(256) k_mlp_extract(Args a, float *__restrict__
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
-  // 4 CTAs per SM: the register limit (64 per thread), below the shared-memory one
-  k_prune_tiles<<<sms * 4, kPtWarps * 32, 0, st>>>(a, w, logit_tau);
+size_t prune_tiles_tc_smem();
+void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, int engine, cudaStream_t st) {
+  if (engine == TPC_MMA_SYNC) {
+    // 4 CTAs per SM: the register limit (64 per thread), below the shared-memory one
+    k_prune_tiles<<<sms * 4, kPtWarps * 32, 0, st>>>(a, w, logit_tau);
+    return;
+  }
+  // 3 CTAs per SM (65 KB of shared memory each): their 128-column tensor-memory
+  // allocations (384 of the SM's 512 columns) never wait on each other
+  k_prune_tiles_tc<<<sms * 3, kTcRows, prune_tiles_tc_smem(), st>>>(a, w, logit_tau);
 }
 
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
@@ -708,6 +922,15 @@ void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit
 }
 
 size_t mlp_score_tc_smem() { return sizeof(TcMlpSmem) + 1024; }
+size_t prune_tiles_tc_smem() { return sizeof(TcPruneSmem) + 1024; }
+
+// the region scorer's shared memory exceeds the 48 KB a kernel gets without
+// opting in: raised once per device, when the weights are loaded (never during
+// stream capture)
+int prune_tiles_prepare() {
+  return cudaFuncSetAttribute(k_prune_tiles_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)prune_tiles_tc_smem()) == cudaSuccess ? 0 : -1;
+}
 
 int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *logit, int *err, int sms,
                         cudaStream_t st) {

@@ -80,7 +80,9 @@ struct MlpW;
 size_t mlp_weights_bytes();
 // rescoring of the ambiguous clusters' pairs from the neighbour tiles' regions,
 // and of the clusters on the overflow list; rewrite their links
-void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
+void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, int engine, cudaStream_t st);
+// opts the tensor-core region scorer in to its shared memory on the current device (0 on success)
+int prune_tiles_prepare();
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
 // FP32 parameters (blob order) + standardisation -> packed BF16 weights
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);

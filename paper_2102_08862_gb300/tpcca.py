@@ -37,7 +37,8 @@ class tpc_tf_config(ctypes.Structure):
                 ("cost_max_q", c_i64), ("n_min", c_i32), ("mode", c_i32), ("tau", c_f32), ("device", c_i32),
                 ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32), ("n_sectors", c_i32),
                 ("nb_tile", c_i32), ("follow", c_i32), ("follow_chi2", c_f32), ("follow_miss", c_i32),
-                ("follow_check", c_i32), ("follow_link_chi2", c_f32), ("follow_link_rows", c_i32)]
+                ("follow_check", c_i32), ("follow_link_chi2", c_f32), ("follow_link_rows", c_i32),
+                ("mlp_engine", c_i32)]
 
 
 class tpc_clusters(ctypes.Structure):
@@ -137,7 +138,8 @@ def load():
     lib.tpc_server_admit.restype = ctypes.c_int
     lib.tpc_track_timeframe_graph.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), c_vp]
     lib.tpc_track_timeframe_graph.restype = ctypes.c_int
-    lib.tpc_tf_autotune.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), ctypes.c_int, c_vp, P(c_i32), P(c_i32)]
+    lib.tpc_tf_autotune.argtypes = [c_vp, P(tpc_clusters), P(tpc_tracks), ctypes.c_int, c_vp, P(c_i32), P(c_i32),
+                                    P(c_i32)]
     lib.tpc_tf_autotune.restype = ctypes.c_int
     sz = ctypes.c_size_t
     lib.tpc_mlp_blob_bytes.argtypes = []
@@ -256,11 +258,11 @@ def tpc_track_timeframe_graph(handle, clusters: tpc_clusters, tracks: tpc_tracks
 
 
 def tpc_tf_autotune(handle, clusters: tpc_clusters, tracks: tpc_tracks, trials: int = 3, stream: int = 0):
-    """(nb_tile, fit_variant) chosen by the autotuner (kept in the handle)."""
-    t, f = c_i32(0), c_i32(0)
+    """(nb_tile, fit_variant, mlp_engine) chosen by the autotuner (kept in the handle)."""
+    t, f, e = c_i32(0), c_i32(0), c_i32(0)
     _check(load().tpc_tf_autotune(handle, ctypes.byref(clusters), ctypes.byref(tracks), trials, stream,
-                                  ctypes.byref(t), ctypes.byref(f)))
-    return int(t.value), int(f.value)
+                                  ctypes.byref(t), ctypes.byref(f), ctypes.byref(e)))
+    return int(t.value), int(f.value), int(e.value)
 
 
 def tpc_tf_arena_bytes(cfg: tpc_tf_config) -> int:
@@ -655,8 +657,12 @@ class TimeFrameTracker:
         return res
 
     def autotune(self, sector, row, pad, time, sorted_input=True, capacity=None, trials=3):
+        """(nb_tile, fit_variant) chosen by the library's autotuner; the tensor-core engine
+        of the rescoring (pruned mode) is kept in self.mlp_engine."""
         cl, tr, n, cap = self.structs(sector, row, pad, time, sorted_input, capacity, host_count=None)
-        return tpc_tf_autotune(self.handle, cl, tr, trials, self.torch.cuda.current_stream(self.device).cuda_stream)
+        tile, fit, self.mlp_engine = tpc_tf_autotune(self.handle, cl, tr, trials,
+                                                     self.torch.cuda.current_stream(self.device).cuda_stream)
+        return tile, fit
 
     def debug_links(self, stream=None):
         t = self.torch

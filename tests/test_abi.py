@@ -40,7 +40,8 @@ int main(void) {
   printf("tpc_tf_config %zu\ntpc_clusters %zu\ntpc_tracks %zu\n", sizeof(tpc_tf_config), sizeof(tpc_clusters),
          sizeof(tpc_tracks));
   F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap); F(tpc_tf_config, follow_chi2);
-  F(tpc_tf_config, follow_check); F(tpc_tf_config, follow_link_rows); F(tpc_tracks, next_track);
+  F(tpc_tf_config, follow_check); F(tpc_tf_config, follow_link_rows); F(tpc_tf_config, mlp_engine);
+  F(tpc_tracks, next_track);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
   printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
   F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device);

@@ -162,10 +162,11 @@ def _pruned_gpu(tpcca, dev, f, blob, tau, **kw):
     return g
 
 
-@pytest.mark.parametrize("row_cap", [0, 16])
-def test_pruned_c1_full_parity(env, c1, row_cap):
-    """row_cap 0: windows staged, rescoring inside the neighbour kernel; row_cap 16:
-    windows read from global memory, rescoring by the separate kernel."""
+@pytest.mark.parametrize("row_cap,engine", [(0, 0), (0, 1), (16, 0)])
+def test_pruned_c1_full_parity(env, c1, row_cap, engine):
+    """row_cap 0: windows staged, the pairs rescored from the tiles' regions (engine
+    0: tcgen05 batches of 128 rows, 1: mma.sync tiles of 16); row_cap 16: windows
+    read from global memory, rescoring by the separate list kernel."""
     tpcca, dev = env
     blob = _net()
     feat, _, _ = orc.training_triplets(c1.sector, c1.row, c1.pad, c1.time)
@@ -173,7 +174,7 @@ def test_pruned_c1_full_parity(env, c1, row_cap):
     o = orc.track(c1.sector, c1.row, c1.pad, c1.time, mlp=blob, tau=tau)
     assert not o["band"].any()
     assert o["stats"][2] > 0, "the classifier changes some choices"
-    g = _pruned_gpu(tpcca, dev, c1, blob, tau, row_cap=row_cap)
+    g = _pruned_gpu(tpcca, dev, c1, blob, tau, row_cap=row_cap, mlp_engine=engine)
     assert g["n_pruned"] == o["stats"][0]
     compare_links(g, o)
     compare_tracks(g, o)
@@ -189,13 +190,14 @@ def test_pruned_extremes_equal_plain(env, c1, tau):
     compare_tracks(g, plain)
 
 
-def test_pruned_links_outside_band_two_sectors(env, two_sectors):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_pruned_links_outside_band_two_sectors(env, two_sectors, engine):
     tpcca, dev = env
     f = two_sectors
     blob = _net(5)
     tau = 0.5
     o = orc.track(f.sector, f.row, f.pad, f.time, mlp=blob, tau=tau)
-    g = _pruned_gpu(tpcca, dev, f, blob, tau)
+    g = _pruned_gpu(tpcca, dev, f, blob, tau, mlp_engine=engine)
     assert o["stats"][0] > 1000 and o["stats"][2] > 50
     assert g["n_pruned"] == o["stats"][0]
     assert np.array_equal(g["order"], o["order"])
@@ -236,6 +238,20 @@ def test_gradient_matches_fp64_oracle(env, two_sectors):
         a, b = grad_g[off:off + k], grad_o[off:off + k]
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
         assert rel <= 2e-2, f"{name}: relative gradient error {rel:.3g}"
+        # element by element: BF16 operands (inputs, weights, the first hidden layer
+        # and the back-propagated errors, each 2^-8 relative) move an entry by a few
+        # BF16 steps of the terms it sums, which cancel more in small entries: the
+        # bound is a floor of 2^-4 of the group's RMS plus 2^-4 of the entry itself
+        # (the largest entry seen on this batch reached about half of it); a wrong
+        # entry (another row's or column's sum, a dropped term) exceeds it
+        floor = 2.0 ** -4 * np.sqrt(np.mean(b * b)) + 1e-12
+        excess = np.abs(a - b) / (floor + 2.0 ** -4 * np.abs(b))
+        assert excess.max() <= 1.0, f"{name}: entry {int(excess.argmax())} off by {excess.max():.3g} of its bound"
+        if k > 1:  # a planted mistake in the oracle's copy (two entries swapped) breaks the bound
+            w = b.copy()
+            i0, i1 = int(np.argmax(np.abs(b))), int(np.argmin(np.abs(b)))
+            w[[i0, i1]] = w[[i1, i0]]
+            assert (np.abs(a - w) / (floor + 2.0 ** -4 * np.abs(w))).max() > 1.0, name
         off += k
 
 
