@@ -422,12 +422,14 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 // One CTA per tile: one thread issues the bulk copies of the tile and its two
 // windows, every thread waits on the mbarrier (bounded), one thread writes the
 // windows' sentinels, and each thread links a contiguous run of clusters.  32
-// registers per thread, so that 8 CTAs of 256 threads share an SM and hide each
-// other's copies and uneven tiles (a persistent, double-buffered form with 4-6
-// CTAs per SM measured 35-45 % slower: its per-tile barrier holds every warp
-// until the tile's slowest one).
+// registers per thread in plain mode, so that 8 CTAs of 256 threads share an SM
+// and hide each other's copies and uneven tiles; 40 in pruned mode (6 CTAs),
+// where the region bookkeeping spills at 32 (a persistent, double-buffered form
+// with 4-6 CTAs per SM measured 35-45 % slower: its per-tile barrier holds every
+// warp until the tile's slowest one).
 template <bool kPrune, int TILE, int WIN, int THREADS>
-__global__ void __launch_bounds__(THREADS, 2048 / THREADS) k_neighbours(Args a, int win_cap) {
+__global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THREADS)
+    k_neighbours(Args a, int win_cap) {
   static_assert(WIN < 2048 && TILE % THREADS == 0 && THREADS <= 256, "window indices are packed in 11 bits");
   __shared__ NbSmem<TILE, WIN> sm;
   __shared__ NbExtra<kPrune> ex;
