@@ -134,6 +134,10 @@ typedef struct {
                             (fifth-generation tensor cores, batches of 256 rows) or TPC_MMA_SYNC (warp-level
                             16-row tiles; the default, faster on the 10 ms frame); both give the same logits
                             to FP32 rounding; tpc_tf_autotune picks one by timing */
+  int32_t persistent;    /* 1: the whole plain path (A0-A5) runs as one persistent launch whose stages are
+                            separated by grid-wide barriers (the batched form replayed from a CUDA graph);
+                            TPC_MODE_PLAIN and follow = 0 only, thread-per-track fit; needs the GPU to itself
+                            (a barrier that waits too long reports TPC_ERR_TIMEOUT).  0: one launch per stage */
 } tpc_tf_config;
 
 typedef struct {      /* input clusters: device pointers, read only, caller owned */

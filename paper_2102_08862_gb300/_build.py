@@ -16,12 +16,13 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpcca.so")
 SOURCES = ["api.cu", "k_index.cu", "k_neighbours.cu", "k_links.cu", "k_fit.cu", "k_sort.cu", "noalloc.cu", "k_mlp.cu",
-           "train.cu", "serve.cu", "k_follow.cu", "k_append.cu"]
+           "train.cu", "serve.cu", "k_follow.cu", "k_append.cu", "k_persistent.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # per translation unit: the Kalman fit uses approximate FP32 division and square
 # root (the fit's tolerance against the FP64 oracle is 1e-4; linking is integer)
-TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"], "k_follow.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"], "k_follow.cu": ["-prec-div=false", "-prec-sqrt=false"],
+            "k_persistent.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc() -> str:

@@ -299,6 +299,9 @@ static int validate_config(const tpc_tf_config *cfg) {
   if (cfg->follow < 0 || cfg->follow > 2) return fail(TPC_ERR_ARG, "tpc_tf_create: follow must be 0, 1 or 2");
   if (cfg->mlp_engine != TPC_MMA_TCGEN05 && cfg->mlp_engine != TPC_MMA_SYNC)
     return fail(TPC_ERR_ARG, "tpc_tf_create: mlp_engine must be TPC_MMA_TCGEN05 or TPC_MMA_SYNC");
+  if (cfg->persistent != 0 && cfg->persistent != 1) return fail(TPC_ERR_ARG, "tpc_tf_create: persistent must be 0 or 1");
+  if (cfg->persistent && (cfg->mode != TPC_MODE_PLAIN || cfg->follow))
+    return fail(TPC_ERR_ARG, "tpc_tf_create: the persistent launch runs the plain path without following");
   if (cfg->follow == 2 && (!(cfg->follow_link_chi2 > 0.0f) || !(cfg->follow_link_chi2 < 1e6f) ||
                            cfg->follow_link_rows < 1 || cfg->follow_link_rows > TPC_NROWS))
     return fail(TPC_ERR_ARG, "tpc_tf_create: follow_link_chi2 must be in (0, 1e6), follow_link_rows in [1, 152]");
@@ -326,6 +329,10 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   }
   cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
+  if (cfg->persistent && persistent_prepare(tf->device) != 0) {
+    delete tf;
+    return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot size the persistent launch");
+  }
   const std::vector<Part> parts = plan_arena(tf, cfg);
   const size_t total = arena_total(parts);
   e = cudaMalloc(&tf->arena, total);
@@ -518,6 +525,42 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   return TPC_OK;
 }
 
+// The plain path as one persistent launch (after the counters' reset and, for
+// unsorted input, the sort).
+static int enqueue_persistent(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStream_t st) {
+  const uint32_t n = cl->n;
+  const bool sorted = (cl->flags & TPC_INPUT_SORTED) != 0;
+  tf->n_ev = 0;
+  tf->launches = 0;
+  if (tf->cfg.profile_stages) cudaEventRecord(tf->ev[0], st);
+  TPC_CK(cudaMemsetAsync(tf->reset, 0, kNCounters * 4 + 8 * (link_tiles(n) + walk_tiles(n)), st));
+  ++tf->launches;
+  if (sorted) {
+    a.sector = cl->sector;
+    a.row = cl->row;
+    a.pad = cl->pad;
+    a.time = cl->time;
+    a.perm = nullptr;
+  } else {
+    a.sector = tf->s_sector;
+    a.row = tf->s_row;
+    a.pad = tf->s_pad;
+    a.time = tf->s_time;
+    a.perm = tf->perm;
+    const int nl = launch_sort(a, cl->sector, cl->row, cl->pad, cl->time, tf->s_sector, tf->s_row, tf->s_pad,
+                               tf->s_time, tf->perm, tf->sort_scratch, tf->sort_scratch_bytes, tf->sms, st);
+    if (nl < 0) return fail(TPC_ERR_CUDA, "sort of unsorted input failed");
+    tf->launches += nl;
+    stage(tf, st, "sort");
+  }
+  if (launch_persistent(a, tf->sms, st) != 0) return fail(TPC_ERR_CUDA, "persistent launch: occupancy query failed");
+  ++tf->launches;
+  stage(tf, st, "persistent");
+  tf->last_n = n;
+  tf->last_sorted = sorted;
+  return TPC_OK;
+}
+
 extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
   g_err.clear();
   if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null argument");
@@ -540,13 +583,18 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   cudaStream_t st = (cudaStream_t)stream;
   Args a;
   fill_args(tf, n, out, a);
-  {
+  if (tf->cfg.persistent) {
+    const int rc = enqueue_persistent(tf, cl, a, st);
+    if (rc != TPC_OK) return rc;
+  } else {
     const int rc = enqueue_linking(tf, cl, a, st, prune);
     if (rc != TPC_OK) return rc;
+    launch_links(a, tf->sms, st);
+    stage(tf, st, "links");
   }
-  launch_links(a, tf->sms, st);
-  stage(tf, st, "links");
-  if (!tf->cfg.follow) {
+  if (tf->cfg.persistent) {
+    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
+  } else if (!tf->cfg.follow) {
     launch_walk(a, tf->sms, st);
     if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "walk");

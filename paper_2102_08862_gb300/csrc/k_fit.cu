@@ -254,11 +254,11 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 // shared memory (bitonic), so that the lanes of a warp fit chains of similar
 // length and finish together; the chain reads of a step stay inside the block's
 // 256 columns (1 KB, cached in L1).
-__global__ void __launch_bounds__(256) k_fit_thread(Args a) {
+__device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t nblk) {
   __shared__ uint32_t s_key[256];
   const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
-  for (uint32_t t0 = blockIdx.x * 256; t0 < nt; t0 += gridDim.x * 256) {
+  for (uint32_t t0 = bid * 256; t0 < nt; t0 += nblk * 256) {
     {
       const uint32_t tt = t0 + threadIdx.x;
       const uint32_t len = tt < nt ? (uint32_t)a.trk_len[tt] : 0u;
@@ -351,6 +351,9 @@ __global__ void __launch_bounds__(256) k_fit_thread(Args a) {
 // the results are identical.  It issues ~32x more warp instructions per track
 // than k_fit_thread (one filter per warp instead of per lane), which the
 // coalesced chain loads do not pay back: the thread kernel stays the default.
+#ifndef TPC_STAGES_ONLY
+__global__ void __launch_bounds__(256) k_fit_thread(Args a) { stage_fit(a, blockIdx.x, gridDim.x); }
+
 __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
   const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
@@ -711,5 +714,7 @@ __global__ void __launch_bounds__(256) k_follow_fit(Args a) {
 }
 
 void launch_follow_fit(const Args &a, int sms, cudaStream_t st) { k_follow_fit<<<sms * 8, 256, 0, st>>>(a); }
+
+#endif  // TPC_STAGES_ONLY
 
 }  // namespace tpc

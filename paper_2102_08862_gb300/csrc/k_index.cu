@@ -38,10 +38,15 @@ __device__ __forceinline__ uint32_t warp_lower_bound_key(const uint16_t *sector,
   return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, less));
 }
 
-__global__ void __launch_bounds__(256) k_row_index(Args a) {
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+// The row index in two parts, so that the persistent kernel can run them with a
+// grid barrier between: (1) one warp per (sector, row) key, warps taken in turn
+// by blocks bid, bid + nblk, ...; (2) one block: the largest row, the
+// monotonicity check and the first neighbour tile of every row (each thread owns
+// a contiguous block of keys; block-wide exclusive scan).
+__device__ __forceinline__ void stage_row_index_keys(const Args &a, uint32_t bid, uint32_t nblk) {
   const int lane = threadIdx.x & 31;
-  if (warp <= a.nkeys) {
+  const int wpb = (int)(blockDim.x >> 5);
+  for (int warp = (int)bid * wpb + (int)(threadIdx.x >> 5); warp <= a.nkeys; warp += (int)nblk * wpb) {
     const uint32_t r = warp_lower_bound_key(a.sector, a.row, a.n, warp);
     if (lane == 0) {
       a.row_begin[warp] = (int32_t)r;
@@ -49,20 +54,12 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
       if (warp == a.nkeys && r != a.n) raise(a.ctr, kErrInput);
     }
   }
-  // the last block to finish computes the largest row and checks monotonicity
-  __shared__ bool s_last;
+}
+
+__device__ __forceinline__ void stage_row_index_table(const Args &a) {
   __shared__ int s_max[8];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned d = atomicAdd(&a.ctr[kCtrIndexDone], 1u);
-    s_last = (d == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // largest row, monotonicity, and the first neighbour tile of every row
-  // (each thread owns a contiguous block of keys; block-wide exclusive scan)
+  __shared__ int s_scan[256];
+  const int lane = threadIdx.x & 31;
   const volatile int32_t *rbv = a.row_begin;
   const int nkeys = a.nkeys, tile = a.nb_tile;
   const int per = (nkeys + blockDim.x - 1) / blockDim.x;
@@ -75,7 +72,6 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
     mx = max(mx, c);
     ntile += (c + tile - 1) / tile;
   }
-  __shared__ int s_scan[256];
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) s_max[threadIdx.x >> 5] = mx;
   s_scan[threadIdx.x] = ntile;
@@ -103,6 +99,24 @@ __global__ void __launch_bounds__(256) k_row_index(Args a) {
     if (m > 65534) raise(a.ctr, kErrRowCap);  // row-local links are 16-bit
   }
 }
+
+#ifndef TPC_STAGES_ONLY
+// one launch: every key has its warp; the last block to finish builds the table
+__global__ void __launch_bounds__(256) k_row_index(Args a) {
+  stage_row_index_keys(a, blockIdx.x, gridDim.x);
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned d = atomicAdd(&a.ctr[kCtrIndexDone], 1u);
+    s_last = (d == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  stage_row_index_table(a);
+}
+#endif
 
 // A0 validation and quantisation, one pass over the sorted clusters: every
 // cluster must have sector < nsect, row < 152, a pad and a time inside the
@@ -137,15 +151,15 @@ __device__ __forceinline__ int2 quant_checked(int sec, int row, float p, float t
   return make_int2(q64(t), y_quant(p, min(row, kNRows - 1)));
 }
 
-__global__ void __launch_bounds__(256) k_quantize(Args a, int vec) {
+__device__ __forceinline__ void stage_quantize(const Args &a, int vec, uint32_t bid, uint32_t nblk) {
   const uint32_t n = a.n;
   const int lane = threadIdx.x & 31;
   const int nsect = a.nsect;
   QCheck ck;
   ck.bad = false;
   const uint32_t nvec = vec ? n / 256u * 256u : 0u;  // clusters handled 8 per thread (whole warps of 256)
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t w0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 8u; w0 < nvec; w0 += stride * 8u) {
+  const uint32_t stride = nblk * blockDim.x;
+  for (uint32_t w0 = (bid * blockDim.x + (threadIdx.x & ~31u)) * 8u; w0 < nvec; w0 += stride * 8u) {
     const uint32_t i0 = w0 + (uint32_t)lane * 8u;
     const uint4 sv = *reinterpret_cast<const uint4 *>(a.sector + i0);
     const uint4 rv = *reinterpret_cast<const uint4 *>(a.row + i0);
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(256) k_quantize(Args a, int vec) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) dst[e] = make_int4(q[2 * e].x, q[2 * e].y, q[2 * e + 1].x, q[2 * e + 1].y);
   }
-  for (uint32_t i = nvec + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {  // the rest
+  for (uint32_t i = nvec + bid * blockDim.x + threadIdx.x; i < n; i += stride) {  // the rest
     const int sec = a.sector[i], row = a.row[i];
     const float p = a.pad[i], t = a.time[i];
     if (i > 0) {
@@ -189,6 +203,9 @@ __global__ void __launch_bounds__(256) k_quantize(Args a, int vec) {
   }
   if (ck.bad) raise(a.ctr, kErrInput);
 }
+
+#ifndef TPC_STAGES_ONLY
+__global__ void __launch_bounds__(256) k_quantize(Args a, int vec) { stage_quantize(a, vec, blockIdx.x, gridDim.x); }
 
 void launch_quantize(const Args &a, int sms, cudaStream_t st) {
   const bool vec = ((((uintptr_t)a.pad | (uintptr_t)a.time | (uintptr_t)a.sector | (uintptr_t)a.row) & 15) == 0);
@@ -213,5 +230,7 @@ void launch_row_index(const Args &a, cudaStream_t st) {
   const int blocks = (warps * 32 + 255) / 256;
   k_row_index<<<blocks, 256, 0, st>>>(a);
 }
+
+#endif  // TPC_STAGES_ONLY
 
 }  // namespace tpc

@@ -43,7 +43,7 @@ __device__ __forceinline__ int key_of(const int32_t *rb, int i, int nkeys) {
 // The row table rb (row_begin) sits in shared memory for up to 36 sectors and is
 // read through the L1 cache for batched calls with more.
 template <bool kSmemRb>
-__global__ void __launch_bounds__(kThreads) k_links(Args a) {
+__device__ __forceinline__ void stage_links(const Args &a) {
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
@@ -141,14 +141,14 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
 // clusters get the track id and are recorded in the chain buffer; the clusters of
 // shorter chains get -1.
 template <bool kSmemRb>
-__global__ void __launch_bounds__(kThreads) k_walk(Args a) {
+__device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t s_warp[kThreads / 32];
   const uint32_t ns = min(a.ctr[kCtrStarts], a.starts_cap);
   const uint32_t n_tiles = (ns + kWalkTileN - 1) / kWalkTileN;
   if (n_tiles == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
       a.ctr[kCtrTracks] = 0;
       if (a.n_tracks_out) *a.n_tracks_out = 0;
     }
@@ -256,6 +256,16 @@ __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
     }
     __syncthreads();
   }
+}
+
+#ifndef TPC_STAGES_ONLY
+template <bool kSmemRb>
+__global__ void __launch_bounds__(kThreads) k_links(Args a) {
+  stage_links<kSmemRb>(a);
+}
+template <bool kSmemRb>
+__global__ void __launch_bounds__(kThreads) k_walk(Args a) {
+  stage_walk<kSmemRb>(a, blockIdx.x);
 }
 
 // Hit removal: the clusters attached to a track, in caller order (an ordered
@@ -399,5 +409,7 @@ void launch_debug_wait(uint64_t *lb, uint32_t *ctr, uint32_t spin_limit, cudaStr
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st) {
   k_debug_links<<<1024, 256, 0, st>>>(a, mup, is_start);
 }
+
+#endif  // TPC_STAGES_ONLY
 
 }  // namespace tpc

@@ -389,9 +389,9 @@ struct __align__(16) NbSmem {
 // ------------------------------------------------------------ tile windows
 // One thread per tile: the tile's cluster range and the ranges of rows r-1 and
 // r+1 whose t_q lies in [t_first - wt, t_last + wt].
-__global__ void __launch_bounds__(256) k_tile_windows(Args a) {
+__device__ __forceinline__ void stage_tile_windows(const Args &a, uint32_t bid, uint32_t nblk) {
   const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+  for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nblk * blockDim.x) {
     // key = last (sector, row) whose first tile is <= t
     int lo = 0, hi = a.nkeys;
     while (hi - lo > 1) {
@@ -427,15 +427,15 @@ __global__ void __launch_bounds__(256) k_tile_windows(Args a) {
 // where the region bookkeeping spills at 32 (a persistent, double-buffered form
 // with 4-6 CTAs per SM measured 35-45 % slower: its per-tile barrier holds every
 // warp until the tile's slowest one).
+// The work of one tile (t < the number of tiles).  `phase` is the parity of the
+// CTA's mbarrier phase to wait for; `init` is set until the CTA has initialised
+// its mbarrier (edge-row tiles do not use it).
 template <bool kPrune, int TILE, int WIN, int THREADS>
-__global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THREADS)
-    k_neighbours(Args a, int win_cap) {
+__device__ __forceinline__ void nb_tile(const Args &a, int win_cap, uint32_t t, uint32_t &phase, bool &init) {
   static_assert(WIN < 2048 && TILE % THREADS == 0 && THREADS <= 256, "window indices are packed in 11 bits");
   __shared__ NbSmem<TILE, WIN> sm;
   __shared__ NbExtra<kPrune> ex;
   __shared__ NbPairs<kPrune> pr;
-  const uint32_t t = blockIdx.x;
-  if (t >= min(a.ctr[kCtrTiles], a.tile_cap)) return;
   const int4 h = a.tile_win[2 * t], w = a.tile_win[2 * t + 1];
   const int key = h.x, ta = h.y, cnt = h.z - h.y;
   const int r = key % kNRows;
@@ -454,9 +454,12 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THRE
     q = &ex.q;
     if (tid == 0) q->count = q->end = 0, q->warps_done = 0;
   }
-  if (tid == 0) mbar_init1(&sm.bar);
-  __syncthreads();  // the barrier is initialised
+  if (init && tid == 0) mbar_init1(&sm.bar);
+  __syncthreads();  // the barrier is initialised; the buffers' previous readers are done
+  init = false;
   if (tid == 0) {
+    // generic-proxy reads of the previous tile are ordered before the copies' writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const uint32_t bc = 8u * (uint32_t)(((ta + cnt + 1) & ~1) - c0);
     const uint32_t bp = staged ? 8u * (uint32_t)(((w.y + 1) & ~1) - p0) : 0u;
     const uint32_t bn = staged ? 8u * (uint32_t)(((w.w + 1) & ~1) - n0) : 0u;
@@ -469,7 +472,9 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THRE
   // timeout, waits once more (bounded) for copies still in flight and leaves the
   // tile unlinked (the decision is taken by the whole CTA at one barrier)
   bool ok = true;
-  for (uint32_t it = 0; !mbar_try(&sm.bar, 0); ++it) {  // try_wait suspends the thread for a while itself
+  const uint32_t ph = phase;
+  phase ^= 1u;
+  for (uint32_t it = 0; !mbar_try(&sm.bar, ph); ++it) {  // try_wait suspends the thread for a while itself
     if (it >= a.spin_limit) {
       ok = false;
       break;
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THRE
   if (__syncthreads_or(!ok)) {
     if (tid == 0) raise(a.ctr, kErrTimeout);
     if (!ok)
-      for (uint32_t it = 0; it < a.spin_limit && !mbar_try(&sm.bar, 0); ++it) {
+      for (uint32_t it = 0; it < a.spin_limit && !mbar_try(&sm.bar, ph); ++it) {
       }
     return;
   }
@@ -510,20 +515,46 @@ __global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THRE
   }
 }
 
+#ifndef TPC_STAGES_ONLY
+template <bool kPrune, int TILE, int WIN, int THREADS>
+__global__ void __launch_bounds__(THREADS, kPrune ? 1536 / THREADS : 2048 / THREADS)
+    k_neighbours(Args a, int win_cap) {
+  const uint32_t t = blockIdx.x;
+  if (t >= min(a.ctr[kCtrTiles], a.tile_cap)) return;
+  uint32_t phase = 0;
+  bool init = true;
+  nb_tile<kPrune, TILE, WIN, THREADS>(a, win_cap, t, phase, init);
+}
+#endif
+
+// all tiles t = bid, bid + nblk, ... in one CTA (the persistent kernel); a tile
+// whose copies timed out records the error and the CTA goes on (its results are
+// not valid then, and the call reports TPC_ERR_TIMEOUT)
+template <bool kPrune, int TILE, int WIN, int THREADS>
+__device__ __forceinline__ void stage_neighbours(const Args &a, int win_cap, uint32_t bid, uint32_t nblk) {
+  const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
+  uint32_t phase = 0;
+  bool init = true;
+  for (uint32_t t = bid; t < ntiles; t += nblk) {
+    nb_tile<kPrune, TILE, WIN, THREADS>(a, win_cap, t, phase, init);
+    __syncthreads();  // the staged buffers are free for the next tile
+  }
+}
+
 // ------------------------------------------------------------- edge-row claims
 // A row-0 cluster j takes as up link the row-1 cluster i with down[i] = j of
 // smallest (cost_i, i); a row-151 cluster k takes as down link the row-150
 // cluster i with up[i] = k of smallest (cost_i, i).  The claimants lie inside
 // j's (k's) time window, so the kernel scans that window of the adjacent row and
 // recomputes each claimant's triplet cost exactly.  grid.y = 72 edge rows.
-__global__ void __launch_bounds__(256) k_edge_claims(Args a) {
-  const int e = blockIdx.y;
+constexpr int kClaimBlocks = 32;  // blocks per edge row
+__device__ __forceinline__ void edge_claims_block(const Args &a, int e, int x) {
   const int s = e >> 1;
   const bool top = (e & 1) != 0;
   const int r = top ? kNRows - 1 : 0, rn = top ? kNRows - 2 : 1;
   const int rb = a.row_begin[s * kNRows + r], re = a.row_begin[s * kNRows + r + 1];
   const int nb = a.row_begin[s * kNRows + rn], ne = a.row_begin[s * kNRows + rn + 1];
-  for (int j = rb + (int)(blockIdx.x * blockDim.x + threadIdx.x); j < re; j += (int)(gridDim.x * blockDim.x)) {
+  for (int j = rb + x * (int)blockDim.x + (int)threadIdx.x; j < re; j += kClaimBlocks * (int)blockDim.x) {
     const int2 qj = a.tq[j];
     const int32_t tj = qj.x, yj = qj.y;
     const int lo = tq_lower_bound(a.tq, nb, ne, tj - a.wt);
@@ -550,6 +581,15 @@ __global__ void __launch_bounds__(256) k_edge_claims(Args a) {
   }
 }
 
+__device__ __forceinline__ void stage_edge_claims(const Args &a, uint32_t bid, uint32_t nblk) {
+  const uint32_t nb = (uint32_t)kClaimBlocks * 2u * (uint32_t)a.nsect;
+  for (uint32_t b = bid; b < nb; b += nblk) edge_claims_block(a, (int)(b / kClaimBlocks), (int)(b % kClaimBlocks));
+}
+
+#ifndef TPC_STAGES_ONLY
+__global__ void __launch_bounds__(256) k_tile_windows(Args a) { stage_tile_windows(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_edge_claims(Args a) { edge_claims_block(a, blockIdx.y, blockIdx.x); }
+
 // ------------------------------------------------------------------ launchers
 void launch_tile_windows(const Args &a, cudaStream_t st) {
   const uint32_t tiles = neighbour_tiles_max(a.n, a.nkeys, a.nb_tile);
@@ -571,6 +611,9 @@ void launch_neighbours(const Args &a, int row_cap, int sms, cudaStream_t st, boo
   else launch_nb<768, 1280>(a, row_cap, st, prune);
 }
 
-void launch_edge_claims(const Args &a, cudaStream_t st) { k_edge_claims<<<dim3(32, 2 * a.nsect), 256, 0, st>>>(a); }
+void launch_edge_claims(const Args &a, cudaStream_t st) {
+  k_edge_claims<<<dim3(kClaimBlocks, 2 * a.nsect), 256, 0, st>>>(a);
+}
+#endif  // TPC_STAGES_ONLY
 
 }  // namespace tpc

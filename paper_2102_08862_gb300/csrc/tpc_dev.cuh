@@ -78,6 +78,8 @@ enum : int {
   kCtrFollowTile = 14,   // track follower: next track to follow
   kCtrFollowTracks = 15, // track follower: tracks after joining
   kCtrFollowPathTile = 16,  // track follower: next tile of joined paths
+  kCtrBarCount = 17,        // persistent kernel: CTAs arrived at the current grid barrier
+  kCtrBarGen = 18,          // persistent kernel: grid barriers passed
   kNCounters = 20
 };
 

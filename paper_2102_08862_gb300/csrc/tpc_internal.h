@@ -111,6 +111,12 @@ inline bool records_aligned(const tpc_tracks *out) {
 }
 // sets the message returned by tpc_last_error() (cleared for TPC_OK); returns code
 int report(int code, const char *msg);
+// the plain path A0-A5 in one persistent launch (k_persistent.cu); the call's reset
+// region must be cleared and, for unsorted input, the sort enqueued before.
+// persistent_prepare(dev) records the kernel's occupancy (once per device, with it
+// current, outside stream capture); both return 0 on success
+int persistent_prepare(int dev);
+int launch_persistent(const Args &a, int sms, cudaStream_t st);
 // device fixed-point conversion q[i] = rint(64 v[i]) (tests of the quantisation contract)
 void launch_debug_quantize(const float *v, uint32_t n, int32_t *q, cudaStream_t st);
 // one look-back wait on lb[1] whose predecessor lb[0] never publishes; gives up

@@ -38,7 +38,7 @@ class tpc_tf_config(ctypes.Structure):
                 ("fit_variant", c_i32), ("profile_stages", c_i32), ("row_cap", c_i32), ("n_sectors", c_i32),
                 ("nb_tile", c_i32), ("follow", c_i32), ("follow_chi2", c_f32), ("follow_miss", c_i32),
                 ("follow_check", c_i32), ("follow_link_chi2", c_f32), ("follow_link_rows", c_i32),
-                ("mlp_engine", c_i32)]
+                ("mlp_engine", c_i32), ("persistent", c_i32)]
 
 
 class tpc_clusters(ctypes.Structure):

@@ -40,7 +40,7 @@ int main(void) {
   printf("tpc_tf_config %zu\ntpc_clusters %zu\ntpc_tracks %zu\n", sizeof(tpc_tf_config), sizeof(tpc_clusters),
          sizeof(tpc_tracks));
   F(tpc_tf_config, cost_max_q); F(tpc_tf_config, tau); F(tpc_tf_config, row_cap); F(tpc_tf_config, follow_chi2);
-  F(tpc_tf_config, follow_check); F(tpc_tf_config, follow_link_rows); F(tpc_tf_config, mlp_engine);
+  F(tpc_tf_config, follow_check); F(tpc_tf_config, follow_link_rows); F(tpc_tf_config, mlp_engine); F(tpc_tf_config, persistent);
   F(tpc_tracks, next_track);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
   printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
@@ -83,6 +83,12 @@ def test_defaults_and_argument_errors(lib):
         setattr(d, k, v)
         assert lib.tpc_tf_create(ctypes.byref(d), ctypes.byref(h)) == tpcca.TPC_ERR_ARG, k
         assert "follow" in tpcca.tpc_last_error()
+    for k, v in (("persistent", 2), ("mode", tpcca.TPC_MODE_PRUNED), ("follow", 1)):
+        d = tpcca.tpc_default_config()
+        d.max_clusters, d.persistent = 100, 1
+        setattr(d, k, v)
+        assert lib.tpc_tf_create(ctypes.byref(d), ctypes.byref(h)) == tpcca.TPC_ERR_ARG, k
+        assert "persistent" in tpcca.tpc_last_error()
     assert lib.tpc_track_timeframe(None, None, None, None) == tpcca.TPC_ERR_ARG
     assert lib.tpc_tf_status(None, None) == tpcca.TPC_ERR_ARG
     lib.tpc_tf_destroy(None)
