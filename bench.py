@@ -43,10 +43,10 @@ NOMINAL_HBM_GBS = 8000.0
 FIT_FLOP_PER_CLUSTER = 200.0  # transport + 2-D update per cluster in a track (algorithmic)
 # DRAM bytes per cluster of k_neighbours from one full ncu capture of the 5 ms frame,
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "c370aa988f7203e7d09dc7afe1f1d3befdd79a3e8bee3f59227246e8649e27c6",
-              "pruned": (135.789568e6 + 129.231616e6) / 16765809, "plain": (135.306240e6 + 93.925376e6) / 16765809}
+NB_TRAFFIC = {"sha256": "8464b29b659b8e1acd75cb55e3d9b9ec1c0eb0d1a0ed04012ddc9fab41c0703f",
+              "pruned": (135.739648e6 + 119.180800e6) / 16765809, "plain": (135.317760e6 + 93.424128e6) / 16765809}
 # warp instructions per cluster of the same captures (smsp__inst_executed.sum / clusters)
-NB_INST = {"pruned": 426533997 / 16765809, "plain": 366935837 / 16765809}
+NB_INST = {"pruned": 401141061 / 16765809, "plain": 366996795 / 16765809}
 
 
 def neighbours_traffic(mode, n):
