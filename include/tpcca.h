@@ -383,6 +383,8 @@ typedef struct {
   float pos_weight;  /* weight of label-1 rows in the loss (default 1) */
   uint32_t max_batch;/* largest batch of a step (default 8192) */
   int32_t device;    /* CUDA device ordinal */
+  int32_t engine;    /* tensor-core engine of the forward/backward kernel: TPC_MMA_TCGEN05 (default)
+                        or TPC_MMA_SYNC; both are bitwise reproducible from step to step */
 } tpc_mlp_train_config;
 
 void tpc_mlp_default_train_config(tpc_mlp_train_config *cfg);
@@ -408,7 +410,9 @@ int tpc_mlp_train_step(tpc_mlp_trainer *tr, const float *feat, const uint8_t *la
 int tpc_mlp_trainer_gradient(tpc_mlp_trainer *tr, const float *feat, const uint8_t *label, const int32_t *index,
                              uint32_t batch, float *grad, float *loss, void *stream);
 
-/* Write the current weights as a blob into host memory (synchronises). */
+/* Write the current weights as a blob into host memory (synchronises).  Returns
+ * TPC_ERR_TIMEOUT (the blob is still written) when a bounded tensor-core wait of an
+ * earlier step gave up; that step's gradient was zero. */
 int tpc_mlp_trainer_blob(tpc_mlp_trainer *tr, void *blob, size_t bytes);
 
 /* ----------------------------------------------------------------------------

@@ -55,7 +55,13 @@
  * Decisions that FP32 arithmetic could take differently are recorded.  Each
  * decision has a margin: a gated chi2 against chi2_max, and the gap between the
  * best and next chi2 of a row, in units of 2 % of (1 + chi2); |sin phi| against
- * 0.999, in units of 1e-3.  A cluster keeps the smallest margin of any decision
+ * 0.999, in units of 1e-4 (the relative tolerance within which an FP32 fit of
+ * the same clusters agrees with the FP64 one).  In the link search (X) a gate
+ * decision counts only where it can change the outcome: a cluster's chi2 against
+ * chi2_max where, passing, the cluster would be the row's best (no cluster
+ * passes, it is the best, or it is within the tie tolerance of the best), and
+ * the test whether a row is searched only where one of the row's clusters could
+ * pass.  A cluster keeps the smallest margin of any decision
  * about it (by any track).  A final track's margin is the smallest over the own
  * decisions of the tracks of its path, its clusters and every cluster its path
  * proposed.  A margin below 1 marks a track whose membership an FP32 follower
@@ -74,7 +80,7 @@
 /* margins are reported in units of these tolerances: a margin below 1 marks a
  * decision that an FP32 implementation may take the other way */
 #define FL_TOL_CHI2 0.02 /* chi2 comparisons: 2 % of (1 + chi2) */
-#define FL_TOL_SIN 1e-3  /* |sin phi| against the 0.999 stop */
+#define FL_TOL_SIN 1e-4  /* |sin phi| against the 0.999 stop: the fit's FP32 tolerance on sin phi */
 #define FL_TOL_Y 1e-3    /* a predicted y against the edge of the pad area, cm */
 #define FL_K 0.00149896229
 #define FL_SECTOR_RAD (20.0 * 3.14159265358979323846 / 180.0)
@@ -355,7 +361,20 @@ static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *f
   int32_t *pred = (int32_t *)malloc(sizeof(int32_t) * (nf + 1));
   int32_t *prop = (int32_t *)malloc(sizeof(int32_t) * (nf + 1));
   double *bmargin = (double *)malloc(sizeof(double) * (nf + 1));
-  if (!pred || !prop || !bmargin) return;
+  /* one row's candidates (at most the row's clusters) */
+  int64_t rowmax = 1;
+  for (int64_t k = 0; k < (int64_t)OR_NSECT * OR_NROWS; ++k)
+    if (x->row_first[k + 1] - x->row_first[k] > rowmax) rowmax = x->row_first[k + 1] - x->row_first[k];
+  int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * rowmax);
+  double *cg2 = (double *)malloc(sizeof(double) * rowmax);
+  if (!pred || !prop || !bmargin || !cand || !cg2) {
+    free(pred);
+    free(prop);
+    free(bmargin);
+    free(cand);
+    free(cg2);
+    return;
+  }
   for (int64_t t = 0; t < nf; ++t) {
     pred[t] = prop[t] = -1;
     bmargin[t] = INFINITY;
@@ -411,25 +430,33 @@ static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *f
     if (r0 < OR_NROWS) fl_margin(&mg, (fl_x[r0] - xr) / FL_TOL_Y);
     if (r0 > 0) fl_margin(&mg, (xr - fl_x[r0 - 1]) / FL_TOL_Y);
     double xcur = xr;
+    const double tol_gate = FL_TOL_CHI2 * (1.0 + fp->chi2_max);
     for (int r = r0; r < OR_NROWS && r < r0 + fp->xs_rows; ++r) {
       if (fl_transport(q, C2, fl_x[r] - xcur, &mg)) break;
       xcur = fl_x[r];
-      /* a row is searched only where the gate reaches the pad plane (|y| up to
-       * npads pitch / 2): chi2 >= r_y^2 / S_yy */
-      double over = fabs(q[0]) - 0.5 * (double)fl_npads[r] * (double)fl_pitch[r] * 1e-4 -
-                    sqrt(fp->chi2_max * (C2[0] + FL_VY));
-      fl_margin(&mg, fabs(over) / FL_TOL_Y);
-      if (over > 0.0) continue;
-      /* the first clusters of s2's tracks in this row under the gate */
-      int64_t k = (int64_t)s2 * OR_NROWS + r, best = -1, second = -1;
-      double b = 0.0, sec = INFINITY;
+      /* the first clusters of s2's tracks in this row, with their gated chi2 */
+      int64_t k = (int64_t)s2 * OR_NROWS + r, nc = 0;
+      double gmin = INFINITY;
       for (int64_t c = x->row_first[k]; c < x->row_first[k + 1]; ++c) {
         if (first_of[c] < 0) continue;
         double ym = fl_y(r, x->sp[c]), zm = FL_CM_PER_BIN * ((double)x->st[c] - ra->t_ref);
-        double g2 = fl_chi2(q, C2, ym, zm);
-        double g = fabs(g2 - fp->chi2_max) / (FL_TOL_CHI2 * (1.0 + fp->chi2_max));
-        fl_margin(&mg, g);
-        fl_margin(&bmargin[first_of[c]], g);
+        cand[nc] = c;
+        cg2[nc] = fl_chi2(q, C2, ym, zm);
+        if (cg2[nc] < gmin) gmin = cg2[nc];
+        ++nc;
+      }
+      /* a row is searched only where the gate reaches the pad plane (|y| up to
+       * npads pitch / 2): chi2 >= r_y^2 / S_yy.  Searching the row or not changes
+       * the outcome only when one of its clusters could pass the gate. */
+      double over = fabs(q[0]) - 0.5 * (double)fl_npads[r] * (double)fl_pitch[r] * 1e-4 -
+                    sqrt(fp->chi2_max * (C2[0] + FL_VY));
+      if (gmin <= fp->chi2_max + tol_gate) fl_margin(&mg, fabs(over) / FL_TOL_Y);
+      if (over > 0.0) continue;
+      int64_t best = -1, second = -1;
+      double b = 0.0, sec = INFINITY;
+      for (int64_t e = 0; e < nc; ++e) {
+        const int64_t c = cand[e];
+        const double g2 = cg2[e];
         if (g2 > fp->chi2_max) continue;
         if (best < 0 || g2 < b) {
           second = best;
@@ -440,6 +467,16 @@ static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *f
           second = c;
           sec = g2;
         }
+      }
+      /* a cluster's gate decision matters when, passing, it would be the row's
+       * best: no cluster passes, or it is the best, or it is within the tie
+       * tolerance of the best (a cluster further above the best cannot become it) */
+      for (int64_t e = 0; e < nc; ++e) {
+        const int64_t c = cand[e];
+        if (best >= 0 && c != best && cg2[e] - b >= FL_TOL_CHI2 * (1.0 + b)) continue;
+        const double g = fabs(cg2[e] - fp->chi2_max) / tol_gate;
+        fl_margin(&mg, g);
+        fl_margin(&bmargin[first_of[c]], g);
       }
       if (best < 0) continue;
       if (second >= 0) {
@@ -482,6 +519,8 @@ static void fl_sector_links(const fl_ctx *x, const int32_t *ct, const int32_t *f
   free(pred);
   free(prop);
   free(bmargin);
+  free(cand);
+  free(cg2);
 }
 
 /* See the file header.  Inputs: the sorted frame, its (sector, row) ranges, the

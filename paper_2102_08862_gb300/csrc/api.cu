@@ -105,6 +105,7 @@ struct tpc_tf {
   uint8_t *f_status = nullptr;
   uint32_t *f_pred_claim = nullptr;  // [track_list_cap] join proposals, then [N] cluster claims
   int32_t *f_succ = nullptr;
+  int4 *f_xlist = nullptr;  // cross-sector link search: [track_list_cap][2]
   uint32_t *f_npick = nullptr;
   uint32_t *f_map = nullptr;
   float *f_t16 = nullptr;
@@ -267,6 +268,7 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->f_status, fol ? TL : 0},
       {(void **)&tf->f_pred_claim, fol ? (TL + N + 4) * 4 : 0},
       {(void **)&tf->f_succ, fol ? TL * 4 : 0},
+      {(void **)&tf->f_xlist, cfg->follow == 2 ? TL * 32 : 0},
       {(void **)&tf->f_npick, fol ? TL * 4 : 0},
       {(void **)&tf->f_map, fol ? (TL + 1) * 4 : 0},
       {(void **)&tf->f_t16, fol ? (N / 16 + 2) * 4 : 0},
@@ -442,6 +444,7 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
     a.fl.pred = tf->f_pred_claim;
     a.fl.claim = tf->f_pred_claim + tf->track_list_cap;
     a.fl.succ = tf->f_succ;
+    a.fl.xlist = tf->f_xlist;
     a.fl.npick = tf->f_npick;
     a.fl.map = tf->f_map;
     a.fl.t16 = tf->f_t16;
@@ -596,9 +599,9 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
   } else if (!tf->cfg.follow) {
     launch_walk(a, tf->sms, st);
-    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "walk");
     launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "fit");
     tf->launches += 3;  // links, walk, fit
   } else {
@@ -637,7 +640,7 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
       TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, (size_t)tf->track_list_cap * 4, st));
       launch_sector_links(a, tf->sms, st);
       stage(tf, st, "sector_links");
-      tf->launches += 3;  // pred reset, links, resolve
+      tf->launches += 4;  // pred reset, exits, searches, resolve
     }
   }
   TPC_CK(cudaGetLastError());
@@ -901,7 +904,8 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   const int rc0 = tpc_track_timeframe(tf, &dcl, &dt, stream);
   tf->record_ct = false;
   if (rc0 != TPC_OK) return rc0;
-  // cluster_track back while the fit runs; then the count, then exactly that many records
+  // cluster_track back on the second stream once the fit has written it, beside the
+  // count and then exactly that many records on the call's stream
   if (n > 0) {
     TPC_CK(cudaStreamWaitEvent(tf->aux_stream, tf->ev_ct, 0));
     TPC_CK(cudaMemcpyAsync(out->cluster_track, tf->h_ct, (size_t)n * 4, cudaMemcpyDeviceToHost, tf->aux_stream));

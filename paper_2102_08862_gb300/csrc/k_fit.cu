@@ -14,7 +14,11 @@
 // chain[step][track], so the threads of a block read words of the same 1 KB span;
 // each block sorts its 256 tracks by chain length first, so that the lanes of a
 // warp finish together; the next cluster's (pad, time) is loaded before the
-// current step's arithmetic.
+// current step's arithmetic, and the cluster's cluster_track entry (the track id)
+// is written when it is loaded: the fit visits every member of every track in
+// any case, and its scattered stores overlap arithmetic there instead of
+// lengthening the walk's pointer chase.  Tracks past the record capacity get
+// their cluster_track entries without a fit.
 //
 // FP32 accuracy.  Three choices keep the FP32 filter within 1e-4 of an FP64 one:
 //  * the covariance is carried as C = U D U^T (U unit upper triangular, D
@@ -74,29 +78,42 @@ __device__ __forceinline__ float zeta_local(float time, float tref) {
 
 // transport by dx; false (state untouched) when |sin phi| would reach 0.999
 __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
+  // Every product and sum is an explicit rounded operation (__fmul_rn, __fadd_rn,
+  // __fmaf_rn): the compiler may otherwise fuse a product into a following sum in
+  // one translation unit and not in another, and the stage kernels and the
+  // persistent kernel must give the same bits.
   const float s1 = k.p[2], t = k.p[3];
-  const float cv = -kBz * k.p[4];
-  const float s2 = s1 + cv * dx;
+  const float cv = __fmul_rn(-kBz, k.p[4]);
+  const float s2 = __fmaf_rn(cv, dx, s1);
   if (fabsf(s2) >= 0.999f || fabsf(s1) >= 0.999f) return false;
-  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1)), c2 = sqrtf((1.0f - s2) * (1.0f + s2));
-  const float A = s1 + s2, D = c1 + c2, iD = 1.0f / D;
-  const float dy = dx * A * iD;
-  const float l = sqrtf(dx * dx + dy * dy);
-  const float u = 0.5f * cv * l;
-  const float ds = l * asinc(u);
+  // cos phi, 1 / cos phi and the chord length from reciprocal square roots (one
+  // special-function op each, and the divisions by c1, c2 and l become products)
+  const float q1 = __fmul_rn(1.0f - s1, 1.0f + s1), q2 = __fmul_rn(1.0f - s2, 1.0f + s2);
+  const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
+  const float c1 = __fmul_rn(q1, ic1), c2 = __fmul_rn(q2, ic2);
+  const float A = __fadd_rn(s1, s2), D = __fadd_rn(c1, c2), iD = 1.0f / D;
+  const float dy = __fmul_rn(__fmul_rn(dx, A), iD);
+  const float dx2 = __fmul_rn(dx, dx);
+  const float l2 = __fmaf_rn(dy, dy, dx2), il = rsqrtf(l2);
+  const float l = __fmul_rn(l2, il);
+  const float u = __fmul_rn(__fmul_rn(0.5f, cv), l);
+  const float ds = __fmul_rn(l, asinc(u));
   // Jacobian entries above the unit diagonal
-  const float iD2 = iD * iD;
-  const float Fys = dx * (2.0f * D + A * (s1 / c1 + s2 / c2)) * iD2;  // dy/ds1
-  const float Fyc = dx * dx * (D + A * s2 / c2) * iD2;                // dy/dc
-  const float g = 1.0f / sqrtf((1.0f - u) * (1.0f + u));              // d(arc)/d(chord)
-  const float dyl = dy / l;
-  const float a = Fys, b = -kBz * Fyc;                                // row y: (s, Q)
-  const float e = t * g * dyl * Fys;                                  // row zeta: s
-  const float f = ds;                                                 //           t
-  const float gq = -kBz * t * (g * dyl * Fyc + 0.5f * l * l * asinc_d(u));  //     Q
-  const float h = -kBz * dx;                                          // row s: Q
-  k.p[0] += dy;
-  k.p[1] += t * ds;
+  const float iD2 = __fmul_rn(iD, iD);
+  const float tn2 = __fmul_rn(s2, ic2);  // tan phi2
+  const float Fys = __fmul_rn(__fmul_rn(dx, __fmaf_rn(A, __fmaf_rn(s1, ic1, tn2), __fmul_rn(2.0f, D))), iD2);  // dy/ds1
+  const float Fyc = __fmul_rn(__fmul_rn(dx2, __fmaf_rn(A, tn2, D)), iD2);  // dy/dc
+  const float g = rsqrtf(__fmul_rn(1.0f - u, 1.0f + u));                // d(arc)/d(chord)
+  const float dyl = __fmul_rn(dy, il);
+  const float gdyl = __fmul_rn(g, dyl);
+  const float a = Fys, b = __fmul_rn(-kBz, Fyc);                          // row y: (s, Q)
+  const float e = __fmul_rn(__fmul_rn(t, gdyl), Fys);                     // row zeta: s
+  const float f = ds;                                                     //           t
+  const float gq = __fmul_rn(__fmul_rn(-kBz, t),
+                             __fmaf_rn(gdyl, Fyc, __fmul_rn(__fmul_rn(__fmul_rn(0.5f, l), l), asinc_d(u))));  // Q
+  const float h = __fmul_rn(-kBz, dx);                                    // row s: Q
+  k.p[0] = __fadd_rn(k.p[0], dy);
+  k.p[1] = __fmaf_rn(t, ds, k.p[1]);
   k.p[2] = s2;
   // U <- F U (rows 0 and 1 use the old row 2)
   float *U = k.u;
@@ -122,7 +139,7 @@ __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
     g[j] = k.d[j] * f[j];
     b[j] = 0.0f;
   }
-  const float r = meas - k.p[M];
+  const float r = __fsub_rn(meas, k.p[M]);  // (not fused with the caller's scaling of meas)
   float alpha = V, ibeta = 1.0f / V;
 #pragma unroll
   for (int j = M; j < 5; ++j) {
@@ -194,9 +211,10 @@ __device__ __forceinline__ int kf_seed(Kf &k, int r0, int r1, int r2, float pad0
   const float cross = kRowDx * (sag.hi + sag.lo) * 1e-4f;  // cm^2
   const float ax = (float)mid * kRowDx, bx = (float)last * kRowDx;
   const float ayc = (ay.hi + ay.lo) * 1e-4f, byc = (by.hi + by.lo) * 1e-4f;
-  const float d01 = sqrtf(ax * ax + ayc * ayc), d02 = sqrtf(bx * bx + byc * byc);
+  // sums of two products rounded explicitly (the same bits in every kernel)
+  const float d01 = sqrtf(__fmaf_rn(ax, ax, __fmul_rn(ayc, ayc))), d02 = sqrtf(__fmaf_rn(bx, bx, __fmul_rn(byc, byc)));
   const float ex = bx - ax, ey = byc - ayc;
-  const float d12 = sqrtf(ex * ex + ey * ey);
+  const float d12 = sqrtf(__fmaf_rn(ex, ex, __fmul_rn(ey, ey)));
   float cv = 2.0f * cross / (d01 * d02 * d12);
   float u = 0.5f * cv * d02;
   int status = 0;
@@ -206,7 +224,7 @@ __device__ __forceinline__ int kf_seed(Kf &k, int r0, int r1, int r2, float pad0
     u = 0.0f;
   }
   const float sth = byc / d02, cth = bx / d02;  // chord direction first -> last
-  float s0 = sth * sqrtf((1.0f - u) * (1.0f + u)) - cth * u;  // sin(chord angle - asin u)
+  float s0 = __fmaf_rn(sth, sqrtf((1.0f - u) * (1.0f + u)), -__fmul_rn(cth, u));  // sin(chord angle - asin u)
   if (fabsf(s0) >= 0.999f) {
     status |= 1;
     cv = 0.0f;
@@ -256,12 +274,15 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 // 256 columns (1 KB, cached in L1).
 __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t nblk) {
   __shared__ uint32_t s_key[256];
-  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
+  // every listed track gets its cluster_track entries; the first track_capacity
+  // are also fitted
+  const uint32_t nl = min(a.ctr[kCtrTracks], a.track_list_cap);
+  const uint32_t nt = min(nl, a.track_capacity);
   const size_t stride = a.track_list_cap;
-  for (uint32_t t0 = bid * 256; t0 < nt; t0 += nblk * 256) {
+  for (uint32_t t0 = bid * 256; t0 < nl; t0 += nblk * 256) {
     {
       const uint32_t tt = t0 + threadIdx.x;
-      const uint32_t len = tt < nt ? (uint32_t)a.trk_len[tt] : 0u;
+      const uint32_t len = tt < nl ? (uint32_t)a.trk_len[tt] : 0u;
       s_key[threadIdx.x] = (len << 8) | threadIdx.x;
       __syncthreads();
       for (int k = 2; k <= 256; k <<= 1)
@@ -279,16 +300,21 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
     }
     const uint32_t t = t0 + (s_key[threadIdx.x] & 255u);
     __syncthreads();  // s_key is rewritten by the next round
-    if (t >= nt) continue;
+    if (t >= nl) continue;
     // the chain's clusters were recorded by the walk as chain[step][track]
     const int32_t *ch = a.chain + t;
     const int L = a.trk_len[t];
+    if (t >= nt) {  // past the record capacity: the cluster -> track entries only
+      for (int q = 0; q < L; ++q) a.cluster_track[caller_index(a, ch[(size_t)q * stride])] = (int32_t)t;
+      continue;
+    }
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     const int32_t start = ch[0], mid = ch[(size_t)(L / 2) * stride], last = ch[(size_t)(L - 1) * stride];
     const int rlast = r0 + L - 1;
     const float tref = a.time[start];
     const float pad0 = a.pad[start];
+    a.cluster_track[caller_index(a, start)] = (int32_t)t;
     // y reference: the first cluster's y (rounded to FP32, in um)
     float h0, l0;
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
@@ -300,10 +326,12 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
     int used = 1, lastrow = r0;
     float pd = 0.f, tm = 0.f;
     int32_t c2 = -1;
+    // (each cluster's cluster_track entry is written when its (pad, time) is loaded)
     if (L > 1) {
       const int32_t c1 = ch[stride];
       pd = a.pad[c1];
       tm = a.time[c1];
+      a.cluster_track[caller_index(a, c1)] = (int32_t)t;
     }
     if (L > 2) c2 = ch[2 * stride];
     for (int q = 1; q < L; ++q) {
@@ -311,10 +339,13 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
       if (q + 1 < L) {
         pd = a.pad[c2];
         tm = a.time[c2];
+        a.cluster_track[caller_index(a, c2)] = (int32_t)t;
         if (q + 2 < L) c2 = ch[(size_t)(q + 2) * stride];
       }
       if (!kf_transport(k, kRowDx)) {
         status |= 2;
+        for (int e = q + 2; e < L; ++e)  // the steps not loaded yet
+          a.cluster_track[caller_index(a, ch[(size_t)e * stride])] = (int32_t)t;
         break;
       }
       kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
@@ -355,13 +386,18 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) { stage_fit(a, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
-  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
+  const uint32_t nl = min(a.ctr[kCtrTracks], a.track_list_cap);
+  const uint32_t nt = min(nl, a.track_capacity);
   const size_t stride = a.track_list_cap;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += warps) {
+  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nl; t += warps) {
     const int32_t *ch = a.chain + t;
     const int L = a.trk_len[t];
+    if (t >= nt) {  // past the record capacity: the cluster -> track entries only
+      for (int q = lane; q < L; q += 32) a.cluster_track[caller_index(a, ch[(size_t)q * stride])] = (int32_t)t;
+      continue;
+    }
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     float pv0 = 0.f, pv1 = 0.f, pv2 = 0.f, pv3 = 0.f, pv4 = 0.f;
@@ -376,6 +412,7 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
         if (q == 0) first = c;
         pq = a.pad[c];
         tq = a.time[c];
+        a.cluster_track[caller_index(a, c)] = (int32_t)t;
       }
       if (b == 0) { pv0 = pq; tv0 = tq; }
       else if (b == 1) { pv1 = pq; tv1 = tq; }

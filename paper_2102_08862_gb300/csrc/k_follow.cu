@@ -465,115 +465,152 @@ __device__ __forceinline__ float chi2_5(const float *d, const float *S) {
 
 }  // namespace
 
-// One thread per followed track: the link proposal to the track continuing it in
-// the neighbouring sector (succ reused), claimed with atomicMin in pred (reset).
-__global__ void __launch_bounds__(kThreads) k_sector_links(Args a) {
+// The link search in two kernels, so that the lanes of a warp do the same work:
+// k_sector_exit gives every followed track one thread that transports its state
+// row by row to the row where it leaves the sector's pad area (most tracks never
+// do, or after a few rows) and lists the tracks that leave it, with that state;
+// k_sector_search gives every listed track one thread for the expensive part
+// (covariance to the exit, rotation, the row-by-row search of the neighbouring
+// sector).  In one kernel a warp's few leaving tracks searched while its other
+// lanes idled (4.6 of 32 lanes active).
+__global__ void __launch_bounds__(kThreads) k_sector_exit(Args a) {
   const uint32_t nf = min(a.ctr[kCtrFollowTracks], a.track_capacity);
-  const float kCb = 0.93969262f, kSb = 0.34202014f;  // cos, sin of 20 deg
-  for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < nf; A += gridDim.x * blockDim.x) {
-    int32_t prop = -1;
-    const int rl = a.o_row_last[A];
-    if (a.o_status[A] == 0 && rl < kNRows - 1) {
-      const int sec = a.o_sector[A];
-      const float tref = a.t_ref[A];
-      Fs f;
-      fs_load_record(a, A, f);
-      // the exit row: the state alone is transported row by row; at the exit the
-      // covariance is transported from the record in one step (the Jacobian of
-      // the composed transport is the product of the per-row ones)
-      float ps[5];
+  const uint32_t n_up = (nf + 31u) & ~31u;  // whole warps, for the list's shared atomic
+  const int lane = threadIdx.x & 31;
+  for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < n_up; A += gridDim.x * blockDim.x) {
+    int exit_row = -1;
+    float ps[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (A < nf) {
+      a.fl.succ[A] = -1;
+      const int rl = a.o_row_last[A];
+      if (a.o_status[A] == 0 && rl < kNRows - 1) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) ps[i] = f.p[i];
-      int rcur = rl, exit_row = -1;
-      for (int r = rl + 1; r < kNRows && r <= rl + a.fl.link_rows; ++r) {
-        if (!fs_transport_state(ps, (float)(r - rcur) * kRowDx)) break;
-        rcur = r;
-        const float edge = 0.5f * (float)row_npads(r) * (float)row_pitch_um(r) * 1e-4f;
-        if (fabsf(ps[0]) > edge) {
-          exit_row = r;
-          break;
-        }
-      }
-      if (exit_row >= 0) {
-        if (fs_transport(f, (float)(exit_row - rl) * kRowDx)) {
-#pragma unroll
-          for (int i = 0; i < 5; ++i) f.p[i] = ps[i];
-        } else {
-          exit_row = -1;
-        }
-      }
-      // rotation into the neighbouring sector's frame
-      const float s = f.p[2];
-      if (exit_row >= 0 && fabsf(s) < 0.999f) {
-        const bool up = f.p[0] > 0.0f;
-        const float sb = up ? kSb : -kSb;
-        const float cp = sqrtf((1.0f - s) * (1.0f + s));
-        const float s2 = s * kCb - cp * sb, c2 = cp * kCb + s * sb;
-        const float x0 = row_x(exit_row);
-        if (c2 > 0.0f && fabsf(s2) < 0.999f) {
-          const float xr = x0 * kCb + f.p[0] * sb;
-          const float cv = -kBz * f.p[4];
-          float J[5][5];
-#pragma unroll
-          for (int i = 0; i < 5; ++i)
-#pragma unroll
-            for (int j = 0; j < 5; ++j) J[i][j] = i == j && i != 0 && i != 2 ? 1.0f : 0.0f;
-          J[0][0] = kCb - sb * s2 / c2;
-          J[1][0] = -f.p[3] * sb / c2;
-          J[2][0] = -cv * sb;
-          J[2][2] = c2 / cp;
-          Fs g;
-          g.p[0] = -x0 * sb + f.p[0] * kCb;
-          g.p[1] = f.p[1];
-          g.p[2] = s2;
-          g.p[3] = f.p[3];
-          g.p[4] = f.p[4];
-          float JC[5][5];
-#pragma unroll
-          for (int i = 0; i < 5; ++i)
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-              float acc = 0.0f;
-#pragma unroll
-              for (int k = 0; k < 5; ++k) acc = fmaf(J[i][k], f.c[lt(k, j)], acc);
-              JC[i][j] = acc;
-            }
-#pragma unroll
-          for (int i = 0; i < 5; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) {
-              float acc = 0.0f;
-#pragma unroll
-              for (int k = 0; k < 5; ++k) acc = fmaf(JC[i][k], J[j][k], acc);
-              g.c[lt(i, j)] = acc;
-            }
-          const int side = sec / 18, ls = sec % 18;
-          const int s2ec = side * 18 + (up ? (ls + 1) % 18 : (ls + 17) % 18);
-          int r0 = 0;
-          while (r0 < kNRows && row_x(r0) < xr) ++r0;
-          float xcur = xr;
-          for (int r = r0; r < kNRows && r < r0 + a.fl.link_rows; ++r) {
-            if (!fs_transport(g, row_x(r) - xcur)) break;
-            xcur = row_x(r);
-            int32_t B;
-            const int32_t c = fs_best_first(a, g, s2ec, r, tref, &B);
-            if (c < 0) continue;
-            if (a.o_status[B] == 0) {
-              Fs h;
-              fs_load_record(a, B, h);
-              if (fs_transport(h, row_x(r) - a.x[B])) {
-                h.p[1] += kCmPerBin * (a.t_ref[B] - tref);
-                float d[5], S[15];
-#pragma unroll
-                for (int i = 0; i < 5; ++i) d[i] = g.p[i] - h.p[i];
-#pragma unroll
-                for (int i = 0; i < 15; ++i) S[i] = g.c[i] + h.c[i];
-                const float q5 = chi2_5(d, S);
-                if (q5 >= 0.0f && q5 <= a.fl.chi2_link) prop = B;
-              }
-            }
+        for (int i = 0; i < 5; ++i) ps[i] = a.params[(size_t)A * 5 + i];
+        int rcur = rl;
+        for (int r = rl + 1; r < kNRows && r <= rl + a.fl.link_rows; ++r) {
+          if (!fs_transport_state(ps, (float)(r - rcur) * kRowDx)) break;
+          rcur = r;
+          const float edge = 0.5f * (float)row_npads(r) * (float)row_pitch_um(r) * 1e-4f;
+          if (fabsf(ps[0]) > edge) {
+            exit_row = r;
             break;
           }
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, exit_row >= 0);
+    if (m) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&a.ctr[kCtrLinkList], (uint32_t)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (exit_row >= 0) {
+        const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        a.fl.xlist[2 * (size_t)slot] = make_int4((int)A, exit_row, __float_as_int(ps[4]), 0);
+        a.fl.xlist[2 * (size_t)slot + 1] =
+            make_int4(__float_as_int(ps[0]), __float_as_int(ps[1]), __float_as_int(ps[2]), __float_as_int(ps[3]));
+      }
+    }
+  }
+}
+
+// One thread per listed track: the link proposal to the track continuing it in
+// the neighbouring sector (succ), claimed with atomicMin in pred (reset).
+__global__ void __launch_bounds__(kThreads) k_sector_search(Args a) {
+  const uint32_t nl = a.ctr[kCtrLinkList];
+  const float kCb = 0.93969262f, kSb = 0.34202014f;  // cos, sin of 20 deg
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nl; e += gridDim.x * blockDim.x) {
+    const int4 h0 = a.fl.xlist[2 * (size_t)e], h1 = a.fl.xlist[2 * (size_t)e + 1];
+    const uint32_t A = (uint32_t)h0.x;
+    int exit_row = h0.y;
+    int32_t prop = -1;
+    const int rl = a.o_row_last[A];
+    const int sec = a.o_sector[A];
+    const float tref = a.t_ref[A];
+    Fs f;
+    fs_load_record(a, A, f);
+    // the covariance is transported from the record to the exit in one step (the
+    // Jacobian of the composed transport is the product of the per-row ones); the
+    // state is the row-by-row one of the exit search
+    if (fs_transport(f, (float)(exit_row - rl) * kRowDx)) {
+      f.p[0] = __int_as_float(h1.x);
+      f.p[1] = __int_as_float(h1.y);
+      f.p[2] = __int_as_float(h1.z);
+      f.p[3] = __int_as_float(h1.w);
+      f.p[4] = __int_as_float(h0.z);
+    } else {
+      exit_row = -1;
+    }
+    // rotation into the neighbouring sector's frame
+    const float s = f.p[2];
+    if (exit_row >= 0 && fabsf(s) < 0.999f) {
+      const bool up = f.p[0] > 0.0f;
+      const float sb = up ? kSb : -kSb;
+      const float cp = sqrtf((1.0f - s) * (1.0f + s));
+      const float s2 = s * kCb - cp * sb, c2 = cp * kCb + s * sb;
+      const float x0 = row_x(exit_row);
+      if (c2 > 0.0f && fabsf(s2) < 0.999f) {
+        const float xr = x0 * kCb + f.p[0] * sb;
+        const float cv = -kBz * f.p[4];
+        float J[5][5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int j = 0; j < 5; ++j) J[i][j] = i == j && i != 0 && i != 2 ? 1.0f : 0.0f;
+        J[0][0] = kCb - sb * s2 / c2;
+        J[1][0] = -f.p[3] * sb / c2;
+        J[2][0] = -cv * sb;
+        J[2][2] = c2 / cp;
+        Fs g;
+        g.p[0] = -x0 * sb + f.p[0] * kCb;
+        g.p[1] = f.p[1];
+        g.p[2] = s2;
+        g.p[3] = f.p[3];
+        g.p[4] = f.p[4];
+        float JC[5][5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc = fmaf(J[i][k], f.c[lt(k, j)], acc);
+            JC[i][j] = acc;
+          }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int j = 0; j <= i; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc = fmaf(JC[i][k], J[j][k], acc);
+            g.c[lt(i, j)] = acc;
+          }
+        const int side = sec / 18, ls = sec % 18;
+        const int s2ec = side * 18 + (up ? (ls + 1) % 18 : (ls + 17) % 18);
+        int r0 = 0;
+        while (r0 < kNRows && row_x(r0) < xr) ++r0;
+        float xcur = xr;
+        for (int r = r0; r < kNRows && r < r0 + a.fl.link_rows; ++r) {
+          if (!fs_transport(g, row_x(r) - xcur)) break;
+          xcur = row_x(r);
+          int32_t B;
+          const int32_t c = fs_best_first(a, g, s2ec, r, tref, &B);
+          if (c < 0) continue;
+          if (a.o_status[B] == 0) {
+            Fs h;
+            fs_load_record(a, B, h);
+            if (fs_transport(h, row_x(r) - a.x[B])) {
+              h.p[1] += kCmPerBin * (a.t_ref[B] - tref);
+              float d[5], S[15];
+#pragma unroll
+              for (int i = 0; i < 5; ++i) d[i] = g.p[i] - h.p[i];
+#pragma unroll
+              for (int i = 0; i < 15; ++i) S[i] = g.c[i] + h.c[i];
+              const float q5 = chi2_5(d, S);
+              if (q5 >= 0.0f && q5 <= a.fl.chi2_link) prop = B;
+            }
+          }
+          break;
         }
       }
     }
@@ -591,7 +628,8 @@ __global__ void __launch_bounds__(kThreads) k_sector_links_resolve(Args a) {
 }
 
 void launch_sector_links(const Args &a, int sms, cudaStream_t st) {
-  k_sector_links<<<sms * 4, kThreads, 0, st>>>(a);
+  k_sector_exit<<<sms * 4, kThreads, 0, st>>>(a);
+  k_sector_search<<<sms * 4, kThreads, 0, st>>>(a);
   k_sector_links_resolve<<<sms * 4, kThreads, 0, st>>>(a);
 }
 

@@ -14,9 +14,14 @@
 // decoupled look-back across tiles.  k_walk gives each start hit one thread: it
 // follows the chain n_min - 1 links to decide whether it is a track, takes its
 // track id from a second ordered compaction, then walks the whole chain writing
-// cluster_track and the chain's cluster positions as [step][track], so the fit
-// reads them coalesced with no pointer chasing.  Isolated clusters and members
-// of short chains get cluster_track = -1, so every entry is written exactly once.
+// the chain's cluster positions as [step][track], so the fit reads them coalesced
+// with no pointer chasing.  Isolated clusters (here) and members of short chains
+// (in the walk) get cluster_track = -1; members of tracks get their id from the
+// fit, which reads every chain step anyway, so every entry is written exactly
+// once.  The 4-byte cluster_track stores land on scattered rows and each partly
+// fills a 32-byte sector that the memory must read back; in the latency-bound
+// walk they cost 0.21 of its 0.38 ms on the 10 ms frame, in the issue-bound fit
+// about 0.13 ms.
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -138,8 +143,8 @@ __device__ __forceinline__ void stage_links(const Args &a) {
 // A4: one start hit per thread (kWalkChains; walking two or four chains per
 // thread interleaved was slower: more threads hide the pointer chase better).
 // Chains that reach n_min clusters become tracks (ids in start order); their
-// clusters get the track id and are recorded in the chain buffer; the clusters of
-// shorter chains get -1.
+// clusters are recorded in the chain buffer (the fit writes their cluster_track
+// entries); the clusters of shorter chains get -1 here.
 template <bool kSmemRb>
 __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
@@ -226,8 +231,8 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
         if (kept[q] && id[q] >= a.track_list_cap) raise(a.ctr, kErrCapacity);
         w[q] = st[q].x >= 0 && (!kept[q] || id[q] < a.track_list_cap);
         v[q] = kept[q] ? (int32_t)id[q] : -1;
-        // second walk: members of tracks get the id and go to the chain buffer,
-        // members of short chains get -1
+        // second walk: members of tracks go to the chain buffer (the fit gives
+        // them their cluster_track entry), members of short chains get -1
         c[q] = w[q] ? st[q].x : -1;
         kk[q] = st[q].y;
       }
@@ -239,7 +244,7 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
         if (c[q] >= 0) {
           any = true;
           if (kept[q]) __stcs(a.chain + (size_t)m * stride + id[q], c[q]);
-          __stcs(a.cluster_track + caller_index(a, c[q]), v[q]);
+          else __stcs(a.cluster_track + caller_index(a, c[q]), v[q]);
           if (m + 1 < (kept[q] ? kNRows : len[q])) next(c[q], kk[q]); else c[q] = -1;
           if (c[q] < 0 && kept[q]) a.trk_len[id[q]] = m + 1;
         }

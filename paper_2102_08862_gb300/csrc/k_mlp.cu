@@ -436,15 +436,17 @@ __global__ void k_mlp_pack(const float *__restrict__ theta, const float *__restr
 // One CTA of 128 threads scores 128 rows at a time on the fifth-generation tensor
 // cores: thread r writes row r's standardised BF16 inputs in the core-matrix
 // layout; one tcgen05.mma (M 128, N 64, K 16) puts layer 1 in tensor memory (64
-// FP32 columns); each thread loads its row back (tcgen05.ld), adds the bias,
-// applies ReLU, rounds to BF16 and writes the row of H1; four MMAs (K 64) give
-// layer 2; each thread finishes its row's logit in FP32.  Completion of the MMAs
-// is signalled through an mbarrier (bounded wait).
+// FP32 columns); each thread loads its row back (tcgen05.ld, 32 columns per
+// load), adds the bias, applies ReLU, rounds to BF16 and writes the row of H1;
+// four MMAs (K 64) give layer 2; each thread finishes its row's logit in FP32.
+// The epilogues work on column pairs (packed FP32 adds and FMAs, one BF16x2
+// conversion per pair).  Completion of the MMAs is signalled through an mbarrier
+// (bounded wait).
 struct __align__(1024) TcMlpSmem {
-  unsigned char x[128 * 16 * 2];   // inputs, core-matrix layout (K 16)
-  unsigned char h[128 * 64 * 2];   // first hidden layer (K 64)
-  unsigned char w1[64 * 16 * 2];   // W1 (N 64, K 16)
-  unsigned char w2[64 * 64 * 2];   // W2 (N 64, K 64)
+  unsigned char x[2][128 * 16 * 2];   // inputs of the two tiles, core-matrix layout (K 16)
+  unsigned char h[2][128 * 64 * 2];   // their first hidden layers (K 64)
+  unsigned char w1[64 * 16 * 2];      // W1 (N 64, K 16)
+  unsigned char w2[64 * 64 * 2];      // W2 (N 64, K 64)
   float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
   uint64_t mbar;
   uint32_t tmem;
@@ -473,74 +475,81 @@ __device__ __forceinline__ void tc_stage_weights(TcMlpSmem &sm, const MlpW *__re
   }
 }
 
-// thread r's input row: 16 standardised BF16 values (12 + 4 zeros), or zeros
-__device__ __forceinline__ void tc_put_input(TcMlpSmem &sm, int r, const float *f, bool valid) {
-  __align__(16) __nv_bfloat16 v[16];
+// row r's input in the tile at x: 16 standardised BF16 values (12 + 4 zeros), or zeros
+__device__ __forceinline__ void tc_put_input(unsigned char *x, const float *mean, const float *inv_std, int r,
+                                             const float *f, bool valid) {
+  uint32_t w[8];
 #pragma unroll
-  for (int c = 0; c < 16; ++c)
-    v[c] = (valid && c < kMlpIn) ? __float2bfloat16_rn(__fmul_rn(__fsub_rn(f[c], sm.mean[c]), sm.inv_std[c]))
-                                 : __float2bfloat16_rn(0.0f);
-  *reinterpret_cast<uint4 *>(sm.x + core_offset(r, 0, 16)) = reinterpret_cast<const uint4 *>(v)[0];
-  *reinterpret_cast<uint4 *>(sm.x + core_offset(r, 8, 16)) = reinterpret_cast<const uint4 *>(v)[1];
+  for (int p = 0; p < 8; ++p) {
+    const int c = 2 * p;
+    uint32_t h = 0;
+    if (valid && c < kMlpIn) {
+      const float lo = __fmul_rn(__fsub_rn(f[c], mean[c]), inv_std[c]);
+      const float hi = __fmul_rn(__fsub_rn(f[c + 1], mean[c + 1]), inv_std[c + 1]);
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
+    }
+    w[p] = h;
+  }
+  *reinterpret_cast<uint4 *>(x + core_offset(r, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4 *>(x + core_offset(r, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-// The two tensor-core layers for the 128 rows staged in sm.x; returns thread r's
-// logit (false if a bounded wait gave up).
-__device__ __forceinline__ bool tc_mlp_rows(TcMlpSmem &sm, uint32_t tmem, float b3, float &logit) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid == 0) {
-    tc_mma_bf16(tmem, tc_desc(smem_u32(sm.x), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), tc_idesc_bf16(128, 64),
-                false);
-    tc_commit(&sm.mbar);
-  }
-  bool ok = mbar_wait(&sm.mbar, 0, 1u << 22);
-  tc_fence_after();
-  float z[16];
-  if (ok) {
+// Epilogue of the first layer for the row in this thread's tensor-memory lane:
+// columns [0, 64) + b1, ReLU, BF16, written as row hr of the K = 64 core-matrix
+// operand at hb.  Pairs of columns go through packed FP32 adds and one
+// conversion + max per BF16 pair.
+__device__ __forceinline__ void tc_epi_hidden(uint32_t lane_addr, const float *b1, unsigned char *hb, int hr) {
+  uint32_t z[32];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      tc_ld16(lane_base + 16 * q, z);
-      tc_wait_ld();
-      __align__(16) __nv_bfloat16 hv[16];
+  for (int hf = 0; hf < 2; ++hf) {
+    tc_ld32(lane_addr + 32u * hf, z);
+    tc_wait_ld();
 #pragma unroll
-      for (int c = 0; c < 16; ++c) hv[c] = __float2bfloat16_rn(fmaxf(z[c] + sm.b1[16 * q + c], 0.f));
-      *reinterpret_cast<uint4 *>(sm.h + core_offset(tid, 16 * q, 64)) = reinterpret_cast<const uint4 *>(hv)[0];
-      *reinterpret_cast<uint4 *>(sm.h + core_offset(tid, 16 * q + 8, 64)) = reinterpret_cast<const uint4 *>(hv)[1];
+    for (int g = 0; g < 4; ++g) {  // 8 columns: one 16-byte row of a core matrix
+      const float4 ba = *reinterpret_cast<const float4 *>(b1 + 32 * hf + 8 * g);
+      const float4 bb = *reinterpret_cast<const float4 *>(b1 + 32 * hf + 8 * g + 4);
+      const uint32_t bw[8] = {__float_as_uint(ba.x), __float_as_uint(ba.y), __float_as_uint(ba.z),
+                              __float_as_uint(ba.w), __float_as_uint(bb.x), __float_as_uint(bb.y),
+                              __float_as_uint(bb.z), __float_as_uint(bb.w)};
+      uint32_t w[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int c = 8 * g + 2 * p;
+        w[p] = bf16x2_relu(f2_add(f2_pack(z[c], z[c + 1]), f2_pack(bw[2 * p], bw[2 * p + 1])));
+      }
+      *reinterpret_cast<uint4 *>(hb + core_offset(hr, 32 * hf + 8 * g, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
-  fence_async_smem();
-  tc_fence_before();
-  ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
-  tc_fence_after();
-  if (tid == 0 && ok) {
-    const uint32_t h0 = smem_u32(sm.h), w0 = smem_u32(sm.w2);
+}
+
+// Epilogue of the second layer: b3 + sum_c w3[c] max(z[c] + b2[c], 0) over the
+// 64 columns of this thread's lane (two packed FP32 accumulators)
+__device__ __forceinline__ float tc_epi_logit(uint32_t lane_addr, const float *b2, const float *w3, float b3) {
+  uint32_t z[32];
+  uint64_t acc = 0;
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      tc_mma_bf16(tmem, tc_desc(h0 + 256 * s, 128, 1024), tc_desc(w0 + 256 * s, 128, 1024), tc_idesc_bf16(128, 64),
-                  s > 0);
-    tc_commit(&sm.mbar);
-  }
-  if (ok) ok = mbar_wait(&sm.mbar, 1, 1u << 22);
-  tc_fence_after();
-  float acc = b3;
-  if (ok) {
+  for (int hf = 0; hf < 2; ++hf) {
+    tc_ld32(lane_addr + 32u * hf, z);
+    tc_wait_ld();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      tc_ld16(lane_base + 16 * q, z);
-      tc_wait_ld();
+    for (int g = 0; g < 8; ++g) {
+      const float4 bq = *reinterpret_cast<const float4 *>(b2 + 32 * hf + 4 * g);
+      const float4 wq = *reinterpret_cast<const float4 *>(w3 + 32 * hf + 4 * g);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc = fmaf(fmaxf(z[c] + sm.b2[16 * q + c], 0.f), sm.w3[16 * q + c], acc);
+      for (int p = 0; p < 2; ++p) {
+        const int c = 4 * g + 2 * p;
+        const uint64_t v = f2_add(f2_pack(z[c], z[c + 1]),
+                                  p ? f2_pack(__float_as_uint(bq.z), __float_as_uint(bq.w))
+                                    : f2_pack(__float_as_uint(bq.x), __float_as_uint(bq.y)));
+        const float lo = fmaxf(__uint_as_float((uint32_t)v), 0.f), hi = fmaxf(__uint_as_float((uint32_t)(v >> 32)), 0.f);
+        acc = f2_fma(f2_pack(__float_as_uint(lo), __float_as_uint(hi)),
+                     p ? f2_pack(__float_as_uint(wq.z), __float_as_uint(wq.w))
+                       : f2_pack(__float_as_uint(wq.x), __float_as_uint(wq.y)),
+                     acc);
+      }
     }
   }
-  tc_fence_before();
-  __syncthreads();  // sm.x, sm.h and the accumulators are free again
-  logit = acc;
-  return __syncthreads_and(ok);
+  return b3 + (__uint_as_float((uint32_t)acc) + __uint_as_float((uint32_t)(acc >> 32)));
 }
 
 // Rows of the neighbour tiles' regions on the tcgen05 path.  A CTA of 256
@@ -647,15 +656,21 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
           sm.pk[tid] = q.z;
         }
         {  // input row (zeros past the batch)
-          __align__(16) __nv_bfloat16 v[16];
+          uint32_t w[8];
 #pragma unroll
-          for (int cc = 0; cc < 16; ++cc)
-            v[cc] = (mine && cc < kMlpIn)
-                        ? __float2bfloat16_rn(__fmul_rn(__fsub_rn(f[cc], sm.mean[cc]), sm.inv_std[cc]))
-                        : __float2bfloat16_rn(0.0f);
+          for (int p = 0; p < 8; ++p) {
+            const int cc = 2 * p;
+            uint32_t h = 0;
+            if (mine && cc < kMlpIn) {
+              const float lo = __fmul_rn(__fsub_rn(f[cc], sm.mean[cc]), sm.inv_std[cc]);
+              const float hi = __fmul_rn(__fsub_rn(f[cc + 1], sm.mean[cc + 1]), sm.inv_std[cc + 1]);
+              asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
+            }
+            w[p] = h;
+          }
           unsigned char *xb = sm.x + 4096 * half;
-          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 0, 16)) = reinterpret_cast<const uint4 *>(v)[0];
-          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 8, 16)) = reinterpret_cast<const uint4 *>(v)[1];
+          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
         const bool two = rows > 128;  // second half in use
         // layer 1
@@ -669,24 +684,10 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
                         tc_desc(smem_u32(sm.w1), 128, 256), idesc, false);
           tc_commit(&sm.mbar);
         }
-        ok = mbar_wait(&sm.mbar, phase, a.spin_limit);
+        ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, phase, a.spin_limit));
         phase ^= 1u;
         tc_fence_after();
-        float z[16];
-        if (ok && (half == 0 || two)) {
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            tc_ld16(lane_base + 16 * qq, z);
-            tc_wait_ld();
-            __align__(16) __nv_bfloat16 hv[16];
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc) hv[cc] = __float2bfloat16_rn(fmaxf(z[cc] + sm.b1[16 * qq + cc], 0.f));
-            unsigned char *hb = sm.h + 16384 * half;
-            *reinterpret_cast<uint4 *>(hb + core_offset(hr, 16 * qq, 64)) = reinterpret_cast<const uint4 *>(hv)[0];
-            *reinterpret_cast<uint4 *>(hb + core_offset(hr, 16 * qq + 8, 64)) =
-                reinterpret_cast<const uint4 *>(hv)[1];
-          }
-        }
+        if (ok && (half == 0 || two)) tc_epi_hidden(lane_base, sm.b1, sm.h + 16384 * half, hr);
         fence_async_smem();
         tc_fence_before();
         ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
@@ -702,20 +703,10 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
           }
           tc_commit(&sm.mbar);
         }
-        ok = mbar_wait(&sm.mbar, phase, a.spin_limit);
+        ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, phase, a.spin_limit));
         phase ^= 1u;
         tc_fence_after();
-        float acc = b3;
-        if (ok && (half == 0 || two)) {
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            tc_ld16(lane_base + 16 * qq, z);
-            tc_wait_ld();
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc) acc = fmaf(fmaxf(z[cc] + sm.b2[16 * qq + cc], 0.f), sm.w3[16 * qq + cc], acc);
-          }
-        }
-        sm.lg[tid] = acc;
+        sm.lg[tid] = (ok && (half == 0 || two)) ? tc_epi_logit(lane_base, sm.b2, sm.w3, b3) : b3;
         tc_fence_before();
         ok = __syncthreads_and(ok);
         if (!ok) break;
@@ -750,37 +741,95 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
   if (warp == 0) tc_dealloc(tmem, 128);
 }
 
-// logits of raw feature rows (float[m][12]) on the tcgen05 path
-__global__ void __launch_bounds__(128) k_mlp_score_tc(const MlpW *__restrict__ W, const float *__restrict__ feat,
-                                                      uint32_t m, float *__restrict__ logit, int *err) {
+// logits of raw feature rows (float[m][12]) on the tcgen05 path.  A CTA of 128
+// threads takes two 128-row tiles per step (thread r holds row r of both; tile h
+// accumulates in tensor-memory columns 64 h ..): both tiles' MMAs of a layer are
+// issued together and complete behind one mbarrier wait, so each wait and CTA
+// barrier serves 256 rows; the next step's features are loaded while the current
+// step runs.  4 CTAs share an SM (tensor memory: 4 x 128 of 512 columns).
+__global__ void __launch_bounds__(128, 4) k_mlp_score_tc(const MlpW *__restrict__ W, const float *__restrict__ feat,
+                                                         uint32_t m, float *__restrict__ logit, int *err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   TcMlpSmem &sm = *reinterpret_cast<TcMlpSmem *>(smraw);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   tc_stage_weights(sm, W);
   if (tid == 0) mbar_init(&sm.mbar, 1);
-  if ((tid >> 5) == 0) tc_alloc(&sm.tmem, 64);
+  if (warp == 0) tc_alloc(&sm.tmem, 128);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem;
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
   const float b3 = W->b3;
-  const uint32_t tiles = (m + 127) / 128;
-  for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const uint32_t row = t * 128 + tid;
-    float f[kMlpIn];
-    load_feature_row(feat, row, m, f);
-    tc_put_input(sm, tid, f, row < m);
-    float lg;
-    if (!tc_mlp_rows(sm, tmem, b3, lg)) {
-      if (tid == 0) atomicOr(err, (int)kErrTimeout);
-      break;
-    }
-    if (row < m) logit[row] = lg;
+  const uint32_t steps = (m + 255) / 256;
+  const uint32_t idesc = tc_idesc_bf16(128, 64);
+  float fa[kMlpIn], fb[kMlpIn];
+  if (blockIdx.x < steps) {
+    load_feature_row(feat, blockIdx.x * 256 + tid, m, fa);
+    load_feature_row(feat, blockIdx.x * 256 + 128 + tid, m, fb);
   }
+  bool ok = true;
+  for (uint32_t u = blockIdx.x; u < steps && ok; u += gridDim.x) {
+    const uint32_t ra = u * 256 + tid, rb = ra + 128;
+    tc_put_input(sm.x[0], sm.mean, sm.inv_std, tid, fa, ra < m);
+    tc_put_input(sm.x[1], sm.mean, sm.inv_std, tid, fb, rb < m);
+    if (u + gridDim.x < steps) {  // the next step's rows
+      load_feature_row(feat, (u + gridDim.x) * 256 + tid, m, fa);
+      load_feature_row(feat, (u + gridDim.x) * 256 + 128 + tid, m, fb);
+    }
+    // layer 1: X (128 x 16) W1^T of both tiles
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        tc_mma_bf16(tmem + 64u * h, tc_desc(smem_u32(sm.x[h]), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), idesc,
+                    false);
+      tc_commit(&sm.mbar);
+    }
+    ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, 0, 1u << 22));  // warp-uniform (tcgen05.ld)
+    tc_fence_after();
+    if (ok) {
+      tc_epi_hidden(lane_addr, sm.b1, sm.h[0], tid);
+      tc_epi_hidden(lane_addr + 64u, sm.b1, sm.h[1], tid);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
+    tc_fence_after();
+    if (!ok) break;
+    // layer 2: H1 (128 x 64) W2^T of both tiles, four K = 16 steps each
+    if (tid == 0) {
+      const uint32_t w0 = smem_u32(sm.w2);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t h0 = smem_u32(sm.h[h]);
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4)
+          tc_mma_bf16(tmem + 64u * h, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), idesc,
+                      k4 > 0);
+      }
+      tc_commit(&sm.mbar);
+    }
+    ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, 1, 1u << 22));
+    tc_fence_after();
+    float la = 0.f, lb = 0.f;
+    if (ok) {
+      la = tc_epi_logit(lane_addr, sm.b2, sm.w3, b3);
+      lb = tc_epi_logit(lane_addr + 64u, sm.b2, sm.w3, b3);
+    }
+    tc_fence_before();
+    ok = __syncthreads_and(ok);  // sm.x, sm.h and the accumulators are free again
+    if (ok && ra < m) logit[ra] = la;
+    if (ok && rb < m) logit[rb] = lb;
+  }
+  if (!ok && tid == 0) atomicOr(err, (int)kErrTimeout);
   tc_fence_before();
   __syncthreads();
-  if ((tid >> 5) == 0) tc_dealloc(tmem, 64);
+  if (warp == 0) tc_dealloc(tmem, 128);
 }
 
 // ------------------------------------------------------------------ scoring
@@ -944,10 +993,10 @@ int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *log
       return -1;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  // at most 7 CTAs fit an SM (31 KB of shared memory each), so their 64-column
-  // tensor-memory allocations (512 columns per SM) never wait on each other
-  const uint32_t tiles = (m + 127) / 128;
-  const uint32_t grid = tiles < (uint32_t)sms * 4 ? tiles : (uint32_t)sms * 4;
+  // 4 CTAs per SM (52 KB of shared memory each): their 128-column tensor-memory
+  // allocations (512 columns per SM) never wait on each other
+  const uint32_t steps = (m + 255) / 256;
+  const uint32_t grid = steps < (uint32_t)sms * 4 ? steps : (uint32_t)sms * 4;
   k_mlp_score_tc<<<grid, 128, mlp_score_tc_smem(), st>>>(w, feat, m, logit, err);
   return 0;
 }

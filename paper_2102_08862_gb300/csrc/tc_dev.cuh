@@ -104,4 +104,35 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (row), as raw
+// bits; complete after tc_wait_ld()
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// packed pairs: (a.lo + b.lo, a.hi + b.hi) and (a * b + c) per lane, IEEE FP32
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo, uint32_t hi) { return (uint64_t)lo | ((uint64_t)hi << 32); }
+// max(bf16(lo), 0), max(bf16(hi), 0) packed as bf16x2 (lo in the low half); a NaN
+// gives 0, like a ReLU written as x > 0 ? x : 0
+__device__ __forceinline__ uint32_t bf16x2_relu(uint64_t v) {
+  uint32_t h, z;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "r"((uint32_t)(v >> 32)), "r"((uint32_t)v));
+  asm("max.bf16x2 %0, %1, %2;" : "=r"(z) : "r"(h), "r"(0u));
+  return z;
+}
+
 }  // namespace tpc

@@ -80,6 +80,7 @@ enum : int {
   kCtrFollowPathTile = 16,  // track follower: next tile of joined paths
   kCtrBarCount = 17,        // persistent kernel: CTAs arrived at the current grid barrier
   kCtrBarGen = 18,          // persistent kernel: grid barriers passed
+  kCtrLinkList = 19,        // cross-sector links: tracks that leave their sector (searched)
   kNCounters = 20
 };
 
@@ -155,6 +156,7 @@ struct Args {
     float chi2_link;    // cross-sector links (follow = 2)
     int32_t link_rows;
     int32_t *next;      // [track_capacity] caller's next_track, nullptr when not asked
+    int4 *xlist;        // [track_list_cap][2] tracks that leave their sector: (A, exit row, -, -), state at the exit
   } fl;
 };
 // rows of a neighbour tile's region in pruned mode

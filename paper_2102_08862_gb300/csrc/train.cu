@@ -22,6 +22,7 @@
 
 #include "../../include/tpcca.h"
 #include "mlp_dev.cuh"
+#include "tc_dev.cuh"
 #include "tpc_internal.h"
 
 using namespace tpc;
@@ -302,6 +303,361 @@ __global__ void __launch_bounds__(kTrWarps * 32) k_train_fwd_bwd(const float *__
   }
 }
 
+// ------------------------------------------------ tcgen05 forward/backward
+// The same step on the fifth-generation tensor cores.  A CTA of 128 threads takes
+// 128-row tiles (thread r holds row r); per tile four groups of tcgen05.mma (M
+// 128, BF16 operands staged in shared memory in the no-swizzle K-major
+// core-matrix layout, FP32 accumulators in tensor memory), each followed by a
+// tcgen05.ld epilogue of the thread's row:
+//   Z1 = X W1^T     -> H1 = relu(Z1 + b1) (BF16; the ReLU mask kept in registers)
+//   Z2 = H1 W2^T    -> logit, loss, dl; dZ2 = (Z2 + b2 > 0) dl w3 (BF16)
+//   dH1 = dZ2 W2    -> dZ1 = mask1 dH1 (BF16)
+//   G += [dZ2^T; dZ1^T] [H1 | X | 1]^T   (M 128 = 64 + 64 units, N 96, K = the rows)
+// The last product stacks both weight gradients (and, through a column of ones,
+// both bias gradients) into one M = 128 accumulation that stays in tensor memory
+// across the CTA's tiles: G[o][i] = dW2[o][i], G[o][80] = db2[o], G[64 + u][64 + c]
+// = dW1[u][c], G[64 + u][80] = db1[u]; its off-diagonal blocks are computed and
+// ignored.  The transposed operands are written by the threads, two rows per
+// 32-bit word (a lane pair swaps halves through a shuffle).  dw3 = sum_r dl h2 is
+// reduced over each warp's rows by a butterfly (each lane ends with two of the 64
+// sums) and kept in registers across tiles.  Each CTA writes its partial to its own
+// slot, as in the mma.sync kernel, so a step is bitwise reproducible.
+constexpr int kTcTrRows = 128;
+constexpr int kTcGN = 96;  // columns of the gradient accumulation: 64 (H1) + 16 (X, 12 used) + 16 (ones at 80)
+struct __align__(1024) TrainTcSmem {
+  unsigned char x[kTcTrRows * 16 * 2];    // X (K 16)
+  unsigned char w1[kMlpH * 16 * 2];       // W1 (N 64, K 16)
+  unsigned char w2[kMlpH * kMlpH * 2];    // W2 (N 64, K 64)
+  unsigned char w2t[kMlpH * kMlpH * 2];   // W2^T (N 64, K 64): dH1 = dZ2 W2
+  unsigned char hd[kTcTrRows * kMlpH * 2];  // H1 (K 64) for layer 2, then dZ2 (K 64) for dH1
+  unsigned char ag[128 * kTcTrRows * 2];  // [dZ2^T; dZ1^T] (M 128, K = rows)
+  unsigned char bg[kTcGN * kTcTrRows * 2];  // [H1^T; X^T; ones] (N 96, K = rows)
+  float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
+  float gw3[kTrWarps][kMlpH];
+  float gb3[kTrWarps], loss[kTrWarps];
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+// bf16 bits of v
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// Row pairs into a transposed K-major operand (K = the tile's rows): lane pair
+// (2j, 2j + 1) holds rows r, r + 1 and columns n, n + 1 (BF16 bits lo16 = column
+// n, hi16 = column n + 1); the even lane writes column n's word (rows r, r + 1),
+// the odd lane column n + 1's.
+__device__ __forceinline__ void tc_put_t2(unsigned char *base, int n, int r, uint32_t pair, int lane) {
+  const bool odd = lane & 1;
+  const uint32_t give = odd ? (pair & 0xffffu) : (pair >> 16);  // the column the partner writes
+  const uint32_t got = __shfl_xor_sync(0xffffffffu, give, 1);
+  const uint32_t word = odd ? (got | (pair & 0xffff0000u)) : ((pair & 0xffffu) | (got << 16));
+  const int rr = r & ~1, nn = n + (odd ? 1 : 0);
+  *reinterpret_cast<uint32_t *>(base + core_offset(nn, rr, kTcTrRows)) = word;
+}
+
+__global__ void __launch_bounds__(kTcTrRows) k_train_fwd_bwd_tc(const float *__restrict__ feat,
+                                                               const uint8_t *__restrict__ label,
+                                                               const int32_t *__restrict__ idx, uint32_t B,
+                                                               const MlpW *__restrict__ W, float pos_weight,
+                                                               float inv_B, float *__restrict__ partial,
+                                                               uint32_t *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smraw_[];
+  TrainTcSmem &sm = *reinterpret_cast<TrainTcSmem *>(
+      (reinterpret_cast<uintptr_t>(smraw_) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // ---- weights, constant rows of the gradient operand
+  for (int e = tid; e < kMlpH * 2; e += blockDim.x) {
+    const int n = e >> 1, g = e & 1;
+    *reinterpret_cast<uint4 *>(sm.w1 + core_offset(n, 8 * g, 16)) =
+        *reinterpret_cast<const uint4 *>(W->w1 + n * kXS + 8 * g);
+  }
+  for (int e = tid; e < kMlpH * 8; e += blockDim.x) {
+    const int n = e >> 3, g = e & 7;
+    *reinterpret_cast<uint4 *>(sm.w2 + core_offset(n, 8 * g, 64)) =
+        *reinterpret_cast<const uint4 *>(W->w2 + n * kW2S + 8 * g);
+    *reinterpret_cast<uint4 *>(sm.w2t + core_offset(n, 8 * g, 64)) =
+        *reinterpret_cast<const uint4 *>(W->w2t + n * kW2S + 8 * g);
+  }
+  for (int e = tid; e < kMlpH; e += blockDim.x) {
+    sm.b1[e] = W->b1[e];
+    sm.b2[e] = W->b2[e];
+    sm.w3[e] = W->w3[e];
+  }
+  for (int e = tid; e < kMlpIn; e += blockDim.x) {
+    sm.mean[e] = W->mean[e];
+    sm.inv_std[e] = W->inv_std[e];
+  }
+  for (int e = tid; e < (int)sizeof(sm.bg) / 16; e += blockDim.x)  // rows 76-95 stay zero except the ones row
+    reinterpret_cast<uint4 *>(sm.bg)[e] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) mbar_init(&sm.mbar, 1);
+  if (warp == 0) tc_alloc(&sm.tmem, 256);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  const uint32_t zl = tmem + ((uint32_t)(32 * warp) << 16);  // this thread's lane, columns 0-63: Z
+  const uint32_t tg = tmem + 128u;                            // columns 128-223: G
+  const float b3 = W->b3;
+  const uint32_t id16 = tc_idesc_bf16(128, 64), idg = tc_idesc_bf16(128, kTcGN);
+  float gw3a = 0.f, gw3b = 0.f, gb3 = 0.f, lossa = 0.f;  // dw3 of columns o3, o3 + 1 over this warp's rows
+  const int o3 = 2 * lane;  // the two columns the butterfly leaves with this lane
+  uint32_t phase = 0;
+  bool ok = true, any = false;
+  auto mma_wait = [&]() {  // warp-uniform result: the tcgen05.ld that follow are warp-collective
+    const bool r = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, phase, 1u << 22));
+    phase ^= 1u;
+    tc_fence_after();
+    return r;
+  };
+  const uint32_t tiles = (B + kTcTrRows - 1) / kTcTrRows;
+  for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    const uint32_t row = t * kTcTrRows + tid;
+    const bool valid = row < B;
+    const uint32_t src = valid ? (idx ? (uint32_t)idx[row] : row) : 0u;
+    // ---- inputs (the previous tile's gradient MMA reads bg and ag: wait for it)
+    float xf[kMlpIn];
+#pragma unroll
+    for (int c = 0; c < kMlpIn; ++c) xf[c] = valid ? __ldg(feat + (size_t)src * kMlpIn + c) : 0.f;
+    if (any) ok = mma_wait();
+    uint32_t xp[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const int c = 2 * p;
+      xp[p] = (valid && c < kMlpIn)
+                  ? (bf16_bits(__fmul_rn(__fsub_rn(xf[c], sm.mean[c]), sm.inv_std[c])) |
+                     (bf16_bits(__fmul_rn(__fsub_rn(xf[c + 1], sm.mean[c + 1]), sm.inv_std[c + 1])) << 16))
+                  : 0u;
+    }
+    *reinterpret_cast<uint4 *>(sm.x + core_offset(tid, 0, 16)) = make_uint4(xp[0], xp[1], xp[2], xp[3]);
+    *reinterpret_cast<uint4 *>(sm.x + core_offset(tid, 8, 16)) = make_uint4(xp[4], xp[5], xp[6], xp[7]);
+#pragma unroll
+    for (int p = 0; p < kMlpIn / 2; ++p) tc_put_t2(sm.bg, kMlpH + 2 * p, tid, xp[p], lane);
+    *reinterpret_cast<uint16_t *>(sm.bg + core_offset(80, tid, kTcTrRows)) = valid ? 0x3f80u : 0u;  // 1.0
+    // ---- layer 1
+    fence_async_smem();
+    tc_fence_before();
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (!ok) break;
+    if (tid == 0) {
+      tc_mma_bf16(tmem, tc_desc(smem_u32(sm.x), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), id16, false);
+      tc_commit(&sm.mbar);
+    }
+    ok = mma_wait();
+    uint32_t m1a = 0, m1b = 0;  // ReLU mask of Z1, columns 0-31 and 32-63
+    if (ok) {
+      uint32_t z[32];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        tc_ld32(zl + 32u * hf, z);
+        tc_wait_ld();
+        uint32_t m = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = 8 * g + 2 * q, col = 32 * hf + c;
+            const float v0 = __uint_as_float(z[c]) + sm.b1[col], v1 = __uint_as_float(z[c + 1]) + sm.b1[col + 1];
+            m |= (v0 > 0.f ? 1u : 0u) << c;
+            m |= (v1 > 0.f ? 1u : 0u) << (c + 1);
+            w[q] = bf16_bits(fmaxf(v0, 0.f)) | (bf16_bits(fmaxf(v1, 0.f)) << 16);
+            tc_put_t2(sm.bg, col, tid, w[q], lane);
+          }
+          *reinterpret_cast<uint4 *>(sm.hd + core_offset(tid, 32 * hf + 8 * g, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        if (hf == 0) m1a = m; else m1b = m;
+      }
+    }
+    // ---- layer 2 and the output
+    fence_async_smem();
+    tc_fence_before();
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (!ok) break;
+    if (tid == 0) {
+      const uint32_t h0 = smem_u32(sm.hd), w0 = smem_u32(sm.w2);
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4)
+        tc_mma_bf16(tmem, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), id16, k4 > 0);
+      tc_commit(&sm.mbar);
+    }
+    ok = mma_wait();
+    float dl = 0.f;
+    if (ok) {
+      uint32_t z[32];
+      float acc = b3;
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        tc_ld32(zl + 32u * hf, z);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc = fmaf(fmaxf(__uint_as_float(z[c]) + sm.b2[32 * hf + c], 0.f), sm.w3[32 * hf + c], acc);
+      }
+      const float y = (valid && label[src]) ? 1.f : 0.f, wt = y > 0.f ? pos_weight : 1.f;
+      dl = valid ? wt * (1.f / (1.f + expf(-acc)) - y) * inv_B : 0.f;
+      if (valid) lossa += wt * (fmaxf(acc, 0.f) + log1pf(expf(-fabsf(acc))) - y * acc) * inv_B;
+      gb3 += dl;
+      // dZ2 (BF16) for dH1 and for the gradient product; dw3 = dl h2 reduced over the warp
+      float r32[32];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        tc_ld32(zl + 32u * hf, z);
+        tc_wait_ld();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = 8 * g + 2 * q, col = 32 * hf + c;
+            const float v0 = __uint_as_float(z[c]) + sm.b2[col], v1 = __uint_as_float(z[c + 1]) + sm.b2[col + 1];
+            const float d0 = v0 > 0.f ? dl * sm.w3[col] : 0.f, d1 = v1 > 0.f ? dl * sm.w3[col + 1] : 0.f;
+            w[q] = bf16_bits(d0) | (bf16_bits(d1) << 16);
+            tc_put_t2(sm.ag, col, tid, w[q], lane);
+            // butterfly, first step: lanes with bit 4 keep columns 32-63, the others 0-31
+            const float h0 = dl * fmaxf(v0, 0.f), h1 = dl * fmaxf(v1, 0.f);
+            if (hf == 0) {
+              r32[c] = h0;
+              r32[c + 1] = h1;
+            } else {
+              const bool hi = lane & 16;
+              const float k0 = hi ? h0 : r32[c], s0 = hi ? r32[c] : h0;
+              const float k1 = hi ? h1 : r32[c + 1], s1 = hi ? r32[c + 1] : h1;
+              r32[c] = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+              r32[c + 1] = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+            }
+          }
+          *reinterpret_cast<uint4 *>(sm.hd + core_offset(tid, 32 * hf + 8 * g, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      // butterfly, remaining steps: 32 -> 16 -> 8 -> 4 -> 2 columns per lane
+#pragma unroll
+      for (int w = 16, bit = 8; w > 1; w >>= 1, bit >>= 1) {
+        const bool hi = lane & bit;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          if (c >= w) break;
+          const float k = hi ? r32[c + w] : r32[c], sd = hi ? r32[c] : r32[c + w];
+          r32[c] = k + __shfl_xor_sync(0xffffffffu, sd, bit);
+        }
+      }
+      gw3a += r32[0];
+      gw3b += r32[1];
+    }
+    // ---- dH1 = dZ2 W2, then the first ReLU
+    fence_async_smem();
+    tc_fence_before();
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (!ok) break;
+    if (tid == 0) {
+      const uint32_t d0 = smem_u32(sm.hd), w0 = smem_u32(sm.w2t);
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4)
+        tc_mma_bf16(tmem, tc_desc(d0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), id16, k4 > 0);
+      tc_commit(&sm.mbar);
+    }
+    ok = mma_wait();
+    if (ok) {
+      uint32_t z[32];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        tc_ld32(zl + 32u * hf, z);
+        tc_wait_ld();
+        const uint32_t m = hf ? m1b : m1a;
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          const float d0 = (m >> c) & 1u ? __uint_as_float(z[c]) : 0.f;
+          const float d1 = (m >> (c + 1)) & 1u ? __uint_as_float(z[c + 1]) : 0.f;
+          tc_put_t2(sm.ag, kMlpH + 32 * hf + c, tid, bf16_bits(d0) | (bf16_bits(d1) << 16), lane);
+        }
+      }
+    }
+    // ---- G += [dZ2^T; dZ1^T] [H1 | X | 1]^T over this tile's rows (waited for at
+    // the next tile's start or after the loop)
+    fence_async_smem();
+    tc_fence_before();
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (!ok) break;
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(sm.ag), b0 = smem_u32(sm.bg);
+#pragma unroll
+      for (int k = 0; k < kTcTrRows / 16; ++k)
+        tc_mma_bf16(tg, tc_desc(a0 + 256 * k, 128, 16 * kTcTrRows), tc_desc(b0 + 256 * k, 128, 16 * kTcTrRows), idg,
+                    any || k > 0);
+      tc_commit(&sm.mbar);
+    }
+    any = true;
+  }
+  if (ok && any) ok = mma_wait();  // the last gradient product
+  ok = __syncthreads_and(ok);
+  // ---- this CTA's partial gradient
+  float *P = partial + (size_t)blockIdx.x * kPartStride;
+  {
+    // thread r reads row r of G: r < 64 -> dW2 row r and db2; r >= 64 -> dW1 row r - 64 and db1
+    uint32_t g[32];
+    const uint32_t gl = tg + ((uint32_t)(32 * warp) << 16);
+    const bool w2row = tid < kMlpH;
+    const int u = w2row ? tid : tid - kMlpH;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {  // columns 32 q .. 32 q + 31
+      if (any && ok) {
+        tc_ld32(gl + 32u * q, g);
+        tc_wait_ld();
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) g[c] = 0u;
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = 32 * q + c;
+        const float v = __uint_as_float(g[c]);
+        if (w2row) {
+          if (col < kMlpH) P[kOffW2 + u * kMlpH + col] = v;
+          else if (col == 80) P[kOffB2 + u] = v;
+        } else {
+          if (col >= kMlpH && col < kMlpH + kMlpIn) P[kOffW1 + u * kMlpIn + (col - kMlpH)] = v;
+          else if (col == 80) P[kOffB1 + u] = v;
+        }
+      }
+    }
+  }
+  sm.gw3[warp][o3] = gw3a;
+  sm.gw3[warp][o3 + 1] = gw3b;
+  for (int o = 16; o > 0; o >>= 1) {
+    gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
+    lossa += __shfl_xor_sync(0xffffffffu, lossa, o);
+  }
+  if (lane == 0) {
+    sm.gb3[warp] = gb3;
+    sm.loss[warp] = lossa;
+  }
+  __syncthreads();
+  for (int e = tid; e < kMlpH; e += blockDim.x) {
+    float s3 = 0.f;
+#pragma unroll
+    for (int w = 0; w < kTrWarps; ++w) s3 += sm.gw3[w][e];
+    P[kOffW3 + e] = s3;
+  }
+  if (tid == 0) {
+    float s = 0.f, l = 0.f;
+    for (int w = 0; w < kTrWarps; ++w) {
+      s += sm.gb3[w];
+      l += sm.loss[w];
+    }
+    P[kOffB3] = s;
+    P[kMlpNParam] = l;
+    if (!ok) atomicOr(err, (uint32_t)kErrTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 256);
+}
+
 // Sum of the CTA partials (fixed order), optional Adam step on the FP32 master
 // parameters, and the BF16 re-pack of each parameter.  One thread per parameter.
 __global__ void k_train_update(const float *__restrict__ partial, int nparts, float *__restrict__ theta,
@@ -396,6 +752,7 @@ struct tpc_mlp_trainer {
   tpc_mlp_train_config cfg;
   int device = 0, sms = 0, max_parts = 0, step = 0;
   float *theta = nullptr, *m1 = nullptr, *m2 = nullptr, *mean = nullptr, *inv_std = nullptr, *partial = nullptr;
+  uint32_t *err = nullptr;  // kErrTimeout when a tensor-core wait gave up (read by tpc_mlp_trainer_blob)
   double *stat_part = nullptr;
   MlpW *w = nullptr;
   char *mem = nullptr;
@@ -426,11 +783,19 @@ int parse_blob(const void *blob, size_t bytes, const float **body) {
 
 int launch_step(tpc_mlp_trainer *tr, const float *feat, const uint8_t *label, const int32_t *idx, uint32_t batch,
                 float *grad, float *loss, bool update, cudaStream_t st) {
-  const uint32_t groups = (batch + kTrRows - 1) / kTrRows;
-  const int parts = (int)(groups < (uint32_t)tr->max_parts ? groups : (uint32_t)tr->max_parts);
-  k_train_fwd_bwd<<<parts, kTrWarps * 32, sizeof(TrainSmem), st>>>(feat, label, idx, batch, tr->w,
-                                                                   tr->cfg.pos_weight, 1.0f / (float)batch,
-                                                                   tr->partial);
+  int parts;
+  if (tr->cfg.engine == TPC_MMA_TCGEN05) {
+    const uint32_t tiles = (batch + kTcTrRows - 1) / kTcTrRows;
+    parts = (int)(tiles < (uint32_t)tr->max_parts ? tiles : (uint32_t)tr->max_parts);
+    k_train_fwd_bwd_tc<<<parts, kTcTrRows, sizeof(TrainTcSmem) + 1024, st>>>(
+        feat, label, idx, batch, tr->w, tr->cfg.pos_weight, 1.0f / (float)batch, tr->partial, tr->err);
+  } else {
+    const uint32_t groups = (batch + kTrRows - 1) / kTrRows;
+    parts = (int)(groups < (uint32_t)tr->max_parts ? groups : (uint32_t)tr->max_parts);
+    k_train_fwd_bwd<<<parts, kTrWarps * 32, sizeof(TrainSmem), st>>>(feat, label, idx, batch, tr->w,
+                                                                     tr->cfg.pos_weight, 1.0f / (float)batch,
+                                                                     tr->partial);
+  }
   float bc1 = 1.f, bc2 = 1.f;
   if (update) {
     tr->step += 1;
@@ -456,6 +821,7 @@ extern "C" void tpc_mlp_default_train_config(tpc_mlp_train_config *c) {
   c->pos_weight = 1.0f;
   c->max_batch = 8192;
   c->device = 0;
+  c->engine = TPC_MMA_TCGEN05;
 }
 
 extern "C" int tpc_mlp_trainer_create(const tpc_mlp_train_config *cfg, const void *init_blob, size_t bytes,
@@ -468,6 +834,8 @@ extern "C" int tpc_mlp_trainer_create(const tpc_mlp_train_config *cfg, const voi
   if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
       !(cfg->eps > 0.f) || !(cfg->pos_weight > 0.f))
     return fail(TPC_ERR_ARG, "tpc_mlp_trainer_create: bad optimiser settings");
+  if (cfg->engine != TPC_MMA_TCGEN05 && cfg->engine != TPC_MMA_SYNC)
+    return fail(TPC_ERR_ARG, "tpc_mlp_trainer_create: engine must be TPC_MMA_TCGEN05 or TPC_MMA_SYNC");
   const float *body = nullptr;
   int rc = parse_blob(init_blob, bytes, &body);
   if (rc != TPC_OK) return rc;
@@ -478,10 +846,12 @@ extern "C" int tpc_mlp_trainer_create(const tpc_mlp_train_config *cfg, const voi
   cudaDeviceGetAttribute(&tr->sms, cudaDevAttrMultiProcessorCount, tr->device);
   const uint32_t groups = (cfg->max_batch + kTrRows - 1) / kTrRows;
   tr->max_parts = (int)(groups < (uint32_t)(2 * tr->sms) ? groups : (uint32_t)(2 * tr->sms));
-  const size_t fbytes = (3 * kMlpNParam + 2 * kMlpIn + 8) * 4;
   const size_t pbytes = (size_t)tr->max_parts * kPartStride * 4;
   const size_t sbytes = (size_t)kStatBlocks * 2 * kMlpIn * 8;
-  const size_t total = fbytes + pbytes + sbytes + sizeof(MlpW) + 4 * 256;
+  // the parts carved below, each rounded up to 256 bytes
+  const auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t total = a256(sizeof(MlpW)) + 3 * a256(kMlpNParam * 4) + 2 * a256(kMlpIn * 4) + a256(pbytes) +
+                       a256(sbytes) + a256(4);
   cudaError_t e = cudaMalloc(&tr->mem, total);
   if (e != cudaSuccess) {
     delete tr;
@@ -501,7 +871,12 @@ extern "C" int tpc_mlp_trainer_create(const tpc_mlp_train_config *cfg, const voi
   tr->inv_std = reinterpret_cast<float *>(carve(kMlpIn * 4));
   tr->partial = reinterpret_cast<float *>(carve(pbytes));
   tr->stat_part = reinterpret_cast<double *>(carve(sbytes));
+  tr->err = reinterpret_cast<uint32_t *>(carve(4));
   e = cudaFuncSetAttribute(k_train_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_train_fwd_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(TrainTcSmem) + 1024));
+  if (e == cudaSuccess) e = cudaMemset(tr->err, 0, 4);
   if (e == cudaSuccess) e = cudaMemcpy(tr->mean, body, kMlpIn * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(tr->inv_std, body + kMlpIn, kMlpIn * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(tr->theta, body + 2 * kMlpIn, kMlpNParam * 4, cudaMemcpyHostToDevice);
@@ -581,6 +956,10 @@ extern "C" int tpc_mlp_trainer_blob(tpc_mlp_trainer *tr, void *blob, size_t byte
   TR_CK(cudaMemcpy(body, tr->mean, kMlpIn * 4, cudaMemcpyDeviceToHost));
   TR_CK(cudaMemcpy(body + kMlpIn, tr->inv_std, kMlpIn * 4, cudaMemcpyDeviceToHost));
   TR_CK(cudaMemcpy(body + 2 * kMlpIn, tr->theta, kMlpNParam * 4, cudaMemcpyDeviceToHost));
+  uint32_t err = 0;
+  TR_CK(cudaMemcpy(&err, tr->err, 4, cudaMemcpyDeviceToHost));
+  if (err & kErrTimeout)
+    return fail(TPC_ERR_TIMEOUT, "tpc_mlp_trainer_blob: a tensor-core wait of an earlier step gave up");
   return TPC_OK;
 }
 

@@ -54,7 +54,7 @@ class tpc_tracks(ctypes.Structure):
 
 class tpc_mlp_train_config(ctypes.Structure):
     _fields_ = [("lr", c_f32), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32), ("pos_weight", c_f32),
-                ("max_batch", c_u32), ("device", c_i32)]
+                ("max_batch", c_u32), ("device", c_i32), ("engine", c_i32)]
 
 
 class tpc_server_config(ctypes.Structure):

@@ -44,7 +44,7 @@ int main(void) {
   F(tpc_tracks, next_track);
   F(tpc_clusters, time); F(tpc_tracks, params); F(tpc_tracks, status); F(tpc_tracks, n_tracks_host);
   printf("tpc_mlp_train_config %zu\n", sizeof(tpc_mlp_train_config));
-  F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device);
+  F(tpc_mlp_train_config, pos_weight); F(tpc_mlp_train_config, max_batch); F(tpc_mlp_train_config, device); F(tpc_mlp_train_config, engine);
   return 0;
 }''')
     exe = tmp_path / "layout"

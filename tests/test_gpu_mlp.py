@@ -218,16 +218,21 @@ def _rows(f, n=None):
     return (feat, lab) if n is None else (feat[:n], lab[:n])
 
 
-def test_gradient_matches_fp64_oracle(env, two_sectors):
+@pytest.mark.parametrize("engine", [0, 1])  # tcgen05 (tensor memory), mma.sync
+def test_gradient_matches_fp64_oracle(env, two_sectors, engine):
     tpcca, dev = env
-    feat, lab = _rows(two_sectors, 1000)  # 1000 rows: 15 groups of 64 and a ragged tail
+    # 1000 rows: 15 groups of 64 (mma.sync) or 7 tiles of 128 (tcgen05) and a ragged tail
+    feat, lab = _rows(two_sectors, 1000)
     mean, inv_std, theta = random_net(11, feature_scale=True)
     blob = orc.mlp_blob(mean, inv_std, theta)
     pw = 1.8
     loss_o, grad_o = orc.mlp_loss_grad(theta, mean, inv_std, feat, lab, pos_weight=pw)
-    tr = tpcca.Trainer(blob, pos_weight=pw, max_batch=4096)
+    tr = tpcca.Trainer(blob, pos_weight=pw, max_batch=4096, engine=engine)
     try:
-        grad_g, loss_g = tr.gradient(_dev_tensor(feat, dev), _dev_tensor(lab, dev))
+        F, L = _dev_tensor(feat, dev), _dev_tensor(lab, dev)
+        grad_g, loss_g = tr.gradient(F, L)
+        again, loss_again = tr.gradient(F, L)
+        assert torch.equal(grad_g, again) and loss_g == loss_again  # bitwise reproducible
     finally:
         tr.close()
     grad_g = grad_g.cpu().numpy().astype(np.float64)
@@ -255,13 +260,14 @@ def test_gradient_matches_fp64_oracle(env, two_sectors):
         off += k
 
 
-def test_gradient_with_index_gather(env, c1):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_gradient_with_index_gather(env, c1, engine):
     tpcca, dev = env
     feat, lab = _rows(c1)
     idx = np.random.default_rng(2).permutation(feat.shape[0])[:200].astype(np.int32)
     mean, inv_std, theta = random_net(12, feature_scale=True)
     blob = orc.mlp_blob(mean, inv_std, theta)
-    tr = tpcca.Trainer(blob)
+    tr = tpcca.Trainer(blob, engine=engine)
     try:
         g1, l1 = tr.gradient(_dev_tensor(feat, dev), _dev_tensor(lab, dev), _dev_tensor(idx, dev))
         g2, l2 = tr.gradient(_dev_tensor(feat[idx], dev), _dev_tensor(lab[idx], dev))
@@ -270,13 +276,14 @@ def test_gradient_with_index_gather(env, c1):
     assert torch.equal(g1, g2) and l1 == l2
 
 
-def test_first_adam_step_closed_form(env, c1):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_first_adam_step_closed_form(env, c1, engine):
     tpcca, dev = env
     feat, lab = _rows(c1)
     mean, inv_std, theta = random_net(13, feature_scale=True)
     blob = orc.mlp_blob(mean, inv_std, theta)
     lr = 1e-3
-    tr = tpcca.Trainer(blob, lr=lr)
+    tr = tpcca.Trainer(blob, lr=lr, engine=engine)
     try:
         F, L = _dev_tensor(feat, dev), _dev_tensor(lab, dev)
         g, _ = tr.gradient(F, L)
