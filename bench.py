@@ -173,10 +173,16 @@ def bf16_peak():
 def dense_scorer(tr, torch, dev, stream, rows=5_200_000, reps=20):
     """The classifier on a dense block of feature rows (tpc_mlp_score_ex), both
     tensor-core engines: 5.2 M rows of 48 B (250 MB, larger than L2), seeded normal
-    features.  FLOP per row: 2 (16*64 + 64*64 + 64)."""
+    features with the classifier's own feature means and spreads (so that the
+    standardised inputs are unit normal, like real triplets').  FLOP per row:
+    2 (16*64 + 64*64 + 64)."""
     g = torch.Generator(device=dev)
     g.manual_seed(11)
-    feat = torch.randn(rows, 12, device=dev, generator=g)
+    from paper_2102_08862_gb300 import tpcca
+    blob, _ = classifier()
+    mean, inv_std, _ = tpcca.unpack_blob(blob)
+    feat = torch.randn(rows, 12, device=dev, generator=g) / torch.from_numpy(inv_std).to(dev) + \
+        torch.from_numpy(mean).to(dev)
     flop = 2.0 * (16 * 64 + 64 * 64 + 64) * rows
     bf16, kind = bf16_peak()
     out = {"rows": rows, "flop_per_row": flop / rows, "peak_tflops": bf16, "peak_kind": kind}

@@ -94,6 +94,7 @@ struct tpc_tf {
   PruneRow *q_rows = nullptr; // per-tile regions of rescored pairs (pruned mode only)
   int32_t *q_count = nullptr;
   MlpW *mlp = nullptr;        // packed weights (allocated by tpc_mlp_load)
+  MlpHead mlp_head = {};      // host copy of the values every scored row reads
   float *mlp_stage = nullptr; // FP32 blob body staged for packing
   bool mlp_ready = false;
   float logit_tau = 0.f;
@@ -1019,6 +1020,27 @@ extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
   }
   TPC_CK(cudaMemcpy(tf->mlp_stage, static_cast<const char *>(blob) + 16, need - 16, cudaMemcpyHostToDevice));
   const float *body = tf->mlp_stage;
+  {  // host copy: blob body = mean (12), inv_std (12), theta (W1, b1, W2, b2, w3, b3)
+    const float *hb = reinterpret_cast<const float *>(static_cast<const char *>(blob) + 16);
+    const float *th = hb + 24;
+    const auto bf16_round = [](float v) {  // nearest, ties to even (finite values)
+      uint32_t u;
+      std::memcpy(&u, &v, 4);
+      u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+      float r;
+      std::memcpy(&r, &u, 4);
+      return r;
+    };
+    for (int i = 0; i < 12; ++i) {
+      tf->mlp_head.mean[i] = hb[i];
+      tf->mlp_head.inv_std[i] = hb[12 + i];
+    }
+    for (int o = 0; o < 64; ++o) {
+      tf->mlp_head.b2[o] = th[kOffB2 + o];
+      tf->mlp_head.w3[o] = bf16_round(th[kOffW3 + o]);
+    }
+    tf->mlp_head.b3 = th[kOffB3];
+  }
   launch_mlp_pack(body + 24, body, body + 12, tf->mlp, 0);
   TPC_CK(cudaGetLastError());
   TPC_CK(cudaDeviceSynchronize());
@@ -1040,8 +1062,8 @@ extern "C" int tpc_mlp_score_ex(tpc_tf *tf, const float *feat, uint32_t m, float
   TPC_CK(cudaSetDevice(tf->device));
   if (engine == TPC_MMA_SYNC) {
     launch_mlp_score(tf->mlp, feat, m, logit, tf->sms, (cudaStream_t)stream);
-  } else if (launch_mlp_score_tc(tf->mlp, feat, m, logit, reinterpret_cast<int *>(tf->reset + kCtrErr), tf->sms,
-                                 (cudaStream_t)stream) < 0) {
+  } else if (launch_mlp_score_tc(tf->mlp, tf->mlp_head, feat, m, logit, reinterpret_cast<int *>(tf->reset + kCtrErr),
+                                 tf->sms, (cudaStream_t)stream) < 0) {
     return fail(TPC_ERR_CUDA, "tpc_mlp_score: tensor-core kernel configuration failed");
   }
   TPC_CK(cudaGetLastError());

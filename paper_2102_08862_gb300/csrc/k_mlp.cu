@@ -475,25 +475,6 @@ __device__ __forceinline__ void tc_stage_weights(TcMlpSmem &sm, const MlpW *__re
   }
 }
 
-// row r's input in the tile at x: 16 standardised BF16 values (12 + 4 zeros), or zeros
-__device__ __forceinline__ void tc_put_input(unsigned char *x, const float *mean, const float *inv_std, int r,
-                                             const float *f, bool valid) {
-  uint32_t w[8];
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int c = 2 * p;
-    uint32_t h = 0;
-    if (valid && c < kMlpIn) {
-      const float lo = __fmul_rn(__fsub_rn(f[c], mean[c]), inv_std[c]);
-      const float hi = __fmul_rn(__fsub_rn(f[c + 1], mean[c + 1]), inv_std[c + 1]);
-      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
-    }
-    w[p] = h;
-  }
-  *reinterpret_cast<uint4 *>(x + core_offset(r, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-  *reinterpret_cast<uint4 *>(x + core_offset(r, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-}
-
 // Epilogue of the first layer for the row in this thread's tensor-memory lane:
 // columns [0, 64) + b1, ReLU, BF16, written as row hr of the K = 64 core-matrix
 // operand at hb.  Pairs of columns go through packed FP32 adds and one
@@ -741,18 +722,94 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
   if (warp == 0) tc_dealloc(tmem, 128);
 }
 
-// logits of raw feature rows (float[m][12]) on the tcgen05 path.  A CTA of 128
-// threads takes two 128-row tiles per step (thread r holds row r of both; tile h
-// accumulates in tensor-memory columns 64 h ..): both tiles' MMAs of a layer are
-// issued together and complete behind one mbarrier wait, so each wait and CTA
-// barrier serves 256 rows; the next step's features are loaded while the current
-// step runs.  4 CTAs share an SM (tensor memory: 4 x 128 of 512 columns).
-__global__ void __launch_bounds__(128, 4) k_mlp_score_tc(const MlpW *__restrict__ W, const float *__restrict__ feat,
-                                                         uint32_t m, float *__restrict__ logit, int *err) {
+// ---- the standalone scorer's variants of the helpers above.  The bias b1 is a
+// product of the first layer: W1's input columns 12 and 13 hold the BF16 parts
+// b1_hi = bf16(b1) and b1_lo = bf16(b1 - b1_hi) and every X row holds 1, 1 there,
+// so Z1 = X W1^T already contains b1 (to ~2^-17 of it); the epilogue only clamps
+// and rounds.  The standardisation, b2 and w3 come from the constant bank (the
+// MlpHead parameter): shared-memory loads of them kept the scorer's load/store
+// pipe at 50 % with the tensor pipe at 9 %.
+__device__ __forceinline__ void tc_fold_b1(TcMlpSmem &sm, const MlpW *__restrict__ W) {
+  for (int n = threadIdx.x; n < kMlpH; n += blockDim.x) {
+    const float b = W->b1[n];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+    *reinterpret_cast<__nv_bfloat16 *>(sm.w1 + core_offset(n, 12, 16)) = hi;
+    *reinterpret_cast<__nv_bfloat16 *>(sm.w1 + core_offset(n, 13, 16)) = lo;
+  }
+}
+
+// first-layer epilogue with the bias already in Z1: ReLU and BF16 only
+__device__ __forceinline__ void tc_epi_hidden_nb(uint32_t lane_addr, unsigned char *hb, int hr) {
+  uint32_t z[32];
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    tc_ld32(lane_addr + 32u * hf, z);
+    tc_wait_ld();
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t w[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) w[p] = bf16x2_relu(f2_pack(z[8 * g + 2 * p], z[8 * g + 2 * p + 1]));
+      *reinterpret_cast<uint4 *>(hb + core_offset(hr, 32 * hf + 8 * g, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// second-layer epilogue of one row with the per-row constants in the parameter
+// bank (operands of the FP32 instructions themselves: no shared-memory loads)
+__device__ __forceinline__ float tc_epi_logit_c(uint32_t lane_addr, const MlpHead &hd) {
+  float z[16];
+  float acc0 = hd.b3, acc1 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tc_ld16(lane_addr + 16u * q, z);
+    tc_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+      acc0 = fmaf(fmaxf(z[c] + hd.b2[16 * q + c], 0.f), hd.w3[16 * q + c], acc0);
+      acc1 = fmaf(fmaxf(z[c + 1] + hd.b2[16 * q + c + 1], 0.f), hd.w3[16 * q + c + 1], acc1);
+    }
+  }
+  return acc0 + acc1;
+}
+
+// row r of the tile at x: standardised BF16 inputs, then 1, 1 (the bias columns), 0, 0
+__device__ __forceinline__ void tc_put_input_c(unsigned char *x, int r, const float *f, bool valid,
+                                               const MlpHead &hd) {
+  uint32_t w[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int c = 2 * p;
+    uint32_t v = 0;
+    if (valid) {
+      const float lo = __fmul_rn(__fsub_rn(f[c], hd.mean[c]), hd.inv_std[c]);
+      const float hi = __fmul_rn(__fsub_rn(f[c + 1], hd.mean[c + 1]), hd.inv_std[c + 1]);
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(hi), "f"(lo));
+    }
+    w[p] = v;
+  }
+  *reinterpret_cast<uint4 *>(x + core_offset(r, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4 *>(x + core_offset(r, 8, 16)) = make_uint4(w[4], w[5], 0x3f803f80u, 0u);
+}
+
+// logits of raw feature rows (float[m][12]) on the tcgen05 path.  A CTA of 256
+// threads takes two 128-row tiles per step: warpgroup h (threads 128 h ..) holds
+// tile h, thread r of it row r (tensor-memory lane r, columns 64 h ..).  Both
+// tiles' MMAs of a layer are issued together and complete behind one mbarrier
+// wait; the next step's row is loaded while the current step runs.  4 CTAs share
+// an SM (tensor memory: 4 x 128 of 512 columns; 64 registers a thread), 32 warps
+// in all, which hide the MMA and load latencies; the per-row constants are kernel
+// parameters (MlpHead), so the epilogues read no shared memory.
+__global__ void __launch_bounds__(256, 4) k_mlp_score_tc(const MlpW *__restrict__ W, const __grid_constant__ MlpHead hd,
+                                                         const float *__restrict__ feat, uint32_t m,
+                                                         float *__restrict__ logit, int *err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   TcMlpSmem &sm = *reinterpret_cast<TcMlpSmem *>(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, h = tid >> 7, r = tid & 127;
   tc_stage_weights(sm, W);
+  __syncthreads();  // the bias columns overwrite part of the staged W1 rows
+  tc_fold_b1(sm, W);
   if (tid == 0) mbar_init(&sm.mbar, 1);
   if (warp == 0) tc_alloc(&sm.tmem, 128);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -760,42 +817,31 @@ __global__ void __launch_bounds__(128, 4) k_mlp_score_tc(const MlpW *__restrict_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm.tmem;
-  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
-  const float b3 = W->b3;
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)h;
   const uint32_t steps = (m + 255) / 256;
   const uint32_t idesc = tc_idesc_bf16(128, 64);
-  float fa[kMlpIn], fb[kMlpIn];
-  if (blockIdx.x < steps) {
-    load_feature_row(feat, blockIdx.x * 256 + tid, m, fa);
-    load_feature_row(feat, blockIdx.x * 256 + 128 + tid, m, fb);
-  }
+  float f[kMlpIn];
+  if (blockIdx.x < steps) load_feature_row(feat, blockIdx.x * 256 + 128 * h + r, m, f);
   bool ok = true;
   for (uint32_t u = blockIdx.x; u < steps && ok; u += gridDim.x) {
-    const uint32_t ra = u * 256 + tid, rb = ra + 128;
-    tc_put_input(sm.x[0], sm.mean, sm.inv_std, tid, fa, ra < m);
-    tc_put_input(sm.x[1], sm.mean, sm.inv_std, tid, fb, rb < m);
-    if (u + gridDim.x < steps) {  // the next step's rows
-      load_feature_row(feat, (u + gridDim.x) * 256 + tid, m, fa);
-      load_feature_row(feat, (u + gridDim.x) * 256 + 128 + tid, m, fb);
-    }
-    // layer 1: X (128 x 16) W1^T of both tiles
+    const uint32_t row = u * 256 + 128 * h + r;
+    tc_put_input_c(sm.x[h], r, f, row < m, hd);
+    if (u + gridDim.x < steps) load_feature_row(feat, (u + gridDim.x) * 256 + 128 * h + r, m, f);  // next step
+    // layer 1: X (128 x 16) W1^T of both tiles (b1 included)
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        tc_mma_bf16(tmem + 64u * h, tc_desc(smem_u32(sm.x[h]), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), idesc,
+      for (int t = 0; t < 2; ++t)
+        tc_mma_bf16(tmem + 64u * t, tc_desc(smem_u32(sm.x[t]), 128, 256), tc_desc(smem_u32(sm.w1), 128, 256), idesc,
                     false);
       tc_commit(&sm.mbar);
     }
     ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, 0, 1u << 22));  // warp-uniform (tcgen05.ld)
     tc_fence_after();
-    if (ok) {
-      tc_epi_hidden(lane_addr, sm.b1, sm.h[0], tid);
-      tc_epi_hidden(lane_addr + 64u, sm.b1, sm.h[1], tid);
-    }
+    if (ok) tc_epi_hidden_nb(lane_addr, sm.h[h], r);
     fence_async_smem();
     tc_fence_before();
     ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
@@ -805,26 +851,21 @@ __global__ void __launch_bounds__(128, 4) k_mlp_score_tc(const MlpW *__restrict_
     if (tid == 0) {
       const uint32_t w0 = smem_u32(sm.w2);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t h0 = smem_u32(sm.h[h]);
+      for (int t = 0; t < 2; ++t) {
+        const uint32_t h0 = smem_u32(sm.h[t]);
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4)
-          tc_mma_bf16(tmem + 64u * h, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), idesc,
+          tc_mma_bf16(tmem + 64u * t, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), idesc,
                       k4 > 0);
       }
       tc_commit(&sm.mbar);
     }
     ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, 1, 1u << 22));
     tc_fence_after();
-    float la = 0.f, lb = 0.f;
-    if (ok) {
-      la = tc_epi_logit(lane_addr, sm.b2, sm.w3, b3);
-      lb = tc_epi_logit(lane_addr + 64u, sm.b2, sm.w3, b3);
-    }
+    const float lg = ok ? tc_epi_logit_c(lane_addr, hd) : 0.f;
     tc_fence_before();
     ok = __syncthreads_and(ok);  // sm.x, sm.h and the accumulators are free again
-    if (ok && ra < m) logit[ra] = la;
-    if (ok && rb < m) logit[rb] = lb;
+    if (ok && row < m) logit[row] = lg;
   }
   if (!ok && tid == 0) atomicOr(err, (int)kErrTimeout);
   tc_fence_before();
@@ -981,8 +1022,8 @@ int prune_tiles_prepare() {
                               (int)prune_tiles_tc_smem()) == cudaSuccess ? 0 : -1;
 }
 
-int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *logit, int *err, int sms,
-                        cudaStream_t st) {
+int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, uint32_t m, float *logit, int *err,
+                        int sms, cudaStream_t st) {
   if (m == 0) return 0;
   static bool configured[64] = {};
   int dev = 0;
@@ -997,7 +1038,7 @@ int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *log
   // allocations (512 columns per SM) never wait on each other
   const uint32_t steps = (m + 255) / 256;
   const uint32_t grid = steps < (uint32_t)sms * 4 ? steps : (uint32_t)sms * 4;
-  k_mlp_score_tc<<<grid, 128, mlp_score_tc_smem(), st>>>(w, feat, m, logit, err);
+  k_mlp_score_tc<<<grid, 256, mlp_score_tc_smem(), st>>>(w, head, feat, m, logit, err);
   return 0;
 }
 

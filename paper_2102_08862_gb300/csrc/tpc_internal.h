@@ -87,11 +87,18 @@ void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaSt
 // FP32 parameters (blob order) + standardisation -> packed BF16 weights
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);
 void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit, int sms, cudaStream_t st);
+// The classifier's FP32 values that every row of the dense scorer reads (the
+// standardisation, the second layer's bias, the BF16-rounded output weights and
+// the output bias), kept on the host when the weights are loaded and passed to the
+// kernel as a parameter, so that they are read from the constant bank.
+struct MlpHead {
+  float b2[64], w3[64], mean[12], inv_std[12], b3;
+};
 // the same on the tcgen05 tensor cores (128-row tiles, accumulators in tensor
 // memory); *err (device) is set if a bounded wait gave up; returns < 0 on a
 // launch-configuration failure
-int launch_mlp_score_tc(const MlpW *w, const float *feat, uint32_t m, float *logit, int *err, int sms,
-                        cudaStream_t st);
+int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, uint32_t m, float *logit, int *err,
+                        int sms, cudaStream_t st);
 void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,
                         cudaStream_t st);
 // floor(sqrt(v)) for 0 <= v < 2^62, exact

@@ -357,7 +357,7 @@ __device__ __forceinline__ void tc_put_t2(unsigned char *base, int n, int r, uin
   *reinterpret_cast<uint32_t *>(base + core_offset(nn, rr, kTcTrRows)) = word;
 }
 
-__global__ void __launch_bounds__(kTcTrRows) k_train_fwd_bwd_tc(const float *__restrict__ feat,
+__global__ void __launch_bounds__(kTcTrRows, 2) k_train_fwd_bwd_tc(const float *__restrict__ feat,
                                                                const uint8_t *__restrict__ label,
                                                                const int32_t *__restrict__ idx, uint32_t B,
                                                                const MlpW *__restrict__ W, float pos_weight,
@@ -413,14 +413,22 @@ __global__ void __launch_bounds__(kTcTrRows) k_train_fwd_bwd_tc(const float *__r
     return r;
   };
   const uint32_t tiles = (B + kTcTrRows - 1) / kTcTrRows;
+  // this thread's row of tile t: features and label (loaded one tile ahead)
+  float xf[kMlpIn];
+  float ylab = 0.f;
+  const auto load_row = [&](uint32_t t) {
+    const uint32_t row = t * kTcTrRows + tid;
+    const bool v = row < B;
+    const uint32_t sr = v ? (idx ? (uint32_t)idx[row] : row) : 0u;
+#pragma unroll
+    for (int c = 0; c < kMlpIn; ++c) xf[c] = v ? __ldg(feat + (size_t)sr * kMlpIn + c) : 0.f;
+    ylab = (v && label[sr]) ? 1.f : 0.f;
+  };
+  if (blockIdx.x < tiles) load_row(blockIdx.x);
   for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
     const uint32_t row = t * kTcTrRows + tid;
     const bool valid = row < B;
-    const uint32_t src = valid ? (idx ? (uint32_t)idx[row] : row) : 0u;
     // ---- inputs (the previous tile's gradient MMA reads bg and ag: wait for it)
-    float xf[kMlpIn];
-#pragma unroll
-    for (int c = 0; c < kMlpIn; ++c) xf[c] = valid ? __ldg(feat + (size_t)src * kMlpIn + c) : 0.f;
     if (any) ok = mma_wait();
     uint32_t xp[8];
 #pragma unroll
@@ -436,6 +444,8 @@ __global__ void __launch_bounds__(kTcTrRows) k_train_fwd_bwd_tc(const float *__r
 #pragma unroll
     for (int p = 0; p < kMlpIn / 2; ++p) tc_put_t2(sm.bg, kMlpH + 2 * p, tid, xp[p], lane);
     *reinterpret_cast<uint16_t *>(sm.bg + core_offset(80, tid, kTcTrRows)) = valid ? 0x3f80u : 0u;  // 1.0
+    const float y = ylab;
+    if (t + gridDim.x < tiles) load_row(t + gridDim.x);  // the next tile's row, in flight during this one
     // ---- layer 1
     fence_async_smem();
     tc_fence_before();
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(kTcTrRows) k_train_fwd_bwd_tc(const float *__r
 #pragma unroll
         for (int c = 0; c < 32; ++c) acc = fmaf(fmaxf(__uint_as_float(z[c]) + sm.b2[32 * hf + c], 0.f), sm.w3[32 * hf + c], acc);
       }
-      const float y = (valid && label[src]) ? 1.f : 0.f, wt = y > 0.f ? pos_weight : 1.f;
+      const float wt = y > 0.f ? pos_weight : 1.f;
       dl = valid ? wt * (1.f / (1.f + expf(-acc)) - y) * inv_B : 0.f;
       if (valid) lossa += wt * (fmaxf(acc, 0.f) + log1pf(expf(-fabsf(acc))) - y * acc) * inv_B;
       gb3 += dl;
