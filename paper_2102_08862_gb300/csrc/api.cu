@@ -63,6 +63,8 @@ struct tpc_tf {
   uint16_t *mup16 = nullptr;
   int2 *starts = nullptr;
   int32_t *trk_key = nullptr, *trk_len = nullptr, *chain = nullptr;
+  uint16_t *trk_rl = nullptr;
+  uint32_t *sec_tr = nullptr;  // [2][nsect] first track id and track count of each sector
   uint32_t *reset = nullptr;
   size_t reset_bytes_max = 0;
   uint16_t *s_sector = nullptr, *s_row = nullptr;
@@ -113,7 +115,7 @@ struct tpc_tf {
   // CUDA graph of one call (tpc_track_timeframe_graph)
   cudaStream_t cap_stream = nullptr;
   // host-buffer calls: cluster_track is copied back on aux_stream as soon as it is
-  // final (after the walk; after relabelling in follow mode), while the fit runs
+  // final (after the assignment pass; after relabelling in follow mode), while the fit runs
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_ct = nullptr;
   bool record_ct = false;
@@ -212,6 +214,8 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->starts, (N / 2 + 2) * 8},
       {(void **)&tf->trk_key, (size_t)(tf->track_list_cap + 1) * 4},
       {(void **)&tf->trk_len, (size_t)(tf->track_list_cap + 1) * 4},
+      {(void **)&tf->trk_rl, (size_t)(tf->track_list_cap + 8) * 2},  // read in groups of 8
+      {(void **)&tf->sec_tr, (size_t)tf->nsect * 8},
       {(void **)&tf->chain, (size_t)kNRows * tf->track_list_cap * 4},
       {(void **)&tf->reset, tf->reset_bytes_max},
       {(void **)&tf->s_sector, (N + 8) * 2},
@@ -332,6 +336,10 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
     return fail(TPC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   }
   cudaDeviceGetAttribute(&tf->sms, cudaDevAttrMultiProcessorCount, tf->device);
+  if (assign_prepare() != 0) {
+    delete tf;
+    return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot configure the assignment kernel");
+  }
   if (cfg->persistent && persistent_prepare(tf->device) != 0) {
     delete tf;
     return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot size the persistent launch");
@@ -415,6 +423,9 @@ static void fill_args(tpc_tf *tf, uint32_t n, const tpc_tracks *out, Args &a) {
   a.starts = tf->starts;
   a.trk_key = tf->trk_key;
   a.trk_len = tf->trk_len;
+  a.trk_rl = tf->trk_rl;
+  a.sec_first = tf->sec_tr;
+  a.sec_cnt = tf->sec_tr + tf->nsect;
   a.chain = tf->chain;
   a.ctr = tf->reset;
   const size_t tiles_l = link_tiles(n);
@@ -601,10 +612,12 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   } else if (!tf->cfg.follow) {
     launch_walk(a, tf->sms, st);
     stage(tf, st, "walk");
-    launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+    launch_assign(a, tf->sms, st);
     if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
+    stage(tf, st, "assign");
+    launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
     stage(tf, st, "fit");
-    tf->launches += 3;  // links, walk, fit
+    tf->launches += 4;  // links, walk, assign, fit
   } else {
     // chains and their fit into the follower's records, then following and joining
     // (cluster_track holds the chain ids in between), then the refit of the
@@ -626,6 +639,8 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     ac.n_tracks_out = nullptr;
     launch_walk(ac, tf->sms, st);
     stage(tf, st, "walk");
+    launch_assign(ac, tf->sms, st);
+    stage(tf, st, "assign");
     launch_fit(ac, tf->sms, tf->cfg.fit_variant, st);
     stage(tf, st, "fit");
     TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, ((size_t)tf->track_list_cap + n) * 4, st));
@@ -636,7 +651,7 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     launch_follow_ct(a, tf->sms, st);
     if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
     stage(tf, st, "relabel");
-    tf->launches += 8;  // links, walk, fit, claim reset, time samples, follow, refit, relabel
+    tf->launches += 9;  // links, walk, assign, fit, claim reset, time samples, follow, refit, relabel
     if (tf->cfg.follow == 2 && out->next_track && out->track_capacity > 0) {
       TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, (size_t)tf->track_list_cap * 4, st));
       launch_sector_links(a, tf->sms, st);
@@ -905,8 +920,8 @@ extern "C" int tpc_track_timeframe_host(tpc_tf *tf, const tpc_clusters *cl, cons
   const int rc0 = tpc_track_timeframe(tf, &dcl, &dt, stream);
   tf->record_ct = false;
   if (rc0 != TPC_OK) return rc0;
-  // cluster_track back on the second stream once the fit has written it, beside the
-  // count and then exactly that many records on the call's stream
+  // cluster_track back on the second stream while the fit runs; then the count and
+  // exactly that many records on the call's stream
   if (n > 0) {
     TPC_CK(cudaStreamWaitEvent(tf->aux_stream, tf->ev_ct, 0));
     TPC_CK(cudaMemcpyAsync(out->cluster_track, tf->h_ct, (size_t)n * 4, cudaMemcpyDeviceToHost, tf->aux_stream));

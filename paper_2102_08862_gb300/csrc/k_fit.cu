@@ -14,11 +14,7 @@
 // chain[step][track], so the threads of a block read words of the same 1 KB span;
 // each block sorts its 256 tracks by chain length first, so that the lanes of a
 // warp finish together; the next cluster's (pad, time) is loaded before the
-// current step's arithmetic, and the cluster's cluster_track entry (the track id)
-// is written when it is loaded: the fit visits every member of every track in
-// any case, and its scattered stores overlap arithmetic there instead of
-// lengthening the walk's pointer chase.  Tracks past the record capacity get
-// their cluster_track entries without a fit.
+// current step's arithmetic.
 //
 // FP32 accuracy.  Three choices keep the FP32 filter within 1e-4 of an FP64 one:
 //  * the covariance is carried as C = U D U^T (U unit upper triangular, D
@@ -274,15 +270,12 @@ __device__ __forceinline__ void kf_covariance(const Kf &k, float *c) {
 // 256 columns (1 KB, cached in L1).
 __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t nblk) {
   __shared__ uint32_t s_key[256];
-  // every listed track gets its cluster_track entries; the first track_capacity
-  // are also fitted
-  const uint32_t nl = min(a.ctr[kCtrTracks], a.track_list_cap);
-  const uint32_t nt = min(nl, a.track_capacity);
+  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
-  for (uint32_t t0 = bid * 256; t0 < nl; t0 += nblk * 256) {
+  for (uint32_t t0 = bid * 256; t0 < nt; t0 += nblk * 256) {
     {
       const uint32_t tt = t0 + threadIdx.x;
-      const uint32_t len = tt < nl ? (uint32_t)a.trk_len[tt] : 0u;
+      const uint32_t len = tt < nt ? (uint32_t)a.trk_len[tt] : 0u;
       s_key[threadIdx.x] = (len << 8) | threadIdx.x;
       __syncthreads();
       for (int k = 2; k <= 256; k <<= 1)
@@ -300,21 +293,16 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
     }
     const uint32_t t = t0 + (s_key[threadIdx.x] & 255u);
     __syncthreads();  // s_key is rewritten by the next round
-    if (t >= nl) continue;
+    if (t >= nt) continue;
     // the chain's clusters were recorded by the walk as chain[step][track]
     const int32_t *ch = a.chain + t;
     const int L = a.trk_len[t];
-    if (t >= nt) {  // past the record capacity: the cluster -> track entries only
-      for (int q = 0; q < L; ++q) a.cluster_track[caller_index(a, ch[(size_t)q * stride])] = (int32_t)t;
-      continue;
-    }
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     const int32_t start = ch[0], mid = ch[(size_t)(L / 2) * stride], last = ch[(size_t)(L - 1) * stride];
     const int rlast = r0 + L - 1;
     const float tref = a.time[start];
     const float pad0 = a.pad[start];
-    a.cluster_track[caller_index(a, start)] = (int32_t)t;
     // y reference: the first cluster's y (rounded to FP32, in um)
     float h0, l0;
     two_diff(pad0, 0.5f * (float)(row_npads(r0) - 1), h0, l0);
@@ -326,12 +314,10 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
     int used = 1, lastrow = r0;
     float pd = 0.f, tm = 0.f;
     int32_t c2 = -1;
-    // (each cluster's cluster_track entry is written when its (pad, time) is loaded)
     if (L > 1) {
       const int32_t c1 = ch[stride];
       pd = a.pad[c1];
       tm = a.time[c1];
-      a.cluster_track[caller_index(a, c1)] = (int32_t)t;
     }
     if (L > 2) c2 = ch[2 * stride];
     for (int q = 1; q < L; ++q) {
@@ -339,13 +325,10 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
       if (q + 1 < L) {
         pd = a.pad[c2];
         tm = a.time[c2];
-        a.cluster_track[caller_index(a, c2)] = (int32_t)t;
         if (q + 2 < L) c2 = ch[(size_t)(q + 2) * stride];
       }
       if (!kf_transport(k, kRowDx)) {
         status |= 2;
-        for (int e = q + 2; e < L; ++e)  // the steps not loaded yet
-          a.cluster_track[caller_index(a, ch[(size_t)e * stride])] = (int32_t)t;
         break;
       }
       kf_measure<0>(k, y_local_um(cpd, r0 + q, yref_um) * 1e-4f, kVy);
@@ -386,18 +369,13 @@ __device__ __forceinline__ void stage_fit(const Args &a, uint32_t bid, uint32_t 
 __global__ void __launch_bounds__(256) k_fit_thread(Args a) { stage_fit(a, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
-  const uint32_t nl = min(a.ctr[kCtrTracks], a.track_list_cap);
-  const uint32_t nt = min(nl, a.track_capacity);
+  const uint32_t nt = min(min(a.ctr[kCtrTracks], a.track_list_cap), a.track_capacity);
   const size_t stride = a.track_list_cap;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nl; t += warps) {
+  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += warps) {
     const int32_t *ch = a.chain + t;
     const int L = a.trk_len[t];
-    if (t >= nt) {  // past the record capacity: the cluster -> track entries only
-      for (int q = lane; q < L; q += 32) a.cluster_track[caller_index(a, ch[(size_t)q * stride])] = (int32_t)t;
-      continue;
-    }
     const int key = a.trk_key[t];
     const int r0 = key % kNRows;
     float pv0 = 0.f, pv1 = 0.f, pv2 = 0.f, pv3 = 0.f, pv4 = 0.f;
@@ -412,7 +390,6 @@ __global__ void __launch_bounds__(256) k_fit_warp(Args a) {
         if (q == 0) first = c;
         pq = a.pad[c];
         tq = a.time[c];
-        a.cluster_track[caller_index(a, c)] = (int32_t)t;
       }
       if (b == 0) { pv0 = pq; tv0 = tq; }
       else if (b == 1) { pv1 = pq; tv1 = tq; }

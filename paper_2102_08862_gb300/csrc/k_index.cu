@@ -60,6 +60,10 @@ __device__ __forceinline__ void stage_row_index_table(const Args &a) {
   __shared__ int s_max[8];
   __shared__ int s_scan[256];
   const int lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < a.nsect; q += blockDim.x) {  // the walk's per-sector track ranges
+    a.sec_first[q] = ~0u;
+    a.sec_cnt[q] = 0u;
+  }
   const volatile int32_t *rbv = a.row_begin;
   const int nkeys = a.nkeys, tile = a.nb_tile;
   const int per = (nkeys + blockDim.x - 1) / blockDim.x;

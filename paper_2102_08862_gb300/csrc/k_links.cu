@@ -15,13 +15,14 @@
 // follows the chain n_min - 1 links to decide whether it is a track, takes its
 // track id from a second ordered compaction, then walks the whole chain writing
 // the chain's cluster positions as [step][track], so the fit reads them coalesced
-// with no pointer chasing.  Isolated clusters (here) and members of short chains
-// (in the walk) get cluster_track = -1; members of tracks get their id from the
-// fit, which reads every chain step anyway, so every entry is written exactly
-// once.  The 4-byte cluster_track stores land on scattered rows and each partly
-// fills a 32-byte sector that the memory must read back; in the latency-bound
-// walk they cost 0.21 of its 0.38 ms on the 10 ms frame, in the issue-bound fit
-// about 0.13 ms.
+// with no pointer chasing, and records each track's first row and length and
+// each sector's range of track ids.  k_assign then writes cluster_track one
+// (sector, row) at a time: a CTA builds the row in shared memory (-1, then the
+// id of every track of the sector that crosses the row, at its member there) and
+// writes it out coalesced.  Written from the walk (or the fit), the 4-byte stores
+// landed on scattered rows, each a separate L2 transaction that partly filled a
+// 32-byte sector the memory read back before writing: 0.21 of the walk's 0.38 ms
+// on the 10 ms frame, or 0.12 ms of the fit's time.
 #include "tpc_dev.cuh"
 #include "tpc_internal.h"
 
@@ -107,7 +108,6 @@ __device__ __forceinline__ void stage_links(const Args &a) {
       }
       skey[q] = key;
       if (mdn < 0 && mup >= 0) flags |= 1u << q;
-      if (mdn < 0 && mup < 0) a.cluster_track[caller_index(a, i)] = -1;
     }
     if (i0 + kItems <= (int)n) {
       auto pk = [&](int q) { return (uint32_t)m16[q] | ((uint32_t)m16[q + 1] << 16); };
@@ -143,8 +143,7 @@ __device__ __forceinline__ void stage_links(const Args &a) {
 // A4: one start hit per thread (kWalkChains; walking two or four chains per
 // thread interleaved was slower: more threads hide the pointer chase better).
 // Chains that reach n_min clusters become tracks (ids in start order); their
-// clusters are recorded in the chain buffer (the fit writes their cluster_track
-// entries); the clusters of shorter chains get -1 here.
+// clusters are recorded in the chain buffer; cluster_track comes from k_assign.
 template <bool kSmemRb>
 __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
@@ -220,7 +219,6 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
     }
     __syncthreads();
     uint32_t id[C];
-    int32_t v[C];
     bool w[C];
     {
       uint32_t nx = s_prefix + excl;
@@ -229,10 +227,9 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
         id[q] = nx;
         nx += kept[q];
         if (kept[q] && id[q] >= a.track_list_cap) raise(a.ctr, kErrCapacity);
-        w[q] = st[q].x >= 0 && (!kept[q] || id[q] < a.track_list_cap);
-        v[q] = kept[q] ? (int32_t)id[q] : -1;
-        // second walk: members of tracks go to the chain buffer (the fit gives
-        // them their cluster_track entry), members of short chains get -1
+        w[q] = kept[q] && id[q] < a.track_list_cap;
+        // second walk: the members of tracks go to the chain buffer (the
+        // assignment pass gives every cluster its cluster_track entry)
         c[q] = w[q] ? st[q].x : -1;
         kk[q] = st[q].y;
       }
@@ -243,16 +240,28 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
       for (int q = 0; q < C; ++q)
         if (c[q] >= 0) {
           any = true;
-          if (kept[q]) __stcs(a.chain + (size_t)m * stride + id[q], c[q]);
-          else __stcs(a.cluster_track + caller_index(a, c[q]), v[q]);
-          if (m + 1 < (kept[q] ? kNRows : len[q])) next(c[q], kk[q]); else c[q] = -1;
-          if (c[q] < 0 && kept[q]) a.trk_len[id[q]] = m + 1;
+          __stcs(a.chain + (size_t)m * stride + id[q], c[q]);
+          if (m + 1 < kNRows) next(c[q], kk[q]); else c[q] = -1;
+          if (c[q] < 0) a.trk_len[id[q]] = m + 1;
         }
       if (!any) break;
     }
 #pragma unroll
-    for (int q = 0; q < C; ++q)
-      if (kept[q] && w[q]) a.trk_key[id[q]] = st[q].y;
+    for (int q = 0; q < C; ++q) {
+      const int key = st[q].y, sec = w[q] ? key / kNRows : -1;
+      if (w[q]) {
+        a.trk_key[id[q]] = key;
+        a.trk_rl[id[q]] = (uint16_t)((key - sec * kNRows) | (a.trk_len[id[q]] << 8));
+      }
+      // the sector's id range: one atomic pair per warp and sector (a warp's tracks
+      // are consecutive, so the lowest lane of a group holds the group's first id);
+      // one pair per track put ~12 k atomics on each of 36 addresses on the 10 ms frame
+      const unsigned grp = __match_any_sync(0xffffffffu, sec);
+      if (w[q] && (threadIdx.x & 31) == __ffs(grp) - 1) {
+        atomicMin(&a.sec_first[sec], id[q]);
+        atomicAdd(&a.sec_cnt[sec], (uint32_t)__popc(grp));
+      }
+    }
     if (tile == n_tiles - 1 && threadIdx.x == 0) {
       const uint32_t nt = s_prefix + total;
       a.ctr[kCtrTracks] = nt;
@@ -260,6 +269,84 @@ __device__ __forceinline__ void stage_walk(const Args &a, uint32_t bid) {
       if (a.track_capacity > 0 && nt > a.track_capacity) raise(a.ctr, kErrCapacity);
     }
     __syncthreads();
+  }
+}
+
+// cluster_track of one (sector, row) per CTA step.  The sector's tracks have
+// contiguous ids (start order is sector-major); each one that crosses row r has its
+// member there at chain step r - first row.  A thread takes 8 consecutive tracks:
+// one 16-byte load of their (first row, length) words, then their chain loads,
+// issued together.  With a shared-memory buffer (kCap entries) the row is built
+// there (-1, then the ids) and written out coalesced, in chunks of kCap clusters
+// for longer rows: the global memory sees whole lines only.  Without one (kCap =
+// 0, inside the persistent kernel, whose occupancy the buffer would cut) the row
+// is filled with -1 in global memory and the ids are stored over it while its
+// lines are in L2.
+constexpr int kAssignBatch = 3;  // groups of 8 tracks a thread loads per round
+template <int kCap>
+__device__ __forceinline__ void stage_assign(const Args &a, uint32_t bid, uint32_t nblk, int32_t *buf) {
+  const size_t stride = a.track_list_cap;
+  const uint32_t nl = min(a.ctr[kCtrTracks], a.track_list_cap);
+  for (uint32_t key = bid; key < (uint32_t)a.nkeys; key += nblk) {
+    const int rb = a.row_begin[key], re = a.row_begin[key + 1];
+    const uint32_t sec = key / kNRows;
+    const int r = (int)(key - sec * kNRows);
+    const uint32_t t0 = a.sec_first[sec];
+    const uint32_t t1 = t0 == ~0u ? t0 : min(nl, t0 + a.sec_cnt[sec]);
+    const int chunk = kCap > 0 ? kCap : (re > rb ? re - rb : 1);
+    for (int base = rb; base < re; base += chunk) {
+      const int end = min(re, base + chunk);
+      if (kCap > 0) {
+        for (int i = (int)threadIdx.x; i < end - base; i += blockDim.x) buf[i] = -1;
+      } else {
+        for (int i = base + (int)threadIdx.x; i < end; i += blockDim.x) a.cluster_track[caller_index(a, i)] = -1;
+      }
+      __syncthreads();  // the fill before the ids, for every thread of the CTA
+      if (t0 < t1) {
+        // kAssignBatch groups of 8 track ids per thread and round: their (first row,
+        // length) words are loaded together, then all their chain loads, so that a
+        // round costs two memory latencies whatever its size
+        const uint32_t a0 = t0 & ~7u;  // 8-aligned groups of track ids (trk_rl is 16-byte aligned)
+        const uint32_t span = 8u * blockDim.x;
+        for (uint32_t g0 = a0 + 8u * threadIdx.x; g0 < t1; g0 += kAssignBatch * span) {
+          uint4 w[kAssignBatch];
+#pragma unroll
+          for (int b = 0; b < kAssignBatch; ++b) {
+            const uint32_t g = g0 + (uint32_t)b * span;
+            w[b] = g < t1 ? *reinterpret_cast<const uint4 *>(a.trk_rl + g) : make_uint4(0u, 0u, 0u, 0u);
+          }
+          int32_t c[kAssignBatch][8];
+#pragma unroll
+          for (int b = 0; b < kAssignBatch; ++b) {
+            const uint32_t g = g0 + (uint32_t)b * span;
+            const uint32_t wv[4] = {w[b].x, w[b].y, w[b].z, w[b].w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const uint32_t t = g + (uint32_t)e;
+              const uint32_t rl = (wv[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+              const int m = r - (int)(rl & 0xffu), len = (int)(rl >> 8);
+              c[b][e] = (t >= t0 && t < t1 && m >= 0 && m < len) ? a.chain[(size_t)m * stride + t] : -1;
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < kAssignBatch; ++b)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int32_t ce = c[b][e];
+              if (ce >= base && ce < end) {
+                const int32_t t = (int32_t)(g0 + (uint32_t)b * span + (uint32_t)e);
+                if (kCap > 0) buf[ce - base] = t;
+                else a.cluster_track[caller_index(a, ce)] = t;
+              }
+            }
+        }
+      }
+      __syncthreads();
+      if (kCap > 0) {
+        for (int i = (int)threadIdx.x; i < end - base; i += blockDim.x) a.cluster_track[caller_index(a, base + i)] = buf[i];
+        __syncthreads();  // buf is refilled by the next chunk or key
+      }
+    }
   }
 }
 
@@ -271,6 +358,11 @@ __global__ void __launch_bounds__(kThreads) k_links(Args a) {
 template <bool kSmemRb>
 __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
   stage_walk<kSmemRb>(a, blockIdx.x);
+}
+constexpr int kAssignCap = 12288;  // clusters of a row built in shared memory at once (48 KB)
+__global__ void __launch_bounds__(kThreads) k_assign(Args a) {
+  extern __shared__ int32_t assign_buf[];
+  stage_assign<kAssignCap>(a, blockIdx.x, gridDim.x, assign_buf);
 }
 
 // Hit removal: the clusters attached to a track, in caller order (an ordered
@@ -397,6 +489,18 @@ void launch_links(const Args &a, int sms, cudaStream_t st) {
 void launch_walk(const Args &a, int sms, cudaStream_t st) {
   if (a.nkeys <= kNKeys) k_walk<true><<<sms * 8, kThreads, 0, st>>>(a);
   else k_walk<false><<<sms * 8, kThreads, 0, st>>>(a);
+}
+
+void launch_assign(const Args &a, int sms, cudaStream_t st) {
+  // 4 CTAs per SM by shared memory (48 KB each)
+  const uint32_t grid = (uint32_t)a.nkeys < (uint32_t)sms * 4 ? (uint32_t)a.nkeys : (uint32_t)sms * 4;
+  k_assign<<<grid ? grid : 1, kThreads, kAssignCap * 4, st>>>(a);
+}
+
+int assign_prepare() {
+  return cudaFuncSetAttribute(k_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, kAssignCap * 4) == cudaSuccess
+             ? 0
+             : -1;
 }
 
 // Failure path of the bounded waits: tile 1 of a look-back whose tile 0 never

@@ -8,10 +8,10 @@
 // stages that depend on each other: validation and quantisation together with
 // the (sector, row) keys; the tile table (one block); the tile windows; the
 // neighbours; the edge-row claims; the mutual links and start hits; the chain
-// walk; the Kalman fit.  The grid is as many CTAs as fit on the GPU at once, so
-// that every CTA is resident; each barrier wait is bounded and records
-// TPC_ERR_TIMEOUT when it gives up (another kernel holding SMs would do that),
-// after which every CTA returns.
+// walk; the cluster_track assignment together with the Kalman fit.  The grid is
+// as many CTAs as fit on the GPU at once, so that every CTA is resident; each
+// barrier wait is bounded and records TPC_ERR_TIMEOUT when it gives up (another
+// kernel holding SMs would do that), after which every CTA returns.
 #define TPC_STAGES_ONLY
 #include "k_index.cu"
 #include "k_neighbours.cu"
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256, 6) k_track_persistent(Args a, int vec, in
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;
   stage_walk<false>(a, bid);
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;
+  stage_assign<0>(a, bid, nblk, nullptr);  // (reads the chains, as the fit does: no barrier between them)
   stage_fit(a, bid, nblk);
 }
 

@@ -48,6 +48,8 @@ int scratch_for_device(int dev, void **addr, int *sms) {
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
       return report(TPC_ERR_CUDA, "tpc_track_timeframe_noalloc: cannot query the SM count");
+    if (assign_prepare() != 0)
+      return report(TPC_ERR_CUDA, "tpc_track_timeframe_noalloc: cannot configure the assignment kernel");
     g_addr[dev] = p;
     g_sms[dev] = n;
   }
@@ -87,6 +89,9 @@ size_t carve(unsigned char *base, uint32_t n, uint32_t list_cap, Args *a, size_t
   a->trk_key = reinterpret_cast<int32_t *>(take(((size_t)list_cap + 1) * 4));
   a->trk_len = reinterpret_cast<int32_t *>(take(((size_t)list_cap + 1) * 4));
   a->chain = reinterpret_cast<int32_t *>(take((size_t)kNRows * list_cap * 4));
+  a->trk_rl = reinterpret_cast<uint16_t *>(take(((size_t)list_cap + 8) * 2));  // read in groups of 8
+  a->sec_first = reinterpret_cast<uint32_t *>(take((size_t)kNSect * 8));
+  a->sec_cnt = a->sec_first ? a->sec_first + kNSect : nullptr;
   return off;
 }
 
@@ -175,6 +180,7 @@ extern "C" int tpc_track_timeframe_noalloc(const tpc_tf_config *cfg, const tpc_c
   launch_edge_claims(a, st);
   launch_links(a, sms, st);
   launch_walk(a, sms, st);
+  launch_assign(a, sms, st);
   launch_fit(a, sms, TPC_FIT_THREAD, st);
   if (cudaGetLastError() != cudaSuccess) return report(TPC_ERR_CUDA, "tpc_track_timeframe_noalloc: launch failed");
   if (out->n_tracks_host) {

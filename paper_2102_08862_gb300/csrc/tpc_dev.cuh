@@ -111,6 +111,9 @@ struct Args {
   int32_t *trk_key;        // [track list capacity] (sector*152 + row) of the track's first cluster
   int32_t *trk_len;        // [track list capacity] chain length
   int32_t *chain;          // [152][track list capacity] sorted positions of each track's clusters
+  uint16_t *trk_rl;        // [track list capacity] first row | chain length << 8 (the assignment pass)
+  uint32_t *sec_first;     // [nsect] smallest track id of each sector (~0u: none), reset by the row index
+  uint32_t *sec_cnt;       // [nsect] tracks of each sector
   uint64_t *lb_links;      // look-back words, one per 1024-cluster tile
   uint64_t *lb_keep;       // look-back words, one per 1024-start tile
   uint32_t *ctr;           // counters (kNCounters)

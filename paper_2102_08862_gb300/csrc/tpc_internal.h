@@ -36,6 +36,10 @@ void launch_neighbours(const Args &a, int row_cap, int sms, cudaStream_t st, boo
 void launch_edge_claims(const Args &a, cudaStream_t st);
 void launch_links(const Args &a, int sms, cudaStream_t st);
 void launch_walk(const Args &a, int sms, cudaStream_t st);
+// cluster_track, one (sector, row) per CTA step: -1, then each crossing track's id
+void launch_assign(const Args &a, int sms, cudaStream_t st);
+// opts the assignment kernel in to its 48 KB of shared memory (0 on success)
+int assign_prepare();
 void launch_debug_links(const Args &a, int32_t *mup, uint8_t *is_start, cudaStream_t st);
 void launch_fit(const Args &a, int sms, int variant, cudaStream_t st);
 // track follower: pick-ups, claims and join proposals (k_follow); the joined
