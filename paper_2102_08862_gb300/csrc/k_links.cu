@@ -48,19 +48,23 @@ __device__ __forceinline__ int key_of(const int32_t *rb, int i, int nkeys) {
 // A2 + A3: mup[i] = up[i] if down[up[i]] = i; start(i) = no mutual down, a mutual up.
 // The row table rb (row_begin) sits in shared memory for up to 36 sectors and is
 // read through the L1 cache for batched calls with more.
-template <bool kSmemRb>
+// THREADS threads of a CTA take a 2048-cluster tile, kLinkTileN / THREADS consecutive
+// clusters each (8 for the persistent kernel's 256 threads, 4 for k_links' 512).
+template <bool kSmemRb, int THREADS>
 __device__ __forceinline__ void stage_links(const Args &a) {
+  constexpr int kItems = kLinkTileN / THREADS;
+  static_assert(kItems == 4 || kItems % 8 == 0, "the 16-bit link stores take 4 or 8 per vector");
   __shared__ int32_t s_rb[kSmemRb ? kNKeys + 1 : 1];
   __shared__ uint32_t s_tile, s_prefix;
-  __shared__ uint32_t s_warp[kThreads / 32];
+  __shared__ uint32_t s_warp[THREADS / 32];
   const int nkeys = a.nkeys;
   const int32_t *rb = a.row_begin;
   if constexpr (kSmemRb) {
-    for (int k = threadIdx.x; k <= nkeys; k += kThreads) s_rb[k] = a.row_begin[k];
+    for (int k = threadIdx.x; k <= nkeys; k += THREADS) s_rb[k] = a.row_begin[k];
     rb = s_rb;
   }
   const uint32_t n = a.n;
-  const uint32_t n_tiles = (n + kLinkTile - 1) / kLinkTile;
+  const uint32_t n_tiles = (n + kLinkTileN - 1) / kLinkTileN;
   const uint64_t keep = l2_keep_policy();
   bool bad = false;
   for (;;) {
@@ -68,12 +72,12 @@ __device__ __forceinline__ void stage_links(const Args &a) {
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const int i0 = (int)(tile * kLinkTile + threadIdx.x * kItems);
+    const int i0 = (int)(tile * kLinkTileN + threadIdx.x * kItems);
     int key = i0 < (int)n ? key_of(rb, i0, nkeys) : 0;
     uint32_t flags = 0;
     uint16_t m16[kItems];
     int32_t skey[kItems];
-    // all loads first: the thread's 8 links (64 contiguous bytes), then the 16
+    // all loads first: the thread's links (8 B each, contiguous), then the
     // partner links they point to, so that the gathers are in flight together
     int2 l[kItems];
     if (i0 + kItems <= (int)n) {
@@ -111,17 +115,21 @@ __device__ __forceinline__ void stage_links(const Args &a) {
     }
     if (i0 + kItems <= (int)n) {
       auto pk = [&](int q) { return (uint32_t)m16[q] | ((uint32_t)m16[q + 1] << 16); };
+      if constexpr (kItems == 4) {
+        st_keep_v2(a.mup16 + i0, make_uint2(pk(0), pk(2)), keep);
+      } else {
 #pragma unroll
-      for (int v = 0; v < kItems / 8; ++v)
-        st_keep_v4(a.mup16 + i0 + 8 * v, make_uint4(pk(8 * v), pk(8 * v + 2), pk(8 * v + 4), pk(8 * v + 6)),
-                   keep);
+        for (int v = 0; v < kItems / 8; ++v)
+          st_keep_v4(a.mup16 + i0 + 8 * v, make_uint4(pk(8 * v), pk(8 * v + 2), pk(8 * v + 4), pk(8 * v + 6)),
+                     keep);
+      }
     } else {
 #pragma unroll
       for (int q = 0; q < kItems; ++q)
         if (i0 + q < (int)n) st_keep_u16(a.mup16 + i0 + q, m16[q], keep);
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan<kThreads>((uint32_t)__popc(flags), s_warp, &total);
+    const uint32_t excl = block_exclusive_scan<THREADS>((uint32_t)__popc(flags), s_warp, &total);
     if (threadIdx.x < 32) {
       const uint32_t pre = lookback_exclusive(a.lb_links, tile, total, a.ctr, a.spin_limit);
       if (threadIdx.x == 0) s_prefix = pre;
@@ -351,9 +359,11 @@ __device__ __forceinline__ void stage_assign(const Args &a, uint32_t bid, uint32
 }
 
 #ifndef TPC_STAGES_ONLY
+constexpr int kLinkThreads = 256;
+constexpr int kLinkCtasPerSm = 5;  // the register limit at 48 per thread: their look-back waits overlap
 template <bool kSmemRb>
-__global__ void __launch_bounds__(kThreads) k_links(Args a) {
-  stage_links<kSmemRb>(a);
+__global__ void __launch_bounds__(kLinkThreads) k_links(Args a) {
+  stage_links<kSmemRb, kLinkThreads>(a);
 }
 template <bool kSmemRb>
 __global__ void __launch_bounds__(kThreads) k_walk(Args a) {
@@ -479,11 +489,11 @@ __global__ void k_debug_links(Args a, int32_t *mup, uint8_t *is_start) {
 }
 
 void launch_links(const Args &a, int sms, cudaStream_t st) {
-  const uint32_t tiles = (a.n + kLinkTile - 1) / kLinkTile;
-  // 5 CTAs per SM (the register limit at 48 per thread): their look-back waits overlap
-  const uint32_t grid = tiles < (uint32_t)sms * 5u ? (tiles ? tiles : 1u) : (uint32_t)sms * 5u;
-  if (a.nkeys <= kNKeys) k_links<true><<<grid, kThreads, 0, st>>>(a);
-  else k_links<false><<<grid, kThreads, 0, st>>>(a);
+  const uint32_t tiles = (a.n + kLinkTileN - 1) / kLinkTileN;
+  const uint32_t cap = (uint32_t)sms * (uint32_t)kLinkCtasPerSm;
+  const uint32_t grid = tiles < cap ? (tiles ? tiles : 1u) : cap;
+  if (a.nkeys <= kNKeys) k_links<true><<<grid, kLinkThreads, 0, st>>>(a);
+  else k_links<false><<<grid, kLinkThreads, 0, st>>>(a);
 }
 
 void launch_walk(const Args &a, int sms, cudaStream_t st) {

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256, 6) k_track_persistent(Args a, int vec, in
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;
   stage_edge_claims(a, bid, nblk);
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;
-  stage_links<false>(a);
+  stage_links<false, 256>(a);
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;
   stage_walk<false>(a, bid);
   if (!grid_sync(a.ctr, nblk, a.spin_limit)) return;

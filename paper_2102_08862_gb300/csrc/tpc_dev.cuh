@@ -194,6 +194,10 @@ __device__ __forceinline__ void st_keep_v4(void *addr, uint4 v, uint64_t pol) {
                "r"(v.z), "r"(v.w), "l"(pol)
                : "memory");
 }
+__device__ __forceinline__ void st_keep_v2(void *addr, uint2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(addr), "r"(v.x), "r"(v.y), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void st_keep_u16(uint16_t *addr, uint16_t v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(addr), "h"(v), "l"(pol) : "memory");
 }
