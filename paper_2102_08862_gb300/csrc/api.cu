@@ -117,6 +117,10 @@ struct tpc_tf {
   // host-buffer calls: cluster_track is copied back on aux_stream as soon as it is
   // final (after the assignment pass; after relabelling in follow mode), while the fit runs
   cudaStream_t aux_stream = nullptr;
+  // the cluster_track assignment runs on side_stream while the fit runs on the
+  // call's stream (both only read the chains); forked and joined by events
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_ct = nullptr;
   bool record_ct = false;
   // host-buffer calls on large sorted frames: sector ranges copied in on copy_stream
@@ -167,6 +171,9 @@ static void free_all(tpc_tf *tf) {
   if (tf->graph_exec) cudaGraphExecDestroy(tf->graph_exec);
   if (tf->cap_stream) cudaStreamDestroy(tf->cap_stream);
   if (tf->aux_stream) cudaStreamDestroy(tf->aux_stream);
+  if (tf->side_stream) cudaStreamDestroy(tf->side_stream);
+  if (tf->ev_fork) cudaEventDestroy(tf->ev_fork);
+  if (tf->ev_join) cudaEventDestroy(tf->ev_join);
   if (tf->ev_ct) cudaEventDestroy(tf->ev_ct);
   if (tf->copy_stream) cudaStreamDestroy(tf->copy_stream);
   for (int k = 0; k < kMaxRanges; ++k) {
@@ -339,6 +346,12 @@ extern "C" int tpc_tf_create(const tpc_tf_config *cfg, tpc_tf **out) {
   if (assign_prepare() != 0) {
     delete tf;
     return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot configure the assignment kernel");
+  }
+  if (cudaStreamCreateWithFlags(&tf->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&tf->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&tf->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    free_all(tf);
+    return fail(TPC_ERR_CUDA, "tpc_tf_create: cannot create the side stream");
   }
   if (cfg->persistent && persistent_prepare(tf->device) != 0) {
     delete tf;
@@ -576,6 +589,29 @@ static int enqueue_persistent(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaS
   return TPC_OK;
 }
 
+// A4 assignment and A5 fit.  Both only read the chains, so the assignment runs on
+// the side stream while the fit runs on st (with stage profiling they run one
+// after the other on st, so that each has its own time).  cluster_track is final
+// when the assignment ends (ev_ct, for the host-buffer path).
+static int enqueue_assign_fit(tpc_tf *tf, const Args &a, cudaStream_t st) {
+  if (tf->cfg.profile_stages) {
+    launch_assign(a, tf->sms, st);
+    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));
+    stage(tf, st, "assign");
+    launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+    stage(tf, st, "fit");
+    return TPC_OK;
+  }
+  TPC_CK(cudaEventRecord(tf->ev_fork, st));
+  TPC_CK(cudaStreamWaitEvent(tf->side_stream, tf->ev_fork, 0));
+  launch_assign(a, tf->sms, tf->side_stream);
+  if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, tf->side_stream));
+  TPC_CK(cudaEventRecord(tf->ev_join, tf->side_stream));
+  launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
+  TPC_CK(cudaStreamWaitEvent(st, tf->ev_join, 0));
+  return TPC_OK;
+}
+
 extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc_tracks *out, void *stream) {
   g_err.clear();
   if (!tf || !cl || !out) return fail(TPC_ERR_ARG, "tpc_track_timeframe: null argument");
@@ -612,11 +648,10 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
   } else if (!tf->cfg.follow) {
     launch_walk(a, tf->sms, st);
     stage(tf, st, "walk");
-    launch_assign(a, tf->sms, st);
-    if (tf->record_ct) TPC_CK(cudaEventRecord(tf->ev_ct, st));  // cluster_track is final
-    stage(tf, st, "assign");
-    launch_fit(a, tf->sms, tf->cfg.fit_variant, st);
-    stage(tf, st, "fit");
+    {
+      const int rc = enqueue_assign_fit(tf, a, st);  // cluster_track is final after the assignment
+      if (rc != TPC_OK) return rc;
+    }
     tf->launches += 4;  // links, walk, assign, fit
   } else {
     // chains and their fit into the follower's records, then following and joining
@@ -639,10 +674,13 @@ extern "C" int tpc_track_timeframe(tpc_tf *tf, const tpc_clusters *cl, const tpc
     ac.n_tracks_out = nullptr;
     launch_walk(ac, tf->sms, st);
     stage(tf, st, "walk");
-    launch_assign(ac, tf->sms, st);
-    stage(tf, st, "assign");
-    launch_fit(ac, tf->sms, tf->cfg.fit_variant, st);
-    stage(tf, st, "fit");
+    {
+      const bool rec = tf->record_ct;
+      tf->record_ct = false;  // in follow mode cluster_track is final after the relabelling
+      const int rc = enqueue_assign_fit(tf, ac, st);
+      tf->record_ct = rec;
+      if (rc != TPC_OK) return rc;
+    }
     TPC_CK(cudaMemsetAsync(tf->f_pred_claim, 0xff, ((size_t)tf->track_list_cap + n) * 4, st));
     launch_follow(a, tf->sms, st);
     stage(tf, st, "follow");
