@@ -1089,7 +1089,6 @@ extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
       tf->mlp_head.inv_std[i] = hb[12 + i];
     }
     for (int o = 0; o < 64; ++o) {
-      tf->mlp_head.b2[o] = th[kOffB2 + o];
       tf->mlp_head.w3[o] = bf16_round(th[kOffW3 + o]);
     }
     tf->mlp_head.b3 = th[kOffB3];

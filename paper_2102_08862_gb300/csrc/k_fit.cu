@@ -125,13 +125,17 @@ __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
 }
 
 // Bierman's U-D update for a scalar measurement of state component M with
-// variance V; accumulates the normalised innovation into chi2.
+// variance V; accumulates the normalised innovation into chi2.  U(0,1) is 0 in
+// every state the filter reaches: the seed has U = I, the transport never couples
+// y and zeta (their Jacobian entry is 0), and an update of either component
+// leaves it 0 (its factor f = U(0,1) or its accumulator b[0] is 0 at that step).
+// The steps that would only multiply by 1 or add 0 are left out.
 template <int M>
 __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
   float f[5], g[5], b[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
-    f[j] = j < M ? 0.0f : (j == M ? 1.0f : k.u[ui(M < j ? M : 0, M < j ? j : 1)]);
+    f[j] = j < M || (M == 0 && j == 1) ? 0.0f : (j == M ? 1.0f : k.u[ui(M < j ? M : 0, M < j ? j : 1)]);
     g[j] = k.d[j] * f[j];
     b[j] = 0.0f;
   }
@@ -139,6 +143,7 @@ __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
   float alpha = V, ibeta = 1.0f / V;
 #pragma unroll
   for (int j = M; j < 5; ++j) {
+    if (M == 0 && j == 1) continue;  // f[1] = U(0,1) = 0: alpha, D(1), U(0,1) and b[0] stay
     const float beta = alpha;
     alpha = fmaf(f[j], g[j], beta);
     const float ia = 1.0f / alpha;
@@ -146,6 +151,7 @@ __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
     k.d[j] *= beta * ia;
 #pragma unroll
     for (int i = 0; i < j; ++i) {
+      if (i == 0 && j == 1) continue;  // (M = 1) b[0] = 0 and U(0,1) = 0 stay
       const float uij = k.u[ui(i, j)];
       k.u[ui(i, j)] = fmaf(b[i], lam, uij);
       b[i] = fmaf(g[j], uij, b[i]);

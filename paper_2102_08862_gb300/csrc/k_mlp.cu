@@ -447,7 +447,7 @@ struct __align__(1024) TcMlpSmem {
   unsigned char h[2][128 * 64 * 2];   // their first hidden layers (K 64)
   unsigned char w1[64 * 16 * 2];      // W1 (N 64, K 16)
   unsigned char w2[64 * 64 * 2];      // W2 (N 64, K 64)
-  float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
+  unsigned char wb2[64 * 16 * 2];     // b2 as three BF16 parts in K columns 12..14 (N 64, K 16), else 0
   uint64_t mbar;
   uint32_t tmem;
 };
@@ -464,14 +464,18 @@ __device__ __forceinline__ void tc_stage_weights(TcMlpSmem &sm, const MlpW *__re
     *reinterpret_cast<uint4 *>(sm.w2 + core_offset(n, 8 * g, 64)) =
         *reinterpret_cast<const uint4 *>(W->w2 + n * kW2S + 8 * g);
   }
-  for (int e = tid; e < kMlpH; e += blockDim.x) {
-    sm.b1[e] = W->b1[e];
-    sm.b2[e] = W->b2[e];
-    sm.w3[e] = W->w3[e];
-  }
-  for (int e = tid; e < kMlpIn; e += blockDim.x) {
-    sm.mean[e] = W->mean[e];
-    sm.inv_std[e] = W->inv_std[e];
+  // b2 = hi + mid + lo exactly (each part takes the next 8 significant bits), so
+  // that one K = 16 MMA against the input tile's columns of ones adds it to Z2
+  for (int n = tid; n < kMlpH; n += blockDim.x) {
+    const float b = W->b2[n];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    const float r1 = b - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    const uint32_t w6 = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(mid) << 16);
+    const uint32_t w7 = (uint32_t)__bfloat16_as_ushort(lo);
+    *reinterpret_cast<uint4 *>(sm.wb2 + core_offset(n, 0, 16)) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(sm.wb2 + core_offset(n, 8, 16)) = make_uint4(0u, 0u, w6, w7);
   }
 }
 
@@ -722,11 +726,14 @@ __global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *
   if (warp == 0) tc_dealloc(tmem, 128);
 }
 
-// ---- the standalone scorer's variants of the helpers above.  The bias b1 is a
-// product of the first layer: W1's input columns 12 and 13 hold the BF16 parts
-// b1_hi = bf16(b1) and b1_lo = bf16(b1 - b1_hi) and every X row holds 1, 1 there,
-// so Z1 = X W1^T already contains b1 (to ~2^-17 of it); the epilogue only clamps
-// and rounds.  The standardisation, b2 and w3 come from the constant bank (the
+// ---- the standalone scorer's variants of the helpers above.  The biases are
+// products of the MMAs: every X row holds 1 in input columns 12, 13 and 14; W1's
+// columns 12 and 13 hold the BF16 parts b1_hi = bf16(b1) and b1_lo = bf16(b1 -
+// b1_hi) (its column 14 is 0), so Z1 = X W1^T already contains b1 (to ~2^-17 of
+// it) and the first epilogue only clamps and rounds; one more K = 16 MMA of the
+// same X against a matrix holding b2's three BF16 parts (hi, mid, lo: exactly b2)
+// in columns 12..14 starts Z2 at b2, so the second epilogue is a clamp and an FMA
+// per column.  The standardisation and w3 come from the constant bank (the
 // MlpHead parameter): shared-memory loads of them kept the scorer's load/store
 // pipe at 50 % with the tensor pipe at 9 %.
 __device__ __forceinline__ void tc_fold_b1(TcMlpSmem &sm, const MlpW *__restrict__ W) {
@@ -766,15 +773,15 @@ __device__ __forceinline__ float tc_epi_logit_c(uint32_t lane_addr, const MlpHea
     tc_ld16(lane_addr + 16u * q, z);
     tc_wait_ld();
 #pragma unroll
-    for (int c = 0; c < 16; c += 2) {
-      acc0 = fmaf(fmaxf(z[c] + hd.b2[16 * q + c], 0.f), hd.w3[16 * q + c], acc0);
-      acc1 = fmaf(fmaxf(z[c + 1] + hd.b2[16 * q + c + 1], 0.f), hd.w3[16 * q + c + 1], acc1);
+    for (int c = 0; c < 16; c += 2) {  // Z2 holds b2 already
+      acc0 = fmaf(fmaxf(z[c], 0.f), hd.w3[16 * q + c], acc0);
+      acc1 = fmaf(fmaxf(z[c + 1], 0.f), hd.w3[16 * q + c + 1], acc1);
     }
   }
   return acc0 + acc1;
 }
 
-// row r of the tile at x: standardised BF16 inputs, then 1, 1 (the bias columns), 0, 0
+// row r of the tile at x: standardised BF16 inputs, then 1, 1, 1 (the bias columns), 0
 __device__ __forceinline__ void tc_put_input_c(unsigned char *x, int r, const float *f, bool valid,
                                                const MlpHead &hd) {
   uint32_t w[6];
@@ -790,7 +797,7 @@ __device__ __forceinline__ void tc_put_input_c(unsigned char *x, int r, const fl
     w[p] = v;
   }
   *reinterpret_cast<uint4 *>(x + core_offset(r, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-  *reinterpret_cast<uint4 *>(x + core_offset(r, 8, 16)) = make_uint4(w[4], w[5], 0x3f803f80u, 0u);
+  *reinterpret_cast<uint4 *>(x + core_offset(r, 8, 16)) = make_uint4(w[4], w[5], 0x3f803f80u, 0x3f80u);
 }
 
 // logits of raw feature rows (float[m][12]) on the tcgen05 path.  A CTA of 256
@@ -847,16 +854,20 @@ __global__ void __launch_bounds__(256, 4) k_mlp_score_tc(const MlpW *__restrict_
     ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
     tc_fence_after();
     if (!ok) break;
-    // layer 2: H1 (128 x 64) W2^T of both tiles, four K = 16 steps each
+    // layer 2: b2 (X against the parts of b2), then H1 (128 x 64) W2^T in four K = 16
+    // steps, for both tiles
     if (tid == 0) {
       const uint32_t w0 = smem_u32(sm.w2);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const uint32_t h0 = smem_u32(sm.h[t]);
 #pragma unroll
+        tc_mma_bf16(tmem + 64u * t, tc_desc(smem_u32(sm.x[t]), 128, 256), tc_desc(smem_u32(sm.wb2), 128, 256), idesc,
+                    false);  // b2
+#pragma unroll
         for (int k4 = 0; k4 < 4; ++k4)
           tc_mma_bf16(tmem + 64u * t, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024), idesc,
-                      k4 > 0);
+                      true);
       }
       tc_commit(&sm.mbar);
     }
@@ -1034,7 +1045,7 @@ int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, u
       return -1;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  // 4 CTAs per SM (52 KB of shared memory each): their 128-column tensor-memory
+  // 4 CTAs per SM (54 KB of shared memory each): their 128-column tensor-memory
   // allocations (512 columns per SM) never wait on each other
   const uint32_t steps = (m + 255) / 256;
   const uint32_t grid = steps < (uint32_t)sms * 4 ? steps : (uint32_t)sms * 4;

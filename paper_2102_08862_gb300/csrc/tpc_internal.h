@@ -92,11 +92,11 @@ void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaSt
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);
 void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit, int sms, cudaStream_t st);
 // The classifier's FP32 values that every row of the dense scorer reads (the
-// standardisation, the second layer's bias, the BF16-rounded output weights and
-// the output bias), kept on the host when the weights are loaded and passed to the
-// kernel as a parameter, so that they are read from the constant bank.
+// standardisation, the BF16-rounded output weights and the output bias), kept on
+// the host when the weights are loaded and passed to the kernel as a parameter,
+// so that they are read from the constant bank.
 struct MlpHead {
-  float b2[64], w3[64], mean[12], inv_std[12], b3;
+  float w3[64], mean[12], inv_std[12], b3;
 };
 // the same on the tcgen05 tensor cores (128-row tiles, accumulators in tensor
 // memory); *err (device) is set if a bounded wait gave up; returns < 0 on a
