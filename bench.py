@@ -43,10 +43,10 @@ NOMINAL_HBM_GBS = 8000.0
 FIT_FLOP_PER_CLUSTER = 200.0  # transport + 2-D update per cluster in a track (algorithmic)
 # DRAM bytes per cluster of k_neighbours from one full ncu capture of the 5 ms frame,
 # valid while k_neighbours.cu is the file captured (its SHA-256)
-NB_TRAFFIC = {"sha256": "8464b29b659b8e1acd75cb55e3d9b9ec1c0eb0d1a0ed04012ddc9fab41c0703f",
-              "pruned": (135.739648e6 + 119.180800e6) / 16765809, "plain": (135.317760e6 + 93.424128e6) / 16765809}
+NB_TRAFFIC = {"sha256": "c49e6b95d87b0a1218176aefeb1a58d21a49c22321a8e12a8e8096b79f970c7b",
+              "pruned": (135.706880e6 + 119.200768e6) / 16765809, "plain": (135.304704e6 + 93.305600e6) / 16765809}
 # warp instructions per cluster of the same captures (smsp__inst_executed.sum / clusters)
-NB_INST = {"pruned": 401141061 / 16765809, "plain": 366996795 / 16765809}
+NB_INST = {"pruned": 401113197 / 16765809, "plain": 367001219 / 16765809}
 
 
 def neighbours_traffic(mode, n):

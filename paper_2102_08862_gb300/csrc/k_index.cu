@@ -64,17 +64,25 @@ __device__ __forceinline__ void stage_row_index_table(const Args &a) {
     a.sec_first[q] = ~0u;
     a.sec_cnt[q] = 0u;
   }
-  const volatile int32_t *rbv = a.row_begin;
+  // row_begin was written by the other blocks of this launch: read at L2 (ld.cg),
+  // eight keys' entries per round trip
+  const int32_t *rbg = a.row_begin;
   const int nkeys = a.nkeys, tile = a.nb_tile;
   const int per = (nkeys + blockDim.x - 1) / blockDim.x;
   const int k0 = threadIdx.x * per, k1 = min(nkeys, k0 + per);
   int mx = 0, ntile = 0;
-  for (int k = k0; k < k1; ++k) {
-    const int32_t b = rbv[k], e = rbv[k + 1];
-    if (e < b) raise(a.ctr, kErrInput);
-    const int c = max(0, e - b);
-    mx = max(mx, c);
-    ntile += (c + tile - 1) / tile;
+  for (int k = k0; k < k1; k += 8) {
+    int32_t v[9];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) v[u] = k + u <= k1 ? __ldcg(rbg + k + u) : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k + u < k1) {
+        if (v[u + 1] < v[u]) raise(a.ctr, kErrInput);
+        const int c = max(0, v[u + 1] - v[u]);
+        mx = max(mx, c);
+        ntile += (c + tile - 1) / tile;
+      }
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) s_max[threadIdx.x >> 5] = mx;
@@ -87,9 +95,16 @@ __device__ __forceinline__ void stage_row_index_table(const Args &a) {
     __syncthreads();
   }
   int off = s_scan[threadIdx.x] - ntile;
-  for (int k = k0; k < k1; ++k) {
-    a.tile_off[k] = off;
-    off += (max(0, rbv[k + 1] - rbv[k]) + tile - 1) / tile;
+  for (int k = k0; k < k1; k += 8) {
+    int32_t v[9];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) v[u] = k + u <= k1 ? __ldcg(rbg + k + u) : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k + u < k1) {
+        a.tile_off[k + u] = off;
+        off += (max(0, v[u + 1] - v[u]) + tile - 1) / tile;
+      }
   }
   if (threadIdx.x == blockDim.x - 1) {
     a.tile_off[nkeys] = s_scan[threadIdx.x];

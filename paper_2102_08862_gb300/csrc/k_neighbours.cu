@@ -406,12 +406,28 @@ __device__ __forceinline__ void stage_tile_windows(const Args &a, uint32_t bid, 
     if (r >= 1 && r <= kNRows - 2 && tb > ta) {
       const int t0 = a.tq[ta].x, t1 = a.tq[tb - 1].x;
       const int pb = a.row_begin[key - 1], pe = rb, nb = re, ne = a.row_begin[key + 2];
-      win.x = tq_lower_bound(a.tq, pb, pe, t0 - a.wt);
-      win.y = tq_lower_bound(a.tq, pb, pe, t1 + a.wt + 1);
-      win.z = tq_lower_bound(a.tq, nb, ne, t0 - a.wt);
-      win.w = tq_lower_bound(a.tq, nb, ne, t1 + a.wt + 1);
-      if (win.y < win.x) win.y = win.x;  // only with unsorted (invalid) input
-      if (win.w < win.z) win.w = win.z;
+      // the four lower bounds (first e in [lo, hi) with t_q(e) >= x) advance
+      // together, so that their loads are in flight at once; a finished search
+      // keeps loading its own position (< n: the array is padded) and ignores it
+      int lo[4] = {pb, pb, nb, nb}, hi[4] = {pe, pe, ne, ne};
+      const int x[4] = {t0 - a.wt, t1 + a.wt + 1, t0 - a.wt, t1 + a.wt + 1};
+      for (;;) {
+        bool more = false;
+        int tm[4], mid[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          mid[s] = (int)(((unsigned)lo[s] + (unsigned)hi[s]) >> 1);
+          tm[s] = a.tq[mid[s]].x;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (lo[s] < hi[s]) {
+            if (tm[s] < x[s]) lo[s] = mid[s] + 1; else hi[s] = mid[s];
+            more |= lo[s] < hi[s];
+          }
+        if (!more) break;
+      }
+      win = make_int4(lo[0], max(lo[1], lo[0]), lo[2], max(lo[3], lo[2]));  // (max: only with unsorted input)
     }
     a.tile_win[2 * t] = make_int4(key, ta, max(ta, tb), 0);
     a.tile_win[2 * t + 1] = win;
