@@ -39,6 +39,24 @@ namespace tpc {
 
 namespace {
 
+// The hardware's approximate reciprocal and reciprocal square root (PTX
+// rcp.approx.ftz.f32, at most 1 ulp; rsqrt.approx.ftz.f32, relative error below
+// 2^-22.9; denormal operands and results are flushed to zero), written as the
+// instructions themselves so that every translation unit that holds the filter
+// issues the same ones whatever its compile flags: the filter's operands are far
+// from the denormal range, and without the flush each call carries the
+// instructions that rescale a denormal operand.
+__device__ __forceinline__ float kf_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float kf_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // index of U(i, j), i < j, in the packed strictly-upper triangle
 __host__ __device__ constexpr int ui(int i, int j) { return 4 * i - i * (i - 1) / 2 + (j - i - 1); }
 
@@ -85,12 +103,12 @@ __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
   // cos phi, 1 / cos phi and the chord length from reciprocal square roots (one
   // special-function op each, and the divisions by c1, c2 and l become products)
   const float q1 = __fmul_rn(1.0f - s1, 1.0f + s1), q2 = __fmul_rn(1.0f - s2, 1.0f + s2);
-  const float ic1 = rsqrtf(q1), ic2 = rsqrtf(q2);
+  const float ic1 = kf_rsqrt(q1), ic2 = kf_rsqrt(q2);
   const float c1 = __fmul_rn(q1, ic1), c2 = __fmul_rn(q2, ic2);
-  const float A = __fadd_rn(s1, s2), D = __fadd_rn(c1, c2), iD = 1.0f / D;
+  const float A = __fadd_rn(s1, s2), D = __fadd_rn(c1, c2), iD = kf_rcp(D);
   const float dy = __fmul_rn(__fmul_rn(dx, A), iD);
   const float dx2 = __fmul_rn(dx, dx);
-  const float l2 = __fmaf_rn(dy, dy, dx2), il = rsqrtf(l2);
+  const float l2 = __fmaf_rn(dy, dy, dx2), il = kf_rsqrt(l2);
   const float l = __fmul_rn(l2, il);
   const float u = __fmul_rn(__fmul_rn(0.5f, cv), l);
   const float ds = __fmul_rn(l, asinc(u));
@@ -99,7 +117,7 @@ __device__ __forceinline__ bool kf_transport(Kf &k, float dx) {
   const float tn2 = __fmul_rn(s2, ic2);  // tan phi2
   const float Fys = __fmul_rn(__fmul_rn(dx, __fmaf_rn(A, __fmaf_rn(s1, ic1, tn2), __fmul_rn(2.0f, D))), iD2);  // dy/ds1
   const float Fyc = __fmul_rn(__fmul_rn(dx2, __fmaf_rn(A, tn2, D)), iD2);  // dy/dc
-  const float g = rsqrtf(__fmul_rn(1.0f - u, 1.0f + u));                // d(arc)/d(chord)
+  const float g = kf_rsqrt(__fmul_rn(1.0f - u, 1.0f + u));                // d(arc)/d(chord)
   const float dyl = __fmul_rn(dy, il);
   const float gdyl = __fmul_rn(g, dyl);
   const float a = Fys, b = __fmul_rn(-kBz, Fyc);                          // row y: (s, Q)
@@ -146,7 +164,7 @@ __device__ __forceinline__ void kf_measure(Kf &k, float meas, float V) {
     if (M == 0 && j == 1) continue;  // f[1] = U(0,1) = 0: alpha, D(1), U(0,1) and b[0] stay
     const float beta = alpha;
     alpha = fmaf(f[j], g[j], beta);
-    const float ia = 1.0f / alpha;
+    const float ia = kf_rcp(alpha);
     const float lam = -f[j] * ibeta;
     k.d[j] *= beta * ia;
 #pragma unroll
