@@ -761,7 +761,7 @@ def main():
                              pad=hp.data_ptr(), time=ht.data_ptr())
     htr = tpcca.tpc_tracks(cluster_track=hct.data_ptr(), track_capacity=tcap, n_tracks=hn.ctypes.data,
                            **{k: v.data_ptr() for k, v in host_out.items()})
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 30))  # host-side copies vary on a shared host: average 30 calls
     for _ in range(2):
         assert tpcca.tpc_track_timeframe_host(tr.handle, hcl, htr, sh) == 0, tpcca.tpc_last_error()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -20,8 +20,11 @@ SOURCES = ["api.cu", "k_index.cu", "k_neighbours.cu", "k_links.cu", "k_fit.cu", 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # per translation unit: the Kalman fit uses approximate FP32 division and square
-# root (the fit's tolerance against the FP64 oracle is 1e-4; linking is integer)
-TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"], "k_follow.cu": ["-prec-div=false", "-prec-sqrt=false"],
+# root (the fit's tolerance against the FP64 oracle is 1e-4; linking is integer);
+# the follower's searches also flush denormals (its operands are far from that
+# range, and the approximate division and square root then need no rescaling)
+TU_FLAGS = {"k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"],
+            "k_follow.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
             "k_persistent.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
