@@ -132,6 +132,40 @@ def test_scores_match_oracle_logits(env, c1, engine):
     assert (flips > 0).mean() < 0.4  # the bound widens only for rows near a rounding midpoint
 
 
+@pytest.mark.parametrize("engine", [0, 1])  # tcgen05 (tensor memory), mma.sync
+def test_scores_carry_the_second_layer_bias_exactly(env, engine):
+    """With W1, b1 and W2 zero, Z2 = b2 exactly and the logit is b3 + sum_o w3_o b2_o (all
+    positive here, so every unit is active and rounding errors of b2 add up): the GPU may differ
+    from the FP64 oracle only by its FP32 sum of 65 positive terms, at most 64 x 2^-24 = 2^-18 of
+    the sum in any summation order.  Each b2 needs all 24 bits of its significand (1 + 2^-9 +
+    2^-17 times a power of two: three BF16 parts); carried as two parts it would be off by 2^-17
+    of itself, twice the bound."""
+    tpcca, dev = env
+    from mlp_util import theta_views, zero_theta
+    rng = np.random.default_rng(21)
+    theta = zero_theta()
+    v = theta_views(theta)
+    frac = np.float32(1.0 + 2.0 ** -9 + 2.0 ** -17)
+    v["b2"][:] = (frac * np.float32(2.0) ** rng.integers(-6, 3, 64)).astype(np.float32)
+    v["w3"][:] = np.abs(rng.standard_normal(64)) * 0.5 + 0.05
+    v["b3"][:] = 0.25
+    mean, inv_std = np.zeros(12, np.float32), np.ones(12, np.float32)
+    blob = orc.mlp_blob(mean, inv_std, theta)
+    feat = rng.standard_normal((1000, 12)).astype(np.float32)
+    want = orc.mlp_logits(blob, feat)
+    assert np.all(want == want[0])  # the inputs do not reach the logit
+    tr = tpcca.TimeFrameTracker(1024)
+    try:
+        tr.load_mlp(blob)
+        got = tr.score(_dev_tensor(feat, dev), engine=engine).cpu().numpy().astype(np.float64)
+        torch.cuda.synchronize()
+        assert tpcca.tpc_tf_status(tr.handle, 0) == 0
+    finally:
+        tr.close()
+    total = float(want[0])  # b3 + sum of the positive products: the scale of the FP32 sum
+    np.testing.assert_allclose(got, want, rtol=0, atol=2.0 ** -18 * total)
+
+
 def test_score_and_pruned_mode_need_weights(env, c1):
     tpcca, dev = env
     tr = tpcca.TimeFrameTracker(c1.n + 16, mode=tpcca.TPC_MODE_PRUNED, tau=0.5)
