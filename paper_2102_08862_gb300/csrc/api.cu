@@ -95,6 +95,10 @@ struct tpc_tf {
   int4 *amb = nullptr;        // clusters listed for rescoring (arena, pruned mode only)
   PruneRow *q_rows = nullptr; // per-tile regions of rescored pairs (pruned mode only)
   int32_t *q_count = nullptr;
+  float *rr_feat = nullptr, *rr_logit = nullptr;  // the regions' rows as dense feature rows, their logits
+  int4 *rr_meta = nullptr;                        // each dense row's (cluster, j, k)
+  int64_t *rr_cost = nullptr;                     // and its cost
+  uint32_t *rr_tbase = nullptr;                   // each region's first dense row
   MlpW *mlp = nullptr;        // packed weights (allocated by tpc_mlp_load)
   MlpHead mlp_head = {};      // host copy of the values every scored row reads
   float *mlp_stage = nullptr; // FP32 blob body staged for packing
@@ -266,6 +270,12 @@ static std::vector<Part> plan_arena(tpc_tf *tf, const tpc_tf_config *cfg) {
       {(void **)&tf->q_rows,
        cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * sizeof(PruneRow) : 0},
       {(void **)&tf->q_count, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * 4 : 0},
+      {(void **)&tf->rr_feat,
+       cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * kMlpIn * 4 : 0},
+      {(void **)&tf->rr_logit, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * 4 : 0},
+      {(void **)&tf->rr_meta, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * 16 : 0},
+      {(void **)&tf->rr_cost, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * kPruneRegionRows * 8 : 0},
+      {(void **)&tf->rr_tbase, cfg->mode == TPC_MODE_PRUNED ? (size_t)tf->tile_cap * 4 : 0},
       {(void **)&tf->f_params, fol ? TL * 5 * 4 : 0},
       {(void **)&tf->f_cov, fol ? TL * 15 * 4 : 0},
       {(void **)&tf->f_tref, fol ? TL * 4 : 0},
@@ -539,11 +549,12 @@ static int enqueue_linking(tpc_tf *tf, const tpc_clusters *cl, Args &a, cudaStre
   stage(tf, st, "neighbours");
   tf->launches += 4;
   if (prune) {
-    launch_prune_tiles(a, tf->mlp, tf->logit_tau, tf->sms, tf->cfg.mlp_engine, st);
+    launch_region_rescore(a, tf->mlp, tf->mlp_head, tf->rr_feat, tf->rr_meta, tf->rr_cost, tf->rr_logit, tf->rr_tbase,
+                          tf->logit_tau, tf->sms, tf->cfg.mlp_engine, st);
     stage(tf, st, "prune_tiles");
     launch_prune(a, tf->mlp, tf->logit_tau, tf->sms, st);
     stage(tf, st, "prune_list");
-    tf->launches += 2;
+    tf->launches += 4;
   }
   launch_edge_claims(a, st);
   stage(tf, st, "edge_claims");
@@ -1096,7 +1107,8 @@ extern "C" int tpc_mlp_load(tpc_tf *tf, const void *blob, size_t bytes) {
   launch_mlp_pack(body + 24, body, body + 12, tf->mlp, 0);
   TPC_CK(cudaGetLastError());
   TPC_CK(cudaDeviceSynchronize());
-  if (prune_tiles_prepare() != 0) return fail(TPC_ERR_CUDA, "tpc_mlp_load: cannot configure the region scorer");
+  if (mlp_score_tc_prepare() != 0)
+    return fail(TPC_ERR_CUDA, "tpc_mlp_load: cannot configure the region scorer");
   tf->mlp_ready = true;
   return TPC_OK;
 }

@@ -8,13 +8,13 @@
 // whose score sigmoid(logit) reaches tau, or the plain choice when none does.
 // Only ~2 % of clusters are ambiguous at Pb-Pb-like densities.  The neighbour
 // kernel writes the pairs of a tile's ambiguous clusters into the tile's own
-// region (i, j, k, candidate counts); k_prune_tiles gives each region to one
-// warp, which computes the features of its rows, stages them as BF16 in shared
-// memory, runs the MLP on 16-pair tensor-core tiles and decides each cluster from
-// its contiguous rows.  Clusters that the neighbour kernel could not put in a
-// region (windows too large to stage, or the region full) are listed instead,
-// and k_prune rescores those: each warp takes 32 listed clusters and
-// re-enumerates their pairs from global memory.
+// region (i, j, k, candidate counts, quantised coordinates); k_region_feat packs
+// the regions' rows into a dense array of feature rows, the dense scorer (tcgen05
+// or mma.sync) scores it, and k_region_decide decides each cluster from its
+// contiguous rows.  Clusters that the neighbour kernel could not put in a region
+// (windows too large to stage, or the region full) are listed instead, and
+// k_prune rescores those: each warp takes 32 listed clusters and re-enumerates
+// their pairs from global memory.
 #include "mlp_dev.cuh"
 #include "tc_dev.cuh"
 #include "tpc_internal.h"
@@ -301,111 +301,6 @@ __global__ void __launch_bounds__(kPruneWarps * 32) k_prune(Args a, const MlpW *
   flush(true);
 }
 
-// Rows of the neighbour tiles' regions: one warp per tile region, features
-// staged 32 rows at a time (small per-warp buffers, so that 24 warps fit on an SM).
-constexpr int kPtWarps = 8;
-constexpr int kPtRows = 32;
-struct __align__(16) TilesSmem {
-  __nv_bfloat16 w1[kMlpH * kXS];
-  __nv_bfloat16 w2[kMlpH * kW2S];
-  float b1[kMlpH], b2[kMlpH], w3[kMlpH];
-  float mean[kMlpIn], inv_std[kMlpIn];
-  __nv_bfloat16 x[kPtWarps][kPtRows * kXS];
-  int64_t pc[kPtWarps][kPruneRegionRows];
-  int32_t pi[kPtWarps][kPruneRegionRows];
-  float lg[kPtWarps][kPruneRegionRows];
-};
-static_assert(sizeof(TilesSmem) <= 48 * 1024, "static shared memory");
-
-__global__ void __launch_bounds__(kPtWarps * 32, 4) k_prune_tiles(Args a, const MlpW *__restrict__ W,
-                                                                  float logit_tau) {
-  __shared__ TilesSmem sm;
-  {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const uint4 *s1 = reinterpret_cast<const uint4 *>(W->w1);
-    for (int e = tid; e < (int)(sizeof(sm.w1) / 16); e += nt) reinterpret_cast<uint4 *>(sm.w1)[e] = s1[e];
-    const uint4 *s2 = reinterpret_cast<const uint4 *>(W->w2);
-    for (int e = tid; e < (int)(sizeof(sm.w2) / 16); e += nt) reinterpret_cast<uint4 *>(sm.w2)[e] = s2[e];
-    for (int e = tid; e < kMlpH; e += nt) {
-      sm.b1[e] = W->b1[e];
-      sm.b2[e] = W->b2[e];
-      sm.w3[e] = W->w3[e];
-    }
-    for (int e = tid; e < kMlpIn; e += nt) {
-      sm.mean[e] = W->mean[e];
-      sm.inv_std[e] = W->inv_std[e];
-    }
-  }
-  __syncthreads();
-  const float b3 = W->b3;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16 *xs = sm.x[warp];
-  int64_t *pc = sm.pc[warp];
-  int32_t *pi = sm.pi[warp];
-  float *lg = sm.lg[warp];
-  const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
-  uint32_t clusters = 0;
-  for (uint32_t tile = blockIdx.x * kPtWarps + warp; tile < ntiles; tile += gridDim.x * kPtWarps) {
-    const int cnt = min(a.q_count[tile], kPruneRegionRows);
-    if (cnt < 2) continue;  // warp-uniform
-    const PruneRow *rows = a.q_rows + (size_t)tile * kPruneRegionRows;
-    const int r = a.tile_win[2 * tile].x % kNRows;  // the tile's pad row
-    for (int base = 0; base < cnt; base += kPtRows) {
-      const int m = min(kPtRows, cnt - base);
-      for (int rr = lane; rr < m; rr += 32) {
-        const int4 *pr = reinterpret_cast<const int4 *>(rows + base + rr);
-        const int4 q = pr[0], c1 = pr[1], c2 = pr[2];  // (i, j, k, cn), (ti, yi, tj, yj), (tk, yk, -, -)
-        const int64_t c = triplet_cost(c1.w - c1.y, c2.y - c1.y, c1.z - c1.x, c2.x - c1.x);
-        float f[kMlpIn];
-        triplet_features(r, c1.w, c1.y, c2.y, c1.z, c1.x, c2.x, c, q.w & 0xffff, (int)((unsigned)q.w >> 16),
-                         a.cost_max, f);
-        store_input_row(xs + rr * kXS, f, sm.mean, sm.inv_std);
-        pc[base + rr] = c;
-        pi[base + rr] = q.x;
-      }
-      const int ntile = (m + 15) >> 4;
-      for (int rr = m + lane; rr < ntile * 16; rr += 32) {
-        reinterpret_cast<uint4 *>(xs + rr * kXS)[0] = make_uint4(0, 0, 0, 0);
-        reinterpret_cast<uint4 *>(xs + rr * kXS)[1] = make_uint4(0, 0, 0, 0);
-      }
-      __syncwarp();
-      for (int tt = 0; tt < ntile; ++tt) {
-        float l0, l1;
-        mlp_forward_tile(xs + tt * 16 * kXS, sm.w1, sm.w2, sm.b1, sm.b2, sm.w3, b3, l0, l1);
-        const int g = lane >> 2;
-        if ((lane & 3) == 0) {
-          if (tt * 16 + g < m) lg[base + tt * 16 + g] = l0;
-          if (tt * 16 + g + 8 < m) lg[base + tt * 16 + g + 8] = l1;
-        }
-      }
-      __syncwarp();
-    }
-    // a cluster's rows are contiguous: the lane holding its first row keeps the
-    // smallest (cost, j, k) among the rows that pass (j, k compared as sorted
-    // positions, which order the clusters of one row as their row-local indices)
-    for (int rr = lane; rr < cnt; rr += 32) {
-      const int i = pi[rr];
-      if (rr > 0 && pi[rr - 1] == i) continue;
-      ++clusters;
-      int64_t bestc = INT64_MAX;
-      int bj = 0x7fffffff, bk = 0x7fffffff;
-      for (int m = rr; m < cnt && pi[m] == i; ++m) {
-        if (!(lg[m] >= logit_tau)) continue;
-        const int qj = rows[m].j, qk = rows[m].k;
-        if (pc[m] < bestc || (pc[m] == bestc && (qj < bj || (qj == bj && qk < bk)))) {
-          bestc = pc[m];
-          bj = qj;
-          bk = qk;
-        }
-      }
-      if (bestc != INT64_MAX) a.link[i] = make_int2(bj, bk);
-    }
-    __syncwarp();
-  }
-  for (int o = 16; o > 0; o >>= 1) clusters += __shfl_xor_sync(0xffffffffu, clusters, o);
-  if (lane == 0 && clusters) atomicAdd(&a.ctr[kCtrQueued], clusters);
-}
-
 // ------------------------------------------------------------------ packing
 // theta (blob order: W1, b1, W2, b2, w3, b3) -> BF16 tiles; one thread per entry
 __global__ void k_mlp_pack(const float *__restrict__ theta, const float *__restrict__ mean,
@@ -433,15 +328,13 @@ __global__ void k_mlp_pack(const float *__restrict__ theta, const float *__restr
 }
 
 // ------------------------------------------------------ tcgen05 MLP (128 rows)
-// One CTA of 128 threads scores 128 rows at a time on the fifth-generation tensor
-// cores: thread r writes row r's standardised BF16 inputs in the core-matrix
-// layout; one tcgen05.mma (M 128, N 64, K 16) puts layer 1 in tensor memory (64
-// FP32 columns); each thread loads its row back (tcgen05.ld, 32 columns per
-// load), adds the bias, applies ReLU, rounds to BF16 and writes the row of H1;
-// four MMAs (K 64) give layer 2; each thread finishes its row's logit in FP32.
-// The epilogues work on column pairs (packed FP32 adds and FMAs, one BF16x2
-// conversion per pair).  Completion of the MMAs is signalled through an mbarrier
-// (bounded wait).
+// The dense scorer on the fifth-generation tensor cores, per 128-row tile: thread
+// r writes row r's standardised BF16 inputs in the core-matrix layout; one
+// tcgen05.mma (M 128, N 64, K 16) puts layer 1, bias included, in tensor memory
+// (64 FP32 columns); each thread loads its row back (tcgen05.ld, 32 columns per
+// load), applies ReLU, rounds to BF16 and writes the row of H1; five MMAs (b2,
+// then K 64) give layer 2; each thread finishes its row's logit in FP32.
+// Completion of the MMAs is signalled through an mbarrier (bounded wait).
 struct __align__(1024) TcMlpSmem {
   unsigned char x[2][128 * 16 * 2];   // inputs of the two tiles, core-matrix layout (K 16)
   unsigned char h[2][128 * 64 * 2];   // their first hidden layers (K 64)
@@ -479,254 +372,7 @@ __device__ __forceinline__ void tc_stage_weights(TcMlpSmem &sm, const MlpW *__re
   }
 }
 
-// Epilogue of the first layer for the row in this thread's tensor-memory lane:
-// columns [0, 64) + b1, ReLU, BF16, written as row hr of the K = 64 core-matrix
-// operand at hb.  Pairs of columns go through packed FP32 adds and one
-// conversion + max per BF16 pair.
-__device__ __forceinline__ void tc_epi_hidden(uint32_t lane_addr, const float *b1, unsigned char *hb, int hr) {
-  uint32_t z[32];
-#pragma unroll
-  for (int hf = 0; hf < 2; ++hf) {
-    tc_ld32(lane_addr + 32u * hf, z);
-    tc_wait_ld();
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {  // 8 columns: one 16-byte row of a core matrix
-      const float4 ba = *reinterpret_cast<const float4 *>(b1 + 32 * hf + 8 * g);
-      const float4 bb = *reinterpret_cast<const float4 *>(b1 + 32 * hf + 8 * g + 4);
-      const uint32_t bw[8] = {__float_as_uint(ba.x), __float_as_uint(ba.y), __float_as_uint(ba.z),
-                              __float_as_uint(ba.w), __float_as_uint(bb.x), __float_as_uint(bb.y),
-                              __float_as_uint(bb.z), __float_as_uint(bb.w)};
-      uint32_t w[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int c = 8 * g + 2 * p;
-        w[p] = bf16x2_relu(f2_add(f2_pack(z[c], z[c + 1]), f2_pack(bw[2 * p], bw[2 * p + 1])));
-      }
-      *reinterpret_cast<uint4 *>(hb + core_offset(hr, 32 * hf + 8 * g, 64)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-  }
-}
-
-// Epilogue of the second layer: b3 + sum_c w3[c] max(z[c] + b2[c], 0) over the
-// 64 columns of this thread's lane (two packed FP32 accumulators)
-__device__ __forceinline__ float tc_epi_logit(uint32_t lane_addr, const float *b2, const float *w3, float b3) {
-  uint32_t z[32];
-  uint64_t acc = 0;
-#pragma unroll
-  for (int hf = 0; hf < 2; ++hf) {
-    tc_ld32(lane_addr + 32u * hf, z);
-    tc_wait_ld();
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const float4 bq = *reinterpret_cast<const float4 *>(b2 + 32 * hf + 4 * g);
-      const float4 wq = *reinterpret_cast<const float4 *>(w3 + 32 * hf + 4 * g);
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int c = 4 * g + 2 * p;
-        const uint64_t v = f2_add(f2_pack(z[c], z[c + 1]),
-                                  p ? f2_pack(__float_as_uint(bq.z), __float_as_uint(bq.w))
-                                    : f2_pack(__float_as_uint(bq.x), __float_as_uint(bq.y)));
-        const float lo = fmaxf(__uint_as_float((uint32_t)v), 0.f), hi = fmaxf(__uint_as_float((uint32_t)(v >> 32)), 0.f);
-        acc = f2_fma(f2_pack(__float_as_uint(lo), __float_as_uint(hi)),
-                     p ? f2_pack(__float_as_uint(wq.z), __float_as_uint(wq.w))
-                       : f2_pack(__float_as_uint(wq.x), __float_as_uint(wq.y)),
-                     acc);
-      }
-    }
-  }
-  return b3 + (__uint_as_float((uint32_t)acc) + __uint_as_float((uint32_t)(acc >> 32)));
-}
-
-// Rows of the neighbour tiles' regions on the tcgen05 path.  A CTA of 256
-// threads takes 32 consecutive tile regions at a time and packs their rows,
-// region after region, into batches of at most 256 rows (a region holds at most
-// 128 rows and never straddles two batches): thread r computes row r's features
-// into the core-matrix layout; each layer is two M = 128 MMAs (rows 0-127 into
-// tensor-memory columns 0-63, rows 128-255 into columns 64-127) sharing the
-// weights; and the thread holding a cluster's first row picks the smallest
-// passing (cost, j, k) among the cluster's contiguous rows (a cluster's rows all
-// sit in one region).  Regions hold ~17 rows on the 10 ms frame: the batches are
-// short chains of staging, MMA and epilogue, bound by their latency, so a CTA
-// takes 256 rows per step rather than 128.
-constexpr int kTcRegions = 32;  // regions examined per step
-constexpr int kTcRows = 256;    // rows per batch (two M = 128 halves)
-struct __align__(1024) TcPruneSmem {
-  unsigned char x[kTcRows * 16 * 2];   // inputs, core-matrix layout (K 16), half h at h * 4096
-  unsigned char h[kTcRows * 64 * 2];   // first hidden layer (K 64), half h at h * 16384
-  unsigned char w1[64 * 16 * 2];
-  unsigned char w2[64 * 64 * 2];
-  float b1[kMlpH], b2[kMlpH], w3[kMlpH], mean[kMlpIn], inv_std[kMlpIn];
-  int64_t pc[kTcRows];
-  int32_t pi[kTcRows], pj[kTcRows], pk[kTcRows];
-  float lg[kTcRows];
-  int32_t off[kTcRegions + 1];  // region row offsets inside the group (regions with < 2 rows count 0)
-  uint64_t mbar;
-  uint32_t tmem;
-};
-
-__global__ void __launch_bounds__(kTcRows) k_prune_tiles_tc(Args a, const MlpW *__restrict__ W, float logit_tau) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  TcPruneSmem &sm = *reinterpret_cast<TcPruneSmem *>(smraw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int half = tid >> 7, hr = tid & 127;  // the thread's MMA half and row (= tensor-memory lane) in it
-  for (int e = tid; e < kMlpH * 2; e += blockDim.x) {
-    const int n = e >> 1, g = e & 1;
-    *reinterpret_cast<uint4 *>(sm.w1 + core_offset(n, 8 * g, 16)) =
-        *reinterpret_cast<const uint4 *>(W->w1 + n * kXS + 8 * g);
-  }
-  for (int e = tid; e < kMlpH * 8; e += blockDim.x) {
-    const int n = e >> 3, g = e & 7;
-    *reinterpret_cast<uint4 *>(sm.w2 + core_offset(n, 8 * g, 64)) =
-        *reinterpret_cast<const uint4 *>(W->w2 + n * kW2S + 8 * g);
-  }
-  for (int e = tid; e < kMlpH; e += blockDim.x) {
-    sm.b1[e] = W->b1[e];
-    sm.b2[e] = W->b2[e];
-    sm.w3[e] = W->w3[e];
-  }
-  for (int e = tid; e < kMlpIn; e += blockDim.x) {
-    sm.mean[e] = W->mean[e];
-    sm.inv_std[e] = W->inv_std[e];
-  }
-  if (tid == 0) mbar_init(&sm.mbar, 1);
-  if (warp == 0) tc_alloc(&sm.tmem, 128);
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = sm.tmem;
-  // warp w reads tensor-memory lanes 32 (w % 4) ..; its half's columns start at 64 * half
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)half;
-  const float b3 = W->b3;
-  const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
-  const uint32_t idesc = tc_idesc_bf16(128, 64);
-  uint32_t clusters = 0, phase = 0;
-  bool ok = true;
-  for (uint32_t g0 = blockIdx.x * kTcRegions; g0 < ntiles && ok; g0 += gridDim.x * kTcRegions) {
-    const int nreg = (int)min((uint32_t)kTcRegions, ntiles - g0);
-    if (tid < 32) {  // row offsets of the group's regions
-      int c = lane < nreg ? min(a.q_count[g0 + lane], kPruneRegionRows) : 0;
-      if (c < 2) c = 0;
-      int x = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      sm.off[lane + 1] = x;
-      if (lane == 0) sm.off[0] = 0;
-    }
-    __syncthreads();
-    for (int s = 0; s < nreg && ok;) {
-      int e = s;  // regions [s, e) fill the batch
-      while (e < nreg && sm.off[e + 1] - sm.off[s] <= kTcRows) ++e;
-      const int rows = sm.off[e] - sm.off[s];
-      if (rows > 0) {
-        const bool mine = tid < rows;
-        float f[kMlpIn];
-        if (mine) {
-          const int gr = sm.off[s] + tid;
-          int g = s;
-          while (sm.off[g + 1] <= gr) ++g;
-          const uint32_t tile = g0 + (uint32_t)g;
-          const int4 *pr =
-              reinterpret_cast<const int4 *>(a.q_rows + (size_t)tile * kPruneRegionRows + (gr - sm.off[g]));
-          const int4 q = pr[0], c1 = pr[1], c2 = pr[2];  // (i, j, k, cn), (ti, yi, tj, yj), (tk, yk, -, -)
-          const int r = a.tile_win[2 * tile].x % kNRows;
-          const int64_t c = triplet_cost(c1.w - c1.y, c2.y - c1.y, c1.z - c1.x, c2.x - c1.x);
-          triplet_features(r, c1.w, c1.y, c2.y, c1.z, c1.x, c2.x, c, q.w & 0xffff, (int)((unsigned)q.w >> 16),
-                           a.cost_max, f);
-          sm.pc[tid] = c;
-          sm.pi[tid] = q.x;
-          sm.pj[tid] = q.y;
-          sm.pk[tid] = q.z;
-        }
-        {  // input row (zeros past the batch)
-          uint32_t w[8];
-#pragma unroll
-          for (int p = 0; p < 8; ++p) {
-            const int cc = 2 * p;
-            uint32_t h = 0;
-            if (mine && cc < kMlpIn) {
-              const float lo = __fmul_rn(__fsub_rn(f[cc], sm.mean[cc]), sm.inv_std[cc]);
-              const float hi = __fmul_rn(__fsub_rn(f[cc + 1], sm.mean[cc + 1]), sm.inv_std[cc + 1]);
-              asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
-            }
-            w[p] = h;
-          }
-          unsigned char *xb = sm.x + 4096 * half;
-          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-          *reinterpret_cast<uint4 *>(xb + core_offset(hr, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-        }
-        const bool two = rows > 128;  // second half in use
-        // layer 1
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-          for (int hh = 0; hh < (two ? 2 : 1); ++hh)
-            tc_mma_bf16(tmem + 64u * hh, tc_desc(smem_u32(sm.x) + 4096 * hh, 128, 256),
-                        tc_desc(smem_u32(sm.w1), 128, 256), idesc, false);
-          tc_commit(&sm.mbar);
-        }
-        ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, phase, a.spin_limit));
-        phase ^= 1u;
-        tc_fence_after();
-        if (ok && (half == 0 || two)) tc_epi_hidden(lane_base, sm.b1, sm.h + 16384 * half, hr);
-        fence_async_smem();
-        tc_fence_before();
-        ok = __syncthreads_and(ok);  // layer 2 only if every thread saw layer 1 complete
-        tc_fence_after();
-        if (!ok) break;
-        if (tid == 0) {
-          for (int hh = 0; hh < (two ? 2 : 1); ++hh) {
-            const uint32_t h0 = smem_u32(sm.h) + 16384 * hh, w0 = smem_u32(sm.w2);
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4)
-              tc_mma_bf16(tmem + 64u * hh, tc_desc(h0 + 256 * k4, 128, 1024), tc_desc(w0 + 256 * k4, 128, 1024),
-                          idesc, k4 > 0);
-          }
-          tc_commit(&sm.mbar);
-        }
-        ok = __all_sync(0xffffffffu, mbar_wait(&sm.mbar, phase, a.spin_limit));
-        phase ^= 1u;
-        tc_fence_after();
-        sm.lg[tid] = (ok && (half == 0 || two)) ? tc_epi_logit(lane_base, sm.b2, sm.w3, b3) : b3;
-        tc_fence_before();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        // a cluster's rows are contiguous: the thread holding its first row decides
-        if (mine && (tid == 0 || sm.pi[tid - 1] != sm.pi[tid])) {
-          const int i = sm.pi[tid];
-          ++clusters;
-          int64_t bestc = INT64_MAX;
-          int bj = 0x7fffffff, bk = 0x7fffffff;
-          for (int m = tid; m < rows && sm.pi[m] == i; ++m) {
-            if (!(sm.lg[m] >= logit_tau)) continue;
-            const int qj = sm.pj[m], qk = sm.pk[m];
-            if (sm.pc[m] < bestc || (sm.pc[m] == bestc && (qj < bj || (qj == bj && qk < bk)))) {
-              bestc = sm.pc[m];
-              bj = qj;
-              bk = qk;
-            }
-          }
-          if (bestc != INT64_MAX) a.link[i] = make_int2(bj, bk);
-        }
-        __syncthreads();  // the batch's rows are free again
-      }
-      s = e;
-    }
-    __syncthreads();  // sm.off is rewritten for the next group
-  }
-  if (!ok && tid == 0) raise(a.ctr, kErrTimeout);
-  for (int o = 16; o > 0; o >>= 1) clusters += __shfl_xor_sync(0xffffffffu, clusters, o);
-  if (lane == 0 && clusters) atomicAdd(&a.ctr[kCtrQueued], clusters);
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, 128);
-}
-
-// ---- the standalone scorer's variants of the helpers above.  The biases are
+// ---- helpers of the dense scorer.  The biases are
 // products of the MMAs: every X row holds 1 in input columns 12, 13 and 14; W1's
 // columns 12 and 13 hold the BF16 parts b1_hi = bf16(b1) and b1_lo = bf16(b1 -
 // b1_hi) (its column 14 is 0), so Z1 = X W1^T already contains b1 (to ~2^-17 of
@@ -808,9 +454,13 @@ __device__ __forceinline__ void tc_put_input_c(unsigned char *x, int r, const fl
 // an SM (tensor memory: 4 x 128 of 512 columns; 64 registers a thread), 32 warps
 // in all, which hide the MMA and load latencies; the per-row constants are kernel
 // parameters (MlpHead), so the epilogues read no shared memory.
+// With m_dev set, the rows are the first min(*m_dev, m) (a count written on the
+// device by an earlier kernel of the stream; m is then the buffers' capacity).
 __global__ void __launch_bounds__(256, 4) k_mlp_score_tc(const MlpW *__restrict__ W, const __grid_constant__ MlpHead hd,
                                                          const float *__restrict__ feat, uint32_t m,
+                                                         const uint32_t *__restrict__ m_dev,
                                                          float *__restrict__ logit, int *err) {
+  if (m_dev) m = min(m, *m_dev);
   extern __shared__ __align__(1024) unsigned char smraw[];
   TcMlpSmem &sm = *reinterpret_cast<TcMlpSmem *>(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, h = tid >> 7, r = tid & 127;
@@ -888,7 +538,9 @@ __global__ void __launch_bounds__(256, 4) k_mlp_score_tc(const MlpW *__restrict_
 // logits of raw feature rows (float[m][12]); one warp per 16 rows
 __global__ void __launch_bounds__(kPruneWarps * 32) k_mlp_score(const MlpW *__restrict__ W,
                                                                 const float *__restrict__ feat, uint32_t m,
+                                                                const uint32_t *__restrict__ m_dev,
                                                                 float *__restrict__ logit) {
+  if (m_dev) m = min(m, *m_dev);  // (as in k_mlp_score_tc)
   __shared__ PruneSmem sm;
   stage_weights(sm, W);
   __syncthreads();
@@ -995,16 +647,115 @@ __global__ void __launch_bounds__(256) k_mlp_extract(Args a, float *__restrict__
 }
 
 // ------------------------------------------------------------------ launchers
-size_t prune_tiles_tc_smem();
-void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, int engine, cudaStream_t st) {
-  if (engine == TPC_MMA_SYNC) {
-    // 4 CTAs per SM: the register limit (64 per thread), below the shared-memory one
-    k_prune_tiles<<<sms * 4, kPtWarps * 32, 0, st>>>(a, w, logit_tau);
-    return;
+// ---- region rescoring in three passes.  (1) k_region_feat packs the rows of the
+// tile regions into one dense array of feature rows: a CTA step takes 32 regions,
+// takes their place in the array with one atomic (regions land in any order, each
+// stays contiguous) and records each region's first row in tbase; every thread
+// computes the 12 features of its rows.  (2) The dense scorer of either engine
+// scores the array at full tensor-core occupancy, reading the row count from the
+// device.  (3) k_region_decide gives each dense row one thread; the thread holding
+// a cluster's first row (a cluster's rows are contiguous, and never span two
+// regions) keeps the smallest (cost, j, k) among the cluster's rows whose logit
+// passes.  Each row's (cluster, j, k) and cost go to meta and cost in pass (1).
+// One kernel that ran the three phases per CTA, as a chain of 256-row batches,
+// was bound by that chain's latency (0.125-0.14 ms on the 10 ms frame against
+// 0.099 ms for the three passes with the tcgen05 scorer).
+constexpr int kRegionGroup = 32;  // regions per CTA step of k_region_feat
+__global__ void __launch_bounds__(256) k_region_feat(Args a, float *__restrict__ feat, int4 *__restrict__ meta,
+                                                     int64_t *__restrict__ cost, uint32_t *__restrict__ tbase) {
+  __shared__ int s_off[kRegionGroup + 1];
+  __shared__ uint32_t s_base;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t ntiles = min(a.ctr[kCtrTiles], a.tile_cap);
+  for (uint32_t g0 = blockIdx.x * kRegionGroup; g0 < ntiles; g0 += gridDim.x * kRegionGroup) {
+    const int nreg = (int)min((uint32_t)kRegionGroup, ntiles - g0);
+    if (tid < 32) {  // the regions' row counts, their offsets and the step's place in the array
+      int c = lane < nreg ? min(a.q_count[g0 + lane], kPruneRegionRows) : 0;
+      if (c < 2) c = 0;
+      int x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t base = 0;
+      if (lane == 31 && x > 0) base = atomicAdd(&a.ctr[kCtrRegionRows], (uint32_t)x);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      if (lane < nreg) tbase[g0 + lane] = base + (uint32_t)(x - c);
+      s_off[lane + 1] = x;
+      if (lane == 0) {
+        s_off[0] = 0;
+        s_base = base;
+      }
+    }
+    __syncthreads();
+    const int total = s_off[kRegionGroup];
+    const uint32_t base = s_base;
+    for (int gr = tid; gr < total; gr += blockDim.x) {
+      int g = 0;  // the region of row gr: the last g with s_off[g] <= gr
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1)
+        if (s_off[g + st] <= gr) g += st;
+      const uint32_t tile = g0 + (uint32_t)g;
+      const int4 *pr = reinterpret_cast<const int4 *>(a.q_rows + (size_t)tile * kPruneRegionRows + (gr - s_off[g]));
+      const int4 q = pr[0], c1 = pr[1], c2 = pr[2];  // (i, j, k, cn), (ti, yi, tj, yj), (tk, yk, -, -)
+      const int r = a.tile_win[2 * tile].x % kNRows;
+      const int64_t c = triplet_cost(c1.w - c1.y, c2.y - c1.y, c1.z - c1.x, c2.x - c1.x);
+      float f[kMlpIn];
+      triplet_features(r, c1.w, c1.y, c2.y, c1.z, c1.x, c2.x, c, q.w & 0xffff, (int)((unsigned)q.w >> 16), a.cost_max,
+                       f);
+      const size_t d = base + (uint32_t)gr;
+      float4 *dst = reinterpret_cast<float4 *>(feat + d * kMlpIn);
+      dst[0] = make_float4(f[0], f[1], f[2], f[3]);
+      dst[1] = make_float4(f[4], f[5], f[6], f[7]);
+      dst[2] = make_float4(f[8], f[9], f[10], f[11]);
+      meta[d] = make_int4(q.x, q.y, q.z, 0);
+      cost[d] = c;
+    }
+    __syncthreads();  // s_off is rewritten by the next step
   }
-  // 3 CTAs per SM (65 KB of shared memory each): their 128-column tensor-memory
-  // allocations (384 of the SM's 512 columns) never wait on each other
-  k_prune_tiles_tc<<<sms * 3, kTcRows, prune_tiles_tc_smem(), st>>>(a, w, logit_tau);
+}
+
+__global__ void __launch_bounds__(256) k_region_decide(Args a, const float *__restrict__ logit,
+                                                       const int4 *__restrict__ meta, const int64_t *__restrict__ cost,
+                                                       uint32_t rows_cap, float logit_tau) {
+  const uint32_t m = min(a.ctr[kCtrRegionRows], rows_cap);
+  uint32_t clusters = 0;
+  for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < m; d += gridDim.x * blockDim.x) {
+    const int4 h = meta[d];  // (cluster, j, k, -)
+    if (d > 0 && meta[d - 1].x == h.x) continue;  // not its cluster's first row
+    ++clusters;
+    int32_t bj = 0x7fffffff, bk = 0x7fffffff;
+    int64_t bestc = INT64_MAX;
+    for (uint32_t e = d; e < m; ++e) {
+      const int4 he = e == d ? h : meta[e];
+      if (he.x != h.x) break;
+      if (!(logit[e] >= logit_tau)) continue;
+      const int64_t c = cost[e];
+      if (c < bestc || (c == bestc && (he.y < bj || (he.y == bj && he.z < bk)))) {
+        bestc = c;
+        bj = he.y;
+        bk = he.z;
+      }
+    }
+    if (bestc != INT64_MAX) a.link[h.x] = make_int2(bj, bk);
+  }
+  for (int o = 16; o > 0; o >>= 1) clusters += __shfl_xor_sync(0xffffffffu, clusters, o);
+  if ((threadIdx.x & 31) == 0 && clusters) atomicAdd(&a.ctr[kCtrQueued], clusters);
+}
+
+size_t mlp_score_tc_smem();
+void launch_region_rescore(const Args &a, const MlpW *w, const MlpHead &head, float *feat, int4 *meta,
+                           int64_t *cost, float *logit, uint32_t *tbase, float logit_tau, int sms, int engine,
+                           cudaStream_t st) {
+  const uint32_t rows_cap = a.tile_cap * (uint32_t)kPruneRegionRows;
+  k_region_feat<<<sms * 8, 256, 0, st>>>(a, feat, meta, cost, tbase);
+  const uint32_t *m_dev = a.ctr + kCtrRegionRows;
+  if (engine == TPC_MMA_SYNC)
+    k_mlp_score<<<sms * 8, kPruneWarps * 32, 0, st>>>(w, feat, rows_cap, m_dev, logit);
+  else  // 4 CTAs per SM, as in launch_mlp_score_tc
+    k_mlp_score_tc<<<sms * 4, 256, mlp_score_tc_smem(), st>>>(w, head, feat, rows_cap, m_dev, logit,
+                                                               reinterpret_cast<int *>(a.ctr + kCtrErr));
+  k_region_decide<<<sms * 8, 256, 0, st>>>(a, logit, meta, cost, rows_cap, logit_tau);
 }
 
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st) {
@@ -1019,23 +770,15 @@ void launch_mlp_score(const MlpW *w, const float *feat, uint32_t m, float *logit
   if (m == 0) return;
   const uint32_t tiles = (m + 15) / 16, blocks = (tiles + kPruneWarps - 1) / kPruneWarps;
   k_mlp_score<<<blocks < (uint32_t)sms * 8 ? blocks : (uint32_t)sms * 8, kPruneWarps * 32, 0, st>>>(w, feat, m,
-                                                                                                    logit);
+                                                                                                    nullptr, logit);
 }
 
 size_t mlp_score_tc_smem() { return sizeof(TcMlpSmem) + 1024; }
-size_t prune_tiles_tc_smem() { return sizeof(TcPruneSmem) + 1024; }
 
-// the region scorer's shared memory exceeds the 48 KB a kernel gets without
-// opting in: raised once per device, when the weights are loaded (never during
-// stream capture)
-int prune_tiles_prepare() {
-  return cudaFuncSetAttribute(k_prune_tiles_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)prune_tiles_tc_smem()) == cudaSuccess ? 0 : -1;
-}
-
-int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, uint32_t m, float *logit, int *err,
-                        int sms, cudaStream_t st) {
-  if (m == 0) return 0;
+// the dense scorer's shared memory exceeds 48 KB: raised once per device (when
+// weights are loaded, so that a captured call never does it; the standalone
+// scorer checks again)
+int mlp_score_tc_prepare() {
   static bool configured[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -1045,11 +788,18 @@ int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, u
       return -1;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
+  return 0;
+}
+
+int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, uint32_t m, float *logit, int *err,
+                        int sms, cudaStream_t st) {
+  if (m == 0) return 0;
+  if (mlp_score_tc_prepare() != 0) return -1;
   // 4 CTAs per SM (54 KB of shared memory each): their 128-column tensor-memory
   // allocations (512 columns per SM) never wait on each other
   const uint32_t steps = (m + 255) / 256;
   const uint32_t grid = steps < (uint32_t)sms * 4 ? steps : (uint32_t)sms * 4;
-  k_mlp_score_tc<<<grid, 256, mlp_score_tc_smem(), st>>>(w, head, feat, m, logit, err);
+  k_mlp_score_tc<<<grid, 256, mlp_score_tc_smem(), st>>>(w, head, feat, m, nullptr, logit, err);
   return 0;
 }
 

@@ -81,7 +81,8 @@ enum : int {
   kCtrBarCount = 17,        // persistent kernel: CTAs arrived at the current grid barrier
   kCtrBarGen = 18,          // persistent kernel: grid barriers passed
   kCtrLinkList = 19,        // cross-sector links: tracks that leave their sector (searched)
-  kNCounters = 20
+  kCtrRegionRows = 20,      // pruned mode: region rows gathered for the dense rescoring
+  kNCounters = 22           // (even: the 8-byte look-back words follow the counters)
 };
 
 // A spin-wait gives up after this many polls (with a short sleep between polls,

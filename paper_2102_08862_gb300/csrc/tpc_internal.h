@@ -82,11 +82,8 @@ void launch_append_range(const uint32_t *range_tracks, uint32_t *acc, uint32_t c
 // link classifier (k_mlp.cu)
 struct MlpW;
 size_t mlp_weights_bytes();
-// rescoring of the ambiguous clusters' pairs from the neighbour tiles' regions,
-// and of the clusters on the overflow list; rewrite their links
-void launch_prune_tiles(const Args &a, const MlpW *w, float logit_tau, int sms, int engine, cudaStream_t st);
-// opts the tensor-core region scorer in to its shared memory on the current device (0 on success)
-int prune_tiles_prepare();
+// rescoring of the clusters on the overflow list; rewrites their links (the tile
+// regions go through launch_region_rescore)
 void launch_prune(const Args &a, const MlpW *w, float logit_tau, int sms, cudaStream_t st);
 // FP32 parameters (blob order) + standardisation -> packed BF16 weights
 void launch_mlp_pack(const float *theta, const float *mean, const float *inv_std, MlpW *w, cudaStream_t st);
@@ -103,6 +100,15 @@ struct MlpHead {
 // launch-configuration failure
 int launch_mlp_score_tc(const MlpW *w, const MlpHead &head, const float *feat, uint32_t m, float *logit, int *err,
                         int sms, cudaStream_t st);
+// opts the tcgen05 dense scorer in to its shared memory on the current device (0 on success)
+int mlp_score_tc_prepare();
+// pruned mode: the tile regions' rows gathered into feat (tile_cap * 128 rows of 12
+// floats; meta and cost: each row's (cluster, j, k) and cost), scored by the dense
+// scorer of the engine into logit, and their clusters decided (tbase: tile_cap
+// region offsets); three launches
+void launch_region_rescore(const Args &a, const MlpW *w, const MlpHead &head, float *feat, int4 *meta,
+                           int64_t *cost, float *logit, uint32_t *tbase, float logit_tau, int sms, int engine,
+                           cudaStream_t st);
 void launch_mlp_extract(const Args &a, float *feat, uint8_t *label, int32_t *tri, uint32_t cap, uint32_t *count,
                         cudaStream_t st);
 // floor(sqrt(v)) for 0 <= v < 2^62, exact
