@@ -130,10 +130,11 @@ typedef struct {
   int32_t follow_check;  /* follow: clusters of another track that must pass the gate before a join (4) */
   float follow_link_chi2;  /* follow 2: 5-parameter agreement of two linked tracks (default 80) */
   int32_t follow_link_rows; /* follow 2: rows searched on either side of a sector boundary (default 152) */
-  int32_t mlp_engine;    /* TPC_MODE_PRUNED: tensor-core engine of the region rescoring, TPC_MMA_TCGEN05
-                            (fifth-generation tensor cores, batches of 256 rows) or TPC_MMA_SYNC (warp-level
-                            16-row tiles; the default, faster on the 10 ms frame); both give the same logits
-                            to FP32 rounding; tpc_tf_autotune picks one by timing */
+  int32_t mlp_engine;    /* TPC_MODE_PRUNED: tensor-core engine of the dense scorer that rescores the
+                            regions' rows, TPC_MMA_TCGEN05 (fifth-generation tensor cores, 128-row tiles;
+                            the default, faster on the 10 ms frame) or TPC_MMA_SYNC (warp-level 16-row
+                            tiles); both give the same logits to FP32 rounding; tpc_tf_autotune picks one
+                            by timing */
   int32_t persistent;    /* 1: the whole plain path (A0-A5) runs as one persistent launch whose stages are
                             separated by grid-wide barriers (the batched form replayed from a CUDA graph);
                             TPC_MODE_PLAIN and follow = 0 only, thread-per-track fit; needs the GPU to itself

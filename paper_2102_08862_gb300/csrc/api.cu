@@ -159,7 +159,7 @@ extern "C" void tpc_default_config(tpc_tf_config *c) {
   c->follow_check = 4;
   c->follow_link_chi2 = 80.0f;
   c->follow_link_rows = TPC_NROWS;
-  c->mlp_engine = TPC_MMA_SYNC;
+  c->mlp_engine = TPC_MMA_TCGEN05;
 }
 
 extern "C" const char *tpc_last_error(void) { return g_err.c_str(); }
