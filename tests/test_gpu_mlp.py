@@ -204,9 +204,10 @@ def _pruned_gpu(tpcca, dev, f, blob, tau, **kw):
 
 @pytest.mark.parametrize("row_cap,engine", [(0, 0), (0, 1), (16, 0)])
 def test_pruned_c1_full_parity(env, c1, row_cap, engine):
-    """row_cap 0: windows staged, the pairs rescored from the tiles' regions (engine
-    0: tcgen05 batches of 128 rows, 1: mma.sync tiles of 16); row_cap 16: windows
-    read from global memory, rescoring by the separate list kernel."""
+    """row_cap 0: windows staged, the pairs rescored from the tiles' regions, packed into
+    dense rows for the dense scorer (engine 0: tcgen05 tiles of 128 rows, 1: mma.sync
+    tiles of 16); row_cap 16: windows read from global memory, rescoring by the
+    separate list kernel."""
     tpcca, dev = env
     blob = _net()
     feat, _, _ = orc.training_triplets(c1.sector, c1.row, c1.pad, c1.time)
