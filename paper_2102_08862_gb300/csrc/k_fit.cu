@@ -623,7 +623,6 @@ __global__ void __launch_bounds__(256) k_follow_fit(Args a) {
     }
     return;
   }
-  const size_t stride = a.track_list_cap;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctr[kCtrFollowPathTile], 1u);
     __syncthreads();

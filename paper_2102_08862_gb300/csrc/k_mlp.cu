@@ -511,7 +511,6 @@ __global__ void __launch_bounds__(256, 4) k_mlp_score_tc(const MlpW *__restrict_
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const uint32_t h0 = smem_u32(sm.h[t]);
-#pragma unroll
         tc_mma_bf16(tmem + 64u * t, tc_desc(smem_u32(sm.x[t]), 128, 256), tc_desc(smem_u32(sm.wb2), 128, 256), idesc,
                     false);  // b2
 #pragma unroll
